@@ -1,0 +1,375 @@
+"""CPU FP64 oracle of the ladder dual-fermion loop (opendf, arXiv:1507.00895).
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+``bench.py``'s CPU-baseline / reference leg may import or run this module.
+It shares no code with the CUDA path (``paper_1507_00895_gb300/csrc``) and
+imports nothing from it; the only common module is the input generator
+``paper_1507_00895_gb300.inputs``, which it does not even need (every
+function here takes plain arrays).
+
+Everything is complex128 numpy, written step by step in the paper's order
+and notation (Section "Ladder dual fermion self-consistency loop"):
+
+  Eq. gd0           G0~_{w,k} = [g_w^-1 + Delta_w - eps_k]^-1 - g_w
+  Eq. dual_bubble   chi~_{W,w}(q) = -(T/N) sum_k G~_{w,k} G~_{w+W,k+q}
+  Eq. spin_symm     gamma^{d/m} = gamma^{uu} +/- gamma^{ud}
+  Eq. lin_alg_inv   (1 - gamma chi~) Gamma = gamma      per (q, W)
+  Gamma^(2)         = gamma chi~ gamma (diagonal only is used)
+  Eq. sd            Sigma~_{w,k} = T/(2N) sum_{W,q} (3[Gm - Gm2/2] + Gd - Gd2/2)_{W,w,w}(q)
+                                   G~_{w+W,k+q}
+  Eq. dyson         G~^-1 = G0~^-1 - Sigma~
+
+Readings of the paper used here (where it is silent or garbled):
+  * grids: fermionic n in [-n_w/2, n_w/2), bosonic m in [-m_max, m_max];
+    g, Delta given on the extended grid so that w+W is on it; outside the
+    box Sigma~ = 0, so G~ = G0~ there;
+  * k_i = 2 pi j / N_k, j = 0..N_k-1, sums over the grid divided by N = N_k^D,
+    k + q taken modulo the grid, flattened in C order (last axis fastest);
+  * eps_k = -2t sum_i cos k_i - 4 t' cos k_x cos k_y (t' only in 2D);
+  * Eq. dual_ladder's "Gamma_{W'',w'}" is Gamma_{W,w'',w'};
+  * Eq. sd's G~_{w,k+q} is G~_{w+W,k+q} (the bubble's pairing);
+  * d = uu + ud, m = uu - ud;
+  * Eq. dyson's "G^(0" is G0~.
+
+Status of each function's parity pin (tests/test_oracle_pins.py):
+  dispersion, bare_dual_g, dyson ............ pinned (closed forms, invariants)
+  dual_bubble_direct / dual_bubble_fft ...... pinned (brute force vs FFT; conjugation
+                                              and particle-hole invariants; sign/prefactor
+                                              by the first-order closed form of Sigma~)
+  ladder_gamma_* / hand LU .................. pinned (LAPACK, geometric series)
+  second_order_diag ......................... pinned (second-order diagram, direct sum)
+  dual_sigma_* .............................. pinned (first/second order in gamma by
+                                              Richardson extrapolation vs closed form /
+                                              direct diagram; point-group, conjugation,
+                                              particle-hole invariants; brute force vs FFT)
+  leading_eigenvalue ........................ pinned (rank-one closed form)
+  df_loop ................................... pinned through its steps; the converged
+                                              values of the paper's figures are not in the
+                                              text, so end-to-end numbers are parity
+                                              unpinned beyond the invariants above.
+"""
+
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+
+
+# ---------------------------------------------------------------------------
+# lattice
+# ---------------------------------------------------------------------------
+
+def kgrid(dim: int, nk: int) -> np.ndarray:
+    """Momentum vectors [N][dim], k_i = 2 pi j_i / N_k, C order."""
+    ks = 2.0 * math.pi * np.arange(nk) / nk
+    mesh = np.meshgrid(*([ks] * dim), indexing="ij")
+    return np.stack([m.reshape(-1) for m in mesh], axis=1)
+
+
+def dispersion(dim: int, nk: int, t: float, tp: float = 0.0) -> np.ndarray:
+    """eps_k on the grid (the paper's hypercubic -2t sum cos k_i, plus the
+    next-neighbour -4t' cos kx cos ky in 2D)."""
+    k = kgrid(dim, nk)
+    eps = -2.0 * t * np.cos(k).sum(axis=1)
+    if tp != 0.0:
+        if dim != 2:
+            raise ValueError("t' is defined for the square lattice only")
+        eps = eps - 4.0 * tp * np.cos(k[:, 0]) * np.cos(k[:, 1])
+    return eps
+
+
+# ---------------------------------------------------------------------------
+# Eq. gd0 and Eq. dyson
+# ---------------------------------------------------------------------------
+
+def bare_dual_g(g: np.ndarray, delta: np.ndarray, eps: np.ndarray) -> np.ndarray:
+    """Eq. gd0: G0~[e, k] = 1/(1/g_e + Delta_e - eps_k) - g_e."""
+    g = g[:, None]
+    return 1.0 / (1.0 / g + delta[:, None] - eps[None, :]) - g
+
+
+def dyson(g0: np.ndarray, sigma: np.ndarray) -> np.ndarray:
+    """Eq. dyson: G~ = 1/(1/G0~ - Sigma~), elementwise."""
+    return 1.0 / (1.0 / g0 - sigma)
+
+
+def dual_g(g0_ext: np.ndarray, sigma_box: np.ndarray, n_w: int, m_max: int) -> np.ndarray:
+    """G~ on the extended grid: Dyson inside the box, G0~ outside (Sigma~ = 0)."""
+    gt = g0_ext.copy()
+    gt[m_max:m_max + n_w] = dyson(g0_ext[m_max:m_max + n_w], sigma_box)
+    return gt
+
+
+# ---------------------------------------------------------------------------
+# Eq. dual_bubble
+# ---------------------------------------------------------------------------
+
+def _shift_index(dim: int, nk: int) -> np.ndarray:
+    """table[k, q] = flat index of k + q (mod grid)."""
+    grid = np.indices([nk] * dim).reshape(dim, -1).T          # [N][dim]
+    s = (grid[:, None, :] + grid[None, :, :]) % nk              # [N][N][dim]
+    flat = np.zeros(s.shape[:2], dtype=np.int64)
+    for d in range(dim):
+        flat = flat * nk + s[:, :, d]
+    return flat
+
+
+def dual_bubble_direct(gt_ext: np.ndarray, n_w: int, m_max: int, beta: float,
+                       dim: int, nk: int) -> np.ndarray:
+    """Eq. dual_bubble by the explicit momentum sum (small grids only).
+
+    gt_ext: [n_w + 2 m_max][N].  Returns chi~ [N_W][n_w][N] with
+    chi~[a, i, q] = -(T/N) sum_k G~[i + m_max, k] G~[i + a, k + q].
+    """
+    T = 1.0 / beta
+    N = nk ** dim
+    kq = _shift_index(dim, nk)
+    nb = 2 * m_max + 1
+    chi = np.zeros((nb, n_w, N), dtype=np.complex128)
+    for a in range(nb):
+        for i in range(n_w):
+            gw = gt_ext[i + m_max]            # G~_{w}
+            gwW = gt_ext[i + a]               # G~_{w+W}, W = (a - m_max)
+            for q in range(N):
+                chi[a, i, q] = -(T / N) * np.sum(gw * gwW[kq[:, q]])
+    return chi
+
+
+def to_real_space(x: np.ndarray, dim: int, nk: int) -> np.ndarray:
+    """f(r) = (1/N) sum_k exp(i k.r) f(k) over the last axis (grid flattened)."""
+    lead = x.shape[:-1]
+    y = np.fft.ifftn(x.reshape(lead + (nk,) * dim), axes=tuple(range(-dim, 0)))
+    return y.reshape(lead + (nk ** dim,))
+
+
+def to_momentum(x: np.ndarray, dim: int, nk: int) -> np.ndarray:
+    """f(k) = sum_r exp(-i k.r) f(r) over the last axis."""
+    lead = x.shape[:-1]
+    y = np.fft.fftn(x.reshape(lead + (nk,) * dim), axes=tuple(range(-dim, 0)))
+    return y.reshape(lead + (nk ** dim,))
+
+
+def reflect(x: np.ndarray, dim: int, nk: int) -> np.ndarray:
+    """f(r) -> f(-r) on the periodic grid, over the last axis."""
+    lead = x.shape[:-1]
+    y = x.reshape(lead + (nk,) * dim)
+    for d in range(dim):
+        ax = len(lead) + d
+        y = np.take(y, (-np.arange(nk)) % nk, axis=ax)
+    return y.reshape(lead + (nk ** dim,))
+
+
+def dual_bubble_fft(gt_ext: np.ndarray, n_w: int, m_max: int, beta: float,
+                    dim: int, nk: int) -> np.ndarray:
+    """Eq. dual_bubble through the lattice Fourier transform.
+
+    sum_k A(k) B(k+q) = N sum_r A(-r) B(r) exp(-i q.r) with
+    A(r) = (1/N) sum_k exp(ik.r) A(k), so
+    chi~_{W,w}(q) = -T sum_r G~_w(-r) G~_{w+W}(r) exp(-i q.r).
+    """
+    T = 1.0 / beta
+    gr = to_real_space(gt_ext, dim, nk)          # [ne][N]
+    gr_m = reflect(gr, dim, nk)                   # G~(-r)
+    nb = 2 * m_max + 1
+    chi = np.empty((nb, n_w, nk ** dim), dtype=np.complex128)
+    for a in range(nb):
+        prod = gr_m[m_max:m_max + n_w] * gr[a:a + n_w]
+        chi[a] = -T * to_momentum(prod, dim, nk)
+    return chi
+
+
+# ---------------------------------------------------------------------------
+# Eq. spin_symm, Eq. lin_alg_inv, Gamma^(2)
+# ---------------------------------------------------------------------------
+
+def channel_vertices(gamma_uu: np.ndarray, gamma_ud: np.ndarray):
+    """Eq. spin_symm: (gamma^d, gamma^m) = (uu + ud, uu - ud)."""
+    return gamma_uu + gamma_ud, gamma_uu - gamma_ud
+
+
+def ladder_matrix(gamma_W: np.ndarray, chi_Wq: np.ndarray) -> np.ndarray:
+    """D = 1 - gamma chi~ for one (q, W): D[w, w'] = delta - gamma[w, w'] chi~[w']."""
+    n = gamma_W.shape[0]
+    return np.eye(n, dtype=np.complex128) - gamma_W * chi_Wq[None, :]
+
+
+def ladder_gamma_full(gamma_W: np.ndarray, chi_Wq: np.ndarray) -> np.ndarray:
+    """Eq. lin_alg_inv for one (q, W): Gamma = (1 - gamma chi~)^-1 gamma (LAPACK)."""
+    return np.linalg.solve(ladder_matrix(gamma_W, chi_Wq), gamma_W)
+
+
+def ladder_gamma_diag(gamma: np.ndarray, chi: np.ndarray) -> np.ndarray:
+    """diag Gamma for every (W, q): gamma [N_W][n][n], chi [N_W][n][N] -> [N_W][n][N].
+
+    One LAPACK solve per (q, W) with all n right-hand sides (batched over q)."""
+    nb, n, N = chi.shape
+    out = np.empty((nb, n, N), dtype=np.complex128)
+    eye = np.eye(n, dtype=np.complex128)
+    for a in range(nb):
+        ga = gamma[a]
+        d = eye[None, :, :] - ga[None, :, :] * chi[a].T[:, None, :]     # [N][n][n]
+        sol = np.linalg.solve(d, np.broadcast_to(ga, (N, n, n)))
+        out[a] = np.diagonal(sol, axis1=1, axis2=2).T
+    return out
+
+
+def second_order_diag(gamma: np.ndarray, chi: np.ndarray) -> np.ndarray:
+    """diag(gamma chi~ gamma) for every (W, q): [N_W][n][N].
+
+    (gamma chi gamma)_{ww} = sum_{w''} gamma_{w w''} chi_{w''} gamma_{w'' w}."""
+    # prod[a, w, w''] = gamma[a, w, w''] * gamma[a, w'', w]
+    prod = gamma * np.transpose(gamma, (0, 2, 1))
+    return np.einsum("awx,axq->awq", prod, chi)
+
+
+def lu_partial_pivot(a: np.ndarray):
+    """Doolittle LU with row partial pivoting, written out: P A = L U.
+
+    Returns (lu, perm) with L unit-lower (below the diagonal of lu) and U
+    on and above it; perm[i] is the original row now at position i."""
+    lu = np.array(a, dtype=np.complex128, copy=True)
+    n = lu.shape[0]
+    perm = np.arange(n)
+    for k in range(n):
+        p = k + int(np.argmax(np.abs(lu[k:, k])))
+        if lu[p, k] == 0:
+            raise ZeroDivisionError("singular matrix")
+        if p != k:
+            lu[[k, p]] = lu[[p, k]]
+            perm[[k, p]] = perm[[p, k]]
+        lu[k + 1:, k] /= lu[k, k]
+        lu[k + 1:, k + 1:] -= np.outer(lu[k + 1:, k], lu[k, k + 1:])
+    return lu, perm
+
+
+def lu_solve(lu: np.ndarray, perm: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Solve A X = B from lu_partial_pivot: forward then back substitution."""
+    n = lu.shape[0]
+    y = np.array(b[perm], dtype=np.complex128, copy=True)
+    for i in range(n):
+        y[i] -= lu[i, :i] @ y[:i]
+    x = y
+    for i in range(n - 1, -1, -1):
+        x[i] = (x[i] - lu[i, i + 1:] @ x[i + 1:]) / lu[i, i]
+    return x
+
+
+def leading_eigenvalue(gamma_W: np.ndarray, chi_Wq: np.ndarray) -> complex:
+    """Largest-modulus eigenvalue of gamma chi~ for one (q, W) (LAPACK zgeev);
+    the ladder is inside its convergence radius only when it is below one."""
+    ev = np.linalg.eigvals(gamma_W * chi_Wq[None, :])
+    return complex(ev[np.argmax(np.abs(ev))])
+
+
+# ---------------------------------------------------------------------------
+# Eq. sd
+# ---------------------------------------------------------------------------
+
+def sd_kernel(gd_diag, gd2_diag, gm_diag, gm2_diag) -> np.ndarray:
+    """The bracket of Eq. sd: 3 [Gm - Gm^(2)/2] + Gd - Gd^(2)/2, [N_W][n][N]."""
+    return 3.0 * (gm_diag - 0.5 * gm2_diag) + (gd_diag - 0.5 * gd2_diag)
+
+
+def dual_sigma_direct(kern: np.ndarray, gt_ext: np.ndarray, n_w: int, m_max: int,
+                      beta: float, dim: int, nk: int) -> np.ndarray:
+    """Eq. sd by the explicit momentum sum (small grids only): [n_w][N]."""
+    T = 1.0 / beta
+    N = nk ** dim
+    kq = _shift_index(dim, nk)
+    nb = 2 * m_max + 1
+    sig = np.zeros((n_w, N), dtype=np.complex128)
+    for i in range(n_w):
+        for a in range(nb):
+            gwW = gt_ext[i + a]
+            for k in range(N):
+                sig[i, k] += np.sum(kern[a, i, :] * gwW[kq[k, :]])
+    return (T / (2.0 * N)) * sig
+
+
+def dual_sigma_fft(kern: np.ndarray, gt_ext: np.ndarray, n_w: int, m_max: int,
+                   beta: float, dim: int, nk: int) -> np.ndarray:
+    """Eq. sd through the lattice Fourier transform.
+
+    sum_q K(q) B(k+q) = N sum_r K(-r) B(r) exp(-i k.r), so
+    Sigma~_w(k) = (T/2) sum_r exp(-ik.r) sum_W K_{W,w}(-r) G~_{w+W}(r)."""
+    T = 1.0 / beta
+    kr_m = reflect(to_real_space(kern, dim, nk), dim, nk)      # K(-r) [N_W][n][N]
+    gr = to_real_space(gt_ext, dim, nk)
+    nb = 2 * m_max + 1
+    acc = np.zeros((n_w, nk ** dim), dtype=np.complex128)
+    for a in range(nb):
+        acc += kr_m[a] * gr[a:a + n_w]
+    return 0.5 * T * to_momentum(acc, dim, nk)
+
+
+# ---------------------------------------------------------------------------
+# the loop
+# ---------------------------------------------------------------------------
+
+@dataclass
+class LoopState:
+    g0_ext: np.ndarray
+    sigma: np.ndarray
+    gt_ext: np.ndarray = None
+    chi: np.ndarray = None
+    kern: np.ndarray = None
+    gd_diag: np.ndarray = None
+    gm_diag: np.ndarray = None
+    residuals: List[float] = field(default_factory=list)
+    sigmas: List[np.ndarray] = field(default_factory=list)
+
+
+def one_iteration(state: LoopState, gamma_d, gamma_m, n_w, m_max, beta, dim, nk,
+                  mix: float = 1.0, bubble=dual_bubble_fft, sigma_fn=dual_sigma_fft):
+    """One pass of the loop: Dyson -> bubble -> ladder (both channels) -> Sigma~.
+
+    Returns the new Sigma~ (mixed: mix * new + (1 - mix) * old) and
+    r = max|Sigma_new - Sigma_old| / max|Sigma_new|."""
+    gt = dual_g(state.g0_ext, state.sigma, n_w, m_max)
+    chi = bubble(gt, n_w, m_max, beta, dim, nk)
+    gd = ladder_gamma_diag(gamma_d, chi)
+    gm = ladder_gamma_diag(gamma_m, chi)
+    kern = sd_kernel(gd, second_order_diag(gamma_d, chi), gm, second_order_diag(gamma_m, chi))
+    sig_new = sigma_fn(kern, gt, n_w, m_max, beta, dim, nk)
+    sig_new = mix * sig_new + (1.0 - mix) * state.sigma
+    den = np.max(np.abs(sig_new))
+    r = float(np.max(np.abs(sig_new - state.sigma)) / den) if den > 0 else 0.0
+    state.gt_ext, state.chi, state.kern = gt, chi, kern
+    state.gd_diag, state.gm_diag = gd, gm
+    state.sigma = sig_new
+    state.residuals.append(r)
+    state.sigmas.append(sig_new.copy())
+    return sig_new, r
+
+
+def df_loop(g, delta, gamma_uu, gamma_ud, *, dim, nk, t, tp, beta, n_w, m_max,
+            n_iter: int, mix: float = 1.0, tol: float = 0.0,
+            sigma0: Optional[np.ndarray] = None) -> LoopState:
+    """The ladder dual-fermion self-consistency loop, n_iter passes (or until r <= tol)."""
+    eps = dispersion(dim, nk, t, tp)
+    g0 = bare_dual_g(np.asarray(g), np.asarray(delta), eps)
+    gamma_d, gamma_m = channel_vertices(np.asarray(gamma_uu), np.asarray(gamma_ud))
+    sigma = np.zeros((n_w, nk ** dim), np.complex128) if sigma0 is None else np.array(sigma0)
+    st = LoopState(g0_ext=g0, sigma=sigma)
+    for _ in range(n_iter):
+        _, r = one_iteration(st, gamma_d, gamma_m, n_w, m_max, beta, dim, nk, mix)
+        if r <= tol:
+            break
+    return st
+
+
+def run_workload(w, n_iter: Optional[int] = None, mix: float = 1.0, tol: float = 0.0,
+                 sigma0=None) -> LoopState:
+    """df_loop on an ``inputs.Workload``-like object (duck typed)."""
+    return df_loop(w.g, w.delta, w.gamma_uu, w.gamma_ud, dim=w.dim, nk=w.nk, t=w.t,
+                   tp=w.tp, beta=w.beta, n_w=w.n_w, m_max=w.m_max,
+                   n_iter=w.n_iter if n_iter is None else n_iter, mix=mix, tol=tol,
+                   sigma0=sigma0)
+
+
+def ladder_lambda(gamma, chi, a: int, q: int) -> complex:
+    """leading_eigenvalue for bosonic index a and momentum index q."""
+    return leading_eigenvalue(gamma[a], chi[a, :, q])

@@ -1,0 +1,401 @@
+"""Pins of the CPU oracle to things other than itself (no GPU).
+
+Each test cites the passage of the paper it fixes.  Closed forms are derived
+by hand for inputs with a known Fourier content; the brute-force sums are
+the definitions written out; invariants follow from the symmetries of the
+inputs.  A few tests plant a plausible mistake in the oracle (monkeypatch,
+CPU only) and check that a pin catches it.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import df_oracle as O
+from paper_1507_00895_gb300 import inputs as I
+
+
+def _rel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+# ---------------------------------------------------------------------------
+# input generator (Eqs. atomic_limit1-4)
+# ---------------------------------------------------------------------------
+
+def test_atom_g_half_filling_closed_form():
+    # Eq. atomic_limit1: (1/2)[1/(iw-U/2) + 1/(iw+U/2)] = -iw / (w^2 + U^2/4)
+    U, beta, nw, mm = 3.0, 4.0, 16, 2
+    g = I.atom_g(U, beta, U / 2, nw, mm)
+    w = I.fermionic_w(beta, I.fermionic_n(nw, mm))
+    assert _rel(g, -1j * w / (w * w + U * U / 4)) < 1e-14
+
+
+def test_atom_density_and_mu():
+    assert abs(I.atom_density(4.0, 10.0, 2.0) - 1.0) < 1e-12          # half filling
+    mu = I.atom_mu_for_density(4.0, 10.0, 0.9)
+    assert abs(I.atom_density(4.0, 10.0, mu) - 0.9) < 1e-12
+    assert abs(mu - math.log(4.5) / 10.0) < 1e-3                      # 2e^{bmu}/(1+2e^{bmu}) = .9
+
+
+def test_atom_vertex_symmetries():
+    # real, symmetric in w<->w', invariant under (W,w,w') -> -(W,w,w')
+    guu, gud = I.atom_vertices(2.5, 3.0, 12, 3)
+    for gm in (guu, gud):
+        assert np.all(np.isfinite(gm))
+        assert np.max(np.abs(gm - gm.transpose(0, 2, 1))) < 1e-12 * np.max(np.abs(gm))
+        assert np.max(np.abs(gm - gm[::-1, ::-1, ::-1])) < 1e-12 * np.max(np.abs(gm))
+
+
+def test_atom_vertex_large_frequency_limit():
+    # at W != 0, w != w', w+w'+2W != 0 and large |w|, |w'| every delta vanishes:
+    # gamma^{ud} -> -U + O(U^3/w^2) and gamma^{uu} = 0 exactly
+    U, beta = 1.0, 200.0
+    guu, gud = I.atom_vertices(U, beta, 400, 1)
+    a, i, j = 0, 5, 390      # W = -2pi/beta, n = -195, n' = 190
+    assert abs(gud[a, i, j] + U) < 1e-2
+    assert guu[a, i, j] == 0.0
+
+
+# ---------------------------------------------------------------------------
+# lattice
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim,nk,tp", [(1, 8, 0.0), (2, 8, 0.0), (2, 16, -0.3), (3, 4, 0.0), (4, 4, 0.0)])
+def test_dispersion_moments(dim, nk, tp):
+    e = O.dispersion(dim, nk, 1.0, tp)
+    assert abs(e[0] - (-2 * dim - 4 * tp)) < 1e-13            # k = 0
+    assert abs(e.mean()) < 1e-13
+    assert abs((e ** 2).mean() - I.second_moment(dim, 1.0, tp)) < 1e-12
+
+
+def test_dispersion_bipartite():
+    e = O.dispersion(2, 8, 1.0).reshape(8, 8)
+    assert np.max(np.abs(np.roll(e, (4, 4), (0, 1)) + e)) < 1e-13   # eps(k+Q) = -eps(k)
+
+
+def test_bare_dual_g_is_dmft_lattice_g_minus_g():
+    # Sigma_DMFT = iw + mu - Delta - 1/g (the paper's lattice-observables section);
+    # G_DMFT = 1/(iw + mu - eps - Sigma_DMFT); Eq. gd0 says G0~ = G_DMFT - g.
+    w = I.workload("square32_tp", nk=8, n_w=8, m_max=2)
+    eps = O.dispersion(2, 8, 1.0, w.tp)
+    iw = 1j * I.fermionic_w(w.beta, I.fermionic_n(w.n_w, w.m_max))
+    sig_dmft = iw + w.mu - w.delta - 1.0 / w.g
+    g_dmft = 1.0 / (iw[:, None] + w.mu - eps[None, :] - sig_dmft[:, None])
+    assert _rel(O.bare_dual_g(w.g, w.delta, eps), g_dmft - w.g[:, None]) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Eq. dual_bubble
+# ---------------------------------------------------------------------------
+
+def _harmonic_g(rng, ne, dim, nk, r0):
+    """G~_e(k) = a_e + b_e exp(i k.r0) + c_e exp(-i k.r0)."""
+    a, b, c = [rng.normal(size=ne) + 1j * rng.normal(size=ne) for _ in range(3)]
+    k = O.kgrid(dim, nk)
+    ph = np.exp(1j * (k @ np.asarray(r0, float)))
+    return a[:, None] + b[:, None] * ph[None] + c[:, None] * np.conj(ph)[None], (a, b, c), k
+
+
+@pytest.mark.parametrize("dim,nk,r0", [(1, 8, [1]), (2, 4, [1, 0]), (2, 8, [1, 2]), (3, 4, [0, 1, 1])])
+def test_bubble_closed_form_single_harmonic(dim, nk, r0):
+    # sum_k G(k) G'(k+q) = N [a a' + b c' e^{-iq.r0} + c b' e^{iq.r0}] when 2 r0 != 0 (mod grid)
+    rng = np.random.default_rng(11)
+    nw, mm, beta = 4, 1, 2.0
+    ne = nw + 2 * mm
+    G, (a, b, c), k = _harmonic_g(rng, ne, dim, nk, r0)
+    ph = np.exp(1j * (k @ np.asarray(r0, float)))
+    T = 1.0 / beta
+    expect = np.empty((2 * mm + 1, nw, nk ** dim), complex)
+    for A in range(2 * mm + 1):
+        for i in range(nw):
+            e1, e2 = i + mm, i + A
+            expect[A, i] = -T * (a[e1] * a[e2] + b[e1] * c[e2] * np.conj(ph) + c[e1] * b[e2] * ph)
+    for fn in (O.dual_bubble_direct, O.dual_bubble_fft):
+        assert _rel(fn(G, nw, mm, beta, dim, nk), expect) < 1e-13
+
+
+@pytest.mark.parametrize("dim,nk", [(1, 8), (2, 4), (2, 8), (3, 4), (4, 4)])
+def test_bubble_direct_vs_fft(dim, nk):
+    rng = np.random.default_rng(dim * 10 + nk)
+    nw, mm = 4, 1
+    G = rng.normal(size=(nw + 2 * mm, nk ** dim)) + 1j * rng.normal(size=(nw + 2 * mm, nk ** dim))
+    a = O.dual_bubble_direct(G, nw, mm, 3.0, dim, nk)
+    b = O.dual_bubble_fft(G, nw, mm, 3.0, dim, nk)
+    assert _rel(b, a) < 1e-13
+
+
+def test_bubble_conjugation_and_particle_hole():
+    # g(-w) = g(w)*, real vertices: chi_{-W,-w}(q) = chi_{W,w}(q)*;
+    # half filling, t' = 0: Im chi_{W=0}(q) = 0
+    w = I.workload("paper_u20", nk=8, n_w=8, m_max=2)
+    g0 = O.bare_dual_g(w.g, w.delta, O.dispersion(2, 8, 1.0))
+    chi = O.dual_bubble_fft(g0, 8, 2, w.beta, 2, 8)
+    assert _rel(chi[::-1, ::-1, :], np.conj(chi)) < 1e-13
+    assert np.max(np.abs(chi[2].imag)) < 1e-14 * np.max(np.abs(chi[2]))
+
+
+def test_planted_bubble_mistake_is_caught(monkeypatch):
+    # k - q instead of k + q in the explicit sum: the closed form must fail
+    orig = O._shift_index
+
+    def wrong(dim, nk):
+        grid = np.indices([nk] * dim).reshape(dim, -1).T
+        s = (grid[:, None, :] - grid[None, :, :]) % nk
+        flat = np.zeros(s.shape[:2], dtype=np.int64)
+        for d in range(dim):
+            flat = flat * nk + s[:, :, d]
+        return flat
+
+    monkeypatch.setattr(O, "_shift_index", wrong)
+    with pytest.raises(AssertionError):
+        test_bubble_closed_form_single_harmonic(2, 8, [1, 2])
+    monkeypatch.setattr(O, "_shift_index", orig)
+
+
+# ---------------------------------------------------------------------------
+# Eq. lin_alg_inv and Gamma^(2)
+# ---------------------------------------------------------------------------
+
+def _random_system(seed, n, rho):
+    rng = np.random.default_rng(seed)
+    gam = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+    chi = rng.normal(size=n) + 1j * rng.normal(size=n)
+    r = np.max(np.abs(np.linalg.eigvals(gam * chi[None, :])))
+    return gam * (rho / r), chi
+
+
+def test_ladder_equals_geometric_series():
+    # Eq. dual_ladder iterated: Gamma = sum_j (gamma chi)^j gamma, for rho(gamma chi) < 1
+    gam, chi = _random_system(3, 12, 0.5)
+    series = np.zeros_like(gam)
+    term = gam.copy()
+    for _ in range(200):
+        series += term
+        term = (gam * chi[None, :]) @ term
+    full = O.ladder_gamma_full(gam, chi)
+    assert _rel(full, series) < 1e-13
+    # and the batched diagonal path agrees with it
+    d = O.ladder_gamma_diag(gam[None], chi[None, :, None])[0, :, 0]
+    assert _rel(d, np.diag(series)) < 1e-13
+
+
+def test_ladder_satisfies_eq_dual_ladder():
+    # Gamma = gamma + gamma chi Gamma outside the radius too (any rho)
+    gam, chi = _random_system(4, 16, 7.0)
+    G = O.ladder_gamma_full(gam, chi)
+    assert _rel(gam + (gam * chi[None, :]) @ G, G) < 1e-12
+
+
+def test_hand_lu_matches_lapack():
+    rng = np.random.default_rng(5)
+    for n in (1, 2, 7, 33):
+        a = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+        b = rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n))
+        lu, perm = O.lu_partial_pivot(a)
+        x = O.lu_solve(lu, perm, b)
+        assert _rel(x, np.linalg.solve(a, b)) < 1e-11
+        # P A = L U
+        L = np.tril(lu, -1) + np.eye(n)
+        U = np.triu(lu)
+        assert _rel(L @ U, a[perm]) < 1e-13
+
+
+def test_second_order_diag_direct_sum():
+    rng = np.random.default_rng(6)
+    nb, n, N = 2, 5, 3
+    gam = rng.normal(size=(nb, n, n)) + 1j * rng.normal(size=(nb, n, n))
+    chi = rng.normal(size=(nb, n, N)) + 1j * rng.normal(size=(nb, n, N))
+    got = O.second_order_diag(gam, chi)
+    for a in range(nb):
+        for q in range(N):
+            for w in range(n):
+                s = 0
+                for x in range(n):
+                    s += gam[a, w, x] * chi[a, x, q] * gam[a, x, w]
+                assert abs(got[a, w, q] - s) < 1e-13 * (1 + abs(s))
+
+
+def test_planted_ladder_order_mistake_is_caught(monkeypatch):
+    # (1 - chi gamma) instead of (1 - gamma chi): the series pin must fail
+    monkeypatch.setattr(O, "ladder_matrix",
+                        lambda g, c: np.eye(g.shape[0]) - c[:, None] * g)
+    with pytest.raises(AssertionError):
+        test_ladder_equals_geometric_series()
+
+
+def test_leading_eigenvalue_rank_one():
+    # gamma = u v^T: gamma chi has the single nonzero eigenvalue sum_j v_j chi_j u_j
+    rng = np.random.default_rng(7)
+    n = 9
+    u = rng.normal(size=n) + 1j * rng.normal(size=n)
+    v = rng.normal(size=n) + 1j * rng.normal(size=n)
+    chi = rng.normal(size=n) + 1j * rng.normal(size=n)
+    lam = O.leading_eigenvalue(np.outer(u, v), chi)
+    assert abs(lam - np.sum(v * chi * u)) < 1e-12 * abs(lam)
+
+
+# ---------------------------------------------------------------------------
+# Eq. sd
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("dim,nk,r0", [(1, 8, [3]), (2, 4, [1, 0]), (2, 8, [2, 1]), (3, 4, [1, 0, 1])])
+def test_sigma_closed_form_single_harmonic(dim, nk, r0):
+    # K(q) = al + be e^{iq.r0}, G~(k) = a + b e^{ik.r0} + c e^{-ik.r0}:
+    # sum_q K(q) G~(k+q) = N [al a + be c e^{-ik.r0}]  (2 r0 != 0 mod grid)
+    rng = np.random.default_rng(12)
+    nw, mm, beta = 4, 1, 1.5
+    nb, ne = 2 * mm + 1, nw + 2 * mm
+    G, (a, b, c), k = _harmonic_g(rng, ne, dim, nk, r0)
+    ph = np.exp(1j * (k @ np.asarray(r0, float)))
+    al = rng.normal(size=(nb, nw)) + 1j * rng.normal(size=(nb, nw))
+    be = rng.normal(size=(nb, nw)) + 1j * rng.normal(size=(nb, nw))
+    kern = al[:, :, None] + be[:, :, None] * ph[None, None, :]
+    T = 1.0 / beta
+    expect = np.zeros((nw, nk ** dim), complex)
+    for i in range(nw):
+        for A in range(nb):
+            expect[i] += (T / 2) * (al[A, i] * a[i + A] + be[A, i] * c[i + A] * np.conj(ph))
+    for fn in (O.dual_sigma_direct, O.dual_sigma_fft):
+        assert _rel(fn(kern, G, nw, mm, beta, dim, nk), expect) < 1e-13
+
+
+@pytest.mark.parametrize("dim,nk", [(1, 8), (2, 4), (3, 4), (4, 2)])
+def test_sigma_direct_vs_fft(dim, nk):
+    rng = np.random.default_rng(dim + 40)
+    nw, mm = 4, 1
+    N = nk ** dim
+    G = rng.normal(size=(nw + 2 * mm, N)) + 1j * rng.normal(size=(nw + 2 * mm, N))
+    K = rng.normal(size=(2 * mm + 1, nw, N)) + 1j * rng.normal(size=(2 * mm + 1, nw, N))
+    assert _rel(O.dual_sigma_fft(K, G, nw, mm, 2.0, dim, nk),
+                O.dual_sigma_direct(K, G, nw, mm, 2.0, dim, nk)) < 1e-13
+
+
+def test_zero_vertex_gives_zero_sigma():
+    # gamma = 0: Sigma~ == 0 and G~ = G_DMFT - g for every iteration
+    w = I.workload("square32_tp", nk=8, n_w=8, m_max=2).scaled(0.0)
+    st = O.run_workload(w, n_iter=3)
+    assert np.all(st.sigma == 0)
+    eps = O.dispersion(2, 8, 1.0, w.tp)
+    assert _rel(st.gt_ext, O.bare_dual_g(w.g, w.delta, eps)) < 1e-14
+
+
+def _one_shot_sigma(w, s):
+    eps = O.dispersion(w.dim, w.nk, w.t, w.tp)
+    g0 = O.bare_dual_g(w.g, w.delta, eps)
+    gd, gm = O.channel_vertices(s * w.gamma_uu, s * w.gamma_ud)
+    st = O.LoopState(g0_ext=g0, sigma=np.zeros((w.n_w, w.N), complex))
+    sig, _ = O.one_iteration(st, gd, gm, w.n_w, w.m_max, w.beta, w.dim, w.nk)
+    return sig, g0
+
+
+def test_sigma_first_and_second_order_in_vertex():
+    """Richardson extrapolation in the vertex scale s.
+
+    O(s):   (T/2) sum_W (3 gm + gd)_{W,w,w} G~loc_{w+W}     (local)
+    O(s^2): T/(2N) sum_{W,q} (1/2)(3 gm chi gm + gd chi gd)_{ww}(q) G~_{w+W,k+q}
+            (the second-order diagram, explicit sums)."""
+    w = I.random_nonsymmetric(n_w=4, m_max=1, dim=2, nk=4, seed=21)
+    nb, nw, N, beta = w.n_bos, w.n_w, w.N, w.beta
+    T = 1.0 / beta
+    g0 = O.bare_dual_g(w.g, w.delta, O.dispersion(2, 4, 1.0))
+    chi = O.dual_bubble_direct(g0, nw, w.m_max, beta, 2, 4)
+    gd, gm = w.gamma_uu + w.gamma_ud, w.gamma_uu - w.gamma_ud
+    rho = max(np.max(np.abs(np.linalg.eigvals(gx[a] * chi[a, :, q][None, :])))
+              for gx in (gd, gm) for a in range(nb) for q in range(N))
+    h = 0.02 / rho
+    pts = h * np.array([-3, -2, -1, 1, 2, 3], float)
+    vals = np.stack([_one_shot_sigma(w, s)[0] for s in pts])          # [6][nw][N]
+    V = np.stack([pts ** p for p in range(1, 7)], axis=1)              # f(0) = 0 exactly
+    coef = np.linalg.solve(V, vals.reshape(6, -1)).reshape(6, nw, N)
+    s1, s2 = coef[0], coef[1]
+
+    gloc = g0.mean(axis=1)
+    e1 = np.zeros((nw, N), complex)
+    for i in range(nw):
+        for A in range(nb):
+            e1[i] += 0.5 * T * (3 * gm[A, i, i] + gd[A, i, i]) * gloc[i + A]
+    assert _rel(s1, e1) < 1e-9
+
+    kq = O._shift_index(2, 4)
+    e2 = np.zeros((nw, N), complex)
+    for i in range(nw):
+        for k in range(N):
+            tot = 0
+            for A in range(nb):
+                for q in range(N):
+                    d2 = 0
+                    for x in range(nw):
+                        d2 += 3 * gm[A, i, x] * chi[A, x, q] * gm[A, x, i]
+                        d2 += gd[A, i, x] * chi[A, x, q] * gd[A, x, i]
+                    tot += 0.5 * d2 * g0[i + A, kq[k, q]]
+            e2[i, k] = T / (2 * N) * tot
+    assert _rel(s2, e2) < 1e-7
+
+
+def test_planted_double_counting_mistake_is_caught(monkeypatch):
+    # dropping the -Gamma^(2)/2 of Eq. sd changes the O(s^2) term
+    monkeypatch.setattr(O, "sd_kernel", lambda gd, gd2, gm, gm2: 3.0 * gm + gd)
+    with pytest.raises(AssertionError):
+        test_sigma_first_and_second_order_in_vertex()
+
+
+def _loop(name, n_iter, **kw):
+    w = I.workload(name, **kw)
+    return w, O.run_workload(w, n_iter=n_iter)
+
+
+def test_sigma_conjugation_symmetry():
+    # g(-w) = g(w)*, Delta likewise, real vertices: Sigma~(k,-w) = Sigma~(k,w)*
+    w, st = _loop("square32_tp", 3, nk=8, n_w=8, m_max=2)
+    s = st.sigma
+    assert _rel(s[::-1], np.conj(s)) < 1e-12
+
+
+def test_sigma_point_group():
+    # D4 of the square lattice (t' included): transpose and k -> -k
+    w, st = _loop("square32_tp", 2, nk=8, n_w=8, m_max=2)
+    s = st.sigma.reshape(8, 8, 8)
+    assert _rel(s.transpose(0, 2, 1), s) < 1e-12
+    flip = s[:, (-np.arange(8)) % 8, :]
+    assert _rel(flip, s) < 1e-12
+    # O_h of the cubic lattice: axis permutations
+    w3 = I.half_filled_atom("c", 3, 4, U=2.0, beta=2.0, n_w=4, m_max=1)
+    s3 = O.run_workload(w3, n_iter=2).sigma.reshape(4, 4, 4, 4)
+    assert _rel(s3.transpose(0, 2, 3, 1), s3) < 1e-12
+    assert _rel(s3.transpose(0, 1, 3, 2), s3) < 1e-12
+
+
+def test_sigma_particle_hole():
+    # half filling, t' = 0: Sigma~(k+Q, w) = -Sigma~(k, w)*
+    w, st = _loop("paper_u20", 3, nk=8, n_w=8, m_max=1)
+    s = st.sigma.reshape(8, 8, 8)
+    shifted = np.roll(s, (4, 4), axis=(1, 2))
+    assert _rel(shifted, -np.conj(s)) < 1e-12
+
+
+def test_paper_workload_converges():
+    # the paper's Example I input (U=20, beta=1) is inside the ladder radius and
+    # the loop contracts; the residual falls geometrically
+    w, st = _loop("paper_u20", 12, nk=8, n_w=16, m_max=1)
+    r = st.residuals
+    assert r[-1] < 1e-10
+    assert all(r[i + 1] < r[i] for i in range(len(r) - 1) if r[i] > 1e-13)
+
+
+def test_cubic_workload_sits_at_lambda_098():
+    # the 3D 16^3 workload's beta puts the leading magnetic eigenvalue of
+    # gamma chi~ at (pi,pi,pi), W=0 at 0.98, just inside the ladder radius
+    import json
+    import os
+    here = os.path.dirname(os.path.abspath(__file__))
+    gold = json.load(open(os.path.join(here, "golden", "cubic16_beta.json")))
+    assert gold["beta"] == I.CUBIC16_BETA_LAMBDA098
+    w = I.workload("cubic16_crit", m_max=0)
+    g0 = O.bare_dual_g(w.g, w.delta, O.dispersion(3, 16, 1.0))
+    chi = O.dual_bubble_fft(g0, w.n_w, 0, w.beta, 3, 16)
+    _, gm = O.channel_vertices(w.gamma_uu, w.gamma_ud)
+    q = 8 * 256 + 8 * 16 + 8
+    lam = O.ladder_lambda(gm, chi, 0, q)
+    assert abs(lam - 0.98) < 1e-9
