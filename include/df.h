@@ -1,0 +1,180 @@
+/*
+ * libdf: the ladder dual-fermion diagram summation of opendf
+ * (Antipov, LeBlanc, Gull, arXiv:1507.00895), GB300 (sm_103a) CUDA.
+ *
+ * Plain C ABI: opaque handle, plain pointers and sizes, a status code from
+ * every call.  All device work runs on the CUDA stream given to df_init
+ * (NULL = the legacy default stream).  There is no CPU fallback: on a
+ * machine without a usable sm_103a GPU, df_init returns DF_ERR_CUDA.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Complex numbers are two doubles (re, im), i.e. the layout of C99
+ * `double _Complex` / `std::complex<double>`.
+ *
+ * Grids (Section "Ladder dual fermion self-consistency loop"):
+ *   fermionic frequencies  w_n = (2n+1) pi/beta,  box n in [-n_w/2, n_w/2)
+ *                          (box index i = n + n_w/2);
+ *   bosonic frequencies    W_m = 2 m pi/beta,     m in [-m_max, m_max]
+ *                          (index a = m + m_max, N_W = 2 m_max + 1);
+ *   extended grid          n in [-n_w/2 - m_max, n_w/2 + m_max)
+ *                          (index e = n + n_w/2 + m_max, n_e = n_w + 2 m_max),
+ *                          so that w + W always lies on it;
+ *   momenta                k_j = 2 pi x_j / N_k, x_j = 0..N_k-1, j = 1..D,
+ *                          flattened with the last axis fastest, N = N_k^D.
+ *
+ * Array layouts (row-major, complex elements):
+ *   g, delta       [n_e]               impurity g_w and hybridisation Delta_w
+ *   gamma_d/_m     [N_W][n_w][n_w]     density / magnetic impurity vertex
+ *                                      gamma_{W,w,w'} (Eq. spin_symm)
+ *   sigma          [n_w][N]            dual self-energy Sigma~_{w,k}
+ *   gtilde         [n_e][N]            dual Green's function G~_{w,k}
+ *   chi            [N_W][n_w][N]       dual bubble chi~_{W,w}(q)
+ *   kernel         [2][N_W][n_w][N]    per channel (0 = d, 1 = m) the bracket
+ *                                      term of Eq. sd: c (Gamma_{W,w,w}(q)
+ *                                      - Gamma^(2)_{W,w,w}(q)/2), c = 1 (d), 3 (m)
+ *   lambda         [2][N_W][N]         leading eigenvalue of gamma chi~
+ *
+ * Ownership: inputs are copied at the call; the caller keeps its buffers.
+ * Device buffers behind the handle are owned by it and freed by df_destroy.
+ * A "_is_device" flag says whether a caller pointer is device memory
+ * (written/read on the handle's stream, no host synchronisation) or host
+ * memory (the call synchronises the stream before returning).
+ *
+ * Errors: DF_ERR_ARG for a NULL handle/pointer or an unsupported size (the
+ * handle is unchanged); DF_ERR_CUDA / DF_ERR_OOM when a CUDA call fails
+ * (the handle stays valid but its results are undefined until the next
+ * successful df_set_sigma / df_init); df_last_error() returns the message.
+ */
+#ifndef LIBDF_DF_H
+#define LIBDF_DF_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct df_ctx df_ctx;
+
+typedef enum df_status {
+  DF_OK = 0,
+  DF_ERR_ARG = 1,             /* bad argument or unsupported size */
+  DF_ERR_CUDA = 2,            /* a CUDA call failed (no GPU, launch error, ...) */
+  DF_ERR_OOM = 3,             /* device allocation failed */
+  DF_ERR_SINGULAR = 4,        /* an exactly zero pivot in a ladder solve */
+  DF_ERR_REFINE_STALL = 5,    /* mixed-precision refinement did not reach its tolerance */
+  DF_ERR_NOT_CONVERGED = 6,   /* df_iterate stopped at max_iter above tol */
+  DF_ERR_TIMEOUT = 7,         /* a bounded device-side wait gave up */
+  DF_WARN_LADDER_RADIUS = 8   /* |leading eigenvalue of gamma chi~| >= 1 was seen: the
+                                 ladder is outside its convergence radius (the paper's
+                                 condition after Eq. lin_alg_inv); results are still
+                                 produced by the direct solve */
+} df_status;
+
+typedef enum df_precision {
+  DF_FP64 = 0,       /* every step in FP64 (complex128) */
+  DF_FP32_IR = 1     /* ladder solves factorised in FP32 (complex64), refined to
+                        FP64 accuracy; bubble, Sigma~ and Dyson stay FP64 */
+} df_precision;
+
+/* Hypercubic lattice eps_k = -2t sum_j cos k_j (the paper's dispersion),
+ * plus -4 tp cos k_1 cos k_2 for dim == 2.  nk must be a power of two in
+ * [2, 64], dim in [1, 4], nk^dim <= 4096. */
+typedef struct df_lattice {
+  int dim;
+  int nk;
+  double tp;
+} df_lattice;
+
+typedef struct df_opts {
+  int n_w;            /* fermionic box size (even, 2..128) */
+  int m_max;          /* bosonic cutoff (0..31) */
+  double mix;         /* Sigma~ <- mix * new + (1 - mix) * old, in (0, 1]; default 1 */
+  int precision;      /* df_precision; default DF_FP64 */
+  int eig_mode;       /* leading eigenvalue of gamma chi~: 0 off, 1 at W = 0 (default), 2 all W */
+  int ir_max_steps;   /* DF_FP32_IR: maximum refinement steps (default 8) */
+  double ir_tol;      /* DF_FP32_IR: relative correction size that stops refinement (default 1e-13) */
+} df_opts;
+
+/* Fill *o with the defaults above (n_w, m_max set to 0: the caller sets them). */
+df_status df_default_opts(df_opts* o);
+
+/* Create a handle and copy the inputs of the paper's input list (g_w,
+ * Delta_w, mu and the two vertex channels).  Builds eps_k and the bare
+ * dual propagator of Eq. gd0,
+ *     G0~_{w,k} = [g_w^-1 + Delta_w - eps_k]^-1 - g_w,
+ * on the extended grid, sets Sigma~ = 0 and G~ = G0~.
+ * beta > 0; mu is kept for observables (the loop itself does not use it);
+ * t is the hopping of eps_k.  g, delta, gamma_d, gamma_m are HOST pointers
+ * with the layouts above.  stream is a cudaStream_t (may be NULL). */
+df_status df_init(df_ctx** out, const df_lattice* lat, double beta, double mu, double t,
+                  const double* g, const double* delta,
+                  const double* gamma_d, const double* gamma_m,
+                  const df_opts* opts, void* stream);
+
+/* Replace g, delta and both vertex channels (same sizes as at df_init),
+ * rebuild G0~ (Eq. gd0), keep Sigma~ and rebuild G~ from it (Eq. dyson).
+ * Pointers are host memory unless is_device != 0. */
+df_status df_set_inputs(df_ctx* c, const double* g, const double* delta,
+                        const double* gamma_d, const double* gamma_m, int is_device);
+
+/* Eq. spin_symm on the host: d = uu + ud, m = uu - ud, over `count` complex
+ * elements.  Any of the output pointers may alias an input. */
+df_status df_vertex_from_spin(const double* gamma_uu, const double* gamma_ud,
+                              double* gamma_d, double* gamma_m, size_t count);
+
+/* Eq. dual_bubble from the current G~:
+ *     chi~_{W,w}(q) = -(T/N) sum_k G~_{w,k} G~_{w+W,k+q},
+ * evaluated as -T sum_r G~_w(-r) G~_{w+W}(r) exp(-i q.r) with shared-memory
+ * lattice FFTs; result kept on the device (df_get_chi). */
+df_status df_bubble(df_ctx* c);
+
+/* Eq. lin_alg_inv for every (q, W) and each channel in channel_mask
+ * (bit 0 = d, bit 1 = m): (1 - gamma chi~) Gamma = gamma, solved by LU with
+ * partial pivoting (in FP64, or FP32 + iterative refinement per
+ * opts.precision); keeps c (Gamma_{W,w,w} - Gamma^(2)_{W,w,w}/2) with
+ * Gamma^(2) = gamma chi~ gamma (the double-counting term of Eq. sd).  With
+ * eig_mode != 0 also estimates the leading eigenvalue of gamma chi~ (FP64
+ * power iteration) and returns DF_WARN_LADDER_RADIUS when one has modulus
+ * >= 1.  Needs df_bubble first. */
+df_status df_bse(df_ctx* c, int channel_mask);
+
+/* Eq. sd and Eq. dyson: from the ladder kernel and G~,
+ *     Sigma~_{w,k} = T/(2N) sum_{W,q} [3(Gm - Gm2/2) + Gd - Gd2/2]_{W,w,w}(q) G~_{w+W,k+q},
+ * mixed with the previous Sigma~, then G~ = 1/(1/G0~ - Sigma~) in the box.
+ * If resid != NULL, synchronises and stores
+ *     r = max|Sigma~_new - Sigma~_old| / max|Sigma~_new|. */
+df_status df_sigma(df_ctx* c, double* resid);
+
+/* The self-consistency loop (the paper: repeat until G~ converges):
+ * df_bubble, df_bse(both), df_sigma, up to max_iter times or until
+ * r <= tol.  Returns DF_ERR_NOT_CONVERGED if tol > 0 was not reached,
+ * DF_WARN_LADDER_RADIUS if the last pass saw |lambda| >= 1, else DF_OK.
+ * iters_done and resid may be NULL. */
+df_status df_iterate(df_ctx* c, int max_iter, double tol, int* iters_done, double* resid);
+
+df_status df_get_sigma(df_ctx* c, double* out, int out_is_device);
+df_status df_set_sigma(df_ctx* c, const double* in, int in_is_device);
+df_status df_get_gtilde(df_ctx* c, double* out, int out_is_device);
+df_status df_get_chi(df_ctx* c, double* out, int out_is_device);
+df_status df_get_kernel(df_ctx* c, double* out, int out_is_device);
+/* lambda [2][N_W][N] complex; ok [2][N_W][N] ints: 1 converged, 0 not
+ * converged, -1 not computed (eig_mode).  ok may be NULL. */
+df_status df_get_lambda(df_ctx* c, double* lambda, int* ok, int out_is_device);
+
+/* Sizes of the handle: n_e, N_W, N (any pointer may be NULL). */
+df_status df_get_sizes(const df_ctx* c, int* n_ext, int* n_bos, int* n_k_total);
+
+/* Wait for all work queued on the handle's stream. */
+df_status df_synchronize(df_ctx* c);
+
+const char* df_last_error(const df_ctx* c);
+const char* df_status_string(df_status s);
+void df_destroy(df_ctx* c);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LIBDF_DF_H */

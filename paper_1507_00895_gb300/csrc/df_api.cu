@@ -1,0 +1,373 @@
+// C ABI of libdf (include/df.h): handle, validation, buffers and the
+// sequence of launches of one pass of the ladder dual-fermion loop.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "df_internal.cuh"
+
+namespace df {
+int* bse_flags(df_ctx* c) { return (int*)(c->red + 2 * c->dm.n_w + 2); }
+}  // namespace df
+
+using namespace df;
+
+namespace {
+
+df_status fail(df_ctx* c, df_status s, const char* what, cudaError_t e = cudaSuccess) {
+  if (c) {
+    char buf[512];
+    if (e != cudaSuccess)
+      snprintf(buf, sizeof buf, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+    else
+      snprintf(buf, sizeof buf, "%s", what);
+    c->err = buf;
+  }
+  return s;
+}
+
+#define DF_CUDA(c, call, what)                                                          \
+  do {                                                                                  \
+    cudaError_t e__ = (call);                                                           \
+    if (e__ != cudaSuccess)                                                             \
+      return fail((c), e__ == cudaErrorMemoryAllocation ? DF_ERR_OOM : DF_ERR_CUDA, (what), e__); \
+  } while (0)
+
+bool is_pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+  return cudaMalloc((void**)p, sizeof(T) * (count ? count : 1));
+}
+
+cudaMemcpyKind kind_to_dev(int is_device) {
+  return is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+}
+cudaMemcpyKind kind_from_dev(int is_device) {
+  return is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+}
+
+df_status copy_out(df_ctx* c, void* dst, const void* src, size_t bytes, int is_device, const char* what) {
+  if (!c) return DF_ERR_ARG;
+  if (!dst) return fail(c, DF_ERR_ARG, "output pointer is NULL");
+  DF_CUDA(c, cudaMemcpyAsync(dst, src, bytes, kind_from_dev(is_device), c->stream), what);
+  if (!is_device) DF_CUDA(c, cudaStreamSynchronize(c->stream), what);
+  return DF_OK;
+}
+
+df_status upload_inputs(df_ctx* c, const double* g, const double* delta, const double* gd, const double* gm,
+                        int is_device) {
+  const Dims& dm = c->dm;
+  const size_t nv = (size_t)dm.nb * dm.n_w * dm.n_w;
+  const cudaMemcpyKind k = kind_to_dev(is_device);
+  DF_CUDA(c, cudaMemcpyAsync(c->g, g, sizeof(double2) * dm.ne, k, c->stream), "copy g");
+  DF_CUDA(c, cudaMemcpyAsync(c->delta, delta, sizeof(double2) * dm.ne, k, c->stream), "copy delta");
+  DF_CUDA(c, cudaMemcpyAsync(c->gam, gd, sizeof(double2) * nv, k, c->stream), "copy gamma_d");
+  DF_CUDA(c, cudaMemcpyAsync(c->gam + nv, gm, sizeof(double2) * nv, k, c->stream), "copy gamma_m");
+  DF_CUDA(c, launch_gamma_gt(c), "gamma o gamma^T");
+  DF_CUDA(c, launch_init_g0(c), "bare dual propagator (Eq. gd0)");
+  DF_CUDA(c, launch_dyson_ifft(c, 0, dm.ne), "Dyson + FFT to real space");
+  return DF_OK;
+}
+
+df_status read_scalars(df_ctx* c, double* resid, int* flags) {
+  // one 32-byte copy: residual max-norms and the solve flags
+  double* h = c->h_red;
+  DF_CUDA(c, cudaMemcpyAsync(h, c->red + 2 * c->dm.n_w, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+          "read residual");
+  DF_CUDA(c, cudaStreamSynchronize(c->stream), "synchronise");
+  if (resid) *resid = (h[1] > 0.0) ? h[0] / h[1] : 0.0;
+  if (flags) memcpy(flags, h + 2, sizeof(int));
+  return DF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+df_status df_default_opts(df_opts* o) {
+  if (!o) return DF_ERR_ARG;
+  o->n_w = 0;
+  o->m_max = 0;
+  o->mix = 1.0;
+  o->precision = DF_FP64;
+  o->eig_mode = 1;
+  o->ir_max_steps = 8;
+  o->ir_tol = 1e-13;
+  return DF_OK;
+}
+
+const char* df_status_string(df_status s) {
+  switch (s) {
+    case DF_OK: return "DF_OK";
+    case DF_ERR_ARG: return "DF_ERR_ARG";
+    case DF_ERR_CUDA: return "DF_ERR_CUDA";
+    case DF_ERR_OOM: return "DF_ERR_OOM";
+    case DF_ERR_SINGULAR: return "DF_ERR_SINGULAR";
+    case DF_ERR_REFINE_STALL: return "DF_ERR_REFINE_STALL";
+    case DF_ERR_NOT_CONVERGED: return "DF_ERR_NOT_CONVERGED";
+    case DF_ERR_TIMEOUT: return "DF_ERR_TIMEOUT";
+    case DF_WARN_LADDER_RADIUS: return "DF_WARN_LADDER_RADIUS";
+  }
+  return "unknown df_status";
+}
+
+const char* df_last_error(const df_ctx* c) { return c ? c->err.c_str() : "NULL handle"; }
+
+df_status df_vertex_from_spin(const double* uu, const double* ud, double* d, double* m, size_t count) {
+  if (!uu || !ud || !d || !m) return DF_ERR_ARG;
+  for (size_t i = 0; i < 2 * count; ++i) {
+    const double a = uu[i], b = ud[i];
+    d[i] = a + b;
+    m[i] = a - b;
+  }
+  return DF_OK;
+}
+
+void df_destroy(df_ctx* c) {
+  if (!c) return;
+  cudaFree(c->g);
+  cudaFree(c->delta);
+  cudaFree(c->gam);
+  cudaFree(c->g0);
+  cudaFree(c->gk);
+  cudaFree(c->gr);
+  cudaFree(c->chi);
+  cudaFree(c->kc);
+  cudaFree(c->prod);
+  cudaFree(c->sigma);
+  cudaFree(c->lam);
+  cudaFree(c->lam_ok);
+  cudaFree(c->red);
+  cudaFree(c->bse_ws);
+  if (c->h_red) cudaFreeHost(c->h_red);
+  delete c;
+}
+
+df_status df_init(df_ctx** out, const df_lattice* lat, double beta, double mu, double t, const double* g,
+                  const double* delta, const double* gamma_d, const double* gamma_m, const df_opts* opts,
+                  void* stream) {
+  if (!out || !lat || !opts || !g || !delta || !gamma_d || !gamma_m) return DF_ERR_ARG;
+  *out = nullptr;
+  if (lat->dim < 1 || lat->dim > 4 || !is_pow2(lat->nk) || lat->nk < 2 || lat->nk > 64) return DF_ERR_ARG;
+  int N = 1;
+  for (int d = 0; d < lat->dim; ++d) N *= lat->nk;
+  if (N > 4096) return DF_ERR_ARG;
+  if (lat->tp != 0.0 && lat->dim != 2) return DF_ERR_ARG;
+  if (opts->n_w < 2 || opts->n_w > 128 || (opts->n_w & 1)) return DF_ERR_ARG;
+  if (opts->m_max < 0 || opts->m_max > 31) return DF_ERR_ARG;
+  if (!(beta > 0.0) || !(opts->mix > 0.0 && opts->mix <= 1.0)) return DF_ERR_ARG;
+  if (opts->precision != DF_FP64 && opts->precision != DF_FP32_IR) return DF_ERR_ARG;
+  if (opts->eig_mode < 0 || opts->eig_mode > 2) return DF_ERR_ARG;
+
+  df_ctx* c = new (std::nothrow) df_ctx();
+  if (!c) return DF_ERR_OOM;
+  c->opts = *opts;
+  c->stream = (cudaStream_t)stream;
+  Dims& dm = c->dm;
+  dm.D = lat->dim;
+  dm.nk = lat->nk;
+  dm.p = 0;
+  while ((1 << dm.p) < lat->nk) ++dm.p;
+  dm.N = N;
+  dm.n_w = opts->n_w;
+  dm.m_max = opts->m_max;
+  dm.nb = 2 * opts->m_max + 1;
+  dm.ne = opts->n_w + 2 * opts->m_max;
+  dm.beta = beta;
+  dm.T = 1.0 / beta;
+  dm.mu = mu;
+  dm.t = t;
+  dm.tp = lat->tp;
+
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev == 0) {
+    df_status s = fail(c, DF_ERR_CUDA, "no CUDA device", e);
+    fprintf(stderr, "libdf: %s\n", c->err.c_str());
+    delete c;
+    return s;
+  }
+  cudaGetDevice(&c->device);
+
+  const size_t nplane = (size_t)dm.ne * dm.N;
+  const size_t nv = (size_t)dm.nb * dm.n_w * dm.n_w;
+  const size_t nchi = (size_t)dm.nb * dm.n_w * dm.N;
+  df_status st = DF_OK;
+#define ALLOC(ptr, count)                                                   \
+  do {                                                                      \
+    cudaError_t ea = dalloc(&(ptr), (count));                               \
+    if (ea != cudaSuccess) { st = fail(c, DF_ERR_OOM, "cudaMalloc " #ptr, ea); goto bad; } \
+  } while (0)
+  ALLOC(c->g, dm.ne);
+  ALLOC(c->delta, dm.ne);
+  ALLOC(c->gam, 2 * nv);
+  ALLOC(c->g0, nplane);
+  ALLOC(c->gk, nplane);
+  ALLOC(c->gr, nplane);
+  ALLOC(c->chi, nchi);
+  ALLOC(c->kc, 2 * nchi);
+  ALLOC(c->prod, nchi);
+  ALLOC(c->sigma, (size_t)dm.n_w * dm.N);
+  ALLOC(c->lam, (size_t)2 * dm.nb * dm.N);
+  ALLOC(c->lam_ok, (size_t)2 * dm.nb * dm.N);
+  ALLOC(c->red, (size_t)2 * dm.n_w + 4);
+  c->bse_grid = bse_default_grid(dm, c->device);
+  c->bse_ws_bytes = bse_workspace_bytes(dm, c->bse_grid);
+  {
+    cudaError_t ea = cudaMalloc(&c->bse_ws, c->bse_ws_bytes);
+    if (ea != cudaSuccess) { st = fail(c, DF_ERR_OOM, "cudaMalloc bse workspace", ea); goto bad; }
+    ea = cudaMallocHost((void**)&c->h_red, 4 * sizeof(double));
+    if (ea != cudaSuccess) { st = fail(c, DF_ERR_OOM, "cudaMallocHost", ea); goto bad; }
+  }
+#undef ALLOC
+  {
+    cudaError_t ea;
+    if ((ea = cudaMemsetAsync(c->sigma, 0, sizeof(double2) * dm.n_w * dm.N, c->stream)) != cudaSuccess ||
+        (ea = cudaMemsetAsync(c->lam, 0, sizeof(double2) * 2 * dm.nb * dm.N, c->stream)) != cudaSuccess ||
+        (ea = cudaMemsetAsync(c->lam_ok, 0xff, sizeof(int) * 2 * dm.nb * dm.N, c->stream)) != cudaSuccess ||
+        (ea = cudaMemsetAsync(c->red, 0, sizeof(double) * (2 * dm.n_w + 4), c->stream)) != cudaSuccess) {
+      st = fail(c, DF_ERR_CUDA, "cudaMemsetAsync", ea);
+      goto bad;
+    }
+  }
+  st = upload_inputs(c, g, delta, gamma_d, gamma_m, 0);
+  if (st != DF_OK) goto bad;
+  {
+    cudaError_t ea = cudaStreamSynchronize(c->stream);
+    if (ea != cudaSuccess) { st = fail(c, DF_ERR_CUDA, "df_init", ea); goto bad; }
+  }
+  *out = c;
+  return DF_OK;
+bad:
+  fprintf(stderr, "libdf: df_init failed: %s\n", c->err.c_str());
+  df_destroy(c);
+  return st;
+}
+
+df_status df_set_inputs(df_ctx* c, const double* g, const double* delta, const double* gd, const double* gm,
+                        int is_device) {
+  if (!c) return DF_ERR_ARG;
+  if (!g || !delta || !gd || !gm) return fail(c, DF_ERR_ARG, "NULL input");
+  df_status s = upload_inputs(c, g, delta, gd, gm, is_device);
+  if (s != DF_OK) return s;
+  if (!is_device) DF_CUDA(c, cudaStreamSynchronize(c->stream), "df_set_inputs");
+  return DF_OK;
+}
+
+df_status df_bubble(df_ctx* c) {
+  if (!c) return DF_ERR_ARG;
+  DF_CUDA(c, launch_bubble(c), "dual bubble (Eq. dual_bubble)");
+  return DF_OK;
+}
+
+df_status df_bse(df_ctx* c, int channel_mask) {
+  if (!c) return DF_ERR_ARG;
+  if (channel_mask < 1 || channel_mask > 3) return fail(c, DF_ERR_ARG, "channel_mask must be 1, 2 or 3");
+  DF_CUDA(c, launch_bse(c, channel_mask), "ladder solve (Eq. lin_alg_inv)");
+  DF_CUDA(c, launch_lambda(c, channel_mask), "leading eigenvalue of gamma chi");
+  return DF_OK;
+}
+
+df_status df_sigma(df_ctx* c, double* resid) {
+  if (!c) return DF_ERR_ARG;
+  DF_CUDA(c, launch_sigma(c, c->opts.mix), "dual self-energy (Eq. sd) + Dyson");
+  ++c->iter_done;
+  if (resid) {
+    int flags = 0;
+    df_status s = read_scalars(c, resid, &flags);
+    if (s != DF_OK) return s;
+    c->last_resid = *resid;
+    if (flags & 1) return fail(c, DF_ERR_SINGULAR, "exactly zero pivot in a ladder solve");
+    if (flags & 2) return DF_WARN_LADDER_RADIUS;
+  }
+  return DF_OK;
+}
+
+df_status df_iterate(df_ctx* c, int max_iter, double tol, int* iters_done, double* resid) {
+  if (!c) return DF_ERR_ARG;
+  if (max_iter < 0) return fail(c, DF_ERR_ARG, "max_iter < 0");
+  double r = -1.0;
+  int it = 0, flags = 0;
+  for (; it < max_iter; ++it) {
+    DF_CUDA(c, launch_bubble(c), "dual bubble (Eq. dual_bubble)");
+    DF_CUDA(c, launch_bse(c, 3), "ladder solve (Eq. lin_alg_inv)");
+    DF_CUDA(c, launch_lambda(c, 3), "leading eigenvalue of gamma chi");
+    DF_CUDA(c, launch_sigma(c, c->opts.mix), "dual self-energy (Eq. sd) + Dyson");
+    ++c->iter_done;
+    if (tol > 0.0 || it == max_iter - 1) {
+      df_status s = read_scalars(c, &r, &flags);
+      if (s != DF_OK) return s;
+      if (flags & 1) {
+        if (iters_done) *iters_done = it + 1;
+        return fail(c, DF_ERR_SINGULAR, "exactly zero pivot in a ladder solve");
+      }
+      if (tol > 0.0 && r <= tol) {
+        ++it;
+        break;
+      }
+    }
+  }
+  if (iters_done) *iters_done = it;
+  if (resid) *resid = r;
+  c->last_resid = r;
+  if (tol > 0.0 && !(r <= tol)) return DF_ERR_NOT_CONVERGED;
+  if (flags & 2) return DF_WARN_LADDER_RADIUS;
+  return DF_OK;
+}
+
+df_status df_get_sigma(df_ctx* c, double* out, int is_device) {
+  if (!c) return DF_ERR_ARG;
+  return copy_out(c, out, c->sigma, sizeof(double2) * c->dm.n_w * c->dm.N, is_device, "df_get_sigma");
+}
+
+df_status df_set_sigma(df_ctx* c, const double* in, int is_device) {
+  if (!c) return DF_ERR_ARG;
+  if (!in) return fail(c, DF_ERR_ARG, "input pointer is NULL");
+  DF_CUDA(c, cudaMemcpyAsync(c->sigma, in, sizeof(double2) * c->dm.n_w * c->dm.N, kind_to_dev(is_device), c->stream),
+          "df_set_sigma");
+  DF_CUDA(c, launch_dyson_ifft(c, c->dm.m_max, c->dm.n_w), "Dyson + FFT to real space");
+  if (!is_device) DF_CUDA(c, cudaStreamSynchronize(c->stream), "df_set_sigma");
+  return DF_OK;
+}
+
+df_status df_get_gtilde(df_ctx* c, double* out, int is_device) {
+  if (!c) return DF_ERR_ARG;
+  return copy_out(c, out, c->gk, sizeof(double2) * c->dm.ne * c->dm.N, is_device, "df_get_gtilde");
+}
+
+df_status df_get_chi(df_ctx* c, double* out, int is_device) {
+  if (!c) return DF_ERR_ARG;
+  return copy_out(c, out, c->chi, sizeof(double2) * c->dm.nb * c->dm.n_w * c->dm.N, is_device, "df_get_chi");
+}
+
+df_status df_get_kernel(df_ctx* c, double* out, int is_device) {
+  if (!c) return DF_ERR_ARG;
+  return copy_out(c, out, c->kc, sizeof(double2) * 2 * c->dm.nb * c->dm.n_w * c->dm.N, is_device,
+                  "df_get_kernel");
+}
+
+df_status df_get_lambda(df_ctx* c, double* lam, int* ok, int is_device) {
+  if (!c) return DF_ERR_ARG;
+  const size_t cnt = (size_t)2 * c->dm.nb * c->dm.N;
+  df_status s = copy_out(c, lam, c->lam, sizeof(double2) * cnt, is_device, "df_get_lambda");
+  if (s != DF_OK || !ok) return s;
+  return copy_out(c, ok, c->lam_ok, sizeof(int) * cnt, is_device, "df_get_lambda");
+}
+
+df_status df_get_sizes(const df_ctx* c, int* n_ext, int* n_bos, int* n_k_total) {
+  if (!c) return DF_ERR_ARG;
+  if (n_ext) *n_ext = c->dm.ne;
+  if (n_bos) *n_bos = c->dm.nb;
+  if (n_k_total) *n_k_total = c->dm.N;
+  return DF_OK;
+}
+
+df_status df_synchronize(df_ctx* c) {
+  if (!c) return DF_ERR_ARG;
+  DF_CUDA(c, cudaStreamSynchronize(c->stream), "df_synchronize");
+  return DF_OK;
+}
+
+}  // extern "C"

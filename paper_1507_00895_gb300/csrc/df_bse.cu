@@ -1,0 +1,393 @@
+// Ladder (Bethe-Salpeter) solves of Eq. lin_alg_inv, FP64 path, and the
+// leading-eigenvalue check of gamma chi~ (the convergence-radius condition
+// stated after Eq. lin_alg_inv).
+//
+// For every (q, W) and channel: D = 1 - gamma_W diag(chi~_W(q)), solve
+// D Gamma = gamma_W, keep only diag Gamma, and write the Eq. sd bracket
+//     kc = c (Gamma_ww - Gamma^(2)_ww / 2),  Gamma^(2)_ww = sum_x gamma_wx chi~_x gamma_xw,
+// with c = 1 (density) or 3 (magnetic).
+//
+// Design: one CTA per system (persistent grid, systems strided by
+// gridDim.x), D factorised in place by right-looking LU with partial
+// pivoting (pivot = largest |re|+|im| in the column, first on ties), the
+// right-hand sides P gamma processed in column chunks.  Because only the
+// diagonal of Gamma is needed, the back substitution for column j stops at
+// row j: LU (n^3/3) + forward (n^3/2) + truncated back substitution (n^3/6)
+// = n^3 complex multiply-adds per system instead of 4n^3/3.  U's columns are
+// pre-scaled by 1/U_kk so that neither substitution divides.
+#include "df_internal.cuh"
+
+namespace df {
+
+constexpr int kBseThreads = 256;
+
+struct BseSmem {
+  // offsets in double2 units inside the dynamic shared block
+  int lu, y, xs, invu, total;
+};
+
+__host__ __device__ inline BseSmem bse_layout(int n, int nc, bool lu_in_smem) {
+  BseSmem L;
+  int off = 0;
+  L.lu = off;
+  if (lu_in_smem) off += n * n;
+  L.y = off;
+  off += n * nc;
+  L.xs = off;
+  off += n;
+  L.invu = off;
+  off += n;
+  L.total = off;
+  return L;
+}
+
+// gg[c][a][i][j] = gamma[c][a][i][j] * gamma[c][a][j][i]  (for Gamma^(2))
+__global__ void gamma_gt_kernel(int n, int count, const double2* __restrict__ gam, double2* __restrict__ gg) {
+  const size_t total = (size_t)count * n * n;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total; idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t mat = idx / ((size_t)n * n);
+    const int rem = (int)(idx - mat * n * n);
+    const int i = rem / n, j = rem - i * n;
+    const double2* G = gam + mat * n * n;
+    gg[idx] = cmul(G[i * n + j], G[j * n + i]);
+  }
+}
+
+template <bool LU_SMEM>
+__global__ void __launch_bounds__(kBseThreads)
+bse_f64_kernel(Dims dm, int ch0, int nch, int nc, const double2* __restrict__ gam,
+               const double2* __restrict__ gg, const double2* __restrict__ chi,
+               double2* __restrict__ kc, double2* __restrict__ ws, int* __restrict__ flags) {
+  extern __shared__ double2 sm[];
+  __shared__ int perm[128];
+  __shared__ int piv_sm;
+  __shared__ double2 pv_sm, oldkk_sm;
+  const int n = dm.n_w, N = dm.N, nb = dm.nb;
+  const BseSmem L = bse_layout(n, nc, LU_SMEM);
+  double2* LU = LU_SMEM ? sm + L.lu : ws + (size_t)blockIdx.x * n * n;
+  double2* Y = sm + L.y;
+  double2* xs = sm + L.xs;
+  double2* invu = sm + L.invu;
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
+  const long systems = (long)nch * nb * N;
+
+  for (long sys = blockIdx.x; sys < systems; sys += gridDim.x) {
+    const int c = ch0 + (int)(sys / ((long)nb * N));
+    const int rem = (int)(sys - (long)(c - ch0) * nb * N);
+    const int a = rem / N, q = rem - a * N;
+    const double2* G = gam + ((size_t)c * nb + a) * n * n;
+    const double2* GG = gg + ((size_t)c * nb + a) * n * n;
+
+    for (int i = tid; i < n; i += blockDim.x) {
+      xs[i] = chi[((size_t)a * n + i) * N + q];
+      perm[i] = i;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < n * n; idx += blockDim.x) {
+      const int i = idx / n, j = idx - i * n;
+      double2 v = cmul(G[idx], xs[j]);
+      v = mk((i == j ? 1.0 : 0.0) - v.x, -v.y);
+      LU[idx] = v;
+    }
+    __syncthreads();
+
+    // ---- LU with partial pivoting ----
+    for (int k = 0; k < n; ++k) {
+      if (warp == 0) {
+        double best = -1.0;
+        int bi = k;
+        for (int r = k + lane; r < n; r += 32) {
+          const double v = cabs1(LU[r * n + k]);
+          if (v > best) { best = v; bi = r; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          const double ov = __shfl_xor_sync(0xffffffffu, best, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if (lane == 0) {
+          piv_sm = bi;
+          const double2 pv = LU[bi * n + k];
+          pv_sm = pv;
+          oldkk_sm = LU[k * n + k];
+          if (pv.x == 0.0 && pv.y == 0.0) {
+            atomicOr(flags, 1);
+            invu[k] = mk(0.0, 0.0);
+          } else {
+            invu[k] = cinv(pv);
+          }
+          if (bi != k) {
+            const int t = perm[k]; perm[k] = perm[bi]; perm[bi] = t;
+          }
+        }
+      }
+      __syncthreads();
+      const int p = piv_sm;
+      const double2 inv = invu[k];
+      // row swap of the columns != k, and the multipliers of column k
+      if (p != k) {
+        for (int col = tid; col < n; col += blockDim.x) {
+          if (col == k) continue;
+          const double2 t = LU[k * n + col];
+          LU[k * n + col] = LU[p * n + col];
+          LU[p * n + col] = t;
+        }
+      }
+      for (int r = k + tid; r < n; r += blockDim.x) {
+        if (r == k) {
+          LU[k * n + k] = pv_sm;
+        } else {
+          const double2 v = (r == p) ? oldkk_sm : LU[r * n + k];
+          LU[r * n + k] = cmul(v, inv);
+        }
+      }
+      __syncthreads();
+      // trailing rank-1 update
+      const int m = n - k - 1;
+      for (int idx = tid; idx < m * m; idx += blockDim.x) {
+        const int r = k + 1 + idx / m, col = k + 1 + idx % m;
+        LU[r * n + col] = cfms(LU[r * n + k], LU[k * n + col], LU[r * n + col]);
+      }
+      __syncthreads();
+    }
+    // scale U's strictly-upper columns by 1/U_kk (unit-diagonal V = U diag(1/U_kk))
+    for (int idx = tid; idx < n * n; idx += blockDim.x) {
+      const int r = idx / n, col = idx - r * n;
+      if (r < col) LU[idx] = cmul(LU[idx], invu[col]);
+    }
+    __syncthreads();
+
+    // ---- diag(Gamma) by chunks of nc right-hand sides ----
+    for (int j0 = 0; j0 < n; j0 += nc) {
+      const int w = min(nc, n - j0);
+      for (int idx = tid; idx < n * w; idx += blockDim.x) {
+        const int r = idx / w, jj = idx - r * w;
+        Y[r * nc + jj] = G[(size_t)perm[r] * n + j0 + jj];
+      }
+      __syncthreads();
+      for (int k = 0; k < n - 1; ++k) {           // unit-lower forward substitution
+        const int m = n - k - 1;
+        for (int idx = tid; idx < m * w; idx += blockDim.x) {
+          const int r = k + 1 + idx / w, jj = idx % w;
+          Y[r * nc + jj] = cfms(LU[r * n + k], Y[k * nc + jj], Y[r * nc + jj]);
+        }
+        __syncthreads();
+      }
+      for (int k = n - 1; k > j0; --k) {          // unit-upper back substitution, rows >= j0 only
+        const int m = k - j0;
+        for (int idx = tid; idx < m * w; idx += blockDim.x) {
+          const int r = j0 + idx / w, jj = idx % w;
+          if (j0 + jj <= r) Y[r * nc + jj] = cfms(LU[r * n + k], Y[k * nc + jj], Y[r * nc + jj]);
+        }
+        __syncthreads();
+      }
+      for (int jj = tid; jj < w; jj += blockDim.x) {
+        const int j = j0 + jj;
+        const double2 gdiag = cmul(Y[j * nc + jj], invu[j]);
+        double2 g2 = mk(0.0, 0.0);
+        for (int x = 0; x < n; ++x) g2 = cfma(GG[(size_t)j * n + x], xs[x], g2);
+        const double wgt = (c == 0) ? 1.0 : 3.0;
+        kc[(((size_t)c * nb + a) * n + j) * N + q] =
+            mk(wgt * (gdiag.x - 0.5 * g2.x), wgt * (gdiag.y - 0.5 * g2.y));
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// leading eigenvalue of A = gamma_W diag(chi~_W(q)) by FP64 power iteration
+// with a Rayleigh-quotient estimate; one CTA handles kQ systems that share
+// (channel, W) so the gamma rows are read once per iteration for all of them.
+// ---------------------------------------------------------------------------
+constexpr int kEigQ = 8;
+constexpr int kEigThreads = 256;
+constexpr int kEigMaxIter = 400;
+
+__global__ void __launch_bounds__(kEigThreads)
+lambda_kernel(Dims dm, int ch0, int nch, int a0, int na, double tol, const double2* __restrict__ gam,
+              const double2* __restrict__ chi, double2* __restrict__ lam, int* __restrict__ ok,
+              int* __restrict__ flags) {
+  extern __shared__ double2 sm[];
+  const int n = dm.n_w, N = dm.N, nb = dm.nb;
+  double2* v = sm;                 // [n][kEigQ]
+  double2* y = v + n * kEigQ;      // [n][kEigQ]
+  double2* xq = y + n * kEigQ;     // [n][kEigQ]
+  __shared__ double2 lam_old[kEigQ], lam_new[kEigQ];
+  __shared__ double nrm[kEigQ];
+  __shared__ int done[kEigQ];
+  const int qtiles = (N + kEigQ - 1) / kEigQ;
+  const int tile = blockIdx.x % qtiles;
+  const int a = a0 + (blockIdx.x / qtiles) % na;
+  const int c = ch0 + blockIdx.x / (qtiles * na);
+  if (c >= ch0 + nch) return;
+  const int q0 = tile * kEigQ;
+  const int nq = min(kEigQ, N - q0);
+  const double2* G = gam + ((size_t)c * nb + a) * n * n;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const double inv_sqrt_n = rsqrt((double)n);
+
+  for (int idx = tid; idx < n * kEigQ; idx += blockDim.x) {
+    const int j = idx / kEigQ, t = idx % kEigQ;
+    xq[idx] = (t < nq) ? chi[((size_t)a * n + j) * N + q0 + t] : mk(0.0, 0.0);
+    v[idx] = mk(inv_sqrt_n, 0.0);
+  }
+  if (tid < kEigQ) {
+    lam_old[tid] = mk(0.0, 0.0);
+    done[tid] = (tid < nq) ? 0 : 1;
+  }
+  __syncthreads();
+  int it = 0;
+  for (; it < kEigMaxIter; ++it) {
+    // y = G (chi o v); warps over rows, lanes over columns
+    for (int i = warp; i < n; i += blockDim.x / 32) {
+      double2 acc[kEigQ];
+#pragma unroll
+      for (int t = 0; t < kEigQ; ++t) acc[t] = mk(0.0, 0.0);
+      for (int j = lane; j < n; j += 32) {
+        const double2 gij = G[(size_t)i * n + j];
+#pragma unroll
+        for (int t = 0; t < kEigQ; ++t) acc[t] = cfma(gij, cmul(xq[j * kEigQ + t], v[j * kEigQ + t]), acc[t]);
+      }
+#pragma unroll
+      for (int t = 0; t < kEigQ; ++t) {
+        for (int o = 16; o > 0; o >>= 1) {
+          acc[t].x += __shfl_xor_sync(0xffffffffu, acc[t].x, o);
+          acc[t].y += __shfl_xor_sync(0xffffffffu, acc[t].y, o);
+        }
+      }
+      if (lane == 0) {
+#pragma unroll
+        for (int t = 0; t < kEigQ; ++t) y[i * kEigQ + t] = acc[t];
+      }
+    }
+    __syncthreads();
+    // Rayleigh quotient v^H y (|v| = 1) and |y|
+    if (warp < kEigQ) {
+      const int t = warp;
+      double2 rq = mk(0.0, 0.0);
+      double yy = 0.0;
+      for (int j = lane; j < n; j += 32) {
+        const double2 vj = v[j * kEigQ + t], yj = y[j * kEigQ + t];
+        rq = cfma(cconj(vj), yj, rq);
+        yy += cabs2(yj);
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        rq.x += __shfl_xor_sync(0xffffffffu, rq.x, o);
+        rq.y += __shfl_xor_sync(0xffffffffu, rq.y, o);
+        yy += __shfl_xor_sync(0xffffffffu, yy, o);
+      }
+      if (lane == 0) {
+        lam_new[t] = rq;
+        nrm[t] = yy > 0.0 ? rsqrt(yy) : 0.0;
+      }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < n * kEigQ; idx += blockDim.x) {
+      const int t = idx % kEigQ;
+      v[idx] = cscale(y[idx], nrm[t]);
+    }
+    if (tid < kEigQ && !done[tid]) {
+      const double2 d = lam_new[tid] - lam_old[tid];
+      if (sqrt(cabs2(d)) <= tol * sqrt(cabs2(lam_new[tid]))) done[tid] = 1;
+      lam_old[tid] = lam_new[tid];
+    }
+    __syncthreads();
+    int all = 1;
+    for (int t = 0; t < kEigQ; ++t) all &= done[t];
+    if (all) break;
+    __syncthreads();
+  }
+  if (tid < nq) {
+    const size_t o = ((size_t)c * nb + a) * N + q0 + tid;
+    lam[o] = lam_new[tid];
+    ok[o] = done[tid];
+    if (lam_new[tid].x * lam_new[tid].x + lam_new[tid].y * lam_new[tid].y >= 1.0) atomicOr(flags, 2);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host launchers
+// ---------------------------------------------------------------------------
+
+static int bse_chunk(int n) { return n <= 32 ? n : (n <= 64 ? 32 : 16); }
+static bool bse_lu_in_smem(int n) { return n <= 96; }
+
+size_t bse_workspace_bytes(const Dims& dm, int grid) {
+  size_t b = (size_t)2 * dm.nb * dm.n_w * dm.n_w * sizeof(double2);      // gamma o gamma^T
+  if (!bse_lu_in_smem(dm.n_w)) b += (size_t)grid * dm.n_w * dm.n_w * sizeof(double2);
+  return b;
+}
+
+static size_t bse_smem_bytes(int n) {
+  return sizeof(double2) * (size_t)bse_layout(n, bse_chunk(n), bse_lu_in_smem(n)).total;
+}
+
+int bse_default_grid(const Dims& dm, int device) {
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  const size_t smem = bse_smem_bytes(dm.n_w);
+  const void* fn = bse_lu_in_smem(dm.n_w) ? (const void*)bse_f64_kernel<true> : (const void*)bse_f64_kernel<false>;
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBseThreads, smem);
+  if (per_sm < 1) per_sm = 1;
+  return sms * per_sm;
+}
+
+static double2* gg_ptr(df_ctx* c) { return (double2*)c->bse_ws; }
+static int* flag_ptr(df_ctx* c) { return bse_flags(c); }
+static double2* lu_ws_ptr(df_ctx* c) {
+  return (double2*)((char*)c->bse_ws + (size_t)2 * c->dm.nb * c->dm.n_w * c->dm.n_w * sizeof(double2));
+}
+
+cudaError_t launch_gamma_gt(df_ctx* c) {
+  const Dims& dm = c->dm;
+  gamma_gt_kernel<<<2 * dm.nb * 8, 256, 0, c->stream>>>(dm.n_w, 2 * dm.nb, c->gam, gg_ptr(c));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bse(df_ctx* c, int channel_mask) {
+  const Dims& dm = c->dm;
+  const int n = dm.n_w;
+  const int nc = bse_chunk(n);
+  const size_t smem = bse_smem_bytes(n);
+  cudaError_t e = cudaMemsetAsync(flag_ptr(c), 0, sizeof(int) * 4, c->stream);
+  if (e != cudaSuccess) return e;
+  for (int ch = 0; ch < 2; ++ch) {
+    if (!(channel_mask & (1 << ch))) continue;
+    const long systems = (long)dm.nb * dm.N;
+    const int grid = (int)(systems < c->bse_grid ? systems : c->bse_grid);
+    if (bse_lu_in_smem(n)) {
+      bse_f64_kernel<true><<<grid, kBseThreads, smem, c->stream>>>(dm, ch, 1, nc, c->gam, gg_ptr(c), c->chi,
+                                                                   c->kc, nullptr, flag_ptr(c));
+    } else {
+      bse_f64_kernel<false><<<grid, kBseThreads, smem, c->stream>>>(dm, ch, 1, nc, c->gam, gg_ptr(c), c->chi,
+                                                                    c->kc, lu_ws_ptr(c), flag_ptr(c));
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_lambda(df_ctx* c, int channel_mask) {
+  const Dims& dm = c->dm;
+  if (c->opts.eig_mode == 0) return cudaSuccess;
+  const int a0 = (c->opts.eig_mode == 1) ? dm.m_max : 0;
+  const int na = (c->opts.eig_mode == 1) ? 1 : dm.nb;
+  const int qtiles = (dm.N + kEigQ - 1) / kEigQ;
+  const size_t smem = sizeof(double2) * 3 * dm.n_w * kEigQ;
+  cudaError_t e = cudaFuncSetAttribute((const void*)lambda_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  for (int ch = 0; ch < 2; ++ch) {
+    if (!(channel_mask & (1 << ch))) continue;
+    lambda_kernel<<<qtiles * na, kEigThreads, smem, c->stream>>>(dm, ch, 1, a0, na, 1e-12, c->gam, c->chi,
+                                                                 c->lam, c->lam_ok, flag_ptr(c));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace df

@@ -1,0 +1,196 @@
+// Internal declarations of libdf: device helpers shared by the kernels and
+// the context layout used by the host code.  Not part of the public ABI
+// (that is include/df.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include "../../include/df.h"
+
+namespace df {
+
+// ---------------------------------------------------------------------------
+// complex arithmetic on double2 / float2 (x = real, y = imag)
+// ---------------------------------------------------------------------------
+
+template <typename R> struct cplx_t;
+template <> struct cplx_t<double> { using type = double2; };
+template <> struct cplx_t<float> { using type = float2; };
+template <typename R> using cplx = typename cplx_t<R>::type;
+
+__host__ __device__ __forceinline__ double2 mk(double x, double y) { return make_double2(x, y); }
+__host__ __device__ __forceinline__ float2 mk(float x, float y) { return make_float2(x, y); }
+
+__host__ __device__ __forceinline__ double2 operator+(double2 a, double2 b) { return mk(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ double2 operator-(double2 a, double2 b) { return mk(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 operator+(float2 a, float2 b) { return mk(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 operator-(float2 a, float2 b) { return mk(a.x - b.x, a.y - b.y); }
+
+template <typename C>
+__host__ __device__ __forceinline__ C cmul(C a, C b) {
+  return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// c - a*b
+template <typename C>
+__host__ __device__ __forceinline__ C cfms(C a, C b, C c) {
+  return mk(fma(-a.x, b.x, fma(a.y, b.y, c.x)), fma(-a.x, b.y, fma(-a.y, b.x, c.y)));
+}
+__host__ __device__ __forceinline__ float2 cfms(float2 a, float2 b, float2 c) {
+  return mk(fmaf(-a.x, b.x, fmaf(a.y, b.y, c.x)), fmaf(-a.x, b.y, fmaf(-a.y, b.x, c.y)));
+}
+// c + a*b
+template <typename C>
+__host__ __device__ __forceinline__ C cfma(C a, C b, C c) {
+  return mk(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+__host__ __device__ __forceinline__ float2 cfma(float2 a, float2 b, float2 c) {
+  return mk(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
+}
+template <typename C>
+__host__ __device__ __forceinline__ C cscale(C a, decltype(a.x) s) { return mk(a.x * s, a.y * s); }
+template <typename C>
+__host__ __device__ __forceinline__ C cconj(C a) { return mk(a.x, -a.y); }
+template <typename C>
+__host__ __device__ __forceinline__ decltype(C().x) cabs1(C a) { return fabs(a.x) + fabs(a.y); }
+template <typename C>
+__host__ __device__ __forceinline__ decltype(C().x) cabs2(C a) { return a.x * a.x + a.y * a.y; }
+// 1/z with a scaling step so that |z|^2 cannot overflow or underflow
+template <typename C>
+__host__ __device__ __forceinline__ C cinv(C z) {
+  using R = decltype(z.x);
+  R s = fabs(z.x) > fabs(z.y) ? fabs(z.x) : fabs(z.y);
+  R inv_s = R(1) / s;
+  R a = z.x * inv_s, b = z.y * inv_s;
+  R d = R(1) / ((a * a + b * b) * s);
+  return mk(a * d, -b * d);
+}
+
+// ---------------------------------------------------------------------------
+// lattice helpers: the grid is N_k^D points, flattened with the last axis
+// fastest; axis d occupies bits [(D-1-d) p, (D-d) p) of the flat index,
+// N_k = 2^p.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int reflect_index(int r, int D, int p) {
+  // flat index of -r (each axis j -> (N_k - j) mod N_k)
+  const int mask = (1 << p) - 1;
+  int out = 0;
+  for (int d = 0; d < D; ++d) {
+    int j = (r >> (d * p)) & mask;
+    out |= ((-j) & mask) << (d * p);
+  }
+  return out;
+}
+
+__device__ __forceinline__ int bitrev_axes(int r, int D, int p) {
+  // reverse the p bits of every axis digit (an involution)
+  if (p == 0) return r;
+  const int mask = (1 << p) - 1;
+  int out = 0;
+  for (int d = 0; d < D; ++d) {
+    int j = (r >> (d * p)) & mask;
+    out |= (int)(__brev((unsigned)j) >> (32 - p)) << (d * p);
+  }
+  return out;
+}
+
+// Twiddles w[m] = exp(-2 pi i m / N_k), m < N_k/2, into shared memory.
+template <typename C>
+__device__ __forceinline__ void load_twiddles(C* tw, int nk) {
+  using R = decltype(C().x);
+  for (int m = threadIdx.x; m < nk / 2; m += blockDim.x) {
+    double s, c;
+    sincospi(-2.0 * (double)m / (double)nk, &s, &c);
+    tw[m] = mk((R)c, (R)s);
+  }
+}
+
+// In-place D-dimensional radix-2 decimation-in-time DFT of the N = 2^(D p)
+// points in shared memory s.  The input must be stored in per-axis
+// bit-reversed order (see bitrev_axes); the output is in natural order.
+// sign: forward (-1) computes X(k) = sum_r exp(-i k.r) x(r); inverse (+1)
+// computes sum_k exp(+i k.r) X(k) (no 1/N).  All threads of the block must
+// call it; it ends with __syncthreads().
+template <typename C>
+__device__ void fft_dit_smem(C* s, int D, int p, const C* tw, bool inverse) {
+  const int half = 1 << (D * p - 1);
+  for (int d = 0; d < D; ++d) {
+    const int base = d * p;  // axis bits [base, base+p)
+    for (int st = 0; st < p; ++st) {
+      const int h = 1 << st;
+      const int bit = base + st;
+      const int lowmask = (1 << bit) - 1;
+      for (int t = threadIdx.x; t < half; t += blockDim.x) {
+        const int i0 = ((t >> bit) << (bit + 1)) | (t & lowmask);
+        const int i1 = i0 | (1 << bit);
+        const int j = (i0 >> base) & (h - 1);
+        C w = tw[j << (p - 1 - st)];
+        if (inverse) w.y = -w.y;
+        C a = s[i0];
+        C b = cmul(s[i1], w);
+        s[i0] = a + b;
+        s[i1] = a - b;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+
+struct Dims {
+  int D, nk, p, N;       // lattice
+  int n_w, m_max, nb, ne;
+  double beta, T, mu, t, tp;
+};
+
+}  // namespace df
+
+struct df_ctx {
+  df::Dims dm;
+  df_opts opts;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  std::string err;
+  // device buffers (complex arrays are double2 = interleaved re, im)
+  double2* g = nullptr;        // [ne]
+  double2* delta = nullptr;    // [ne]
+  double2* gam = nullptr;      // [2][nb][n_w][n_w]  (channel 0 = d, 1 = m)
+  double2* g0 = nullptr;       // [ne][N]  bare dual G0~(k)
+  double2* gk = nullptr;       // [ne][N]  G~(k)
+  double2* gr = nullptr;       // [ne][N]  G~(r)
+  double2* chi = nullptr;      // [nb][n_w][N]
+  double2* kc = nullptr;       // [2][nb][n_w][N] Eq. sd bracket per channel (weights 1, 3)
+  double2* prod = nullptr;     // [nb][n_w][N] K(-r) G~_{w+W}(r)
+  double2* sigma = nullptr;    // [n_w][N]
+  double2* lam = nullptr;      // [2][nb][N] leading eigenvalue of gamma chi
+  int* lam_ok = nullptr;       // [2][nb][N] power iteration converged flag
+  double* red = nullptr;       // [2 n_w] residual partials, [2] final, [2] solve flags (ints)
+  double* h_red = nullptr;     // pinned host mirror of the final residual
+  void* bse_ws = nullptr;      // global scratch of the BSE kernel (large n)
+  size_t bse_ws_bytes = 0;
+  int bse_grid = 0;
+  int iter_done = 0;
+  int sigma_valid = 0;         // gk/gr reflect sigma
+  double last_resid = -1.0;
+  int radius_flag = 0;         // |lambda| >= 1 seen on the last df_bse
+};
+
+// host-side launchers (kernels live in df_fft.cu and df_bse.cu)
+namespace df {
+cudaError_t launch_init_g0(df_ctx* c);
+cudaError_t launch_dyson_ifft(df_ctx* c, int first_plane, int n_planes);
+cudaError_t launch_bubble(df_ctx* c);
+cudaError_t launch_sigma(df_ctx* c, double mix);
+cudaError_t launch_gamma_gt(df_ctx* c);
+cudaError_t launch_bse(df_ctx* c, int channel_mask);
+cudaError_t launch_lambda(df_ctx* c, int channel_mask);
+size_t bse_workspace_bytes(const Dims& dm, int grid);
+int bse_default_grid(const Dims& dm, int device);
+int* bse_flags(df_ctx* c);   // [0]: bit 0 zero pivot, bit 1 |lambda| >= 1
+}  // namespace df

@@ -1,0 +1,280 @@
+"""ctypes binding of libdf (include/df.h): argument marshalling only.
+
+Every step of the ladder dual-fermion loop runs in the CUDA kernels of
+``libdf.so``; this module converts numpy / torch arrays to pointers and
+status codes to exceptions.  There is no fallback: if the library is
+missing or no GPU is usable, loading or ``DualFermion(...)`` raises.
+
+Complex arrays cross the boundary as complex128 (interleaved re, im).
+Device arrays (torch CUDA tensors, complex128, contiguous) are passed
+with ``is_device=1`` and never leave the GPU.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdf.so")
+
+DF_OK = 0
+DF_ERR_ARG = 1
+DF_ERR_CUDA = 2
+DF_ERR_OOM = 3
+DF_ERR_SINGULAR = 4
+DF_ERR_REFINE_STALL = 5
+DF_ERR_NOT_CONVERGED = 6
+DF_ERR_TIMEOUT = 7
+DF_WARN_LADDER_RADIUS = 8
+
+DF_FP64 = 0
+DF_FP32_IR = 1
+
+# every symbol include/df.h declares (checked by the CPU tests)
+EXPORTS = (
+    "df_default_opts", "df_init", "df_set_inputs", "df_vertex_from_spin", "df_bubble", "df_bse",
+    "df_sigma", "df_iterate", "df_get_sigma", "df_set_sigma", "df_get_gtilde", "df_get_chi",
+    "df_get_kernel", "df_get_lambda", "df_get_sizes", "df_synchronize", "df_last_error",
+    "df_status_string", "df_destroy",
+)
+
+
+class DFError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_status_name(status)}: {msg}")
+        self.status = status
+
+
+class df_lattice(C.Structure):
+    _fields_ = [("dim", C.c_int), ("nk", C.c_int), ("tp", C.c_double)]
+
+
+class df_opts(C.Structure):
+    _fields_ = [("n_w", C.c_int), ("m_max", C.c_int), ("mix", C.c_double), ("precision", C.c_int),
+                ("eig_mode", C.c_int), ("ir_max_steps", C.c_int), ("ir_tol", C.c_double)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libdf.so (built by paper_1507_00895_gb300.build.build_lib)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libdf.so not found at {path}: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    D = C.POINTER(C.c_double)
+    I = C.POINTER(C.c_int)
+    sig = {
+        "df_default_opts": [C.POINTER(df_opts)],
+        "df_init": [C.POINTER(P), C.POINTER(df_lattice), C.c_double, C.c_double, C.c_double,
+                    P, P, P, P, C.POINTER(df_opts), P],
+        "df_set_inputs": [P, P, P, P, P, C.c_int],
+        "df_vertex_from_spin": [P, P, P, P, C.c_size_t],
+        "df_bubble": [P],
+        "df_bse": [P, C.c_int],
+        "df_sigma": [P, D],
+        "df_iterate": [P, C.c_int, C.c_double, I, D],
+        "df_get_sigma": [P, P, C.c_int],
+        "df_set_sigma": [P, P, C.c_int],
+        "df_get_gtilde": [P, P, C.c_int],
+        "df_get_chi": [P, P, C.c_int],
+        "df_get_kernel": [P, P, C.c_int],
+        "df_get_lambda": [P, P, P, C.c_int],
+        "df_get_sizes": [P, I, I, I],
+        "df_synchronize": [P],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = C.c_int
+    lib.df_last_error.argtypes = [P]
+    lib.df_last_error.restype = C.c_char_p
+    lib.df_status_string.argtypes = [C.c_int]
+    lib.df_status_string.restype = C.c_char_p
+    lib.df_destroy.argtypes = [P]
+    lib.df_destroy.restype = None
+    _lib = lib
+    return lib
+
+
+def _status_name(s: int) -> str:
+    names = {0: "DF_OK", 1: "DF_ERR_ARG", 2: "DF_ERR_CUDA", 3: "DF_ERR_OOM", 4: "DF_ERR_SINGULAR",
+             5: "DF_ERR_REFINE_STALL", 6: "DF_ERR_NOT_CONVERGED", 7: "DF_ERR_TIMEOUT",
+             8: "DF_WARN_LADDER_RADIUS"}
+    return names.get(s, f"status {s}")
+
+
+def _c128(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.complex128))
+
+
+def _ptr(a):
+    """(pointer, is_device) of a numpy array or a CUDA torch tensor."""
+    if isinstance(a, np.ndarray):
+        return C.c_void_p(a.ctypes.data), 0
+    if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
+        if not a.is_contiguous():
+            raise ValueError("device tensors must be contiguous")
+        return C.c_void_p(a.data_ptr()), (1 if a.is_cuda else 0)
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def current_stream_handle() -> Optional[int]:
+    """cudaStream_t of torch's current stream (None when torch/CUDA absent)."""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:
+        pass
+    return None
+
+
+class DualFermion:
+    """One ladder dual-fermion problem resident on the GPU (a df_ctx handle)."""
+
+    def __init__(self, *, dim: int, nk: int, t: float, tp: float, beta: float, mu: float,
+                 n_w: int, m_max: int, g, delta, gamma_d, gamma_m, mix: float = 1.0,
+                 precision: int = DF_FP64, eig_mode: int = 1, ir_max_steps: int = 8,
+                 ir_tol: float = 1e-13, stream: Optional[int] = None):
+        self.lib = load()
+        self.dim, self.nk, self.n_w, self.m_max = dim, nk, n_w, m_max
+        self.N = nk ** dim
+        self.nb = 2 * m_max + 1
+        self.ne = n_w + 2 * m_max
+        lat = df_lattice(dim, nk, tp)
+        opts = df_opts()
+        self.lib.df_default_opts(C.byref(opts))
+        opts.n_w, opts.m_max, opts.mix, opts.precision = n_w, m_max, mix, precision
+        opts.eig_mode, opts.ir_max_steps, opts.ir_tol = eig_mode, ir_max_steps, ir_tol
+        g, delta = _c128(g), _c128(delta)
+        gd, gm = _c128(gamma_d), _c128(gamma_m)
+        if g.shape != (self.ne,) or delta.shape != (self.ne,):
+            raise ValueError(f"g, delta must have shape ({self.ne},)")
+        if gd.shape != (self.nb, n_w, n_w) or gm.shape != gd.shape:
+            raise ValueError(f"gamma_d, gamma_m must have shape {(self.nb, n_w, n_w)}")
+        if stream is None:
+            stream = current_stream_handle()
+        self._stream = stream
+        h = C.c_void_p()
+        s = self.lib.df_init(C.byref(h), C.byref(lat), beta, mu, t,
+                             g.ctypes.data, delta.ctypes.data, gd.ctypes.data, gm.ctypes.data,
+                             C.byref(opts), C.c_void_p(stream) if stream else None)
+        if s != DF_OK:
+            raise DFError(s, "df_init failed (see stderr)")
+        self.h = h
+
+    @classmethod
+    def from_workload(cls, w, **kw):
+        """Build from an ``inputs.Workload`` (channels combined by df_vertex_from_spin)."""
+        gd, gm = vertex_from_spin(w.gamma_uu, w.gamma_ud)
+        return cls(dim=w.dim, nk=w.nk, t=w.t, tp=w.tp, beta=w.beta, mu=w.mu, n_w=w.n_w,
+                   m_max=w.m_max, g=w.g, delta=w.delta, gamma_d=gd, gamma_m=gm, **kw)
+
+    # -- status ---------------------------------------------------------------
+    def _check(self, s: int, allow=(DF_OK,)):
+        if s in allow:
+            return s
+        msg = self.lib.df_last_error(self.h).decode()
+        raise DFError(s, msg)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.df_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- loop steps -----------------------------------------------------------
+    def bubble(self):
+        self._check(self.lib.df_bubble(self.h))
+
+    def bse(self, channel_mask: int = 3):
+        self._check(self.lib.df_bse(self.h, channel_mask))
+
+    def sigma(self, want_residual: bool = True):
+        r = C.c_double(-1.0)
+        s = self.lib.df_sigma(self.h, C.byref(r) if want_residual else None)
+        self._check(s, (DF_OK, DF_WARN_LADDER_RADIUS))
+        return r.value if want_residual else None
+
+    def iterate(self, max_iter: int, tol: float = 0.0):
+        """Returns (iterations done, residual, status)."""
+        it = C.c_int(0)
+        r = C.c_double(-1.0)
+        s = self.lib.df_iterate(self.h, max_iter, tol, C.byref(it), C.byref(r))
+        self._check(s, (DF_OK, DF_WARN_LADDER_RADIUS, DF_ERR_NOT_CONVERGED))
+        return it.value, r.value, s
+
+    def synchronize(self):
+        self._check(self.lib.df_synchronize(self.h))
+
+    # -- data -----------------------------------------------------------------
+    def _get(self, fn, shape, out=None):
+        if out is None:
+            out = np.empty(shape, np.complex128)
+        p, dev = _ptr(out)
+        self._check(fn(self.h, p, dev))
+        return out
+
+    def get_sigma(self, out=None):
+        return self._get(self.lib.df_get_sigma, (self.n_w, self.N), out)
+
+    def get_gtilde(self, out=None):
+        return self._get(self.lib.df_get_gtilde, (self.ne, self.N), out)
+
+    def get_chi(self, out=None):
+        return self._get(self.lib.df_get_chi, (self.nb, self.n_w, self.N), out)
+
+    def get_kernel(self, out=None):
+        return self._get(self.lib.df_get_kernel, (2, self.nb, self.n_w, self.N), out)
+
+    def get_lambda(self):
+        lam = np.empty((2, self.nb, self.N), np.complex128)
+        ok = np.empty((2, self.nb, self.N), np.int32)
+        self._check(self.lib.df_get_lambda(self.h, lam.ctypes.data, ok.ctypes.data, 0))
+        return lam, ok
+
+    def set_sigma(self, sig):
+        if isinstance(sig, np.ndarray):
+            sig = _c128(sig)
+        p, dev = _ptr(sig)
+        self._check(self.lib.df_set_sigma(self.h, p, dev))
+
+    def set_inputs(self, g, delta, gamma_d, gamma_m):
+        arrs = [a if not isinstance(a, np.ndarray) else _c128(a) for a in (g, delta, gamma_d, gamma_m)]
+        ptrs = [_ptr(a) for a in arrs]
+        dev = {d for _, d in ptrs}
+        if len(dev) != 1:
+            raise ValueError("all inputs must be on the same side (host or device)")
+        self._check(self.lib.df_set_inputs(self.h, *[p for p, _ in ptrs], dev.pop()))
+
+
+def vertex_from_spin(gamma_uu, gamma_ud):
+    """Eq. spin_symm through libdf's host helper: (d, m) = (uu + ud, uu - ud)."""
+    lib = load()
+    uu, ud = _c128(gamma_uu), _c128(gamma_ud)
+    d = np.empty_like(uu)
+    m = np.empty_like(uu)
+    s = lib.df_vertex_from_spin(uu.ctypes.data, ud.ctypes.data, d.ctypes.data, m.ctypes.data, uu.size)
+    if s != DF_OK:
+        raise DFError(s, "df_vertex_from_spin")
+    return d, m
