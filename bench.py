@@ -1,0 +1,384 @@
+#!/usr/bin/env python
+"""(q, W) ladder points/s of the ladder dual-fermion loop on one GB300.
+
+One step = one outer pass of the loop over the whole workload: Dyson and
+lattice FFTs, the dual bubble (Eq. dual_bubble), both ladder channels for
+every (q, W) (Eq. lin_alg_inv, Gamma^(2) fused), the leading eigenvalue of
+gamma chi~ at W = 0, the Schwinger-Dyson convolution (Eq. sd) and Dyson
+(Eq. dyson).  Workload: 2D 32x32 square lattice, t = 1, t' = -0.2, U = 4,
+beta = 10, mu of the Hubbard atom at n = 0.9, n_w = 64 fermionic and 15
+bosonic frequencies (W = -7..7), vertex = atomic closed form + symmetric
+Gaussian (0.05U, seed 2): 15,360 (q, W) points, 30,720 ladders of order
+64 per step.  Every step starts from Sigma~ = 0 (the same first pass), and
+L2 is flushed (256 MiB write) between steps, outside the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs N independent replicas (one parameter point per GPU, no
+collective), launched by torch.distributed.run.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import resource
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "(q,Ω) ladder points/s and time-to-converged Σ̃ at ≤1e-8 vs FP64, mixed vs plain"
+UNIT = "points/s"
+WORKLOAD = "square32_tp"
+WORKLOAD_DESC = ("2D 32x32 square lattice, t=1, t'=-0.2, U=4, beta=10, mu(atom n=0.9), "
+                 "n_w=64, N_W=15 (W=-7..7), atomic vertex + symmetric Gaussian 0.05U (seed 2)")
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# FP64 CUDA-core peak of the GB300: 152 SMs x 2 FP64 FMA/clock/SM x 2 flop x 2.07 GHz
+FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+FLUSH_BYTES = 256 << 20
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: str):
+        self.rows = []
+        self.proc = None
+        self.gpu = gpu_index
+
+    def start(self):
+        try:
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+            if self.gpu is not None:
+                cmd += ["-i", self.gpu]
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = self.rows
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        mx = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def gpu_index_for_smi(local_rank: int):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v.strip() for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids):
+            return ids[local_rank]
+    try:
+        import torch
+        u = str(torch.cuda.get_device_properties(local_rank).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(local_rank)
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle legs (the only place the benchmark runs oracle/)
+# ---------------------------------------------------------------------------
+
+def oracle_sample_step(w, planes, state):
+    """One oracle pass restricted to the ladders of the bosonic planes in
+    `planes` (both channels); the bubble, Sigma~ convolution and Dyson run in
+    full.  Returns the number of (q, W) ladder points processed."""
+    import numpy as np
+    from oracle import df_oracle as O
+    g0, gd, gm = state["g0"], state["gd"], state["gm"]
+    gt = O.dual_g(g0, np.zeros((w.n_w, w.N), complex), w.n_w, w.m_max)
+    chi = O.dual_bubble_fft(gt, w.n_w, w.m_max, w.beta, w.dim, w.nk)
+    kern = np.zeros_like(chi)
+    for a in planes:
+        sl = slice(a, a + 1)
+        dd = O.ladder_gamma_diag(gd[sl], chi[sl])
+        mm = O.ladder_gamma_diag(gm[sl], chi[sl])
+        kern[sl] = O.sd_kernel(dd, O.second_order_diag(gd[sl], chi[sl]), mm, O.second_order_diag(gm[sl], chi[sl]))
+    sig = O.dual_sigma_fft(kern, gt, w.n_w, w.m_max, w.beta, w.dim, w.nk)
+    O.dual_g(g0, sig, w.n_w, w.m_max)
+    return len(planes) * w.N
+
+
+def oracle_state(w):
+    from oracle import df_oracle as O
+    g0 = O.bare_dual_g(w.g, w.delta, O.dispersion(w.dim, w.nk, w.t, w.tp))
+    gd, gm = O.channel_vertices(w.gamma_uu, w.gamma_ud)
+    return {"g0": g0, "gd": gd, "gm": gm}
+
+
+def timed_cpu(fn):
+    r0 = resource.getrusage(resource.RUSAGE_SELF)
+    t0 = time.perf_counter()
+    out = fn()
+    t1 = time.perf_counter()
+    r1 = resource.getrusage(resource.RUSAGE_SELF)
+    cpu = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
+    return out, t1 - t0, cpu
+
+
+def cpu_baseline(w):
+    """The oracle, as it stands, on one full pass of the workload."""
+    st = oracle_state(w)
+    pts, wall, cpu = timed_cpu(lambda: oracle_sample_step(w, range(w.n_bos), st))
+    return {"value": pts / wall, "unit": UNIT, "cores": round(cpu / wall, 2), "kind": "oracle",
+            "sample": f"one full oracle pass of the workload ({pts} (q,W) points, both channels), "
+                      f"{wall:.1f} s wall on {os.cpu_count()} host cores; cores = CPU time / wall time"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1507_00895_gb300 import inputs as I
+    w = I.workload(WORKLOAD)
+    st = oracle_state(w)
+    # calibrate: seconds per bosonic plane, then size each step so that the
+    # whole run stays within about two minutes
+    _, t1, _ = timed_cpu(lambda: oracle_sample_step(w, [w.m_max], st))
+    budget = 120.0 / max(1, args.steps + args.warmup)
+    per = max(1, min(w.n_bos, int(budget / max(t1, 1e-3))))
+    planes_of = lambda i: [(i * per + j) % w.n_bos for j in range(per)]
+    for i in range(args.warmup):
+        oracle_sample_step(w, planes_of(i), st)
+    pts = 0
+    wall = 0.0
+    cpu = 0.0
+    for i in range(args.steps):
+        p, dt, c = timed_cpu(lambda: oracle_sample_step(w, planes_of(args.warmup + i), st))
+        pts += p
+        wall += dt
+        cpu += c
+    value = pts / wall
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * wall / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD_DESC, "planes_per_step": per,
+                                             "points_per_step": per * w.N},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": round(cpu / wall, 2), "kind": "oracle",
+                             "sample": f"{per} of {w.n_bos} bosonic planes per step ({per * w.N} (q,W) "
+                                       f"points, both channels; bubble and Sigma~ in full), "
+                                       f"{os.cpu_count()} host cores"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+
+def read_peaks():
+    try:
+        with open(PEAKS_PATH) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1507_00895_gb300 import build, df, inputs as I
+    if rank == 0:
+        build.build_lib()
+    if world > 1:
+        torch.distributed.barrier()
+    build.build_lib()
+
+    # replicas: rank r runs its own parameter point (seed 2 + r)
+    w = I.workload(WORKLOAD, seed=2 + rank)
+    points = w.n_bos * w.N
+    prec = df.DF_FP64 if args.precision == "fp64" else df.DF_FP32_IR
+    stream = torch.cuda.current_stream()
+    d = df.DualFermion.from_workload(w, precision=prec, eig_mode=1, stream=stream.cuda_stream)
+    zeros = torch.zeros((w.n_w, w.N), dtype=torch.complex128, device="cuda")
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def step():
+        d.bubble()
+        d.bse(3)
+        d.sigma(want_residual=False)
+
+    for _ in range(args.warmup):
+        d.set_sigma(zeros)
+        step()
+    torch.cuda.synchronize()
+
+    # ---- device-timed region ----
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(gpu_index_for_smi(local)) if rank == 0 else None
+    if clocks:
+        clocks.start()
+        time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    d.set_timing(True)
+    for i in range(args.steps):
+        flush.zero_()
+        d.set_sigma(zeros)
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop() if clocks else None
+    timing = d.get_timing()
+    d.set_timing(False)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = sum(step_ms) / len(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * points / (ms * 1e-3)
+    launches = sum(v[1] for v in timing.values())
+
+    # ---- dominant kernel: the ladder solves ----
+    bse_ms, bse_launches = timing["bse"]
+    bse_avg_s = bse_ms / max(1, bse_launches) * 1e-3
+    n = w.n_w
+    systems_per_launch = w.n_bos * w.N               # one channel per launch
+    flop_per_system = 8.0 * n ** 3                   # LU n^3/3 + forward n^3/2 + back n^3/6 complex MACs
+    achieved = systems_per_launch * flop_per_system / bse_avg_s / 1e9
+    if prec == df.DF_FP64:
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+                "kernel": "bse_f64_kernel",
+                "peak_source": "FP64 CUDA cores: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TF/s; "
+                               "1.20 TF/s measured by an FMA loop)",
+                "flop_per_launch": systems_per_launch * flop_per_system,
+                "launch_ms": bse_avg_s * 1e3}
+    else:
+        roof = {"bound": "alu", "achieved": achieved, "peak": None, "unit": "GFLOP/s", "frac": None,
+                "traffic": None, "kernel": "bse_mixed"}
+
+    # ---- end to end through the public API with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        gd, gm = df.vertex_from_spin(w.gamma_uu, w.gamma_ud)
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        h_in = [pin(w.g), pin(w.delta), pin(gd), pin(gm)]
+        h_sig0 = pin(np.zeros((w.n_w, w.N), np.complex128))
+        h_out = torch.empty((w.n_w, w.N), dtype=torch.complex128).pin_memory()
+        bi = sum(t.numel() * t.element_size() for t in h_in) + h_sig0.numel() * 16
+        bo = h_out.numel() * 16
+        for _ in range(2):
+            d.set_sigma(h_sig0)
+            d.set_inputs(*h_in)
+            step()
+            d.get_sigma(h_out)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            d.set_sigma(h_sig0)
+            d.set_inputs(*h_in)
+            step()
+            d.get_sigma(h_out)
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / args.steps
+        if world > 1:
+            t = torch.tensor([e2e_s], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * points / e2e_s, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
+               "ms_per_step": e2e_s * 1e3}
+    d.close()
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(I.workload(WORKLOAD))
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if prec == df.DF_FP64 else "f32+f64-refinement",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC, "points_per_step": points,
+                       "ladders_per_step": 2 * points, "ladder_order": n,
+                       "precision": args.precision, "eigen_check": "W=0, both channels",
+                       "step_start": "Sigma~=0", "l2": "flushed between steps (256 MiB write)",
+                       "parallelism": f"replicas{world}"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in timing.items()},
+            "clocks": clk}
+    print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp64", "fp32ir"], default="fp64")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)       # at least 3 untimed warm-up steps
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -136,8 +136,10 @@ df_status df_bubble(df_ctx* c);
  * opts.precision); keeps c (Gamma_{W,w,w} - Gamma^(2)_{W,w,w}/2) with
  * Gamma^(2) = gamma chi~ gamma (the double-counting term of Eq. sd).  With
  * eig_mode != 0 also estimates the leading eigenvalue of gamma chi~ (FP64
- * power iteration) and returns DF_WARN_LADDER_RADIUS when one has modulus
- * >= 1.  Needs df_bubble first. */
+ * power iteration).  Asynchronous: a zero pivot or |lambda| >= 1 is
+ * recorded on the device and reported by the next df_sigma with a residual
+ * pointer (DF_ERR_SINGULAR / DF_WARN_LADDER_RADIUS) or by df_iterate.
+ * Needs df_bubble first. */
 df_status df_bse(df_ctx* c, int channel_mask);
 
 /* Eq. sd and Eq. dyson: from the ladder kernel and G~,
@@ -165,6 +167,22 @@ df_status df_get_lambda(df_ctx* c, double* lambda, int* ok, int out_is_device);
 
 /* Sizes of the handle: n_e, N_W, N (any pointer may be NULL). */
 df_status df_get_sizes(const df_ctx* c, int* n_ext, int* n_bos, int* n_k_total);
+
+/* Per-kernel device time (CUDA events recorded on the handle's stream
+ * around each kernel group).  df_set_timing(c, 1) clears the totals and
+ * starts recording, df_set_timing(c, 0) stops.  df_get_timing
+ * synchronises and fills, for the first `count` groups, ms[i] = summed
+ * device milliseconds and launches[i] = kernels launched (either pointer
+ * may be NULL).  Groups: */
+enum {
+  DF_T_BUBBLE = 0,   /* Eq. dual_bubble: 1 kernel per df_bubble */
+  DF_T_BSE = 1,      /* Eq. lin_alg_inv: 1 kernel per channel */
+  DF_T_LAMBDA = 2,   /* leading eigenvalue: 1 kernel per channel (eig_mode != 0) */
+  DF_T_SIGMA = 3,    /* Eq. sd + Eq. dyson + residual: 3 kernels per df_sigma */
+  DF_T_COUNT = 4
+};
+df_status df_set_timing(df_ctx* c, int on);
+df_status df_get_timing(df_ctx* c, double* ms, int* launches, int count);
 
 /* Wait for all work queued on the handle's stream. */
 df_status df_synchronize(df_ctx* c);

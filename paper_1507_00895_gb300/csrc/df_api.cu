@@ -71,6 +71,59 @@ df_status upload_inputs(df_ctx* c, const double* g, const double* delta, const d
   return DF_OK;
 }
 
+cudaEvent_t take_event(df_ctx* c) {
+  if (!c->event_pool.empty()) {
+    cudaEvent_t e = c->event_pool.back();
+    c->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Records CUDA events around one kernel group when timing is on.
+struct Timed {
+  df_ctx* c;
+  df_ctx::Mark m;
+  Timed(df_ctx* c_, int slot, int launches) : c(c_) {
+    m.slot = slot;
+    m.launches = launches;
+    m.a = m.b = nullptr;
+    if (c->timing) {
+      m.a = take_event(c);
+      m.b = take_event(c);
+      cudaEventRecord(m.a, c->stream);
+    }
+  }
+  ~Timed() {
+    if (m.a) {
+      cudaEventRecord(m.b, c->stream);
+      c->marks.push_back(m);
+    }
+  }
+};
+
+int n_channels(int mask) { return (mask & 1) + ((mask >> 1) & 1); }
+
+cudaError_t run_bubble(df_ctx* c) {
+  Timed t(c, DF_T_BUBBLE, 1);
+  return launch_bubble(c);
+}
+cudaError_t run_bse(df_ctx* c, int mask) {
+  Timed t(c, DF_T_BSE, n_channels(mask));
+  return launch_bse(c, mask);
+}
+cudaError_t run_lambda(df_ctx* c, int mask) {
+  if (c->opts.eig_mode == 0) return cudaSuccess;
+  Timed t(c, DF_T_LAMBDA, n_channels(mask));
+  return launch_lambda(c, mask);
+}
+cudaError_t run_sigma(df_ctx* c) {
+  Timed t(c, DF_T_SIGMA, 3);
+  return launch_sigma(c, c->opts.mix);
+}
+
 df_status read_scalars(df_ctx* c, double* resid, int* flags) {
   // one 32-byte copy: residual max-norms and the solve flags
   double* h = c->h_red;
@@ -142,6 +195,11 @@ void df_destroy(df_ctx* c) {
   cudaFree(c->red);
   cudaFree(c->bse_ws);
   if (c->h_red) cudaFreeHost(c->h_red);
+  for (auto& m : c->marks) {
+    cudaEventDestroy(m.a);
+    cudaEventDestroy(m.b);
+  }
+  for (auto e : c->event_pool) cudaEventDestroy(e);
   delete c;
 }
 
@@ -258,21 +316,21 @@ df_status df_set_inputs(df_ctx* c, const double* g, const double* delta, const d
 
 df_status df_bubble(df_ctx* c) {
   if (!c) return DF_ERR_ARG;
-  DF_CUDA(c, launch_bubble(c), "dual bubble (Eq. dual_bubble)");
+  DF_CUDA(c, run_bubble(c), "dual bubble (Eq. dual_bubble)");
   return DF_OK;
 }
 
 df_status df_bse(df_ctx* c, int channel_mask) {
   if (!c) return DF_ERR_ARG;
   if (channel_mask < 1 || channel_mask > 3) return fail(c, DF_ERR_ARG, "channel_mask must be 1, 2 or 3");
-  DF_CUDA(c, launch_bse(c, channel_mask), "ladder solve (Eq. lin_alg_inv)");
-  DF_CUDA(c, launch_lambda(c, channel_mask), "leading eigenvalue of gamma chi");
+  DF_CUDA(c, run_bse(c, channel_mask), "ladder solve (Eq. lin_alg_inv)");
+  DF_CUDA(c, run_lambda(c, channel_mask), "leading eigenvalue of gamma chi");
   return DF_OK;
 }
 
 df_status df_sigma(df_ctx* c, double* resid) {
   if (!c) return DF_ERR_ARG;
-  DF_CUDA(c, launch_sigma(c, c->opts.mix), "dual self-energy (Eq. sd) + Dyson");
+  DF_CUDA(c, run_sigma(c), "dual self-energy (Eq. sd) + Dyson");
   ++c->iter_done;
   if (resid) {
     int flags = 0;
@@ -291,10 +349,10 @@ df_status df_iterate(df_ctx* c, int max_iter, double tol, int* iters_done, doubl
   double r = -1.0;
   int it = 0, flags = 0;
   for (; it < max_iter; ++it) {
-    DF_CUDA(c, launch_bubble(c), "dual bubble (Eq. dual_bubble)");
-    DF_CUDA(c, launch_bse(c, 3), "ladder solve (Eq. lin_alg_inv)");
-    DF_CUDA(c, launch_lambda(c, 3), "leading eigenvalue of gamma chi");
-    DF_CUDA(c, launch_sigma(c, c->opts.mix), "dual self-energy (Eq. sd) + Dyson");
+    DF_CUDA(c, run_bubble(c), "dual bubble (Eq. dual_bubble)");
+    DF_CUDA(c, run_bse(c, 3), "ladder solve (Eq. lin_alg_inv)");
+    DF_CUDA(c, run_lambda(c, 3), "leading eigenvalue of gamma chi");
+    DF_CUDA(c, run_sigma(c), "dual self-energy (Eq. sd) + Dyson");
     ++c->iter_done;
     if (tol > 0.0 || it == max_iter - 1) {
       df_status s = read_scalars(c, &r, &flags);
@@ -361,6 +419,43 @@ df_status df_get_sizes(const df_ctx* c, int* n_ext, int* n_bos, int* n_k_total) 
   if (n_ext) *n_ext = c->dm.ne;
   if (n_bos) *n_bos = c->dm.nb;
   if (n_k_total) *n_k_total = c->dm.N;
+  return DF_OK;
+}
+
+df_status df_set_timing(df_ctx* c, int on) {
+  if (!c) return DF_ERR_ARG;
+  if (on) {
+    for (auto& m : c->marks) {
+      c->event_pool.push_back(m.a);
+      c->event_pool.push_back(m.b);
+    }
+    c->marks.clear();
+    for (int i = 0; i < DF_T_COUNT; ++i) {
+      c->t_ms[i] = 0.0;
+      c->t_launches[i] = 0;
+    }
+  }
+  c->timing = on ? 1 : 0;
+  return DF_OK;
+}
+
+df_status df_get_timing(df_ctx* c, double* ms, int* launches, int count) {
+  if (!c) return DF_ERR_ARG;
+  if (count < 0 || count > DF_T_COUNT) return fail(c, DF_ERR_ARG, "count out of range");
+  DF_CUDA(c, cudaStreamSynchronize(c->stream), "df_get_timing");
+  for (auto& m : c->marks) {
+    float t = 0.f;
+    DF_CUDA(c, cudaEventElapsedTime(&t, m.a, m.b), "cudaEventElapsedTime");
+    c->t_ms[m.slot] += t;
+    c->t_launches[m.slot] += m.launches;
+    c->event_pool.push_back(m.a);
+    c->event_pool.push_back(m.b);
+  }
+  c->marks.clear();
+  for (int i = 0; i < count; ++i) {
+    if (ms) ms[i] = c->t_ms[i];
+    if (launches) launches[i] = c->t_launches[i];
+  }
   return DF_OK;
 }
 

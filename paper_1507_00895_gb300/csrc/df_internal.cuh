@@ -7,6 +7,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "../../include/df.h"
 
@@ -179,6 +180,13 @@ struct df_ctx {
   int sigma_valid = 0;         // gk/gr reflect sigma
   double last_resid = -1.0;
   int radius_flag = 0;         // |lambda| >= 1 seen on the last df_bse
+  // per-kernel-group timing (df_set_timing)
+  int timing = 0;
+  struct Mark { int slot; int launches; cudaEvent_t a, b; };
+  std::vector<Mark> marks;
+  std::vector<cudaEvent_t> event_pool;
+  double t_ms[DF_T_COUNT] = {0, 0, 0, 0};
+  int t_launches[DF_T_COUNT] = {0, 0, 0, 0};
 };
 
 // host-side launchers (kernels live in df_fft.cu and df_bse.cu)

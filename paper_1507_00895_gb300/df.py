@@ -37,7 +37,8 @@ DF_FP32_IR = 1
 EXPORTS = (
     "df_default_opts", "df_init", "df_set_inputs", "df_vertex_from_spin", "df_bubble", "df_bse",
     "df_sigma", "df_iterate", "df_get_sigma", "df_set_sigma", "df_get_gtilde", "df_get_chi",
-    "df_get_kernel", "df_get_lambda", "df_get_sizes", "df_synchronize", "df_last_error",
+    "df_get_kernel", "df_get_lambda", "df_get_sizes", "df_set_timing", "df_get_timing",
+    "df_synchronize", "df_last_error",
     "df_status_string", "df_destroy",
 )
 
@@ -89,6 +90,8 @@ def load(path: str = LIB_PATH):
         "df_get_kernel": [P, P, C.c_int],
         "df_get_lambda": [P, P, P, C.c_int],
         "df_get_sizes": [P, I, I, I],
+        "df_set_timing": [P, C.c_int],
+        "df_get_timing": [P, D, I, C.c_int],
         "df_synchronize": [P],
     }
     for name, args in sig.items():
@@ -223,6 +226,19 @@ class DualFermion:
         s = self.lib.df_iterate(self.h, max_iter, tol, C.byref(it), C.byref(r))
         self._check(s, (DF_OK, DF_WARN_LADDER_RADIUS, DF_ERR_NOT_CONVERGED))
         return it.value, r.value, s
+
+    TIMING_GROUPS = ("bubble", "bse", "lambda", "sigma")
+
+    def set_timing(self, on: bool):
+        self._check(self.lib.df_set_timing(self.h, 1 if on else 0))
+
+    def get_timing(self):
+        """{group: (device ms, kernel launches)} since set_timing(True)."""
+        n = len(self.TIMING_GROUPS)
+        ms = (C.c_double * n)()
+        la = (C.c_int * n)()
+        self._check(self.lib.df_get_timing(self.h, ms, la, n))
+        return {g: (ms[i], la[i]) for i, g in enumerate(self.TIMING_GROUPS)}
 
     def synchronize(self):
         self._check(self.lib.df_synchronize(self.h))
