@@ -198,36 +198,45 @@ bse_f64_kernel(Dims dm, int ch0, int nch, int nc, const double2* __restrict__ ga
 
 // ---------------------------------------------------------------------------
 // leading eigenvalue of A = gamma_W diag(chi~_W(q)) by FP64 power iteration
-// with a Rayleigh-quotient estimate; one CTA handles kQ systems that share
-// (channel, W) so the gamma rows are read once per iteration for all of them.
+// with a Rayleigh-quotient estimate.  One CTA handles kEigQ systems that
+// share (channel, W): gamma_W is staged in shared memory once (when it
+// fits) and each thread owns (row, system) pairs of y = A v, so one
+// iteration is n^2 complex multiply-adds per system with no reductions
+// except the per-system Rayleigh quotient.  A system is "converged" when
+// the estimate changes by less than tol relative; iterations stop when all
+// kEigQ systems converged or after kEigMaxIter.
 // ---------------------------------------------------------------------------
 constexpr int kEigQ = 8;
 constexpr int kEigThreads = 256;
-constexpr int kEigMaxIter = 400;
+constexpr int kEigMaxIter = 64;
 
 __global__ void __launch_bounds__(kEigThreads)
-lambda_kernel(Dims dm, int ch0, int nch, int a0, int na, double tol, const double2* __restrict__ gam,
+lambda_kernel(Dims dm, int ch0, int a0, int na, int g_in_smem, double tol, const double2* __restrict__ gam,
               const double2* __restrict__ chi, double2* __restrict__ lam, int* __restrict__ ok,
               int* __restrict__ flags) {
   extern __shared__ double2 sm[];
   const int n = dm.n_w, N = dm.N, nb = dm.nb;
-  double2* v = sm;                 // [n][kEigQ]
-  double2* y = v + n * kEigQ;      // [n][kEigQ]
-  double2* xq = y + n * kEigQ;     // [n][kEigQ]
+  double2* v = sm;                 // [n][kEigQ] current unit vector
+  double2* xq = v + n * kEigQ;     // [n][kEigQ] chi~ of the kEigQ systems
+  double2* y = xq + n * kEigQ;     // [n][kEigQ] A v
+  double2* Gs = y + n * kEigQ;     // [n][n] gamma_W (if g_in_smem)
   __shared__ double2 lam_old[kEigQ], lam_new[kEigQ];
   __shared__ double nrm[kEigQ];
   __shared__ int done[kEigQ];
   const int qtiles = (N + kEigQ - 1) / kEigQ;
   const int tile = blockIdx.x % qtiles;
-  const int a = a0 + (blockIdx.x / qtiles) % na;
-  const int c = ch0 + blockIdx.x / (qtiles * na);
-  if (c >= ch0 + nch) return;
+  const int a = a0 + blockIdx.x / qtiles;
+  const int c = ch0;
+  if (a >= a0 + na) return;
   const int q0 = tile * kEigQ;
   const int nq = min(kEigQ, N - q0);
-  const double2* G = gam + ((size_t)c * nb + a) * n * n;
+  const double2* Gg = gam + ((size_t)c * nb + a) * n * n;
+  const double2* G = g_in_smem ? Gs : Gg;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const double inv_sqrt_n = rsqrt((double)n);
 
+  if (g_in_smem)
+    for (int idx = tid; idx < n * n; idx += blockDim.x) Gs[idx] = Gg[idx];
   for (int idx = tid; idx < n * kEigQ; idx += blockDim.x) {
     const int j = idx / kEigQ, t = idx % kEigQ;
     xq[idx] = (t < nq) ? chi[((size_t)a * n + j) * N + q0 + t] : mk(0.0, 0.0);
@@ -235,35 +244,21 @@ lambda_kernel(Dims dm, int ch0, int nch, int a0, int na, double tol, const doubl
   }
   if (tid < kEigQ) {
     lam_old[tid] = mk(0.0, 0.0);
+    lam_new[tid] = mk(0.0, 0.0);
     done[tid] = (tid < nq) ? 0 : 1;
   }
   __syncthreads();
-  int it = 0;
-  for (; it < kEigMaxIter; ++it) {
-    // y = G (chi o v); warps over rows, lanes over columns
-    for (int i = warp; i < n; i += blockDim.x / 32) {
-      double2 acc[kEigQ];
-#pragma unroll
-      for (int t = 0; t < kEigQ; ++t) acc[t] = mk(0.0, 0.0);
-      for (int j = lane; j < n; j += 32) {
-        const double2 gij = G[(size_t)i * n + j];
-#pragma unroll
-        for (int t = 0; t < kEigQ; ++t) acc[t] = cfma(gij, cmul(xq[j * kEigQ + t], v[j * kEigQ + t]), acc[t]);
-      }
-#pragma unroll
-      for (int t = 0; t < kEigQ; ++t) {
-        for (int o = 16; o > 0; o >>= 1) {
-          acc[t].x += __shfl_xor_sync(0xffffffffu, acc[t].x, o);
-          acc[t].y += __shfl_xor_sync(0xffffffffu, acc[t].y, o);
-        }
-      }
-      if (lane == 0) {
-#pragma unroll
-        for (int t = 0; t < kEigQ; ++t) y[i * kEigQ + t] = acc[t];
-      }
+  for (int it = 0; it < kEigMaxIter; ++it) {
+    // y[i][t] = sum_j G[i][j] chi[j][t] v[j][t]
+    for (int pidx = tid; pidx < n * kEigQ; pidx += blockDim.x) {
+      const int i = pidx / kEigQ, t = pidx % kEigQ;
+      double2 acc = mk(0.0, 0.0);
+      for (int j = 0; j < n; ++j)
+        acc = cfma(G[i * n + j], cmul(xq[j * kEigQ + t], v[j * kEigQ + t]), acc);
+      y[pidx] = acc;
     }
     __syncthreads();
-    // Rayleigh quotient v^H y (|v| = 1) and |y|
+    // per system: Rayleigh quotient v^H y (|v| = 1) and 1/|y|
     if (warp < kEigQ) {
       const int t = warp;
       double2 rq = mk(0.0, 0.0);
@@ -284,10 +279,7 @@ lambda_kernel(Dims dm, int ch0, int nch, int a0, int na, double tol, const doubl
       }
     }
     __syncthreads();
-    for (int idx = tid; idx < n * kEigQ; idx += blockDim.x) {
-      const int t = idx % kEigQ;
-      v[idx] = cscale(y[idx], nrm[t]);
-    }
+    for (int idx = tid; idx < n * kEigQ; idx += blockDim.x) v[idx] = cscale(y[idx], nrm[idx % kEigQ]);
     if (tid < kEigQ && !done[tid]) {
       const double2 d = lam_new[tid] - lam_old[tid];
       if (sqrt(cabs2(d)) <= tol * sqrt(cabs2(lam_new[tid]))) done[tid] = 1;
@@ -295,15 +287,15 @@ lambda_kernel(Dims dm, int ch0, int nch, int a0, int na, double tol, const doubl
     }
     __syncthreads();
     int all = 1;
+#pragma unroll
     for (int t = 0; t < kEigQ; ++t) all &= done[t];
     if (all) break;
-    __syncthreads();
   }
   if (tid < nq) {
     const size_t o = ((size_t)c * nb + a) * N + q0 + tid;
     lam[o] = lam_new[tid];
     ok[o] = done[tid];
-    if (lam_new[tid].x * lam_new[tid].x + lam_new[tid].y * lam_new[tid].y >= 1.0) atomicOr(flags, 2);
+    if (cabs2(lam_new[tid]) >= 1.0) atomicOr(flags, 2);
   }
 }
 
@@ -377,14 +369,15 @@ cudaError_t launch_lambda(df_ctx* c, int channel_mask) {
   const int a0 = (c->opts.eig_mode == 1) ? dm.m_max : 0;
   const int na = (c->opts.eig_mode == 1) ? 1 : dm.nb;
   const int qtiles = (dm.N + kEigQ - 1) / kEigQ;
-  const size_t smem = sizeof(double2) * 3 * dm.n_w * kEigQ;
+  const int g_in_smem = dm.n_w <= 96;
+  const size_t smem = sizeof(double2) * (3 * dm.n_w * kEigQ + (g_in_smem ? dm.n_w * dm.n_w : 0));
   cudaError_t e = cudaFuncSetAttribute((const void*)lambda_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
   for (int ch = 0; ch < 2; ++ch) {
     if (!(channel_mask & (1 << ch))) continue;
-    lambda_kernel<<<qtiles * na, kEigThreads, smem, c->stream>>>(dm, ch, 1, a0, na, 1e-12, c->gam, c->chi,
-                                                                 c->lam, c->lam_ok, flag_ptr(c));
+    lambda_kernel<<<qtiles * na, kEigThreads, smem, c->stream>>>(dm, ch, a0, na, g_in_smem, 1e-12, c->gam,
+                                                                 c->chi, c->lam, c->lam_ok, flag_ptr(c));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
