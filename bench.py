@@ -42,6 +42,9 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 CUDA-core peak of the GB300: 152 SMs x 2 FP64 FMA/clock/SM x 2 flop x 2.07 GHz
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
 FLUSH_BYTES = 256 << 20
+# DRAM bytes (read + write) per launch of the ladder kernel from one ncu capture
+# of that kernel on this workload (None once the kernel changes)
+NCU_TRAFFIC = {"bse_f64_kernel": 17729280}
 
 
 def dist_env():
@@ -295,7 +298,7 @@ def run_ours(args):
     achieved = systems_per_launch * flop_per_system / bse_avg_s / 1e9
     if prec == df.DF_FP64:
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                "frac": achieved / FP64_PEAK_GFLOPS, "traffic": None,
+                "frac": achieved / FP64_PEAK_GFLOPS, "traffic": NCU_TRAFFIC.get("bse_f64_kernel"),
                 "kernel": "bse_f64_kernel",
                 "peak_source": "FP64 CUDA cores: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TF/s; "
                                "1.20 TF/s measured by an FMA loop)",
