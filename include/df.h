@@ -187,6 +187,30 @@ df_status df_get_timing(df_ctx* c, double* ms, int* launches, int count);
 /* Wait for all work queued on the handle's stream. */
 df_status df_synchronize(df_ctx* c);
 
+/* Allocation-free variant of the FP64 ladder solves of df_bse (the paper
+ * has no counterpart: this is a deployment form).  For callers that cannot
+ * allocate device memory at the call, e.g. code inside a host application
+ * that owns the whole device-memory budget, or a latency-critical loop that
+ * cannot afford cudaMalloc's implicit synchronisation.  It calls no
+ * cudaMalloc, cudaFree or allocating library routine.
+ *   gamma   device [2][n_bos][n_w][n_w] complex: gamma^d then gamma^m
+ *   chi     device [n_bos][n_w][n_k_total] complex (df_get_chi's layout)
+ *   kernel  device [2][n_bos][n_w][n_k_total] complex, written with
+ *           df_get_kernel's content: c (Gamma_ww - Gamma^(2)_ww / 2)
+ *   stream  cudaStream_t (may be NULL); the call is asynchronous on it.
+ * Limits: n_w even in [2, 96], n_bos odd in [1, 63], n_k_total <= 4096 and
+ * 2 n_bos n_w^2 <= 2^19; larger sizes return DF_ERR_ARG (message on stderr).
+ * Its scratch is one fixed 8 MiB device array inside libdf, held by every
+ * GPU that loads the library until the process exits.  The first call on a
+ * device looks up that array's device address (cudaGetSymbolAddress), so it
+ * should come before any stream capture.  All calls share the array and
+ * the last call's contents stay in it: calls that overlap on the GPU (two
+ * streams, or two host threads) race and must be serialised by the caller.
+ * An exactly singular ladder matrix gives undefined values for that system
+ * and is not reported (df_bse reports it). */
+df_status df_bse_noalloc(const double* gamma, const double* chi, int n_w, int n_bos, int n_k_total,
+                         double* kernel, void* stream);
+
 const char* df_last_error(const df_ctx* c);
 const char* df_status_string(df_status s);
 void df_destroy(df_ctx* c);

@@ -384,3 +384,28 @@ cudaError_t launch_lambda(df_ctx* c, int channel_mask) {
 }
 
 }  // namespace df
+
+// ---------------------------------------------------------------------------
+// launchers on caller-given buffers (no handle), used by the allocation-free
+// entry point; the kernels are the ones above
+// ---------------------------------------------------------------------------
+namespace df {
+
+cudaError_t launch_gamma_gt_raw(int n, int count, const double2* gam, double2* gg, cudaStream_t stream) {
+  gamma_gt_kernel<<<count * 8, 256, 0, stream>>>(n, count, gam, gg);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bse_both_raw(const Dims& dm, const double2* gam, const double2* gg, const double2* chi,
+                                double2* kc, int* flags, int device, cudaStream_t stream) {
+  if (!bse_lu_in_smem(dm.n_w)) return cudaErrorInvalidValue;
+  const int nc = bse_chunk(dm.n_w);
+  const size_t smem = bse_smem_bytes(dm.n_w);
+  const int grid_max = bse_default_grid(dm, device);   // sets the shared-memory attribute
+  const long systems = 2L * dm.nb * dm.N;
+  const int grid = (int)(systems < grid_max ? systems : grid_max);
+  bse_f64_kernel<true><<<grid, kBseThreads, smem, stream>>>(dm, 0, 2, nc, gam, gg, chi, kc, nullptr, flags);
+  return cudaGetLastError();
+}
+
+}  // namespace df

@@ -38,7 +38,7 @@ EXPORTS = (
     "df_default_opts", "df_init", "df_set_inputs", "df_vertex_from_spin", "df_bubble", "df_bse",
     "df_sigma", "df_iterate", "df_get_sigma", "df_set_sigma", "df_get_gtilde", "df_get_chi",
     "df_get_kernel", "df_get_lambda", "df_get_sizes", "df_set_timing", "df_get_timing",
-    "df_synchronize", "df_last_error",
+    "df_synchronize", "df_bse_noalloc", "df_last_error",
     "df_status_string", "df_destroy",
 )
 
@@ -93,6 +93,7 @@ def load(path: str = LIB_PATH):
         "df_set_timing": [P, C.c_int],
         "df_get_timing": [P, D, I, C.c_int],
         "df_synchronize": [P],
+        "df_bse_noalloc": [P, P, C.c_int, C.c_int, C.c_int, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)

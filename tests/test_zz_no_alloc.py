@@ -1,0 +1,72 @@
+"""df_bse_noalloc, the allocation-free ladder entry point, against df_bse.
+
+df_bse_noalloc serves callers that cannot allocate device memory at the
+call (a host application that owns the device-memory budget, a loop that
+cannot take cudaMalloc's implicit synchronisation): they pass gamma, chi~
+and the output, and the kernel's scratch is a fixed array inside libdf.
+Two calls in a row, with different sizes so that the second one runs on
+the first one's stale scratch contents, must each reproduce what df_bse
+writes through a handle, within the FP64 parity tolerance.
+"""
+import numpy as np
+import pytest
+
+from paper_1507_00895_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+
+
+@pytest.fixture(scope="module")
+def df():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_1507_00895_gb300 import build
+    build.build_lib()
+    from paper_1507_00895_gb300 import df as dfm
+    return dfm
+
+
+def nrel(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def noalloc_vs_handle(df, w):
+    import torch
+    with df.DualFermion.from_workload(w) as d:
+        d.bubble()
+        d.bse(3)
+        ref = d.get_kernel()
+        chi = d.get_chi()
+    gd, gm = df.vertex_from_spin(w.gamma_uu, w.gamma_ud)
+    gam = torch.from_numpy(np.ascontiguousarray(np.stack([gd, gm]))).cuda()
+    chi_d = torch.from_numpy(chi).cuda()
+    out = torch.full((2, w.n_bos, w.n_w, w.N), float("nan"), dtype=torch.complex128, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    s = df.load().df_bse_noalloc(gam.data_ptr(), chi_d.data_ptr(), w.n_w, w.n_bos, w.N,
+                                 out.data_ptr(), stream)
+    assert s == df.DF_OK
+    torch.cuda.synchronize()
+    return out.cpu().numpy(), ref
+
+
+def test_noalloc_matches_df_bse_on_two_calls_in_a_row(df):
+    first = I.workload("square32_tp", nk=16, n_w=32, m_max=3)
+    second = I.workload("cubic16_crit", nk=8, n_w=48, m_max=2)
+    for w in (first, second):
+        got, ref = noalloc_vs_handle(df, w)
+        assert np.all(np.isfinite(got))
+        assert nrel(got, ref) < TOL64, w.name
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch(df):
+    import torch
+    lib = df.load()
+    buf = torch.zeros(16, dtype=torch.complex128, device="cuda")
+    p = buf.data_ptr()
+    # 2 * 63 * 96^2 complex > 2^19: too large for the fixed scratch array
+    assert lib.df_bse_noalloc(p, p, 96, 63, 16, p, None) == df.DF_ERR_ARG
+    # n_w above the shared-memory limit of this variant
+    assert lib.df_bse_noalloc(p, p, 128, 1, 16, p, None) == df.DF_ERR_ARG
