@@ -66,6 +66,7 @@ df_status upload_inputs(df_ctx* c, const double* g, const double* delta, const d
   DF_CUDA(c, cudaMemcpyAsync(c->gam, gd, sizeof(double2) * nv, k, c->stream), "copy gamma_d");
   DF_CUDA(c, cudaMemcpyAsync(c->gam + nv, gm, sizeof(double2) * nv, k, c->stream), "copy gamma_m");
   DF_CUDA(c, launch_gamma_gt(c), "gamma o gamma^T");
+  if (c->mixed_ws) DF_CUDA(c, launch_split_gamma(c), "gamma -> FP32 (hi, lo)");
   DF_CUDA(c, launch_init_g0(c), "bare dual propagator (Eq. gd0)");
   DF_CUDA(c, launch_dyson_ifft(c, 0, dm.ne), "Dyson + FFT to real space");
   return DF_OK;
@@ -194,6 +195,7 @@ void df_destroy(df_ctx* c) {
   cudaFree(c->lam_ok);
   cudaFree(c->red);
   cudaFree(c->bse_ws);
+  cudaFree(c->mixed_ws);
   if (c->h_red) cudaFreeHost(c->h_red);
   for (auto& m : c->marks) {
     cudaEventDestroy(m.a);
@@ -218,6 +220,10 @@ df_status df_init(df_ctx** out, const df_lattice* lat, double beta, double mu, d
   if (!(beta > 0.0) || !(opts->mix > 0.0 && opts->mix <= 1.0)) return DF_ERR_ARG;
   if (opts->precision != DF_FP64 && opts->precision != DF_FP32_IR) return DF_ERR_ARG;
   if (opts->eig_mode < 0 || opts->eig_mode > 2) return DF_ERR_ARG;
+  if (opts->precision == DF_FP32_IR && !mixed_supported(opts->n_w)) {
+    fprintf(stderr, "libdf: DF_FP32_IR supports n_w <= 64\n");
+    return DF_ERR_ARG;
+  }
 
   df_ctx* c = new (std::nothrow) df_ctx();
   if (!c) return DF_ERR_OOM;
@@ -276,6 +282,10 @@ df_status df_init(df_ctx** out, const df_lattice* lat, double beta, double mu, d
   {
     cudaError_t ea = cudaMalloc(&c->bse_ws, c->bse_ws_bytes);
     if (ea != cudaSuccess) { st = fail(c, DF_ERR_OOM, "cudaMalloc bse workspace", ea); goto bad; }
+    if (opts->precision == DF_FP32_IR) {
+      ea = cudaMalloc(&c->mixed_ws, mixed_workspace_bytes(dm));
+      if (ea != cudaSuccess) { st = fail(c, DF_ERR_OOM, "cudaMalloc mixed workspace", ea); goto bad; }
+    }
     ea = cudaMallocHost((void**)&c->h_red, 4 * sizeof(double));
     if (ea != cudaSuccess) { st = fail(c, DF_ERR_OOM, "cudaMallocHost", ea); goto bad; }
   }

@@ -347,6 +347,7 @@ cudaError_t launch_bse(df_ctx* c, int channel_mask) {
   const size_t smem = bse_smem_bytes(n);
   cudaError_t e = cudaMemsetAsync(flag_ptr(c), 0, sizeof(int) * 4, c->stream);
   if (e != cudaSuccess) return e;
+  if (c->opts.precision == DF_FP32_IR) return launch_bse_mixed(c, channel_mask, gg_ptr(c), flag_ptr(c));
   for (int ch = 0; ch < 2; ++ch) {
     if (!(channel_mask & (1 << ch))) continue;
     const long systems = (long)dm.nb * dm.N;

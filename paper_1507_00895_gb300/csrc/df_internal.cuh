@@ -174,6 +174,8 @@ struct df_ctx {
   double* red = nullptr;       // [2 n_w] residual partials, [2] final, [2] solve flags (ints)
   double* h_red = nullptr;     // pinned host mirror of the final residual
   void* bse_ws = nullptr;      // global scratch of the BSE kernel (large n)
+  void* mixed_ws = nullptr;    // DF_FP32_IR: gamma as FP32 (hi, lo) pairs
+  int mixed_grid = 0;
   size_t bse_ws_bytes = 0;
   int bse_grid = 0;
   int iter_done = 0;
@@ -201,4 +203,9 @@ cudaError_t launch_lambda(df_ctx* c, int channel_mask);
 size_t bse_workspace_bytes(const Dims& dm, int grid);
 int bse_default_grid(const Dims& dm, int device);
 int* bse_flags(df_ctx* c);   // [0]: bit 0 zero pivot, bit 1 |lambda| >= 1
+// mixed precision (df_mixed.cu)
+bool mixed_supported(int n_w);
+size_t mixed_workspace_bytes(const Dims& dm);
+cudaError_t launch_split_gamma(df_ctx* c);
+cudaError_t launch_bse_mixed(df_ctx* c, int channel_mask, const double2* gg, int* flags);
 }  // namespace df
