@@ -1,9 +1,11 @@
 """Mixed-precision ladder solves (DF_FP32_IR) against the CPU oracle.
 
-FP32 LU + one FP64-accurate residual correction.  Stated tolerance for the
-refined mixed path: the ladder kernel within 1e-8 of the oracle normwise per
-(channel, W) plane, Sigma~ within 1e-9 normwise (the FP64 path's own bound
-on these workloads is 1e-9/1e-10).
+FP32 LU + one correction with a double-float (~48-bit) residual.  Stated
+tolerance of the refined mixed path: Sigma~ within 1e-8 of the oracle
+normwise; the ladder kernel within 5e-8 normwise per (channel, W) plane.
+The residual's double-float accumulation keeps ~2^-48 relative to the
+partial sums of gamma chi~ X0, whose terms exceed the sum by |gamma chi~|
+(~3e4 on the 32^2 workload), against 2^-53 for an FP64 residual.
 """
 import numpy as np
 import pytest
@@ -13,8 +15,8 @@ from paper_1507_00895_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
-TOL_KERNEL = 1e-8
-TOL_SIGMA = 1e-9
+TOL_KERNEL = 5e-8
+TOL_SIGMA = 1e-8
 
 
 @pytest.fixture(scope="module")
@@ -78,7 +80,9 @@ def test_mixed_square32_tp_full_size(df):
         worst = max(nrel(kern[c, a], kref[c, a]) for c in range(2) for a in range(w.n_bos))
         assert worst < TOL_KERNEL, worst
         d.sigma()
-        assert nrel(d.get_sigma(), st.sigma) < TOL_SIGMA
+        err = nrel(d.get_sigma(), st.sigma)
+        print(f"square32_tp mixed: worst kernel plane {worst:.2e}, Sigma~ {err:.2e}")
+        assert err < TOL_SIGMA
 
 
 def test_mixed_matches_fp64_gpu_over_iterations(df):
