@@ -65,7 +65,7 @@ __device__ __forceinline__ void df_fma(float& hi, float& lo, float a, float b) {
 
 struct MixedSmem {
   // offsets in float2 units
-  int x0, chih, chil, ubuf, lbuf, invu, x0d, gt_h, gt_l, total;
+  int x0, chih, chil, ubuf, lbuf, invu, x0d, gt_h, gt_l, yh, yl, total;
 };
 
 __host__ __device__ inline MixedSmem mixed_layout(int np) {
@@ -80,6 +80,8 @@ __host__ __device__ inline MixedSmem mixed_layout(int np) {
   L.x0d = o;  o += np;             // diag X0 (FP32)
   L.gt_h = o; o += kResChunk * np; // gamma tile, [l][row], hi
   L.gt_l = o; o += kResChunk * np; // lo
+  L.yh = o;   o += np * np;        // Y = chi o X0, hi
+  L.yl = o;   o += np * np;        // lo
   L.total = o;
   return L;
 }
@@ -101,9 +103,6 @@ bse_mixed_kernel(Dims dm, int ch0, int nch, int np, const double2* __restrict__ 
                  const double2* __restrict__ gg, const double2* __restrict__ chi, double2* __restrict__ kc,
                  int* __restrict__ flags) {
   extern __shared__ float2 smf[];
-  __shared__ float cand_v[32];
-  __shared__ int cand_r[32];
-  __shared__ float2 cand_p[32];
   __shared__ int piv_s[128];
   const int n = dm.n_w, N = dm.N, nb = dm.nb;
   const int P = np / kTile;
@@ -117,6 +116,8 @@ bse_mixed_kernel(Dims dm, int ch0, int nch, int np, const double2* __restrict__ 
   float2* x0d = smf + L.x0d;
   float2* gth = smf + L.gt_h;
   float2* gtl = smf + L.gt_l;
+  float2* Yh = smf + L.yh;
+  float2* Yl = smf + L.yl;
   const int t = threadIdx.x;
   const int tr = t % P, tc = t / P;
   const long systems = (long)nch * nb * N;
@@ -155,84 +156,79 @@ bse_mixed_kernel(Dims dm, int ch0, int nch, int np, const double2* __restrict__ 
     }
 
     // ---- elimination with implicit partial pivoting; RHS forward-substituted ----
-    for (int k = 0; k < np; ++k) {
-      const int jk = k / P;
-      const bool own_col = (tc == k % P);
-      if (own_col) {
-        float best = -1.f;
-        int br = 0x7fffffff;
-        float2 bv = make_float2(0.f, 0.f);
+    // k = jk P + kk: jk (the register column of pivot column k) is a
+    // compile-time index after unrolling; the P owners of column k are the
+    // consecutive, P-aligned threads tc == kk and reduce the pivot by shuffles.
+    const unsigned gmask = (P >= 32) ? 0xffffffffu : (((1u << P) - 1u) << ((t & 31) & ~(P - 1)));
 #pragma unroll
-        for (int ii = 0; ii < kTile; ++ii) {
-          if (rowpos[ii] < 0) {
-            float2 v = A[ii][0];
+    for (int jk = 0; jk < kTile; ++jk) {
+      for (int kk = 0; kk < P; ++kk) {
+        const int k = jk * P + kk;
+        const bool own_col = (tc == kk);
+        if (own_col) {
+          float best = -1.f;
+          int br = 0x7fffffff;
+          float2 bv = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int jj = 1; jj < kTile; ++jj) if (jj == jk) v = A[ii][jj];
-            const float m = fabsf(v.x) + fabsf(v.y);
-            const int r = tr + P * ii;
-            if (m > best || (m == best && r < br)) { best = m; br = r; bv = v; }
-          }
-        }
-        cand_v[tr] = best;
-        cand_r[tr] = br;
-        cand_p[tr] = bv;
-      }
-      __syncthreads();
-      float best = -1.f;
-      int p = 0x7fffffff;
-      float2 pv = make_float2(0.f, 0.f);
-      for (int s = 0; s < P; ++s) {
-        const float m = cand_v[s];
-        const int r = cand_r[s];
-        if (m > best || (m == best && r < p)) { best = m; p = r; pv = cand_p[s]; }
-      }
-      const bool singular = (pv.x == 0.f && pv.y == 0.f);
-      const float2 inv = singular ? make_float2(0.f, 0.f) : cinvf(pv);
-      if (t == 0) {
-        piv_s[k] = p;
-        invu[k] = inv;
-        if (singular) atomicOr(flags, 1);
-      }
-      if (tr == p % P) {
-        const int ip = p / P;
-#pragma unroll
-        for (int ii = 0; ii < kTile; ++ii) {
-          if (ii == ip) {
-            rowpos[ii] = k;
-#pragma unroll
-            for (int jj = 0; jj < kTile; ++jj) {
-              const int col = tc + P * jj;
-              if (col > k) ubuf[col] = A[ii][jj];
-              ubuf[np + col] = A[ii][kTile + jj];
+          for (int ii = 0; ii < kTile; ++ii) {
+            if (rowpos[ii] < 0) {
+              const float2 v = A[ii][jk];
+              const float m = fabsf(v.x) + fabsf(v.y);
+              const int r = tr + P * ii;
+              if (m > best || (m == best && r < br)) { best = m; br = r; bv = v; }
             }
           }
+          for (int o = P >> 1; o > 0; o >>= 1) {
+            const float ob = __shfl_xor_sync(gmask, best, o);
+            const int orr = __shfl_xor_sync(gmask, br, o);
+            const float ox = __shfl_xor_sync(gmask, bv.x, o);
+            const float oy = __shfl_xor_sync(gmask, bv.y, o);
+            if (ob > best || (ob == best && orr < br)) { best = ob; br = orr; bv = make_float2(ox, oy); }
+          }
+          if (tr == 0) {
+            const bool singular = (bv.x == 0.f && bv.y == 0.f);
+            piv_s[k] = br;
+            invu[k] = singular ? make_float2(0.f, 0.f) : cinvf(bv);
+            if (singular) atomicOr(flags, 1);
+          }
         }
-      }
-      if (own_col) {
+        __syncthreads();
+        const int p = piv_s[k];
+        const float2 inv = invu[k];
+        if (tr == p % P) {
+          const int ip = p / P;
 #pragma unroll
-        for (int ii = 0; ii < kTile; ++ii) {
-          if (rowpos[ii] < 0) {
+          for (int ii = 0; ii < kTile; ++ii) {
+            if (ii == ip) {
+              rowpos[ii] = k;
 #pragma unroll
-            for (int jj = 0; jj < kTile; ++jj) {
-              if (jj == jk) {
-                const float2 l = cmulf(A[ii][jj], inv);
-                A[ii][jj] = l;
-                lbuf[tr + P * ii] = l;
+              for (int jj = 0; jj < kTile; ++jj) {
+                if (jj > jk || (jj == jk && tc > kk)) ubuf[tc + P * jj] = A[ii][jj];
+                ubuf[np + tc + P * jj] = A[ii][kTile + jj];
               }
             }
           }
         }
-      }
-      __syncthreads();
+        if (own_col) {
 #pragma unroll
-      for (int ii = 0; ii < kTile; ++ii) {
-        if (rowpos[ii] < 0) {
-          const float2 l = lbuf[tr + P * ii];
+          for (int ii = 0; ii < kTile; ++ii) {
+            if (rowpos[ii] < 0) {
+              const float2 l = cmulf(A[ii][jk], inv);
+              A[ii][jk] = l;
+              lbuf[tr + P * ii] = l;
+            }
+          }
+        }
+        __syncthreads();
 #pragma unroll
-          for (int jj = 0; jj < kTile; ++jj) {
-            const int col = tc + P * jj;
-            if (col > k) A[ii][jj] = cfmsf(l, ubuf[col], A[ii][jj]);
-            A[ii][kTile + jj] = cfmsf(l, ubuf[np + col], A[ii][kTile + jj]);
+        for (int ii = 0; ii < kTile; ++ii) {
+          if (rowpos[ii] < 0) {
+            const float2 l = lbuf[tr + P * ii];
+#pragma unroll
+            for (int jj = 0; jj < kTile; ++jj) {
+              if (jj > jk || (jj == jk && tc > kk)) A[ii][jj] = cfmsf(l, ubuf[tc + P * jj], A[ii][jj]);
+              A[ii][kTile + jj] = cfmsf(l, ubuf[np + tc + P * jj], A[ii][kTile + jj]);
+            }
           }
         }
       }
@@ -241,42 +237,57 @@ bse_mixed_kernel(Dims dm, int ch0, int nch, int np, const double2* __restrict__ 
     __syncthreads();   // the last elimination update still reads lbuf / ubuf
 
     // ---- back substitution: X0 row k (logical) from physical row piv[k] ----
-    for (int k = np - 1; k >= 0; --k) {
-      const int p = piv_s[k];
-      float2* ucol = lbuf + (k & 1) * np;
-      if (tc == k % P) {
-        const int jk = k / P;
 #pragma unroll
-        for (int ii = 0; ii < kTile; ++ii) {
+    for (int jk = kTile - 1; jk >= 0; --jk) {
+      for (int kk = P - 1; kk >= 0; --kk) {
+        const int k = jk * P + kk;
+        const int p = piv_s[k];
+        float2* ucol = lbuf + (k & 1) * np;
+        if (tc == kk) {
 #pragma unroll
-          for (int jj = 0; jj < kTile; ++jj)
-            if (jj == jk) ucol[tr + P * ii] = A[ii][jj];
+          for (int ii = 0; ii < kTile; ++ii) ucol[tr + P * ii] = A[ii][jk];
         }
-      }
-      if (tr == p % P) {
-        const int ip = p / P;
-        const float2 inv = invu[k];
+        if (tr == p % P) {
+          const int ip = p / P;
+          const float2 inv = invu[k];
+#pragma unroll
+          for (int ii = 0; ii < kTile; ++ii)
+            if (ii == ip)
+#pragma unroll
+              for (int jj = 0; jj < kTile; ++jj) X0s[k * np + tc + P * jj] = cmulf(A[ii][kTile + jj], inv);
+        }
+        __syncthreads();
 #pragma unroll
         for (int ii = 0; ii < kTile; ++ii) {
-          if (ii == ip) {
+          if (rowpos[ii] < k) {
+            const float2 u = ucol[tr + P * ii];
 #pragma unroll
-            for (int jj = 0; jj < kTile; ++jj) X0s[k * np + tc + P * jj] = cmulf(A[ii][kTile + jj], inv);
+            for (int jj = 0; jj < kTile; ++jj)
+              A[ii][kTile + jj] = cfmsf(u, X0s[k * np + tc + P * jj], A[ii][kTile + jj]);
           }
-        }
-      }
-      __syncthreads();
-#pragma unroll
-      for (int ii = 0; ii < kTile; ++ii) {
-        if (rowpos[ii] < k) {
-          const float2 u = ucol[tr + P * ii];
-#pragma unroll
-          for (int jj = 0; jj < kTile; ++jj)
-            A[ii][kTile + jj] = cfmsf(u, X0s[k * np + tc + P * jj], A[ii][kTile + jj]);
         }
       }
     }
     __syncthreads();
     for (int j = t; j < np; j += blockDim.x) x0d[j] = X0s[j * np + j];
+    // Y = chi o X0 as double-float pairs, once per system
+    for (int idx = t; idx < np * np; idx += blockDim.x) {
+      const int l = idx / np;
+      const float2 xh = chih[l], xl = chil[l];
+      const float2 x = X0s[idx];
+      float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+      df_fma(rh, rl, xh.x, x.x);
+      df_fma(rh, rl, -xh.y, x.y);
+      df_fma(ih, il, xh.x, x.y);
+      df_fma(ih, il, xh.y, x.x);
+      rl = fmaf(xl.x, x.x, fmaf(-xl.y, x.y, rl));
+      il = fmaf(xl.x, x.y, fmaf(xl.y, x.x, il));
+      float sv, ev;
+      two_sum(rh, rl, sv, ev); rh = sv; rl = ev;
+      two_sum(ih, il, sv, ev); ih = sv; il = ev;
+      Yh[idx] = make_float2(rh, ih);
+      Yl[idx] = make_float2(rl, il);
+    }
 
     // ---- residual R = gamma - X0 + gamma (chi o X0), ~48-bit accurate ----
     // two passes of 2 rows each keep the double-float accumulators in registers
@@ -301,25 +312,11 @@ bse_mixed_kernel(Dims dm, int ch0, int nch, int np, const double2* __restrict__ 
         __syncthreads();
         for (int ll = 0; ll < kResChunk; ++ll) {
           const int l = l0 + ll;
-          const float2 xh = chih[l], xl = chil[l];
-          // Y[l][col] = chi_l X0[l][col] as (hi, lo): exact products of the FP32 parts
           float2 yh[kTile], yl[kTile];
 #pragma unroll
           for (int jj = 0; jj < kTile; ++jj) {
-            const float2 x = X0s[l * np + tc + P * jj];
-            float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
-            df_fma(rh, rl, xh.x, x.x);
-            df_fma(rh, rl, -xh.y, x.y);
-            df_fma(ih, il, xh.x, x.y);
-            df_fma(ih, il, xh.y, x.x);
-            rl = fmaf(xl.x, x.x, fmaf(-xl.y, x.y, rl));
-            il = fmaf(xl.x, x.y, fmaf(xl.y, x.x, il));
-            // renormalise
-            float s, e;
-            two_sum(rh, rl, s, e); rh = s; rl = e;
-            two_sum(ih, il, s, e); ih = s; il = e;
-            yh[jj] = make_float2(rh, ih);
-            yl[jj] = make_float2(rl, il);
+            yh[jj] = Yh[l * np + tc + P * jj];
+            yl[jj] = Yl[l * np + tc + P * jj];
           }
 #pragma unroll
           for (int i2 = 0; i2 < 2; ++i2) {
@@ -361,67 +358,67 @@ bse_mixed_kernel(Dims dm, int ch0, int nch, int np, const double2* __restrict__ 
     __syncthreads();
 
     // ---- correction E = D^-1 R: forward substitution over the pivot order ----
-    for (int k = 0; k < np; ++k) {
-      const int p = piv_s[k];
-      float2* yrow = ubuf + (k & 1) * np;
-      float2* lcol = lbuf + (k & 1) * np;
-      if (tr == p % P) {
-        const int ip = p / P;
 #pragma unroll
-        for (int ii = 0; ii < kTile; ++ii)
-          if (ii == ip)
+    for (int jk = 0; jk < kTile; ++jk) {
+      for (int kk = 0; kk < P; ++kk) {
+        const int k = jk * P + kk;
+        const int p = piv_s[k];
+        float2* yrow = ubuf + (k & 1) * np;
+        float2* lcol = lbuf + (k & 1) * np;
+        if (tr == p % P) {
+          const int ip = p / P;
 #pragma unroll
-            for (int jj = 0; jj < kTile; ++jj) yrow[tc + P * jj] = A[ii][kTile + jj];
-      }
-      if (tc == k % P) {
-        const int jk = k / P;
+          for (int ii = 0; ii < kTile; ++ii)
+            if (ii == ip)
 #pragma unroll
-        for (int ii = 0; ii < kTile; ++ii)
+              for (int jj = 0; jj < kTile; ++jj) yrow[tc + P * jj] = A[ii][kTile + jj];
+        }
+        if (tc == kk) {
 #pragma unroll
-          for (int jj = 0; jj < kTile; ++jj)
-            if (jj == jk) lcol[tr + P * ii] = A[ii][jj];
-      }
-      __syncthreads();
+          for (int ii = 0; ii < kTile; ++ii) lcol[tr + P * ii] = A[ii][jk];
+        }
+        __syncthreads();
 #pragma unroll
-      for (int ii = 0; ii < kTile; ++ii) {
-        if (rowpos[ii] > k) {
-          const float2 l = lcol[tr + P * ii];
+        for (int ii = 0; ii < kTile; ++ii) {
+          if (rowpos[ii] > k) {
+            const float2 l = lcol[tr + P * ii];
 #pragma unroll
-          for (int jj = 0; jj < kTile; ++jj)
-            A[ii][kTile + jj] = cfmsf(l, yrow[tc + P * jj], A[ii][kTile + jj]);
+            for (int jj = 0; jj < kTile; ++jj)
+              A[ii][kTile + jj] = cfmsf(l, yrow[tc + P * jj], A[ii][kTile + jj]);
+          }
         }
       }
     }
     __syncthreads();
     // back substitution (X0s reused as the row broadcast)
-    for (int k = np - 1; k >= 0; --k) {
-      const int p = piv_s[k];
-      float2* ucol = lbuf + (k & 1) * np;
-      if (tc == k % P) {
-        const int jk = k / P;
 #pragma unroll
-        for (int ii = 0; ii < kTile; ++ii)
+    for (int jk = kTile - 1; jk >= 0; --jk) {
+      for (int kk = P - 1; kk >= 0; --kk) {
+        const int k = jk * P + kk;
+        const int p = piv_s[k];
+        float2* ucol = lbuf + (k & 1) * np;
+        if (tc == kk) {
 #pragma unroll
-          for (int jj = 0; jj < kTile; ++jj)
-            if (jj == jk) ucol[tr + P * ii] = A[ii][jj];
-      }
-      if (tr == p % P) {
-        const int ip = p / P;
-        const float2 inv = invu[k];
+          for (int ii = 0; ii < kTile; ++ii) ucol[tr + P * ii] = A[ii][jk];
+        }
+        if (tr == p % P) {
+          const int ip = p / P;
+          const float2 inv = invu[k];
 #pragma unroll
-        for (int ii = 0; ii < kTile; ++ii)
-          if (ii == ip)
+          for (int ii = 0; ii < kTile; ++ii)
+            if (ii == ip)
 #pragma unroll
-            for (int jj = 0; jj < kTile; ++jj) X0s[k * np + tc + P * jj] = cmulf(A[ii][kTile + jj], inv);
-      }
-      __syncthreads();
+              for (int jj = 0; jj < kTile; ++jj) X0s[k * np + tc + P * jj] = cmulf(A[ii][kTile + jj], inv);
+        }
+        __syncthreads();
 #pragma unroll
-      for (int ii = 0; ii < kTile; ++ii) {
-        if (rowpos[ii] < k) {
-          const float2 u = ucol[tr + P * ii];
+        for (int ii = 0; ii < kTile; ++ii) {
+          if (rowpos[ii] < k) {
+            const float2 u = ucol[tr + P * ii];
 #pragma unroll
-          for (int jj = 0; jj < kTile; ++jj)
-            A[ii][kTile + jj] = cfmsf(u, X0s[k * np + tc + P * jj], A[ii][kTile + jj]);
+            for (int jj = 0; jj < kTile; ++jj)
+              A[ii][kTile + jj] = cfmsf(u, X0s[k * np + tc + P * jj], A[ii][kTile + jj]);
+          }
         }
       }
     }
@@ -429,16 +426,32 @@ bse_mixed_kernel(Dims dm, int ch0, int nch, int np, const double2* __restrict__ 
 
     // ---- diag Gamma = diag X0 + diag E (FP64), Gamma^(2), Eq. sd bracket ----
     const double2* GG = gg + mat;
-    for (int j = t; j < n; j += blockDim.x) {
-      const float2 x0 = x0d[j], e = X0s[j * np + j];
-      const double2 gdiag = mk((double)x0.x + (double)e.x, (double)x0.y + (double)e.y);
+    // four threads per output frequency j (consecutive lanes, shuffle-reduced)
+    // when the block has whole warps; one thread per j otherwise
+    const int per_j = (blockDim.x >= 32) ? 4 : 1;
+    for (int base = 0; base < per_j * np; base += blockDim.x) {
+      const int idx = base + t;
+      const int j = idx / per_j, part = idx % per_j;
       double2 g2 = mk(0.0, 0.0);
-      for (int x = 0; x < n; ++x) {
-        const double2 cx = mk((double)chih[x].x + (double)chil[x].x, (double)chih[x].y + (double)chil[x].y);
-        g2 = cfma(GG[(size_t)j * n + x], cx, g2);
+      if (j < n) {
+        for (int x = part; x < n; x += per_j) {
+          const double2 cx = mk((double)chih[x].x + (double)chil[x].x, (double)chih[x].y + (double)chil[x].y);
+          g2 = cfma(GG[(size_t)j * n + x], cx, g2);
+        }
       }
-      const double wgt = (c == 0) ? 1.0 : 3.0;
-      kc[(((size_t)c * nb + a) * n + j) * N + q] = mk(wgt * (gdiag.x - 0.5 * g2.x), wgt * (gdiag.y - 0.5 * g2.y));
+      if (per_j == 4) {
+        g2.x += __shfl_xor_sync(0xffffffffu, g2.x, 1);
+        g2.y += __shfl_xor_sync(0xffffffffu, g2.y, 1);
+        g2.x += __shfl_xor_sync(0xffffffffu, g2.x, 2);
+        g2.y += __shfl_xor_sync(0xffffffffu, g2.y, 2);
+      }
+      if (j < n && part == 0) {
+        const float2 x0 = x0d[j], e = X0s[j * np + j];
+        const double2 gdiag = mk((double)x0.x + (double)e.x, (double)x0.y + (double)e.y);
+        const double wgt = (c == 0) ? 1.0 : 3.0;
+        kc[(((size_t)c * nb + a) * n + j) * N + q] =
+            mk(wgt * (gdiag.x - 0.5 * g2.x), wgt * (gdiag.y - 0.5 * g2.y));
+      }
     }
     __syncthreads();
   }
@@ -448,7 +461,12 @@ bse_mixed_kernel(Dims dm, int ch0, int nch, int np, const double2* __restrict__ 
 // host side
 // ---------------------------------------------------------------------------
 
-static int mixed_np(int n) { return ((n + kTile - 1) / kTile) * kTile; }
+// n padded so that P = n_pad / 4 is a power of two (shuffle groups of P lanes)
+static int mixed_np(int n) {
+  int np = kTile;
+  while (np < n) np *= 2;
+  return np;
+}
 
 // the register-resident [D | RHS] tile limits this kernel to n_w <= 64
 bool mixed_supported(int n_w) { return mixed_np(n_w) <= 64; }
