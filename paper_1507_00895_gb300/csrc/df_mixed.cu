@@ -290,6 +290,7 @@ bse_mixed_kernel(Dims dm, int ch0, int nch, int np, const double2* __restrict__ 
     }
 
     // ---- residual R = gamma - X0 + gamma (chi o X0), ~48-bit accurate ----
+    const int lc = np < kResChunk ? np : kResChunk;   // gamma columns per staged tile (divides np)
     // two passes of 2 rows each keep the double-float accumulators in registers
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
@@ -300,17 +301,17 @@ bse_mixed_kernel(Dims dm, int ch0, int nch, int np, const double2* __restrict__ 
         for (int jj = 0; jj < kTile; ++jj)
 #pragma unroll
           for (int e = 0; e < 4; ++e) acc[i2][jj][e] = 0.f;
-      for (int l0 = 0; l0 < np; l0 += kResChunk) {
+      for (int l0 = 0; l0 < np; l0 += lc) {
         __syncthreads();
-        for (int idx = t; idx < kResChunk * np; idx += blockDim.x) {
-          const int r = idx / kResChunk, ll = idx - r * kResChunk;
+        for (int idx = t; idx < lc * np; idx += blockDim.x) {
+          const int r = idx / lc, ll = idx - r * lc;
           const int l = l0 + ll;
           const bool in = (r < n && l < n);
           gth[ll * np + r] = in ? Gh[r * n + l] : make_float2(0.f, 0.f);
           gtl[ll * np + r] = in ? Gl[r * n + l] : make_float2(0.f, 0.f);
         }
         __syncthreads();
-        for (int ll = 0; ll < kResChunk; ++ll) {
+        for (int ll = 0; ll < lc; ++ll) {
           const int l = l0 + ll;
           float2 yh[kTile], yl[kTile];
 #pragma unroll
