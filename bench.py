@@ -41,6 +41,8 @@ WORKLOAD_DESC = ("2D 32x32 square lattice, t=1, t'=-0.2, U=4, beta=10, mu(atom n
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # FP64 CUDA-core peak of the GB300: 152 SMs x 2 FP64 FMA/clock/SM x 2 flop x 2.07 GHz
 FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
+# FP32 CUDA-core peak: 152 SMs x 128 FP32 FMA/clock/SM x 2 flop x 2.07 GHz
+FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07
 FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) per launch of the ladder kernel from one ncu capture
 # of that kernel on this workload (None once the kernel changes)
@@ -214,6 +216,54 @@ def run_reference(args):
 # the GPU arm
 # ---------------------------------------------------------------------------
 
+def time_to_converged(df, I, torch, max_passes=60):
+    """Time to a Sigma~ within 1e-8 of the converged FP64 Sigma~*, per path.
+
+    Workload: the paper's Example I inputs (Hubbard atom, U=20, beta=1,
+    mu=U/2, Delta=4g) on the benchmark's shape (2D 32x32, n_w=64, N_W=15),
+    whose loop converges.  Sigma~* = FP64 loop iterated to r <= 1e-13.  Each
+    path then runs from Sigma~=0, one pass at a time, device-timed with CUDA
+    events; the distance to Sigma~* is checked between passes, outside the
+    timed region."""
+    import numpy as np
+    w = I.workload("paper_u20", nk=32, n_w=64, m_max=7)
+    stream = torch.cuda.current_stream()
+    with df.DualFermion.from_workload(w, eig_mode=1, stream=stream.cuda_stream) as d:
+        it, r, _ = d.iterate(max_passes, tol=1e-13)
+        ref = d.get_sigma()
+    if not r <= 1e-13:
+        return {"workload": "paper Example I inputs, 2D 32x32, n_w=64, N_W=15",
+                "error": f"FP64 reference did not converge (r={r:.2e} after {it} passes)"}
+    out = {"workload": "paper Example I inputs (U=20, beta=1, mu=U/2, Delta=4g), 2D 32x32, n_w=64, N_W=15",
+           "target": "max|Sigma~ - Sigma~*| <= 1e-8 max|Sigma~*|, Sigma~* = FP64 loop at r <= 1e-13",
+           "reference_passes": it}
+    den = float(np.max(np.abs(ref)))
+    for name, prec in (("fp64", df.DF_FP64), ("fp32ir", df.DF_FP32_IR)):
+        with df.DualFermion.from_workload(w, precision=prec, eig_mode=1, stream=stream.cuda_stream) as d:
+            d.iterate(1)                       # warm-up pass (kernels loaded, attributes set)
+            d.set_sigma(np.zeros((w.n_w, w.N), np.complex128))
+            total = 0.0
+            err = None
+            passes = 0
+            for passes in range(1, max_passes + 1):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                d.bubble()
+                d.bse(3)
+                d.sigma(want_residual=False)
+                e1.record(stream)
+                e1.synchronize()
+                total += e0.elapsed_time(e1)
+                err = float(np.max(np.abs(d.get_sigma() - ref)) / den)
+                if err <= 1e-8:
+                    break
+        out[name] = {"passes": passes, "ms": total, "err_vs_fp64_converged": err}
+    if "fp64" in out and "fp32ir" in out:
+        out["speedup_mixed_vs_plain"] = out["fp64"]["ms"] / out["fp32ir"]["ms"]
+    return out
+
+
 def read_peaks():
     try:
         with open(PEAKS_PATH) as f:
@@ -241,72 +291,101 @@ def run_ours(args):
     # replicas: rank r runs its own parameter point (seed 2 + r)
     w = I.workload(WORKLOAD, seed=2 + rank)
     points = w.n_bos * w.N
-    prec = df.DF_FP64 if args.precision == "fp64" else df.DF_FP32_IR
     stream = torch.cuda.current_stream()
-    d = df.DualFermion.from_workload(w, precision=prec, eig_mode=1, stream=stream.cuda_stream)
     zeros = torch.zeros((w.n_w, w.N), dtype=torch.complex128, device="cuda")
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    n = w.n_w
+    systems_per_launch = w.n_bos * w.N               # one channel per launch
+
+    def measure(prec):
+        d = df.DualFermion.from_workload(w, precision=prec, eig_mode=1, stream=stream.cuda_stream)
+
+        def step():
+            d.bubble()
+            d.bse(3)
+            d.sigma(want_residual=False)
+
+        for _ in range(args.warmup):
+            d.set_sigma(zeros)
+            step()
+        torch.cuda.synchronize()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        clocks = ClockSampler(gpu_index_for_smi(local)) if rank == 0 else None
+        if clocks:
+            clocks.start()
+            time.sleep(0.3)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        d.set_timing(True)
+        for i in range(args.steps):
+            flush.zero_()
+            d.set_sigma(zeros)
+            starts[i].record(stream)
+            step()
+            ends[i].record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        clk = clocks.stop() if clocks else None
+        timing = d.get_timing()
+        d.set_timing(False)
+        step_ms = [s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)]
+        ms = sum(step_ms) / len(step_ms)
+        if world > 1:
+            t = torch.tensor([ms], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            ms = float(t.item())
+        bse_ms, bse_launches = timing["bse"]
+        bse_avg_s = bse_ms / max(1, bse_launches) * 1e-3
+        if prec == df.DF_FP64:
+            flop = 8.0 * n ** 3       # LU n^3/3 + forward n^3/2 + truncated back n^3/6 complex MACs
+            achieved = systems_per_launch * flop / bse_avg_s / 1e9
+            roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
+                    "frac": achieved / FP64_PEAK_GFLOPS, "traffic": NCU_TRAFFIC.get("bse_f64_kernel"),
+                    "kernel": "bse_f64_kernel",
+                    "peak_source": "FP64 CUDA cores: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TF/s; "
+                                   "1.20 TF/s measured by an FMA loop)",
+                    "flop_per_launch": systems_per_launch * flop, "launch_ms": bse_avg_s * 1e3}
+        else:
+            # FP32: LU n^3/3 + forward n^3/2 + back n^3/2 + correction forward and back n^3
+            # complex MACs; plus the n^3 complex MACs of the double-float residual
+            flop = 8.0 * (7.0 / 3.0) * n ** 3 + 8.0 * n ** 3
+            achieved = systems_per_launch * flop / bse_avg_s / 1e9
+            roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_GFLOPS, "unit": "GFLOP/s",
+                    "frac": achieved / FP32_PEAK_GFLOPS, "traffic": NCU_TRAFFIC.get("bse_mixed_kernel"),
+                    "kernel": "bse_mixed_kernel",
+                    "peak_source": "FP32 CUDA cores: 152 SM x 128 FMA/clk x 2 flop x 2.07 GHz "
+                                   "(75.2 TF/s measured by an FMA loop); the residual's double-float flops "
+                                   "count once each here but cost ~11 FP32 instructions",
+                    "flop_per_launch": systems_per_launch * flop, "launch_ms": bse_avg_s * 1e3}
+        res = {"value": world * points / (ms * 1e-3), "ms_per_step": ms, "roofline": roof,
+               "gpu_launches": sum(v[1] for v in timing.values()),
+               "kernel_ms_per_step": {k: v[0] / args.steps for k, v in timing.items()},
+               "clocks": clk}
+        return d, res
+
+    plain_d, plain = measure(df.DF_FP64)
+    plain_sigma = None
+    if df.mixed_supported(w.n_w):
+        plain_d.set_sigma(zeros)
+        plain_d.bubble(); plain_d.bse(3); plain_d.sigma(want_residual=False)
+        plain_sigma = plain_d.get_sigma()
+        plain_d.close()
+        d, main = measure(df.DF_FP32_IR)
+        d.set_sigma(zeros)
+        d.bubble(); d.bse(3); d.sigma(want_residual=False)
+        sig = d.get_sigma()
+        main["err_vs_fp64_first_pass"] = float(np.max(np.abs(sig - plain_sigma)) / np.max(np.abs(plain_sigma)))
+        prec = df.DF_FP32_IR
+    else:
+        d, main, prec = plain_d, plain, df.DF_FP64
 
     def step():
         d.bubble()
         d.bse(3)
         d.sigma(want_residual=False)
-
-    for _ in range(args.warmup):
-        d.set_sigma(zeros)
-        step()
-    torch.cuda.synchronize()
-
-    # ---- device-timed region ----
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    clocks = ClockSampler(gpu_index_for_smi(local)) if rank == 0 else None
-    if clocks:
-        clocks.start()
-        time.sleep(0.3)
-    if world > 1:
-        torch.distributed.barrier()
-    torch.cuda.synchronize()
-    d.set_timing(True)
-    for i in range(args.steps):
-        flush.zero_()
-        d.set_sigma(zeros)
-        starts[i].record(stream)
-        step()
-        ends[i].record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
-    clk = clocks.stop() if clocks else None
-    timing = d.get_timing()
-    d.set_timing(False)
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    ms = sum(step_ms) / len(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * points / (ms * 1e-3)
-    launches = sum(v[1] for v in timing.values())
-
-    # ---- dominant kernel: the ladder solves ----
-    bse_ms, bse_launches = timing["bse"]
-    bse_avg_s = bse_ms / max(1, bse_launches) * 1e-3
-    n = w.n_w
-    systems_per_launch = w.n_bos * w.N               # one channel per launch
-    flop_per_system = 8.0 * n ** 3                   # LU n^3/3 + forward n^3/2 + back n^3/6 complex MACs
-    achieved = systems_per_launch * flop_per_system / bse_avg_s / 1e9
-    if prec == df.DF_FP64:
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                "frac": achieved / FP64_PEAK_GFLOPS, "traffic": NCU_TRAFFIC.get("bse_f64_kernel"),
-                "kernel": "bse_f64_kernel",
-                "peak_source": "FP64 CUDA cores: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TF/s; "
-                               "1.20 TF/s measured by an FMA loop)",
-                "flop_per_launch": systems_per_launch * flop_per_system,
-                "launch_ms": bse_avg_s * 1e3}
-    else:
-        roof = {"bound": "alu", "achieved": achieved, "peak": None, "unit": "GFLOP/s", "frac": None,
-                "traffic": None, "kernel": "bse_mixed"}
 
     # ---- end to end through the public API with host buffers ----
     e2e = None
@@ -341,6 +420,9 @@ def run_ours(args):
         e2e = {"value": world * points / e2e_s, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
                "ms_per_step": e2e_s * 1e3}
     d.close()
+    ttc = None
+    if rank == 0 and not args.no_ttc:
+        ttc = time_to_converged(df, I, torch)
 
     if rank != 0:
         if world > 1:
@@ -349,18 +431,21 @@ def run_ours(args):
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(I.workload(WORKLOAD))
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if prec == df.DF_FP64 else "f32+f64-refinement",
-            "data": "synthetic",
+    line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if prec == df.DF_FP64 else "f32+f64-refinement", "data": "synthetic",
             "config": {"workload": WORKLOAD_DESC, "points_per_step": points,
                        "ladders_per_step": 2 * points, "ladder_order": n,
-                       "precision": args.precision, "eigen_check": "W=0, both channels",
-                       "step_start": "Sigma~=0", "l2": "flushed between steps (256 MiB write)",
-                       "parallelism": f"replicas{world}"},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "kernel_ms_per_step": {k: v[0] / args.steps for k, v in timing.items()},
-            "clocks": clk}
+                       "precision": "fp64" if prec == df.DF_FP64 else
+                                    "FP32 LU + one double-float-residual correction (DF_FP32_IR)",
+                       "eigen_check": "W=0, both channels, FP64", "step_start": "Sigma~=0",
+                       "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas{world}"},
+            "roofline": main["roofline"], "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": main["gpu_launches"], "kernel_ms_per_step": main["kernel_ms_per_step"],
+            "err_vs_fp64_first_pass": main.get("err_vs_fp64_first_pass"),
+            "plain_fp64": plain if prec != df.DF_FP64 else None,
+            "time_to_converged": ttc, "clocks": main["clocks"]}
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -376,6 +461,7 @@ def main():
     ap.add_argument("--precision", choices=["fp64", "fp32ir"], default="fp64")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ttc", action="store_true", help="skip the time-to-converged comparison")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)       # at least 3 untimed warm-up steps
     if args.impl == "reference":

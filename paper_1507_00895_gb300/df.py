@@ -285,6 +285,11 @@ class DualFermion:
         self._check(self.lib.df_set_inputs(self.h, *[p for p, _ in ptrs], dev.pop()))
 
 
+def mixed_supported(n_w: int) -> bool:
+    """DF_FP32_IR keeps [D | RHS] in registers: ladder order n_w <= 64."""
+    return 2 <= n_w <= 64
+
+
 def vertex_from_spin(gamma_uu, gamma_ud):
     """Eq. spin_symm through libdf's host helper: (d, m) = (uu + ud, uu - ud)."""
     lib = load()
