@@ -15,31 +15,9 @@
 // row j: LU (n^3/3) + forward (n^3/2) + truncated back substitution (n^3/6)
 // = n^3 complex multiply-adds per system instead of 4n^3/3.  U's columns are
 // pre-scaled by 1/U_kk so that neither substitution divides.
-#include "df_internal.cuh"
+#include "df_bse_dev.cuh"
 
 namespace df {
-
-constexpr int kBseThreads = 256;
-
-struct BseSmem {
-  // offsets in double2 units inside the dynamic shared block
-  int lu, y, xs, invu, total;
-};
-
-__host__ __device__ inline BseSmem bse_layout(int n, int nc, bool lu_in_smem) {
-  BseSmem L;
-  int off = 0;
-  L.lu = off;
-  if (lu_in_smem) off += n * n;
-  L.y = off;
-  off += n * nc;
-  L.xs = off;
-  off += n;
-  L.invu = off;
-  off += n;
-  L.total = off;
-  return L;
-}
 
 // gg[c][a][i][j] = gamma[c][a][i][j] * gamma[c][a][j][i]  (for Gamma^(2))
 __global__ void gamma_gt_kernel(int n, int count, const double2* __restrict__ gam, double2* __restrict__ gg) {
@@ -59,140 +37,16 @@ bse_f64_kernel(Dims dm, int ch0, int nch, int nc, const double2* __restrict__ ga
                const double2* __restrict__ gg, const double2* __restrict__ chi,
                double2* __restrict__ kc, double2* __restrict__ ws, int* __restrict__ flags) {
   extern __shared__ double2 sm[];
-  __shared__ int perm[128];
-  __shared__ int piv_sm;
-  __shared__ double2 pv_sm, oldkk_sm;
+  __shared__ BseF64Shared sh;
   const int n = dm.n_w, N = dm.N, nb = dm.nb;
   const BseSmem L = bse_layout(n, nc, LU_SMEM);
   double2* LU = LU_SMEM ? sm + L.lu : ws + (size_t)blockIdx.x * n * n;
-  double2* Y = sm + L.y;
-  double2* xs = sm + L.xs;
-  double2* invu = sm + L.invu;
-  const int tid = threadIdx.x;
-  const int warp = tid >> 5, lane = tid & 31;
   const long systems = (long)nch * nb * N;
-
   for (long sys = blockIdx.x; sys < systems; sys += gridDim.x) {
     const int c = ch0 + (int)(sys / ((long)nb * N));
     const int rem = (int)(sys - (long)(c - ch0) * nb * N);
     const int a = rem / N, q = rem - a * N;
-    const double2* G = gam + ((size_t)c * nb + a) * n * n;
-    const double2* GG = gg + ((size_t)c * nb + a) * n * n;
-
-    for (int i = tid; i < n; i += blockDim.x) {
-      xs[i] = chi[((size_t)a * n + i) * N + q];
-      perm[i] = i;
-    }
-    __syncthreads();
-    for (int idx = tid; idx < n * n; idx += blockDim.x) {
-      const int i = idx / n, j = idx - i * n;
-      double2 v = cmul(G[idx], xs[j]);
-      v = mk((i == j ? 1.0 : 0.0) - v.x, -v.y);
-      LU[idx] = v;
-    }
-    __syncthreads();
-
-    // ---- LU with partial pivoting ----
-    for (int k = 0; k < n; ++k) {
-      if (warp == 0) {
-        double best = -1.0;
-        int bi = k;
-        for (int r = k + lane; r < n; r += 32) {
-          const double v = cabs1(LU[r * n + k]);
-          if (v > best) { best = v; bi = r; }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-          const double ov = __shfl_xor_sync(0xffffffffu, best, o);
-          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-          if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-        }
-        if (lane == 0) {
-          piv_sm = bi;
-          const double2 pv = LU[bi * n + k];
-          pv_sm = pv;
-          oldkk_sm = LU[k * n + k];
-          if (pv.x == 0.0 && pv.y == 0.0) {
-            atomicOr(flags, 1);
-            invu[k] = mk(0.0, 0.0);
-          } else {
-            invu[k] = cinv(pv);
-          }
-          if (bi != k) {
-            const int t = perm[k]; perm[k] = perm[bi]; perm[bi] = t;
-          }
-        }
-      }
-      __syncthreads();
-      const int p = piv_sm;
-      const double2 inv = invu[k];
-      // row swap of the columns != k, and the multipliers of column k
-      if (p != k) {
-        for (int col = tid; col < n; col += blockDim.x) {
-          if (col == k) continue;
-          const double2 t = LU[k * n + col];
-          LU[k * n + col] = LU[p * n + col];
-          LU[p * n + col] = t;
-        }
-      }
-      for (int r = k + tid; r < n; r += blockDim.x) {
-        if (r == k) {
-          LU[k * n + k] = pv_sm;
-        } else {
-          const double2 v = (r == p) ? oldkk_sm : LU[r * n + k];
-          LU[r * n + k] = cmul(v, inv);
-        }
-      }
-      __syncthreads();
-      // trailing rank-1 update
-      const int m = n - k - 1;
-      for (int idx = tid; idx < m * m; idx += blockDim.x) {
-        const int r = k + 1 + idx / m, col = k + 1 + idx % m;
-        LU[r * n + col] = cfms(LU[r * n + k], LU[k * n + col], LU[r * n + col]);
-      }
-      __syncthreads();
-    }
-    // scale U's strictly-upper columns by 1/U_kk (unit-diagonal V = U diag(1/U_kk))
-    for (int idx = tid; idx < n * n; idx += blockDim.x) {
-      const int r = idx / n, col = idx - r * n;
-      if (r < col) LU[idx] = cmul(LU[idx], invu[col]);
-    }
-    __syncthreads();
-
-    // ---- diag(Gamma) by chunks of nc right-hand sides ----
-    for (int j0 = 0; j0 < n; j0 += nc) {
-      const int w = min(nc, n - j0);
-      for (int idx = tid; idx < n * w; idx += blockDim.x) {
-        const int r = idx / w, jj = idx - r * w;
-        Y[r * nc + jj] = G[(size_t)perm[r] * n + j0 + jj];
-      }
-      __syncthreads();
-      for (int k = 0; k < n - 1; ++k) {           // unit-lower forward substitution
-        const int m = n - k - 1;
-        for (int idx = tid; idx < m * w; idx += blockDim.x) {
-          const int r = k + 1 + idx / w, jj = idx % w;
-          Y[r * nc + jj] = cfms(LU[r * n + k], Y[k * nc + jj], Y[r * nc + jj]);
-        }
-        __syncthreads();
-      }
-      for (int k = n - 1; k > j0; --k) {          // unit-upper back substitution, rows >= j0 only
-        const int m = k - j0;
-        for (int idx = tid; idx < m * w; idx += blockDim.x) {
-          const int r = j0 + idx / w, jj = idx % w;
-          if (j0 + jj <= r) Y[r * nc + jj] = cfms(LU[r * n + k], Y[k * nc + jj], Y[r * nc + jj]);
-        }
-        __syncthreads();
-      }
-      for (int jj = tid; jj < w; jj += blockDim.x) {
-        const int j = j0 + jj;
-        const double2 gdiag = cmul(Y[j * nc + jj], invu[j]);
-        double2 g2 = mk(0.0, 0.0);
-        for (int x = 0; x < n; ++x) g2 = cfma(GG[(size_t)j * n + x], xs[x], g2);
-        const double wgt = (c == 0) ? 1.0 : 3.0;
-        kc[(((size_t)c * nb + a) * n + j) * N + q] =
-            mk(wgt * (gdiag.x - 0.5 * g2.x), wgt * (gdiag.y - 0.5 * g2.y));
-      }
-      __syncthreads();
-    }
+    bse_f64_system(dm, c, a, q, nc, gam, gg, chi, kc, LU, sm + L.y, sm + L.xs, sm + L.invu, sh, flags);
   }
 }
 

@@ -1,195 +1,60 @@
-// Lattice-FFT kernels of the dual-fermion loop: bare dual propagator
-// (Eq. gd0), Dyson + transform to real space (Eq. dyson), the dual bubble
-// (Eq. dual_bubble) and the Schwinger-Dyson convolution (Eq. sd).
+// Lattice-FFT kernels of the dual-fermion loop for one problem: bare dual
+// propagator (Eq. gd0), Dyson + transform to real space (Eq. dyson), the
+// dual bubble (Eq. dual_bubble) and the Schwinger-Dyson convolution
+// (Eq. sd).
 //
 // Every momentum sum over the N = N_k^D grid is a cyclic correlation and is
 // done exactly with D-dimensional FFTs held in shared memory: one CTA per
 // (frequency, frequency) plane, N <= 4096 points (64 KB in complex128).
-#include "df_internal.cuh"
+#include "df_fft_dev.cuh"
 
 namespace df {
 
-constexpr int kFftThreads = 256;
-
-__device__ __forceinline__ double eps_of(int r, int D, int p, double t, double tp) {
-  const int mask = (1 << p) - 1;
-  const double inv_nk = 1.0 / (double)(1 << p);
-  double c[4] = {0, 0, 0, 0};
-  double e = 0.0;
-  for (int d = 0; d < D; ++d) {
-    const int j = (r >> ((D - 1 - d) * p)) & mask;   // coordinate along axis d
-    c[d] = cospi(2.0 * (double)j * inv_nk);
-    e += c[d];
-  }
-  e *= -2.0 * t;
-  if (D == 2) e -= 4.0 * tp * c[0] * c[1];
-  return e;
-}
-
-// Eq. gd0 on the extended grid; G~ = G0~ (Sigma~ = 0).
 __global__ void init_g0_kernel(Dims dm, const double2* __restrict__ g, const double2* __restrict__ delta,
                                double2* __restrict__ g0, double2* __restrict__ gk) {
   const int total = dm.ne * dm.N;
-  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
-    const int e = idx / dm.N, r = idx - e * dm.N;
-    const double2 ge = g[e];
-    const double eps = eps_of(r, dm.D, dm.p, dm.t, dm.tp);
-    double2 den = cinv(ge) + delta[e];
-    den.x -= eps;
-    const double2 v = cinv(den) - ge;
-    g0[idx] = v;
-    gk[idx] = v;
-  }
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x)
+    init_g0_elem(dm, idx, g, delta, g0, gk);
 }
 
-// Per extended plane e in [first, first + count): G~(k) = Dyson(G0~, Sigma~)
-// inside the box (G0~ outside), then G~(r) = (1/N) sum_k exp(ik.r) G~(k).
 __global__ void __launch_bounds__(kFftThreads)
 dyson_ifft_kernel(Dims dm, int first, const double2* __restrict__ g0, const double2* __restrict__ sigma,
                   double2* __restrict__ gk, double2* __restrict__ gr) {
   extern __shared__ double2 sm[];
-  double2* tw = sm;                  // [nk/2]
-  double2* s = sm + dm.nk / 2;       // [N]
-  const int e = first + blockIdx.x;
-  const int i = e - dm.m_max;        // box index or outside
-  const bool in_box = (i >= 0 && i < dm.n_w);
-  load_twiddles(tw, dm.nk);
-  for (int r = threadIdx.x; r < dm.N; r += blockDim.x) {
-    double2 v = g0[(size_t)e * dm.N + r];
-    if (in_box) v = cinv(cinv(v) - sigma[(size_t)i * dm.N + r]);
-    gk[(size_t)e * dm.N + r] = v;
-    s[bitrev_axes(r, dm.D, dm.p)] = v;
-  }
-  __syncthreads();
-  fft_dit_smem(s, dm.D, dm.p, tw, true);
-  const double invN = 1.0 / (double)dm.N;
-  for (int r = threadIdx.x; r < dm.N; r += blockDim.x) gr[(size_t)e * dm.N + r] = cscale(s[r], invN);
+  dyson_ifft_plane(dm, first + blockIdx.x, g0, sigma, gk, gr, sm, sm + dm.nk / 2);
 }
 
-// Eq. dual_bubble: per (a, i) plane, chi~(q) = -T FFT[G~_w(-r) G~_{w+W}(r)](q).
 __global__ void __launch_bounds__(kFftThreads)
 bubble_kernel(Dims dm, const double2* __restrict__ gr, double2* __restrict__ chi) {
   extern __shared__ double2 sm[];
-  double2* tw = sm;
-  double2* s = sm + dm.nk / 2;
   const int a = blockIdx.x / dm.n_w, i = blockIdx.x - a * dm.n_w;
-  const double2* A = gr + (size_t)(i + dm.m_max) * dm.N;   // G~_w
-  const double2* B = gr + (size_t)(i + a) * dm.N;          // G~_{w+W}
-  load_twiddles(tw, dm.nk);
-  for (int r = threadIdx.x; r < dm.N; r += blockDim.x)
-    s[bitrev_axes(r, dm.D, dm.p)] = cmul(A[reflect_index(r, dm.D, dm.p)], B[r]);
-  __syncthreads();
-  fft_dit_smem(s, dm.D, dm.p, tw, false);
-  double2* out = chi + ((size_t)a * dm.n_w + i) * dm.N;
-  for (int q = threadIdx.x; q < dm.N; q += blockDim.x) out[q] = cscale(s[q], -dm.T);
+  bubble_plane(dm, a, i, gr, chi, sm, sm + dm.nk / 2);
 }
 
-// Eq. sd, stage 1: per (a, i) plane, K(r) = (1/N) sum_q exp(iq.r) K(q) with
-// K = kernel_d + kernel_m, then prod(r) = K(-r) G~_{w+W}(r).
 __global__ void __launch_bounds__(kFftThreads)
 sigma_prod_kernel(Dims dm, const double2* __restrict__ kc, const double2* __restrict__ gr,
                   double2* __restrict__ prod) {
   extern __shared__ double2 sm[];
-  double2* tw = sm;
-  double2* s = sm + dm.nk / 2;
   const int a = blockIdx.x / dm.n_w, i = blockIdx.x - a * dm.n_w;
-  const size_t plane = ((size_t)a * dm.n_w + i) * dm.N;
-  const size_t chstride = (size_t)dm.nb * dm.n_w * dm.N;
-  load_twiddles(tw, dm.nk);
-  for (int q = threadIdx.x; q < dm.N; q += blockDim.x)
-    s[bitrev_axes(q, dm.D, dm.p)] = kc[plane + q] + kc[chstride + plane + q];
-  __syncthreads();
-  fft_dit_smem(s, dm.D, dm.p, tw, true);
-  const double invN = 1.0 / (double)dm.N;
-  const double2* B = gr + (size_t)(i + a) * dm.N;
-  for (int r = threadIdx.x; r < dm.N; r += blockDim.x)
-    prod[plane + r] = cmul(cscale(s[reflect_index(r, dm.D, dm.p)], invN), B[r]);
+  sigma_prod_plane(dm, a, i, kc, gr, prod, sm, sm + dm.nk / 2);
 }
 
-template <int NT>
-__device__ __forceinline__ double block_max(double v, double* red_sm) {
-  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) red_sm[w] = v;
-  __syncthreads();
-  if (w == 0) {
-    v = (l < NT / 32) ? red_sm[l] : 0.0;
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (l == 0) red_sm[0] = v;
-  }
-  __syncthreads();
-  v = red_sm[0];
-  __syncthreads();
-  return v;
-}
-
-// Eq. sd, stage 2, fused with mixing, the residual partials and Eq. dyson:
-// per box frequency i, acc(r) = sum_W prod[W][i](r); Sigma~_new(k) =
-// (T/2) FFT[acc](k); Sigma~ <- mix new + (1-mix) old; G~ = 1/(1/G0~ - Sigma~);
-// G~(r) = IFFT[G~(k)] / N.
 __global__ void __launch_bounds__(kFftThreads)
 sigma_dyson_kernel(Dims dm, double mix, const double2* __restrict__ prod, const double2* __restrict__ g0,
                    double2* __restrict__ sigma, double2* __restrict__ gk, double2* __restrict__ gr,
                    double* __restrict__ red) {
   extern __shared__ double2 sm[];
   __shared__ double red_sm[32];
-  double2* tw = sm;
-  double2* s = sm + dm.nk / 2;
-  double2* s2 = s + dm.N;
-  const int i = blockIdx.x;
-  const int e = i + dm.m_max;
-  load_twiddles(tw, dm.nk);
-  for (int r = threadIdx.x; r < dm.N; r += blockDim.x) {
-    double2 acc = mk(0.0, 0.0);
-    for (int a = 0; a < dm.nb; ++a) acc = acc + prod[((size_t)a * dm.n_w + i) * dm.N + r];
-    s[bitrev_axes(r, dm.D, dm.p)] = acc;
-  }
-  __syncthreads();
-  fft_dit_smem(s, dm.D, dm.p, tw, false);
-  const double pref = 0.5 * dm.T;
-  double dmax = 0.0, smax = 0.0;
-  for (int k = threadIdx.x; k < dm.N; k += blockDim.x) {
-    const size_t idx = (size_t)i * dm.N + k;
-    const double2 old = sigma[idx];
-    const double2 nw = cscale(s[k], pref);
-    const double2 sg = mk(mix * nw.x + (1.0 - mix) * old.x, mix * nw.y + (1.0 - mix) * old.y);
-    const double2 d = sg - old;
-    dmax = fmax(dmax, sqrt(cabs2(d)));
-    smax = fmax(smax, sqrt(cabs2(sg)));
-    sigma[idx] = sg;
-    const double2 gnew = cinv(cinv(g0[(size_t)e * dm.N + k]) - sg);
-    gk[(size_t)e * dm.N + k] = gnew;
-    s2[bitrev_axes(k, dm.D, dm.p)] = gnew;
-  }
-  dmax = block_max<kFftThreads>(dmax, red_sm);
-  smax = block_max<kFftThreads>(smax, red_sm);
-  if (threadIdx.x == 0) {
-    red[i] = dmax;
-    red[dm.n_w + i] = smax;
-  }
-  fft_dit_smem(s2, dm.D, dm.p, tw, true);
-  const double invN = 1.0 / (double)dm.N;
-  for (int r = threadIdx.x; r < dm.N; r += blockDim.x) gr[(size_t)e * dm.N + r] = cscale(s2[r], invN);
+  sigma_dyson_plane(dm, blockIdx.x, mix, prod, g0, sigma, gk, gr, red, sm, sm + dm.nk / 2,
+                    sm + dm.nk / 2 + dm.N, red_sm);
 }
 
 __global__ void residual_reduce_kernel(int n, double* red) {
   __shared__ double red_sm[32];
-  double a = 0.0, b = 0.0;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    a = fmax(a, red[j]);
-    b = fmax(b, red[n + j]);
-  }
-  a = block_max<kFftThreads>(a, red_sm);
-  b = block_max<kFftThreads>(b, red_sm);
-  if (threadIdx.x == 0) {
-    red[2 * n] = a;
-    red[2 * n + 1] = b;
-  }
+  residual_reduce_block(n, red, red_sm);
 }
 
-static size_t fft_smem(const Dims& dm, int planes) {
-  return sizeof(double2) * ((size_t)dm.nk / 2 + (size_t)planes * dm.N);
-}
+static size_t fft_smem(const Dims& dm, int planes) { return fft_smem_bytes(dm.nk, dm.N, planes); }
 
 static cudaError_t set_smem(const void* fn, size_t bytes) {
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
