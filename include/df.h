@@ -187,6 +187,53 @@ df_status df_get_timing(df_ctx* c, double* ms, int* launches, int count);
 /* Wait for all work queued on the handle's stream. */
 df_status df_synchronize(df_ctx* c);
 
+/* ---- batches of uneven parameter points ------------------------------------
+ * The same loop for many independent points (lattice, beta, n_w, m_max may all
+ * differ), run together: each stage of a pass is one launch over all points
+ * (the FFT stages over every (point, plane), the FP64 ladders in one
+ * persistent kernel with a cost-sorted atomic work queue, the mixed ladders
+ * in one persistent launch per padded-order class), the pass is captured in
+ * one CUDA graph and replayed, and points that reach tol stop being
+ * updated.  Inputs per point as in df_init (host pointers). */
+typedef struct df_point {
+  int dim;
+  int nk;
+  double tp;
+  double t;
+  double beta;
+  double mu;
+  int n_w;
+  int m_max;
+  const double* g;        /* [n_w + 2 m_max] */
+  const double* delta;    /* [n_w + 2 m_max] */
+  const double* gamma_d;  /* [2 m_max + 1][n_w][n_w] */
+  const double* gamma_m;
+} df_point;
+
+typedef struct df_batch df_batch;
+
+/* precision: DF_FP64 for every point, or DF_FP32_IR (points with n_w <= 64
+ * mixed, larger ones FP64).  tol > 0: a point stops once its residual
+ * r <= tol.  stream may be NULL (the batch then creates its own). */
+df_status df_batch_init(df_batch** out, int npts, const df_point* pts, int precision, double mix, double tol,
+                        void* stream);
+/* Up to max_iter passes (graph replays); stops early when every point has
+ * converged.  Per point: resid[i] (last residual), active[i] (1 = not yet
+ * converged); either may be NULL.  DF_ERR_NOT_CONVERGED if a point is
+ * still active at the end. */
+df_status df_batch_iterate(df_batch* b, int max_iter, int* passes_done, double* resid, int* active);
+df_status df_batch_get_sigma(df_batch* b, int point, double* out, int out_is_device);
+/* Sigma~ = 0 and every point active again (G~ = G0~). */
+df_status df_batch_reset(df_batch* b);
+/* Times one pass for each candidate (FP64 right-hand-side chunk 8/16/32 or
+ * the per-order default, scheduler chunk 1/4 systems), keeps the fastest,
+ * appends it to cache_path (if not NULL) under the batch's size signature
+ * and reads it from there next time.  Resets the batch (df_batch_reset).
+ * chosen (may be NULL): [nc, chunk, 1 if read from the cache]. */
+df_status df_batch_autotune(df_batch* b, const char* cache_path, int* chosen);
+const char* df_batch_last_error(const df_batch* b);
+void df_batch_destroy(df_batch* b);
+
 /* Allocation-free variant of the FP64 ladder solves of df_bse (the paper
  * has no counterpart: this is a deployment form).  For callers that cannot
  * allocate device memory at the call, e.g. code inside a host application

@@ -38,7 +38,8 @@ EXPORTS = (
     "df_default_opts", "df_init", "df_set_inputs", "df_vertex_from_spin", "df_bubble", "df_bse",
     "df_sigma", "df_iterate", "df_get_sigma", "df_set_sigma", "df_get_gtilde", "df_get_chi",
     "df_get_kernel", "df_get_lambda", "df_get_sizes", "df_set_timing", "df_get_timing",
-    "df_synchronize", "df_bse_noalloc", "df_last_error",
+    "df_synchronize", "df_bse_noalloc", "df_batch_init", "df_batch_iterate", "df_batch_get_sigma",
+    "df_batch_reset", "df_batch_autotune", "df_batch_last_error", "df_batch_destroy", "df_last_error",
     "df_status_string", "df_destroy",
 )
 
@@ -51,6 +52,12 @@ class DFError(RuntimeError):
 
 class df_lattice(C.Structure):
     _fields_ = [("dim", C.c_int), ("nk", C.c_int), ("tp", C.c_double)]
+
+
+class df_point(C.Structure):
+    _fields_ = [("dim", C.c_int), ("nk", C.c_int), ("tp", C.c_double), ("t", C.c_double),
+                ("beta", C.c_double), ("mu", C.c_double), ("n_w", C.c_int), ("m_max", C.c_int),
+                ("g", C.c_void_p), ("delta", C.c_void_p), ("gamma_d", C.c_void_p), ("gamma_m", C.c_void_p)]
 
 
 class df_opts(C.Structure):
@@ -94,6 +101,11 @@ def load(path: str = LIB_PATH):
         "df_get_timing": [P, D, I, C.c_int],
         "df_synchronize": [P],
         "df_bse_noalloc": [P, P, C.c_int, C.c_int, C.c_int, P, P],
+        "df_batch_init": [C.POINTER(P), C.c_int, C.c_void_p, C.c_int, C.c_double, C.c_double, P],
+        "df_batch_iterate": [P, C.c_int, I, D, I],
+        "df_batch_get_sigma": [P, C.c_int, P, C.c_int],
+        "df_batch_reset": [P],
+        "df_batch_autotune": [P, C.c_char_p, I],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -105,6 +117,10 @@ def load(path: str = LIB_PATH):
     lib.df_status_string.restype = C.c_char_p
     lib.df_destroy.argtypes = [P]
     lib.df_destroy.restype = None
+    lib.df_batch_last_error.argtypes = [P]
+    lib.df_batch_last_error.restype = C.c_char_p
+    lib.df_batch_destroy.argtypes = [P]
+    lib.df_batch_destroy.restype = None
     _lib = lib
     return lib
 
@@ -283,6 +299,82 @@ class DualFermion:
         if len(dev) != 1:
             raise ValueError("all inputs must be on the same side (host or device)")
         self._check(self.lib.df_set_inputs(self.h, *[p for p, _ in ptrs], dev.pop()))
+
+
+class DualFermionBatch:
+    """Many independent parameter points iterated together (a df_batch handle):
+    one launch per stage over all points, one CUDA graph per pass."""
+
+    def __init__(self, workloads, precision: int = DF_FP64, mix: float = 1.0, tol: float = 0.0,
+                 stream: Optional[int] = None):
+        self.lib = load()
+        self.workloads = list(workloads)
+        n = len(self.workloads)
+        self._keep = []
+        arr = (df_point * n)()
+        for i, w in enumerate(self.workloads):
+            gd, gm = vertex_from_spin(w.gamma_uu, w.gamma_ud)
+            g, dl = _c128(w.g), _c128(w.delta)
+            self._keep += [g, dl, gd, gm]
+            arr[i] = df_point(w.dim, w.nk, w.tp, w.t, w.beta, w.mu, w.n_w, w.m_max,
+                              g.ctypes.data, dl.ctypes.data, gd.ctypes.data, gm.ctypes.data)
+        if stream is None:
+            stream = current_stream_handle()
+        h = C.c_void_p()
+        s = self.lib.df_batch_init(C.byref(h), n, C.cast(arr, C.c_void_p), precision, mix, tol,
+                                   C.c_void_p(stream) if stream else None)
+        if s != DF_OK:
+            raise DFError(s, "df_batch_init failed (see stderr)")
+        self.h = h
+        self.npts = n
+
+    def _check(self, s, allow=(DF_OK,)):
+        if s in allow:
+            return s
+        raise DFError(s, self.lib.df_batch_last_error(self.h).decode())
+
+    def iterate(self, max_iter: int):
+        """Returns (passes, residuals [npts], active [npts], status)."""
+        it = C.c_int(0)
+        r = (C.c_double * self.npts)()
+        a = (C.c_int * self.npts)()
+        s = self._check(self.lib.df_batch_iterate(self.h, max_iter, C.byref(it), r, a),
+                        (DF_OK, DF_ERR_NOT_CONVERGED))
+        return it.value, np.array(r[:]), np.array(a[:]), s
+
+    def get_sigma(self, i: int, out=None):
+        w = self.workloads[i]
+        if out is None:
+            out = np.empty((w.n_w, w.N), np.complex128)
+        p, dev = _ptr(out)
+        self._check(self.lib.df_batch_get_sigma(self.h, i, p, dev))
+        return out
+
+    def reset(self):
+        self._check(self.lib.df_batch_reset(self.h))
+
+    def autotune(self, cache_path: Optional[str] = None):
+        """Returns (rhs chunk, scheduler chunk, from_cache)."""
+        ch = (C.c_int * 3)()
+        self._check(self.lib.df_batch_autotune(self.h, cache_path.encode() if cache_path else None, ch))
+        return ch[0], ch[1], bool(ch[2])
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.df_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
 
 
 def mixed_supported(n_w: int) -> bool:

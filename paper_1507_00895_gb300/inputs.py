@@ -279,3 +279,23 @@ def random_nonsymmetric(n_w: int, m_max: int, dim: int, nk: int, seed: int,
     gud = scale * (rng.normal(size=shape) + 1j * rng.normal(size=shape))
     return Workload("random", dim, nk, 1.0, 0.0, 1.0, beta, 0.5, n_w, m_max,
                     g, delta, guu, gud)
+
+
+def uneven_batch(npts: int = 64, seed: int = 4, max_n_w: int = 128, max_m: int = 15,
+                 grids=((2, 8), (2, 16), (2, 32), (2, 64), (4, 8))):
+    """The uneven batch of parameter points: U ~ U[1, 8], beta ~ U[2, 20],
+    lattice drawn from `grids` ((dim, N_k) pairs; default 8^2, 16^2, 32^2,
+    64^2 and 8^4), n_w in {16, 24, ..., max_n_w}, N_W = 2m + 1 with
+    m in {0..max_m}; half-filled Hubbard-atom inputs with Delta = <eps^2> g.
+    Smaller max_n_w / max_m / grids give the same recipe at test sizes."""
+    rng = np.random.default_rng(seed)
+    out = []
+    nws = list(range(16, max_n_w + 1, 8))
+    for i in range(npts):
+        U = float(rng.uniform(1.0, 8.0))
+        beta = float(rng.uniform(2.0, 20.0))
+        dim, nk = grids[int(rng.integers(0, len(grids)))]
+        n_w = int(nws[int(rng.integers(0, len(nws)))])
+        m = int(rng.integers(0, max_m + 1))
+        out.append(half_filled_atom(f"batch{i}", dim, nk, U=U, beta=beta, n_w=n_w, m_max=m))
+    return out
