@@ -399,9 +399,10 @@ df_status df_batch_init(df_batch** out, int npts, const df_point* pts, int preci
   int ndev = 0;
   if (!b->stream) {
     // graph capture needs a stream other than the legacy default one
-    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaError_t es = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    if (es != cudaSuccess) {
       delete b;
-      fprintf(stderr, "libdf: df_batch_init: no CUDA device\n");
+      fprintf(stderr, "libdf: df_batch_init: cudaStreamCreate: %s\n", cudaGetErrorString(es));
       return DF_ERR_CUDA;
     }
     b->own_stream = true;
@@ -484,7 +485,6 @@ df_status df_batch_init(df_batch** out, int npts, const df_point* pts, int preci
     P.gr = (double2*)take(sizeof(double2) * plane);
     P.chi = (double2*)take(sizeof(double2) * nchi);
     P.kc = (double2*)take(sizeof(double2) * 2 * nchi);
-    take(sizeof(double2) * nchi);   // kc uses two chi-sized blocks
     P.prod = (double2*)take(sizeof(double2) * nchi);
     P.sigma = (double2*)take(sizeof(double2) * (size_t)dm.n_w * dm.N);
     P.red = (double*)take(sizeof(double) * (2 * dm.n_w + 4));
@@ -492,6 +492,11 @@ df_status df_batch_init(df_batch** out, int npts, const df_point* pts, int preci
     if (P.mixed) {
       P.gam_hi = (float2*)take(sizeof(float2) * nv);
       P.gam_lo = (float2*)take(sizeof(float2) * nv);
+    }
+    const char* limit = b->arena + (i + 1 < npts ? off[i + 1] : total);
+    if (cur > limit) {
+      st = bfail(b, DF_ERR_ARG, "internal: point buffers exceed their arena slice");
+      goto bad;
     }
   }
   BALLOC(b->d_pts, sizeof(PointDev) * npts, "point table");
