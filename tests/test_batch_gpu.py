@@ -54,14 +54,16 @@ def test_batch_fp64_matches_oracle_per_point(df):
             assert abs(r[i] - st.residuals[-1]) < 1e-10 * max(1.0, st.residuals[-1])
 
 
-def test_batch_equals_single_handles_bitwise(df):
+def test_batch_equals_single_handles(df):
+    # the same device functions inlined into two kernels may contract
+    # multiply-adds differently: equal to rounding, not bit for bit
     ws = small_batch()
     with df.DualFermionBatch(ws) as b:
         b.iterate(2)
         for i, w in enumerate(ws):
             with df.DualFermion.from_workload(w, eig_mode=0) as d:
                 d.iterate(2)
-                assert np.array_equal(b.get_sigma(i), d.get_sigma()), i
+                assert nrel(b.get_sigma(i), d.get_sigma()) < 1e-13, i
 
 
 def test_batch_mixed_matches_oracle(df):
