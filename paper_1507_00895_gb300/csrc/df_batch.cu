@@ -337,15 +337,21 @@ df_status build_graph(df_batch* b) {
 }
 
 df_status configure_groups(df_batch* b) {
-  // kernel attributes and persistent grids for the current nc / chunk
+  // kernel attributes and persistent grids for the current nc / chunk; the
+  // mixed classes share one kernel, whose shared-memory limit is set once to
+  // the largest class
+  size_t mixed_max = 0;
+  for (auto& g : b->groups)
+    if (g.mixed) mixed_max = std::max(mixed_max, sizeof(float2) * (size_t)mixed_layout(g.np).total);
+  if (mixed_max)
+    B_CUDA(b, cudaFuncSetAttribute((const void*)batch_bse_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)mixed_max),
+           "mixed smem attribute");
   for (auto& g : b->groups) {
     if (g.mixed) {
       const int P = g.np / 4;
       g.threads = P * P;
       g.smem = sizeof(float2) * (size_t)mixed_layout(g.np).total;
-      B_CUDA(b, cudaFuncSetAttribute((const void*)batch_bse_mixed_kernel,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)g.smem),
-             "mixed smem attribute");
       int per = 0;
       cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_bse_mixed_kernel, g.threads, g.smem);
       g.grid = b->sms * std::max(1, per);
