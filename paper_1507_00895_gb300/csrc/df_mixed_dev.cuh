@@ -57,6 +57,19 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float p) {
   hi = s;
   lo += e;
 }
+// (hi, lo) += a * b with a renormalised double-float accumulator: the exact
+// product p + pe (fma), TwoSum into hi, the error and lo folded back by
+// FastTwoSum, so that |lo| <= ulp(hi)/2 after every step and the running
+// error stays ~2^-48 |hi| per step (not ~step * 2^-48 max|hi|).
+__device__ __forceinline__ void dd_fma(float& hi, float& lo, float a, float b) {
+  const float p = a * b;
+  const float pe = fmaf(a, b, -p);
+  float s, e;
+  two_sum(hi, p, s, e);
+  e += lo + pe;
+  hi = s + e;
+  lo = e - (hi - s);
+}
 // acc += a * b exactly for FP32 a, b (the product error goes to lo)
 __device__ __forceinline__ void df_fma(float& hi, float& lo, float a, float b) {
   const float p = a * b;
@@ -305,13 +318,13 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
   // two passes of 2 rows each keep the double-float accumulators in registers
 #pragma unroll
   for (int half = 0; half < 2; ++half) {
-    float acc[2][kTile][4];   // [row][col][re_hi, re_lo, im_hi, im_lo]
+    float acc[2][kTile][6];   // [row][col][re_hi, re_lo, im_hi, im_lo, re_small, im_small]
 #pragma unroll
     for (int i2 = 0; i2 < 2; ++i2)
 #pragma unroll
       for (int jj = 0; jj < kTile; ++jj)
 #pragma unroll
-        for (int e = 0; e < 4; ++e) acc[i2][jj][e] = 0.f;
+        for (int e = 0; e < 6; ++e) acc[i2][jj][e] = 0.f;
     for (int l0 = 0; l0 < np; l0 += lc) {
       __syncthreads();
       for (int idx = t; idx < lc * np; idx += blockDim.x) {
@@ -338,15 +351,15 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
           for (int jj = 0; jj < kTile; ++jj) {
             float* ac = acc[i2][jj];
             // real: gh.x yh.x - gh.y yh.y (+ cross terms in lo)
-            df_fma(ac[0], ac[1], gh.x, yh[jj].x);
-            df_fma(ac[0], ac[1], -gh.y, yh[jj].y);
-            ac[1] = fmaf(gh.x, yl[jj].x, fmaf(-gh.y, yl[jj].y, ac[1]));
-            ac[1] = fmaf(gl.x, yh[jj].x, fmaf(-gl.y, yh[jj].y, ac[1]));
+            dd_fma(ac[0], ac[1], gh.x, yh[jj].x);
+            dd_fma(ac[0], ac[1], -gh.y, yh[jj].y);
+            ac[4] = fmaf(gh.x, yl[jj].x, fmaf(-gh.y, yl[jj].y, ac[4]));
+            ac[4] = fmaf(gl.x, yh[jj].x, fmaf(-gl.y, yh[jj].y, ac[4]));
             // imag: gh.x yh.y + gh.y yh.x
-            df_fma(ac[2], ac[3], gh.x, yh[jj].y);
-            df_fma(ac[2], ac[3], gh.y, yh[jj].x);
-            ac[3] = fmaf(gh.x, yl[jj].y, fmaf(gh.y, yl[jj].x, ac[3]));
-            ac[3] = fmaf(gl.x, yh[jj].y, fmaf(gl.y, yh[jj].x, ac[3]));
+            dd_fma(ac[2], ac[3], gh.x, yh[jj].y);
+            dd_fma(ac[2], ac[3], gh.y, yh[jj].x);
+            ac[5] = fmaf(gh.x, yl[jj].y, fmaf(gh.y, yl[jj].x, ac[5]));
+            ac[5] = fmaf(gl.x, yh[jj].y, fmaf(gl.y, yh[jj].x, ac[5]));
           }
         }
       }
@@ -361,8 +374,8 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
         const int col = tc + P * jj;
         double2 g = (r < n && col < n) ? gam[mat + (size_t)r * n + col] : mk(0.0, 0.0);
         const float2 x = X0s[r * np + col];
-        const double re = g.x - (double)x.x + ((double)acc[i2][jj][0] + (double)acc[i2][jj][1]);
-        const double im = g.y - (double)x.y + ((double)acc[i2][jj][2] + (double)acc[i2][jj][3]);
+        const double re = g.x - (double)x.x + (((double)acc[i2][jj][0] + (double)acc[i2][jj][1]) + (double)acc[i2][jj][4]);
+        const double im = g.y - (double)x.y + (((double)acc[i2][jj][2] + (double)acc[i2][jj][3]) + (double)acc[i2][jj][5]);
         A[ii][kTile + jj] = make_float2((float)re, (float)im);
       }
     }
