@@ -80,7 +80,7 @@ __device__ __forceinline__ void df_fma(float& hi, float& lo, float a, float b) {
 
 struct MixedSmem {
   // offsets in float2 units
-  int x0, chih, chil, ubuf, lbuf, invu, x0d, gt_h, gt_l, yh, yl, total;
+  int x0, chih, chil, ubuf, lbuf, invu, x0d, gt_h, gt_l, yh, yl, chi64, total;
 };
 
 __host__ __device__ inline MixedSmem mixed_layout(int np) {
@@ -97,6 +97,7 @@ __host__ __device__ inline MixedSmem mixed_layout(int np) {
   L.gt_l = o; o += kResChunk * np; // lo
   L.yh = o;   o += np * np;        // Y = chi o X0, hi
   L.yl = o;   o += np * np;        // lo
+  L.chi64 = o; o += 2 * np;        // chi~ in FP64 (double2 = two float2 slots)
   L.total = o;
   return L;
 }
@@ -104,6 +105,7 @@ __host__ __device__ inline MixedSmem mixed_layout(int np) {
 // Shared-memory views of one mixed solve (layout from mixed_layout).
 struct MixedPtrs {
   float2 *X0s, *chih, *chil, *ubuf, *lbuf, *invu, *x0d, *gth, *gtl, *Yh, *Yl;
+  double2* chi64;
   int* piv_s;
 };
 
@@ -121,6 +123,7 @@ __device__ __forceinline__ MixedPtrs mixed_ptrs(float2* smf, int np, int* piv_s)
   m.gtl = smf + L.gt_l;
   m.Yh = smf + L.yh;
   m.Yl = smf + L.yl;
+  m.chi64 = (double2*)(smf + L.chi64);
   m.piv_s = piv_s;
   return m;
 }
@@ -159,6 +162,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
     const float hx = (float)x.x, hy = (float)x.y;
     chih[i] = make_float2(hx, hy);
     chil[i] = make_float2((float)(x.x - (double)hx), (float)(x.y - (double)hy));
+    sp.chi64[i] = x;
   }
   __syncthreads();
 
@@ -172,10 +176,14 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
 #pragma unroll
     for (int jj = 0; jj < kTile; ++jj) {
       const int col = tc + P * jj;
-      float2 g = (r < n && col < n) ? Gh[r * n + col] : make_float2(0.f, 0.f);
-      float2 z = cmulf(g, chih[col]);
-      A[ii][jj] = make_float2((r == col ? 1.f : 0.f) - z.x, -z.y);
-      A[ii][kTile + jj] = g;
+      // D = 1 - gamma chi~ formed in FP64 and rounded once: the diagonal
+      // 1 - gamma_ww chi~_w cancels when |gamma chi~| >> |D|, and a product of
+      // FP32-rounded factors would lose those digits
+      const bool in = (r < n && col < n);
+      const double2 g64 = in ? gam[mat + (size_t)r * n + col] : mk(0.0, 0.0);
+      const double2 z = cmul(g64, sp.chi64[col]);
+      A[ii][jj] = make_float2((float)((r == col ? 1.0 : 0.0) - z.x), (float)(-z.y));
+      A[ii][kTile + jj] = in ? Gh[r * n + col] : make_float2(0.f, 0.f);
     }
   }
 
