@@ -264,6 +264,36 @@ def time_to_converged(df, I, torch, max_passes=60):
     return out
 
 
+def batch_bench(df, I, torch, full: bool, passes: int = 3):
+    """Throughput of the batched loop on the 64-point uneven recipe (seed 4):
+    U ~ U[1,8], beta ~ U[2,20], lattices 8^2..64^2 and 8^4, n_w 16..128,
+    N_W 1..31 (full), or the same recipe capped at n_w <= 64, N_W <= 15 and
+    lattices up to 32^2 (default, to stay within a minute).  One pass = one
+    replay of the captured graph; tiles chosen by the autotuner."""
+    import tempfile
+    if full:
+        ws = I.uneven_batch(64, seed=4)
+        desc = "64 uneven points, full recipe (n_w 16-128, N_W 1-31, 8^2-64^2 and 8^4)"
+    else:
+        ws = I.uneven_batch(64, seed=4, max_n_w=64, max_m=7, grids=((2, 8), (2, 16), (2, 32), (4, 4)))
+        desc = "64 uneven points, capped recipe (n_w 16-64, N_W 1-15, 8^2/16^2/32^2 and 4^4)"
+    pts = sum(w.n_bos * w.N for w in ws)
+    out = {"workload": desc, "points_per_pass": pts, "ladders_per_pass": 2 * pts}
+    cache = os.path.join(tempfile.gettempdir(), "df_batch_tune.txt")
+    for name, prec in (("fp64", df.DF_FP64), ("fp32ir", df.DF_FP32_IR)):
+        with df.DualFermionBatch(ws, precision=prec) as b:
+            nc, ch, cached = b.autotune(cache)
+            b.iterate(1)
+            b.reset()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            b.iterate(passes)
+            dt = (time.perf_counter() - t0) / passes
+        out[name] = {"value": pts / dt, "unit": UNIT, "ms_per_pass": dt * 1e3,
+                     "autotuned": {"rhs_chunk": nc, "sched_chunk": ch, "from_cache": cached}}
+    return out
+
+
 def read_peaks():
     try:
         with open(PEAKS_PATH) as f:
@@ -423,6 +453,9 @@ def run_ours(args):
     ttc = None
     if rank == 0 and not args.no_ttc:
         ttc = time_to_converged(df, I, torch)
+    batch = None
+    if rank == 0 and not args.no_batch:
+        batch = batch_bench(df, I, torch, args.batch_full)
 
     if rank != 0:
         if world > 1:
@@ -445,7 +478,7 @@ def run_ours(args):
             "gpu_launches": main["gpu_launches"], "kernel_ms_per_step": main["kernel_ms_per_step"],
             "err_vs_fp64_first_pass": main.get("err_vs_fp64_first_pass"),
             "plain_fp64": plain if prec != df.DF_FP64 else None,
-            "time_to_converged": ttc, "clocks": main["clocks"]}
+            "time_to_converged": ttc, "batch": batch, "clocks": main["clocks"]}
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -462,6 +495,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttc", action="store_true", help="skip the time-to-converged comparison")
+    ap.add_argument("--no-batch", action="store_true", help="skip the uneven-batch throughput")
+    ap.add_argument("--batch-full", action="store_true", help="uneven batch at the recipe's full sizes")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)       # at least 3 untimed warm-up steps
     if args.impl == "reference":
