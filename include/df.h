@@ -234,6 +234,43 @@ df_status df_batch_autotune(df_batch* b, const char* cache_path, int* chosen);
 const char* df_batch_last_error(const df_batch* b);
 void df_batch_destroy(df_batch* b);
 
+/* ---- learned warm start -------------------------------------------------------
+ * A dense network of 4 layers (n_in -> width -> width -> width -> n_out, tanh
+ * between, linear output) that maps parameters and local inputs of a point
+ * to its dual self-energy, evaluated and trained by libdf's own kernels:
+ * every matrix product rounds its operands to BF16 and accumulates in FP32
+ * on the tensor cores; weights, biases, Adam moments and activations are
+ * FP32.  Weights are Glorot-uniform from `seed`, biases zero.  All data
+ * pointers are device memory (row-major [batch][features]); batch <=
+ * max_batch.  The paper has no counterpart (it starts from Sigma~ = 0). */
+typedef struct df_mlp df_mlp;
+df_status df_mlp_create(df_mlp** out, int n_in, int width, int n_out, int max_batch, unsigned long long seed,
+                        void* stream);
+df_status df_mlp_param_count(const df_mlp* m, long* count);
+/* y[batch][n_out] = net(x[batch][n_in]) */
+df_status df_mlp_forward(df_mlp* m, const float* x, int batch, float* y);
+/* gradients of the mean squared error mean((net(x) - target)^2) with
+ * respect to every parameter, kept inside the handle (df_mlp_grads);
+ * loss_host (may be NULL) receives the loss (synchronises). */
+df_status df_mlp_gradients(df_mlp* m, const float* x, const float* target, int batch, float* loss_host);
+/* one Adam update from the stored gradients (bias-corrected). */
+df_status df_mlp_adam_step(df_mlp* m, float lr, float beta1, float beta2, float eps);
+/* df_mlp_gradients + df_mlp_adam_step(lr, 0.9, 0.999, 1e-8). */
+df_status df_mlp_train_step(df_mlp* m, const float* x, const float* target, int batch, float lr, float* loss_host);
+/* flat parameters [W1 (n_in x width, row-major) b1 W2 b2 W3 b3 W4 b4]: set != 0
+ * copies buf into the network, else the network into buf. */
+df_status df_mlp_params(df_mlp* m, float* buf, int set, int is_device);
+df_status df_mlp_grads(df_mlp* m, float* buf, int is_device);
+const char* df_mlp_last_error(const df_mlp* m);
+void df_mlp_destroy(df_mlp* m);
+/* Set the handle's Sigma~ from one network output y (device, [n_wedge][n_w/2][2]
+ * floats: re, im at w_n >= 0 on the irreducible wedge), de-normalised as
+ * y * sd + mean (same layout, device): Sigma~[i][r] = Y[kmap[r]][n] for
+ * n = i - n_w/2 >= 0 and conj Y[kmap[r]][-n-1] for n < 0; kmap (device int
+ * [N]) maps every momentum to its wedge representative.  Rebuilds G~
+ * (Eq. dyson) like df_set_sigma; asynchronous. */
+df_status df_warmstart_sigma(df_ctx* c, const float* y, const float* mean, const float* sd, const int* kmap);
+
 /* Allocation-free variant of the FP64 ladder solves of df_bse (the paper
  * has no counterpart: this is a deployment form).  For callers that cannot
  * allocate device memory at the call, e.g. code inside a host application

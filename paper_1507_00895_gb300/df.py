@@ -39,7 +39,9 @@ EXPORTS = (
     "df_sigma", "df_iterate", "df_get_sigma", "df_set_sigma", "df_get_gtilde", "df_get_chi",
     "df_get_kernel", "df_get_lambda", "df_get_sizes", "df_set_timing", "df_get_timing",
     "df_synchronize", "df_bse_noalloc", "df_batch_init", "df_batch_iterate", "df_batch_get_sigma",
-    "df_batch_reset", "df_batch_autotune", "df_batch_last_error", "df_batch_destroy", "df_last_error",
+    "df_batch_reset", "df_batch_autotune", "df_batch_last_error", "df_batch_destroy", "df_mlp_create",
+    "df_mlp_param_count", "df_mlp_forward", "df_mlp_gradients", "df_mlp_adam_step", "df_mlp_train_step",
+    "df_mlp_params", "df_mlp_grads", "df_mlp_last_error", "df_mlp_destroy", "df_warmstart_sigma", "df_last_error",
     "df_status_string", "df_destroy",
 )
 
@@ -106,6 +108,15 @@ def load(path: str = LIB_PATH):
         "df_batch_get_sigma": [P, C.c_int, P, C.c_int],
         "df_batch_reset": [P],
         "df_batch_autotune": [P, C.c_char_p, I],
+        "df_mlp_create": [C.POINTER(P), C.c_int, C.c_int, C.c_int, C.c_int, C.c_ulonglong, P],
+        "df_mlp_param_count": [P, C.POINTER(C.c_long)],
+        "df_mlp_forward": [P, P, C.c_int, P],
+        "df_mlp_gradients": [P, P, P, C.c_int, C.POINTER(C.c_float)],
+        "df_mlp_adam_step": [P, C.c_float, C.c_float, C.c_float, C.c_float],
+        "df_mlp_train_step": [P, P, P, C.c_int, C.c_float, C.POINTER(C.c_float)],
+        "df_mlp_params": [P, P, C.c_int, C.c_int],
+        "df_mlp_grads": [P, P, C.c_int],
+        "df_warmstart_sigma": [P, P, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -121,6 +132,10 @@ def load(path: str = LIB_PATH):
     lib.df_batch_last_error.restype = C.c_char_p
     lib.df_batch_destroy.argtypes = [P]
     lib.df_batch_destroy.restype = None
+    lib.df_mlp_last_error.argtypes = [P]
+    lib.df_mlp_last_error.restype = C.c_char_p
+    lib.df_mlp_destroy.argtypes = [P]
+    lib.df_mlp_destroy.restype = None
     _lib = lib
     return lib
 
@@ -375,6 +390,85 @@ class DualFermionBatch:
 
     def __exit__(self, *a):
         self.close()
+
+
+class MLP:
+    """The warm-start network (a df_mlp handle): 4 dense layers
+    n_in -> width -> width -> width -> n_out, BF16 tensor-core products with
+    FP32 accumulation, FP32 parameters.  Data arguments are CUDA float32
+    tensors (row-major [batch][features])."""
+
+    def __init__(self, n_in: int, n_out: int, width: int = 512, max_batch: int = 256, seed: int = 0,
+                 stream: Optional[int] = None):
+        self.lib = load()
+        self.dims = (n_in, width, width, width, n_out)
+        self.max_batch = max_batch
+        if stream is None:
+            stream = current_stream_handle()
+        h = C.c_void_p()
+        s = self.lib.df_mlp_create(C.byref(h), n_in, width, n_out, max_batch, seed,
+                                   C.c_void_p(stream) if stream else None)
+        if s != DF_OK:
+            raise DFError(s, "df_mlp_create failed (see stderr)")
+        self.h = h
+        cnt = C.c_long(0)
+        self.lib.df_mlp_param_count(self.h, C.byref(cnt))
+        self.nparam = cnt.value
+
+    def _check(self, s):
+        if s != DF_OK:
+            raise DFError(s, self.lib.df_mlp_last_error(self.h).decode())
+
+    def forward(self, x, y):
+        self._check(self.lib.df_mlp_forward(self.h, C.c_void_p(x.data_ptr()), x.shape[0], C.c_void_p(y.data_ptr())))
+
+    def gradients(self, x, t):
+        loss = C.c_float(0.0)
+        self._check(self.lib.df_mlp_gradients(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(t.data_ptr()),
+                                              x.shape[0], C.byref(loss)))
+        return loss.value
+
+    def adam_step(self, lr: float, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8):
+        self._check(self.lib.df_mlp_adam_step(self.h, lr, b1, b2, eps))
+
+    def train_step(self, x, t, lr: float, want_loss: bool = False):
+        loss = C.c_float(0.0)
+        self._check(self.lib.df_mlp_train_step(self.h, C.c_void_p(x.data_ptr()), C.c_void_p(t.data_ptr()),
+                                               x.shape[0], lr, C.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+    def params(self) -> np.ndarray:
+        out = np.empty(self.nparam, np.float32)
+        self._check(self.lib.df_mlp_params(self.h, out.ctypes.data, 0, 0))
+        return out
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        self._check(self.lib.df_mlp_params(self.h, flat.ctypes.data, 1, 0))
+
+    def grads(self) -> np.ndarray:
+        out = np.empty(self.nparam, np.float32)
+        self._check(self.lib.df_mlp_grads(self.h, out.ctypes.data, 0))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.df_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def warmstart_sigma(d: "DualFermion", y, mean, sd, kmap):
+    """Set d's Sigma~ from one network output (device float32 tensors y, mean,
+    sd of layout [n_wedge][n_w/2][2], kmap int32 [N])."""
+    s = d.lib.df_warmstart_sigma(d.h, C.c_void_p(y.data_ptr()), C.c_void_p(mean.data_ptr()),
+                                 C.c_void_p(sd.data_ptr()), C.c_void_p(kmap.data_ptr()))
+    d._check(s)
 
 
 def mixed_supported(n_w: int) -> bool:

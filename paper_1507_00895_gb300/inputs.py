@@ -299,3 +299,25 @@ def uneven_batch(npts: int = 64, seed: int = 4, max_n_w: int = 128, max_m: int =
         m = int(rng.integers(0, max_m + 1))
         out.append(half_filled_atom(f"batch{i}", dim, nk, U=U, beta=beta, n_w=n_w, m_max=m))
     return out
+
+
+def warmstart_family(npts: int, seed: int, nk: int = 16, n_w: int = 16, m_max: int = 1,
+                     U=(12.0, 28.0), beta=(0.6, 1.4), tp=(-0.3, 0.0), dmu=(-1.0, 1.0)):
+    """Parameter points of the learned warm start: Hubbard-atom inputs around
+    the paper's Example I (U ~ U[12, 28], beta ~ U[0.6, 1.4], t' ~ U[-0.3, 0],
+    mu = U/2 + U[-1, 1]) on a 2D N_k^2 lattice; g of the atom at mu, the
+    half-filled closed-form vertex, Delta = <eps^2> g.  The loop converges
+    for this family (8-17 passes to r <= 1e-10 on 8^2)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(npts):
+        u = float(rng.uniform(*U))
+        b = float(rng.uniform(*beta))
+        t2 = float(rng.uniform(*tp))
+        mu = u / 2.0 + float(rng.uniform(*dmu))
+        g = atom_g(u, b, mu, n_w, m_max)
+        delta = second_moment(2, 1.0, t2) * g
+        guu, gud = atom_vertices(u, b, n_w, m_max)
+        out.append(Workload(f"ws{seed}_{i}", 2, nk, 1.0, t2, u, b, mu, n_w, m_max, g, delta,
+                            guu.astype(np.complex128), gud.astype(np.complex128)))
+    return out
