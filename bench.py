@@ -294,6 +294,40 @@ def batch_bench(df, I, torch, full: bool, passes: int = 3):
     return out
 
 
+def warmstart_bench(df, I, torch, n_train=2000, n_test=200, steps=3000):
+    """Learned warm start: train the 4x512 network (own BF16 kernels) on
+    converged Sigma~ of n_train points of the warm-start family (2D 16^2,
+    n_w=16, N_W=3, U in [12,28], beta in [0.6,1.4], t' in [-0.3,0],
+    mu = U/2 + [-1,1]) and compare passes / device time to
+    max|Sigma~ - Sigma~*| <= 1e-8 max|Sigma~*| on n_test held-out points
+    from Sigma~ = 0 and from the prediction."""
+    from paper_1507_00895_gb300 import warmstart as W
+    t0 = time.perf_counter()
+    train = I.warmstart_family(n_train, seed=5000, nk=16, n_w=16, m_max=1)
+    X, Y, _, mask = W.generate(train, tol=1e-10)
+    t_gen = time.perf_counter() - t0
+    model = W.WarmStart(X.shape[1], Y.shape[1], nk=16, width=512, max_batch=256, seed=0)
+    t0 = time.perf_counter()
+    hist = model.train(X, Y, steps=steps, batch=256, lr=1e-3, log_every=steps // 4)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    rows = W.evaluate(model, I.warmstart_family(n_test, seed=7000, nk=16, n_w=16, m_max=1), tol=1e-8)
+    import numpy as np
+    cold_p = float(np.mean([r["cold_passes"] for r in rows]))
+    warm_p = float(np.mean([r["warm_passes"] for r in rows]))
+    cold_t = float(np.mean([r["cold_ms"] for r in rows]))
+    warm_t = float(np.mean([r["warm_ms"] for r in rows]))
+    return {"workload": "warm-start family, 2D 16^2, n_w=16, N_W=3 (U 12-28, beta 0.6-1.4, t' -0.3-0, "
+                        "mu = U/2 +- 1)", "network": "4 layers, width 512, BF16 products, FP32 accumulate",
+            "train_points_converged": int(mask.sum()), "train_points": n_train, "test_points": n_test,
+            "data_generation_s": t_gen, "training_s": t_train, "train_steps": steps,
+            "loss_history": hist, "cold_passes": cold_p, "warm_passes": warm_p,
+            "cold_ms": cold_t, "warm_ms": warm_t, "pass_reduction": 1.0 - warm_p / cold_p,
+            "prediction_err_mean": float(np.mean([r["prediction_err"] for r in rows])),
+            "fallbacks": int(sum(r["fallback"] for r in rows)),
+            "target": "max|Sigma~ - Sigma~*| <= 1e-8 max|Sigma~*|, Sigma~* = FP64 loop at r <= 1e-12"}
+
+
 def read_peaks():
     try:
         with open(PEAKS_PATH) as f:
@@ -456,6 +490,9 @@ def run_ours(args):
     batch = None
     if rank == 0 and not args.no_batch:
         batch = batch_bench(df, I, torch, args.batch_full)
+    warm = None
+    if rank == 0 and not args.no_warmstart:
+        warm = warmstart_bench(df, I, torch)
 
     if rank != 0:
         if world > 1:
@@ -478,7 +515,7 @@ def run_ours(args):
             "gpu_launches": main["gpu_launches"], "kernel_ms_per_step": main["kernel_ms_per_step"],
             "err_vs_fp64_first_pass": main.get("err_vs_fp64_first_pass"),
             "plain_fp64": plain if prec != df.DF_FP64 else None,
-            "time_to_converged": ttc, "batch": batch, "clocks": main["clocks"]}
+            "time_to_converged": ttc, "batch": batch, "warm_start": warm, "clocks": main["clocks"]}
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -497,6 +534,7 @@ def main():
     ap.add_argument("--no-ttc", action="store_true", help="skip the time-to-converged comparison")
     ap.add_argument("--no-batch", action="store_true", help="skip the uneven-batch throughput")
     ap.add_argument("--batch-full", action="store_true", help="uneven batch at the recipe's full sizes")
+    ap.add_argument("--no-warmstart", action="store_true", help="skip the learned warm-start measurement")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)       # at least 3 untimed warm-up steps
     if args.impl == "reference":

@@ -45,9 +45,9 @@ def test_forward_matches_oracle(env):
     ref = M.forward(net.params().astype(np.float64), DIMS, x, rounding=True)[-1]
     err = nrel(y.cpu().numpy(), ref)
     print(f"forward err {err:.2e}")
-    # same BF16 operands; FP32 vs FP64 accumulation can flip the BF16 rounding
-    # of a later layer's input, one BF16 ulp (2^-8) on an element
-    assert err < 2e-3
+    # same BF16 operands; FP32 vs FP64 accumulation (a rare BF16 rounding flip
+    # of a later layer's input would show as ~1e-3)
+    assert err < 1e-4
 
 
 def test_gradients_match_oracle(env):
@@ -65,7 +65,7 @@ def test_gradients_match_oracle(env):
             worst = max(worst, nrel(g[part], ref_g[part]))
         o += nW + DIMS[l + 1]
     print(f"gradient worst layer err {worst:.2e}")
-    assert worst < 2e-2
+    assert worst < 5e-3
     # and against the exact FP64 chain rule, to BF16 accuracy
     _, g64 = M.loss_and_grads(net.params().astype(np.float64), DIMS, x, t, rounding=False)
     assert nrel(g, g64) < 5e-2
