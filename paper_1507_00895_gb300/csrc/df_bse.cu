@@ -51,31 +51,59 @@ bse_f64_kernel(Dims dm, int ch0, int nch, int nc, const double2* __restrict__ ga
 }
 
 // ---------------------------------------------------------------------------
-// leading eigenvalue of A = gamma_W diag(chi~_W(q)) by FP64 power iteration
-// with a Rayleigh-quotient estimate.  One CTA handles kEigQ systems that
-// share (channel, W): gamma_W is staged in shared memory once (when it
-// fits) and each thread owns (row, system) pairs of y = A v, so one
-// iteration is n^2 complex multiply-adds per system with no reductions
-// except the per-system Rayleigh quotient.  A system is "converged" when
-// the estimate changes by less than tol relative; iterations stop when all
-// kEigQ systems converged or after kEigMaxIter.
+// leading eigenvalue of A = gamma_W diag(chi~_W(q)): power iteration with a
+// Rayleigh-quotient estimate, first in FP32 (gamma staged in shared memory
+// as complex64) until the estimate settles to FP32 precision, then polished
+// in FP64 from that vector (gamma read in FP64 through L1/L2).  The
+// reported value and its converged flag are those of the FP64 phase.  One
+// CTA handles kEigQ systems that share (channel, W); each thread owns
+// (row, system) pairs of y = A v.
 // ---------------------------------------------------------------------------
 constexpr int kEigQ = 8;
 constexpr int kEigThreads = 256;
-constexpr int kEigMaxIter = 64;
+constexpr int kEigIter32 = 64;
+constexpr int kEigIter64 = 24;
+
+template <typename C, typename R>
+__device__ __forceinline__ void eig_rayleigh(int n, int warp, int lane, const C* v, const C* y, C* lam_new, R* nrm) {
+  if (warp < kEigQ) {
+    const int t = warp;
+    C rq = mk((R)0, (R)0);
+    R yy = 0;
+    for (int j = lane; j < n; j += 32) {
+      const C vj = v[j * kEigQ + t], yj = y[j * kEigQ + t];
+      rq = cfma(cconj(vj), yj, rq);
+      yy += cabs2(yj);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      rq.x += __shfl_xor_sync(0xffffffffu, rq.x, o);
+      rq.y += __shfl_xor_sync(0xffffffffu, rq.y, o);
+      yy += __shfl_xor_sync(0xffffffffu, yy, o);
+    }
+    if (lane == 0) {
+      lam_new[t] = rq;
+      nrm[t] = yy > (R)0 ? (R)1 / sqrt(yy) : (R)0;
+    }
+  }
+}
 
 __global__ void __launch_bounds__(kEigThreads)
-lambda_kernel(Dims dm, int ch0, int a0, int na, int g_in_smem, double tol, const double2* __restrict__ gam,
+lambda_kernel(Dims dm, int ch0, int a0, int na, int unused, double tol, const double2* __restrict__ gam,
               const double2* __restrict__ chi, double2* __restrict__ lam, int* __restrict__ ok,
               int* __restrict__ flags) {
   extern __shared__ double2 sm[];
   const int n = dm.n_w, N = dm.N, nb = dm.nb;
-  double2* v = sm;                 // [n][kEigQ] current unit vector
-  double2* xq = v + n * kEigQ;     // [n][kEigQ] chi~ of the kEigQ systems
-  double2* y = xq + n * kEigQ;     // [n][kEigQ] A v
-  double2* Gs = y + n * kEigQ;     // [n][n] gamma_W (if g_in_smem)
+  double2* v = sm;                       // [n][kEigQ]
+  double2* xq = v + n * kEigQ;
+  double2* y = xq + n * kEigQ;
+  float2* G32 = (float2*)(y + n * kEigQ);  // [n][n]
+  float2* v32 = G32 + n * n;
+  float2* x32 = v32 + n * kEigQ;
+  float2* y32 = x32 + n * kEigQ;
   __shared__ double2 lam_old[kEigQ], lam_new[kEigQ];
+  __shared__ float2 l32_old[kEigQ], l32_new[kEigQ];
   __shared__ double nrm[kEigQ];
+  __shared__ float nrm32[kEigQ];
   __shared__ int done[kEigQ];
   const int qtiles = (N + kEigQ - 1) / kEigQ;
   const int tile = blockIdx.x % qtiles;
@@ -85,58 +113,68 @@ lambda_kernel(Dims dm, int ch0, int a0, int na, int g_in_smem, double tol, const
   const int q0 = tile * kEigQ;
   const int nq = min(kEigQ, N - q0);
   const double2* Gg = gam + ((size_t)c * nb + a) * n * n;
-  const double2* G = g_in_smem ? Gs : Gg;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const double inv_sqrt_n = rsqrt((double)n);
 
-  if (g_in_smem)
-    for (int idx = tid; idx < n * n; idx += blockDim.x) Gs[idx] = Gg[idx];
+  for (int idx = tid; idx < n * n; idx += blockDim.x) {
+    const double2 g = Gg[idx];
+    G32[idx] = make_float2((float)g.x, (float)g.y);
+  }
   for (int idx = tid; idx < n * kEigQ; idx += blockDim.x) {
     const int j = idx / kEigQ, t = idx % kEigQ;
-    xq[idx] = (t < nq) ? chi[((size_t)a * n + j) * N + q0 + t] : mk(0.0, 0.0);
-    v[idx] = mk(inv_sqrt_n, 0.0);
+    const double2 x = (t < nq) ? chi[((size_t)a * n + j) * N + q0 + t] : mk(0.0, 0.0);
+    xq[idx] = x;
+    x32[idx] = make_float2((float)x.x, (float)x.y);
+    v32[idx] = make_float2(rsqrtf((float)n), 0.f);
   }
   if (tid < kEigQ) {
+    l32_old[tid] = make_float2(0.f, 0.f);
+    l32_new[tid] = make_float2(0.f, 0.f);
     lam_old[tid] = mk(0.0, 0.0);
     lam_new[tid] = mk(0.0, 0.0);
     done[tid] = (tid < nq) ? 0 : 1;
   }
   __syncthreads();
-  for (int it = 0; it < kEigMaxIter; ++it) {
-    // y[i][t] = sum_j G[i][j] chi[j][t] v[j][t]
-    for (int pidx = tid; pidx < n * kEigQ; pidx += blockDim.x) {
-      const int i = pidx / kEigQ, t = pidx % kEigQ;
-      double2 acc = mk(0.0, 0.0);
-      for (int j = 0; j < n; ++j)
-        acc = cfma(G[i * n + j], cmul(xq[j * kEigQ + t], v[j * kEigQ + t]), acc);
-      y[pidx] = acc;
+  // ---- FP32 phase ----
+  for (int it = 0; it < kEigIter32; ++it) {
+    for (int p = tid; p < n * kEigQ; p += blockDim.x) {
+      const int i = p / kEigQ, t = p % kEigQ;
+      float2 acc = make_float2(0.f, 0.f);
+      for (int j = 0; j < n; ++j) acc = cfma(G32[i * n + j], cmul(x32[j * kEigQ + t], v32[j * kEigQ + t]), acc);
+      y32[p] = acc;
     }
     __syncthreads();
-    // per system: Rayleigh quotient v^H y (|v| = 1) and 1/|y|
-    if (warp < kEigQ) {
-      const int t = warp;
-      double2 rq = mk(0.0, 0.0);
-      double yy = 0.0;
-      for (int j = lane; j < n; j += 32) {
-        const double2 vj = v[j * kEigQ + t], yj = y[j * kEigQ + t];
-        rq = cfma(cconj(vj), yj, rq);
-        yy += cabs2(yj);
-      }
-      for (int o = 16; o > 0; o >>= 1) {
-        rq.x += __shfl_xor_sync(0xffffffffu, rq.x, o);
-        rq.y += __shfl_xor_sync(0xffffffffu, rq.y, o);
-        yy += __shfl_xor_sync(0xffffffffu, yy, o);
-      }
-      if (lane == 0) {
-        lam_new[t] = rq;
-        nrm[t] = yy > 0.0 ? rsqrt(yy) : 0.0;
-      }
+    eig_rayleigh<float2, float>(n, warp, lane, v32, y32, l32_new, nrm32);
+    __syncthreads();
+    for (int idx = tid; idx < n * kEigQ; idx += blockDim.x) v32[idx] = cscale(y32[idx], nrm32[idx % kEigQ]);
+    if (tid < kEigQ && !done[tid]) {
+      const float2 d = l32_new[tid] - l32_old[tid];
+      if (sqrtf(cabs2(d)) <= 2e-6f * sqrtf(cabs2(l32_new[tid]))) done[tid] = 1;
+      l32_old[tid] = l32_new[tid];
     }
+    __syncthreads();
+    int all = 1;
+#pragma unroll
+    for (int t = 0; t < kEigQ; ++t) all &= done[t];
+    if (all) break;
+  }
+  // ---- FP64 polish from the FP32 vector ----
+  for (int idx = tid; idx < n * kEigQ; idx += blockDim.x) v[idx] = mk((double)v32[idx].x, (double)v32[idx].y);
+  if (tid < kEigQ) done[tid] = (tid < nq) ? 0 : 1;
+  __syncthreads();
+  for (int it = 0; it < kEigIter64; ++it) {
+    for (int p = tid; p < n * kEigQ; p += blockDim.x) {
+      const int i = p / kEigQ, t = p % kEigQ;
+      double2 acc = mk(0.0, 0.0);
+      for (int j = 0; j < n; ++j) acc = cfma(Gg[(size_t)i * n + j], cmul(xq[j * kEigQ + t], v[j * kEigQ + t]), acc);
+      y[p] = acc;
+    }
+    __syncthreads();
+    eig_rayleigh<double2, double>(n, warp, lane, v, y, lam_new, nrm);
     __syncthreads();
     for (int idx = tid; idx < n * kEigQ; idx += blockDim.x) v[idx] = cscale(y[idx], nrm[idx % kEigQ]);
     if (tid < kEigQ && !done[tid]) {
       const double2 d = lam_new[tid] - lam_old[tid];
-      if (sqrt(cabs2(d)) <= tol * sqrt(cabs2(lam_new[tid]))) done[tid] = 1;
+      if (it > 0 && sqrt(cabs2(d)) <= tol * sqrt(cabs2(lam_new[tid]))) done[tid] = 1;
       lam_old[tid] = lam_new[tid];
     }
     __syncthreads();
@@ -224,8 +262,9 @@ cudaError_t launch_lambda(df_ctx* c, int channel_mask) {
   const int a0 = (c->opts.eig_mode == 1) ? dm.m_max : 0;
   const int na = (c->opts.eig_mode == 1) ? 1 : dm.nb;
   const int qtiles = (dm.N + kEigQ - 1) / kEigQ;
-  const int g_in_smem = dm.n_w <= 96;
-  const size_t smem = sizeof(double2) * (3 * dm.n_w * kEigQ + (g_in_smem ? dm.n_w * dm.n_w : 0));
+  const int g_in_smem = 0;
+  const size_t smem = sizeof(double2) * 3 * dm.n_w * kEigQ +
+                      sizeof(float2) * ((size_t)dm.n_w * dm.n_w + 3 * dm.n_w * kEigQ);
   cudaError_t e = cudaFuncSetAttribute((const void*)lambda_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
