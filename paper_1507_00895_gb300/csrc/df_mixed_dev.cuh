@@ -23,13 +23,17 @@
 // identity block (gamma = 0, chi~ = 0 there), which leaves the solution of
 // the first n rows unchanged.
 #pragma once
+#include <cuda_bf16.h>
+
 #include "df_internal.cuh"
 
 namespace df {
 
 
 constexpr int kTile = 4;          // rows / columns per thread
-constexpr int kResChunk = 16;     // gamma columns staged per residual sweep
+constexpr int kResChunk = 16;     // gamma columns staged per residual sweep (SIMT residual)
+constexpr int kSlices = 7;        // base-256 digits of the tensor-core residual (56 bits)
+constexpr int kCB = 16;           // column block of the tensor-core residual
 
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
@@ -78,10 +82,102 @@ __device__ __forceinline__ void df_fma(float& hi, float& lo, float a, float b) {
   lo += e;
 }
 
+
+// ---- tensor-core residual helpers --------------------------------------
+
+// |v| < 2^e: the 7 signed base-256 digits d_s of v / 2^e, v ~ sum_s d_s 2^(e - 8(s+1)),
+// truncated below 2^(e - 56).  Read from the FP64 bits (integer operations only).
+__device__ __forceinline__ void digits_f64(double v, int e, float* d) {
+  const long long bits = __double_as_longlong(v);
+  int E = (int)((bits >> 52) & 0x7FF);
+  unsigned long long M = (unsigned long long)bits & 0xFFFFFFFFFFFFFull;
+  if (E == 0) {
+    if (M == 0) {
+#pragma unroll
+      for (int s = 0; s < kSlices; ++s) d[s] = 0.f;
+      return;
+    }
+    E = 1;
+  } else {
+    M |= (1ull << 52);
+  }
+  const int sh = e - (E - 1023) - 1;                 // >= 0
+  const unsigned long long T = sh <= 3 ? (M << (3 - sh)) : (sh - 3 >= 64 ? 0ull : (M >> (sh - 3)));
+  const float sg = bits < 0 ? -1.f : 1.f;
+#pragma unroll
+  for (int s = 0; s < kSlices; ++s) d[s] = sg * (float)(unsigned)((T >> (48 - 8 * s)) & 0xFFull);
+}
+
+// the same for an FP32 value
+__device__ __forceinline__ void digits_f32(float v, int e, float* d) {
+  const unsigned bits = __float_as_uint(v);
+  int E = (int)((bits >> 23) & 0xFF);
+  unsigned M = bits & 0x7FFFFFu;
+  if (E == 0) {
+    if (M == 0) {
+#pragma unroll
+      for (int s = 0; s < kSlices; ++s) d[s] = 0.f;
+      return;
+    }
+    E = 1;
+  } else {
+    M |= 0x800000u;
+  }
+  const int sh = e - (E - 127) - 1;                  // >= 0
+  const unsigned long long T = sh <= 32 ? ((unsigned long long)M << (32 - sh))
+                                        : (sh - 32 >= 32 ? 0ull : (unsigned long long)(M >> (sh - 32)));
+  const float sg = (bits >> 31) ? -1.f : 1.f;
+#pragma unroll
+  for (int s = 0; s < kSlices; ++s) d[s] = sg * (float)(unsigned)((T >> (48 - 8 * s)) & 0xFFull);
+}
+
+// exponent e with |v| < 2^e (v != 0): unbiased exponent + 1
+__device__ __forceinline__ int exp_bound_f32(float v) {
+  const unsigned bits = __float_as_uint(v) & 0x7FFFFFFFu;
+  if (bits == 0) return -1000;
+  const int E = (int)(bits >> 23);
+  return (E == 0 ? -126 : E - 127) + 1;
+}
+
+// digit matrices: rows of 64 bf16 (32 words); word w of row r stored at
+// w ^ ((r & 7) << 2), so that fragment loads (8 rows x 4 words) hit 32 banks
+__device__ __forceinline__ int swz(int row, int k) {
+  return row * 64 + ((((k >> 1) ^ ((row & 7) << 2))) << 1) + (k & 1);
+}
+__device__ __forceinline__ unsigned ld_frag(const __nv_bfloat16* base, int row, int k) {
+  return *reinterpret_cast<const unsigned*>(base + swz(row, k));
+}
+
+__device__ __forceinline__ void mma_bf16(float* d, const unsigned* a, unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
+      "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ void dd_add(float& hi, float& lo, float v) {
+  float s, e;
+  two_sum(hi, v, s, e);
+  e += lo;
+  hi = s + e;
+  lo = e - (hi - s);
+}
+
 struct MixedSmem {
-  // offsets in float2 units
-  int x0, chih, chil, ubuf, lbuf, invu, x0d, gt_h, gt_l, yh, yl, chi64, total;
+  // offsets in float2 units (8 bytes)
+  int x0, chih, chil, ubuf, lbuf, invu, x0d, chi64, work, gt_h, gt_l, yh, yl, total;
 };
+
+// bytes of the tensor-core residual's work area (n_pad in {32, 64})
+__host__ __device__ inline int tc_work_bytes(int np) {
+  return 2 * kSlices * 2 * np * 64        // Z digits, bf16 [slice][re/im][row][64]
+         + 2 * kSlices * 2 * kCB * 64     // X0 digits of one column block, bf16 [slice][re/im][col][64]
+         + 8 * np * kCB                   // R of one column block, float2 [row][kCB]
+         + 4 * (np + kCB);                // row / column exponents
+}
+
+__host__ __device__ inline bool use_tc_residual(int np) { return np == 32 || np == 64; }
 
 __host__ __device__ inline MixedSmem mixed_layout(int np) {
   MixedSmem L;
@@ -93,11 +189,16 @@ __host__ __device__ inline MixedSmem mixed_layout(int np) {
   L.lbuf = o; o += 2 * np;         // column broadcast, double buffered
   L.invu = o; o += np;
   L.x0d = o;  o += np;             // diag X0 (FP32)
-  L.gt_h = o; o += kResChunk * np; // gamma tile, [l][row], hi
-  L.gt_l = o; o += kResChunk * np; // lo
-  L.yh = o;   o += np * np;        // Y = chi o X0, hi
-  L.yl = o;   o += np * np;        // lo
   L.chi64 = o; o += 2 * np;        // chi~ in FP64 (double2 = two float2 slots)
+  L.work = o;                      // residual work area (one of the two layouts below)
+  // SIMT residual: gamma tiles and Y = chi o X0 as double-float
+  L.gt_h = o;
+  L.gt_l = L.gt_h + kResChunk * np;
+  L.yh = L.gt_l + kResChunk * np;
+  L.yl = L.yh + np * np;
+  const int simt = 2 * kResChunk * np + 2 * np * np;
+  const int tc = (tc_work_bytes(np) + 7) / 8;
+  o += use_tc_residual(np) ? tc : simt;
   L.total = o;
   return L;
 }
@@ -107,6 +208,7 @@ struct MixedPtrs {
   float2 *X0s, *chih, *chil, *ubuf, *lbuf, *invu, *x0d, *gth, *gtl, *Yh, *Yl;
   double2* chi64;
   int* piv_s;
+  unsigned char* work;
 };
 
 __device__ __forceinline__ MixedPtrs mixed_ptrs(float2* smf, int np, int* piv_s) {
@@ -124,6 +226,7 @@ __device__ __forceinline__ MixedPtrs mixed_ptrs(float2* smf, int np, int* piv_s)
   m.Yh = smf + L.yh;
   m.Yl = smf + L.yl;
   m.chi64 = (double2*)(smf + L.chi64);
+  m.work = (unsigned char*)(smf + L.work);
   m.piv_s = piv_s;
   return m;
 }
@@ -302,93 +405,235 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
   }
   __syncthreads();
   for (int j = t; j < np; j += blockDim.x) x0d[j] = X0s[j * np + j];
-  // Y = chi o X0 as double-float pairs, once per system
-  for (int idx = t; idx < np * np; idx += blockDim.x) {
-    const int l = idx / np;
-    const float2 xh = chih[l], xl = chil[l];
-    const float2 x = X0s[idx];
-    float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
-    df_fma(rh, rl, xh.x, x.x);
-    df_fma(rh, rl, -xh.y, x.y);
-    df_fma(ih, il, xh.x, x.y);
-    df_fma(ih, il, xh.y, x.x);
-    rl = fmaf(xl.x, x.x, fmaf(-xl.y, x.y, rl));
-    il = fmaf(xl.x, x.y, fmaf(xl.y, x.x, il));
-    float sv, ev;
-    two_sum(rh, rl, sv, ev); rh = sv; rl = ev;
-    two_sum(ih, il, sv, ev); ih = sv; il = ev;
-    Yh[idx] = make_float2(rh, ih);
-    Yl[idx] = make_float2(rl, il);
-  }
-
-  // ---- residual R = gamma - X0 + gamma (chi o X0), ~48-bit accurate ----
-  const int lc = np < kResChunk ? np : kResChunk;   // gamma columns per staged tile (divides np)
-  // two passes of 2 rows each keep the double-float accumulators in registers
+  if (use_tc_residual(np)) {
+    // ---- residual R = gamma - X0 + Z X0 on the tensor cores, Z = gamma diag(chi~) ----
+    // Z (FP64 products) and X0 (FP32) are cut into 7 base-256 digits relative to
+    // per-row / per-column powers of two; each digit pair's product is exact in
+    // the FP32 accumulator (|d| <= 255, 64 terms, two products: < 2^23), and the
+    // 28 pairs with weight >= 2^-64 are folded, scaled, into a double-float sum.
+    __nv_bfloat16* zs = reinterpret_cast<__nv_bfloat16*>(sp.work);    // [kSlices][2][np][64]
+    __nv_bfloat16* xs = zs + (size_t)kSlices * 2 * np * 64;          // [kSlices][2][kCB][64]
+    float2* Rst = reinterpret_cast<float2*>(xs + (size_t)kSlices * 2 * kCB * 64);   // [np][kCB]
+    int* rowe = reinterpret_cast<int*>(Rst + np * kCB);              // [np]
+    int* cole = rowe + np;                                           // [kCB]
+    const int nthr = blockDim.x;
+    for (int i = t; i < np; i += nthr) rowe[i] = -1000;
+    __syncthreads();
+    for (int idx = t; idx < np * np; idx += nthr) {
+      const int i = idx / np, l = idx - i * np;
+      if (i < n && l < n) {
+        const float2 gg2 = Gh[i * n + l];
+        const float2 xx = chih[l];
+        const float u = (fabsf(gg2.x) + fabsf(gg2.y)) * (fabsf(xx.x) + fabsf(xx.y)) * 1.0001f;
+        if (u > 0.f) atomicMax(&rowe[i], exp_bound_f32(u));
+      }
+    }
+    __syncthreads();
+    for (int idx = t; idx < np * np; idx += nthr) {
+      const int i = idx / np, l = idx - i * np;
+      float dr[kSlices], di[kSlices];
+      if (i < n && l < n && rowe[i] > -1000) {
+        const double2 z = cmul(gam[mat + (size_t)i * n + l], sp.chi64[l]);
+        digits_f64(z.x, rowe[i], dr);
+        digits_f64(z.y, rowe[i], di);
+      } else {
 #pragma unroll
-  for (int half = 0; half < 2; ++half) {
-    float acc[2][kTile][6];   // [row][col][re_hi, re_lo, im_hi, im_lo, re_small, im_small]
+        for (int q2 = 0; q2 < kSlices; ++q2) dr[q2] = di[q2] = 0.f;
+      }
+      const int o = swz(i, l);
 #pragma unroll
-    for (int i2 = 0; i2 < 2; ++i2)
-#pragma unroll
-      for (int jj = 0; jj < kTile; ++jj)
-#pragma unroll
-        for (int e = 0; e < 6; ++e) acc[i2][jj][e] = 0.f;
-    for (int l0 = 0; l0 < np; l0 += lc) {
+      for (int q2 = 0; q2 < kSlices; ++q2) {
+        zs[(size_t)(q2 * 2 + 0) * np * 64 + o] = __float2bfloat16_rn(dr[q2]);
+        zs[(size_t)(q2 * 2 + 1) * np * 64 + o] = __float2bfloat16_rn(di[q2]);
+      }
+    }
+    const int warp = t >> 5, lane = t & 31, gq = lane >> 2, t4 = lane & 3;
+    const int nwarp = nthr >> 5;
+    const int tiles = (np / 16) * (kCB / 8);
+    for (int b = 0; b < np / kCB; ++b) {
       __syncthreads();
-      for (int idx = t; idx < lc * np; idx += blockDim.x) {
-        const int r = idx / lc, ll = idx - r * lc;
-        const int l = l0 + ll;
-        const bool in = (r < n && l < n);
-        gth[ll * np + r] = in ? Gh[r * n + l] : make_float2(0.f, 0.f);
-        gtl[ll * np + r] = in ? Gl[r * n + l] : make_float2(0.f, 0.f);
+      for (int c2 = t; c2 < kCB; c2 += nthr) cole[c2] = -1000;
+      __syncthreads();
+      for (int idx = t; idx < kCB * np; idx += nthr) {
+        const int c2 = idx / np, l = idx - c2 * np;
+        const float2 x = X0s[l * np + b * kCB + c2];
+        const float m = fmaxf(fabsf(x.x), fabsf(x.y));
+        if (m > 0.f) atomicMax(&cole[c2], exp_bound_f32(m));
       }
       __syncthreads();
-      for (int ll = 0; ll < lc; ++ll) {
-        const int l = l0 + ll;
-        float2 yh[kTile], yl[kTile];
+      for (int idx = t; idx < kCB * np; idx += nthr) {
+        const int c2 = idx / np, l = idx - c2 * np;
+        const float2 x = X0s[l * np + b * kCB + c2];
+        float dr[kSlices], di[kSlices];
+        if (cole[c2] > -1000) {
+          digits_f32(x.x, cole[c2], dr);
+          digits_f32(x.y, cole[c2], di);
+        } else {
 #pragma unroll
-        for (int jj = 0; jj < kTile; ++jj) {
-          yh[jj] = Yh[l * np + tc + P * jj];
-          yl[jj] = Yl[l * np + tc + P * jj];
+          for (int q2 = 0; q2 < kSlices; ++q2) dr[q2] = di[q2] = 0.f;
+        }
+        const int o = swz(c2, l);
+#pragma unroll
+        for (int q2 = 0; q2 < kSlices; ++q2) {
+          xs[(size_t)(q2 * 2 + 0) * kCB * 64 + o] = __float2bfloat16_rn(dr[q2]);
+          xs[(size_t)(q2 * 2 + 1) * kCB * 64 + o] = __float2bfloat16_rn(di[q2]);
+        }
+      }
+      __syncthreads();
+      for (int tile = warp; tile < tiles; tile += nwarp) {
+        const int r16 = (tile / (kCB / 8)) * 16, c8 = (tile % (kCB / 8)) * 8;
+        float hr[4] = {0.f, 0.f, 0.f, 0.f}, lr[4] = {0.f, 0.f, 0.f, 0.f};
+        float hm[4] = {0.f, 0.f, 0.f, 0.f}, lm[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int sa = 0; sa < kSlices; ++sa) {
+          const __nv_bfloat16* zr = zs + (size_t)(sa * 2 + 0) * np * 64;
+          const __nv_bfloat16* zi = zs + (size_t)(sa * 2 + 1) * np * 64;
+          for (int sb = 0; sa + sb < kSlices; ++sb) {
+            const __nv_bfloat16* xr = xs + (size_t)(sb * 2 + 0) * kCB * 64;
+            const __nv_bfloat16* xi = xs + (size_t)(sb * 2 + 1) * kCB * 64;
+            float ar[4] = {0.f, 0.f, 0.f, 0.f}, ai[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int kk = 0; kk < np; kk += 16) {
+              unsigned fr[4], fi[4], fn[4];
+              fr[0] = ld_frag(zr, r16 + gq, kk + 2 * t4);
+              fr[1] = ld_frag(zr, r16 + gq + 8, kk + 2 * t4);
+              fr[2] = ld_frag(zr, r16 + gq, kk + 2 * t4 + 8);
+              fr[3] = ld_frag(zr, r16 + gq + 8, kk + 2 * t4 + 8);
+              fi[0] = ld_frag(zi, r16 + gq, kk + 2 * t4);
+              fi[1] = ld_frag(zi, r16 + gq + 8, kk + 2 * t4);
+              fi[2] = ld_frag(zi, r16 + gq, kk + 2 * t4 + 8);
+              fi[3] = ld_frag(zi, r16 + gq + 8, kk + 2 * t4 + 8);
+#pragma unroll
+              for (int q2 = 0; q2 < 4; ++q2) fn[q2] = fi[q2] ^ 0x80008000u;   // -Zi
+              const unsigned br0 = ld_frag(xr, c8 + gq, kk + 2 * t4), br1 = ld_frag(xr, c8 + gq, kk + 2 * t4 + 8);
+              const unsigned bi0 = ld_frag(xi, c8 + gq, kk + 2 * t4), bi1 = ld_frag(xi, c8 + gq, kk + 2 * t4 + 8);
+              mma_bf16(ar, fr, br0, br1);    // + Zr Xr
+              mma_bf16(ar, fn, bi0, bi1);    // - Zi Xi
+              mma_bf16(ai, fr, bi0, bi1);    // + Zr Xi
+              mma_bf16(ai, fi, br0, br1);    // + Zi Xr
+            }
+            const int sc = -8 * (sa + sb + 2);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              const int row = r16 + gq + (e >= 2 ? 8 : 0), col = c8 + 2 * t4 + (e & 1);
+              if (rowe[row] > -1000 && cole[col] > -1000) {
+                const int ex = rowe[row] + cole[col] + sc;
+                dd_add(hr[e], lr[e], ldexpf(ar[e], ex));
+                dd_add(hm[e], lm[e], ldexpf(ai[e], ex));
+              }
+            }
+          }
         }
 #pragma unroll
-        for (int i2 = 0; i2 < 2; ++i2) {
-          const int r = tr + P * (2 * half + i2);
-          const float2 gh = gth[ll * np + r], gl = gtl[ll * np + r];
+        for (int e = 0; e < 4; ++e) {
+          const int row = r16 + gq + (e >= 2 ? 8 : 0), col = c8 + 2 * t4 + (e & 1);
+          const int j = b * kCB + col;
+          const double2 gv = (row < n && j < n) ? gam[mat + (size_t)row * n + j] : mk(0.0, 0.0);
+          const float2 x = X0s[row * np + j];
+          const double re = gv.x - (double)x.x + ((double)hr[e] + (double)lr[e]);
+          const double im = gv.y - (double)x.y + ((double)hm[e] + (double)lm[e]);
+          Rst[row * kCB + col] = make_float2((float)re, (float)im);
+        }
+      }
+      __syncthreads();
+      // hand this column block of R to the owners of its columns (cyclic layout)
 #pragma unroll
+      for (int ii = 0; ii < kTile; ++ii) {
+#pragma unroll
+        for (int jj = 0; jj < kTile; ++jj) {
+          const int col = tc + P * jj;
+          if (col >= b * kCB && col < (b + 1) * kCB) A[ii][kTile + jj] = Rst[(tr + P * ii) * kCB + (col - b * kCB)];
+        }
+      }
+    }
+    __syncthreads();
+  } else {
+    // Y = chi o X0 as double-float pairs, once per system
+    for (int idx = t; idx < np * np; idx += blockDim.x) {
+      const int l = idx / np;
+      const float2 xh = chih[l], xl = chil[l];
+      const float2 x = X0s[idx];
+      float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+      df_fma(rh, rl, xh.x, x.x);
+      df_fma(rh, rl, -xh.y, x.y);
+      df_fma(ih, il, xh.x, x.y);
+      df_fma(ih, il, xh.y, x.x);
+      rl = fmaf(xl.x, x.x, fmaf(-xl.y, x.y, rl));
+      il = fmaf(xl.x, x.y, fmaf(xl.y, x.x, il));
+      float sv, ev;
+      two_sum(rh, rl, sv, ev); rh = sv; rl = ev;
+      two_sum(ih, il, sv, ev); ih = sv; il = ev;
+      Yh[idx] = make_float2(rh, ih);
+      Yl[idx] = make_float2(rl, il);
+    }
+
+    // ---- residual R = gamma - X0 + gamma (chi o X0), ~48-bit accurate ----
+    const int lc = np < kResChunk ? np : kResChunk;   // gamma columns per staged tile (divides np)
+    // two passes of 2 rows each keep the double-float accumulators in registers
+  #pragma unroll
+    for (int half = 0; half < 2; ++half) {
+      float acc[2][kTile][6];   // [row][col][re_hi, re_lo, im_hi, im_lo, re_small, im_small]
+  #pragma unroll
+      for (int i2 = 0; i2 < 2; ++i2)
+  #pragma unroll
+        for (int jj = 0; jj < kTile; ++jj)
+  #pragma unroll
+          for (int e = 0; e < 6; ++e) acc[i2][jj][e] = 0.f;
+      for (int l0 = 0; l0 < np; l0 += lc) {
+        __syncthreads();
+        for (int idx = t; idx < lc * np; idx += blockDim.x) {
+          const int r = idx / lc, ll = idx - r * lc;
+          const int l = l0 + ll;
+          const bool in = (r < n && l < n);
+          gth[ll * np + r] = in ? Gh[r * n + l] : make_float2(0.f, 0.f);
+          gtl[ll * np + r] = in ? Gl[r * n + l] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        for (int ll = 0; ll < lc; ++ll) {
+          const int l = l0 + ll;
+          float2 yh[kTile], yl[kTile];
+  #pragma unroll
           for (int jj = 0; jj < kTile; ++jj) {
-            float* ac = acc[i2][jj];
-            // real: gh.x yh.x - gh.y yh.y (+ cross terms in lo)
-            dd_fma(ac[0], ac[1], gh.x, yh[jj].x);
-            dd_fma(ac[0], ac[1], -gh.y, yh[jj].y);
-            ac[4] = fmaf(gh.x, yl[jj].x, fmaf(-gh.y, yl[jj].y, ac[4]));
-            ac[4] = fmaf(gl.x, yh[jj].x, fmaf(-gl.y, yh[jj].y, ac[4]));
-            // imag: gh.x yh.y + gh.y yh.x
-            dd_fma(ac[2], ac[3], gh.x, yh[jj].y);
-            dd_fma(ac[2], ac[3], gh.y, yh[jj].x);
-            ac[5] = fmaf(gh.x, yl[jj].y, fmaf(gh.y, yl[jj].x, ac[5]));
-            ac[5] = fmaf(gl.x, yh[jj].y, fmaf(gl.y, yh[jj].x, ac[5]));
+            yh[jj] = Yh[l * np + tc + P * jj];
+            yl[jj] = Yl[l * np + tc + P * jj];
+          }
+  #pragma unroll
+          for (int i2 = 0; i2 < 2; ++i2) {
+            const int r = tr + P * (2 * half + i2);
+            const float2 gh = gth[ll * np + r], gl = gtl[ll * np + r];
+  #pragma unroll
+            for (int jj = 0; jj < kTile; ++jj) {
+              float* ac = acc[i2][jj];
+              // real: gh.x yh.x - gh.y yh.y (+ cross terms in lo)
+              dd_fma(ac[0], ac[1], gh.x, yh[jj].x);
+              dd_fma(ac[0], ac[1], -gh.y, yh[jj].y);
+              ac[4] = fmaf(gh.x, yl[jj].x, fmaf(-gh.y, yl[jj].y, ac[4]));
+              ac[4] = fmaf(gl.x, yh[jj].x, fmaf(-gl.y, yh[jj].y, ac[4]));
+              // imag: gh.x yh.y + gh.y yh.x
+              dd_fma(ac[2], ac[3], gh.x, yh[jj].y);
+              dd_fma(ac[2], ac[3], gh.y, yh[jj].x);
+              ac[5] = fmaf(gh.x, yl[jj].y, fmaf(gh.y, yl[jj].x, ac[5]));
+              ac[5] = fmaf(gl.x, yh[jj].y, fmaf(gl.y, yh[jj].x, ac[5]));
+            }
           }
         }
       }
-    }
-    // R = gamma - X0 + acc, in FP64, rounded to FP32 into the RHS registers
-#pragma unroll
-    for (int i2 = 0; i2 < 2; ++i2) {
-      const int ii = 2 * half + i2;
-      const int r = tr + P * ii;
-#pragma unroll
-      for (int jj = 0; jj < kTile; ++jj) {
-        const int col = tc + P * jj;
-        double2 g = (r < n && col < n) ? gam[mat + (size_t)r * n + col] : mk(0.0, 0.0);
-        const float2 x = X0s[r * np + col];
-        const double re = g.x - (double)x.x + (((double)acc[i2][jj][0] + (double)acc[i2][jj][1]) + (double)acc[i2][jj][4]);
-        const double im = g.y - (double)x.y + (((double)acc[i2][jj][2] + (double)acc[i2][jj][3]) + (double)acc[i2][jj][5]);
-        A[ii][kTile + jj] = make_float2((float)re, (float)im);
+      // R = gamma - X0 + acc, in FP64, rounded to FP32 into the RHS registers
+  #pragma unroll
+      for (int i2 = 0; i2 < 2; ++i2) {
+        const int ii = 2 * half + i2;
+        const int r = tr + P * ii;
+  #pragma unroll
+        for (int jj = 0; jj < kTile; ++jj) {
+          const int col = tc + P * jj;
+          double2 g = (r < n && col < n) ? gam[mat + (size_t)r * n + col] : mk(0.0, 0.0);
+          const float2 x = X0s[r * np + col];
+          const double re = g.x - (double)x.x + (((double)acc[i2][jj][0] + (double)acc[i2][jj][1]) + (double)acc[i2][jj][4]);
+          const double im = g.y - (double)x.y + (((double)acc[i2][jj][2] + (double)acc[i2][jj][3]) + (double)acc[i2][jj][5]);
+          A[ii][kTile + jj] = make_float2((float)re, (float)im);
+        }
       }
     }
+    __syncthreads();
   }
-  __syncthreads();
 
   // ---- correction E = D^-1 R: forward substitution over the pivot order ----
 #pragma unroll
