@@ -32,7 +32,7 @@ namespace df {
 
 constexpr int kTile = 4;          // rows / columns per thread
 constexpr int kResChunk = 16;     // gamma columns staged per residual sweep (SIMT residual)
-constexpr int kSlices = 7;        // base-256 digits of the tensor-core residual (56 bits)
+constexpr int kSlices = 8;        // base-128 digits of the tensor-core residual (56 bits)
 constexpr int kCB = 16;           // column block of the tensor-core residual
 
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
@@ -85,7 +85,7 @@ __device__ __forceinline__ void df_fma(float& hi, float& lo, float a, float b) {
 
 // ---- tensor-core residual helpers --------------------------------------
 
-// |v| < 2^e: the 7 signed base-256 digits d_s of v / 2^e, v ~ sum_s d_s 2^(e - 8(s+1)),
+// |v| < 2^e: the 8 signed base-128 digits d_s of v / 2^e, v ~ sum_s d_s 2^(e - 7(s+1)),
 // truncated below 2^(e - 56).  Read from the FP64 bits (integer operations only).
 __device__ __forceinline__ void digits_f64(double v, int e, float* d) {
   const long long bits = __double_as_longlong(v);
@@ -105,7 +105,7 @@ __device__ __forceinline__ void digits_f64(double v, int e, float* d) {
   const unsigned long long T = sh <= 3 ? (M << (3 - sh)) : (sh - 3 >= 64 ? 0ull : (M >> (sh - 3)));
   const float sg = bits < 0 ? -1.f : 1.f;
 #pragma unroll
-  for (int s = 0; s < kSlices; ++s) d[s] = sg * (float)(unsigned)((T >> (48 - 8 * s)) & 0xFFull);
+  for (int s = 0; s < kSlices; ++s) d[s] = sg * (float)(unsigned)((T >> (49 - 7 * s)) & 0x7Full);
 }
 
 // the same for an FP32 value
@@ -128,7 +128,12 @@ __device__ __forceinline__ void digits_f32(float v, int e, float* d) {
                                         : (sh - 32 >= 32 ? 0ull : (unsigned long long)(M >> (sh - 32)));
   const float sg = (bits >> 31) ? -1.f : 1.f;
 #pragma unroll
-  for (int s = 0; s < kSlices; ++s) d[s] = sg * (float)(unsigned)((T >> (48 - 8 * s)) & 0xFFull);
+  for (int s = 0; s < kSlices; ++s) d[s] = sg * (float)(unsigned)((T >> (49 - 7 * s)) & 0x7Full);
+}
+
+// 2^e as a float for e >= -126 (0 below: the terms it scales are < 2^-100 of the result)
+__device__ __forceinline__ float pow2f(int e) {
+  return e < -126 ? 0.f : __int_as_float((e + 127) << 23);
 }
 
 // exponent e with |v| < 2^e (v != 0): unbiased exponent + 1
@@ -482,43 +487,54 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
       __syncthreads();
       for (int tile = warp; tile < tiles; tile += nwarp) {
         const int r16 = (tile / (kCB / 8)) * 16, c8 = (tile % (kCB / 8)) * 8;
-        float hr[4] = {0.f, 0.f, 0.f, 0.f}, lr[4] = {0.f, 0.f, 0.f, 0.f};
-        float hm[4] = {0.f, 0.f, 0.f, 0.f}, lm[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int sa = 0; sa < kSlices; ++sa) {
-          const __nv_bfloat16* zr = zs + (size_t)(sa * 2 + 0) * np * 64;
-          const __nv_bfloat16* zi = zs + (size_t)(sa * 2 + 1) * np * 64;
-          for (int sb = 0; sa + sb < kSlices; ++sb) {
-            const __nv_bfloat16* xr = xs + (size_t)(sb * 2 + 0) * kCB * 64;
-            const __nv_bfloat16* xi = xs + (size_t)(sb * 2 + 1) * kCB * 64;
-            float ar[4] = {0.f, 0.f, 0.f, 0.f}, ai[4] = {0.f, 0.f, 0.f, 0.f};
-            for (int kk = 0; kk < np; kk += 16) {
-              unsigned fr[4], fi[4], fn[4];
-              fr[0] = ld_frag(zr, r16 + gq, kk + 2 * t4);
-              fr[1] = ld_frag(zr, r16 + gq + 8, kk + 2 * t4);
-              fr[2] = ld_frag(zr, r16 + gq, kk + 2 * t4 + 8);
-              fr[3] = ld_frag(zr, r16 + gq + 8, kk + 2 * t4 + 8);
-              fi[0] = ld_frag(zi, r16 + gq, kk + 2 * t4);
-              fi[1] = ld_frag(zi, r16 + gq + 8, kk + 2 * t4);
-              fi[2] = ld_frag(zi, r16 + gq, kk + 2 * t4 + 8);
-              fi[3] = ld_frag(zi, r16 + gq + 8, kk + 2 * t4 + 8);
+        // acc[d][0 / 1][.]: re / im of all digit pairs with sa + sb = d (one
+        // power-of-two weight; exact: at most 8 pairs x 2 x 64 x 127^2 < 2^24)
+        float acc[kSlices][2][4];
 #pragma unroll
-              for (int q2 = 0; q2 < 4; ++q2) fn[q2] = fi[q2] ^ 0x80008000u;   // -Zi
+        for (int d = 0; d < kSlices; ++d)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) acc[d][0][e] = acc[d][1][e] = 0.f;
+        for (int kk = 0; kk < np; kk += 16) {
+#pragma unroll
+          for (int sa = 0; sa < kSlices; ++sa) {
+            const __nv_bfloat16* zr = zs + (size_t)(sa * 2 + 0) * np * 64;
+            const __nv_bfloat16* zi = zs + (size_t)(sa * 2 + 1) * np * 64;
+            unsigned fr[4], fi[4], fn[4];
+            fr[0] = ld_frag(zr, r16 + gq, kk + 2 * t4);
+            fr[1] = ld_frag(zr, r16 + gq + 8, kk + 2 * t4);
+            fr[2] = ld_frag(zr, r16 + gq, kk + 2 * t4 + 8);
+            fr[3] = ld_frag(zr, r16 + gq + 8, kk + 2 * t4 + 8);
+            fi[0] = ld_frag(zi, r16 + gq, kk + 2 * t4);
+            fi[1] = ld_frag(zi, r16 + gq + 8, kk + 2 * t4);
+            fi[2] = ld_frag(zi, r16 + gq, kk + 2 * t4 + 8);
+            fi[3] = ld_frag(zi, r16 + gq + 8, kk + 2 * t4 + 8);
+#pragma unroll
+            for (int q2 = 0; q2 < 4; ++q2) fn[q2] = fi[q2] ^ 0x80008000u;   // -Zi
+#pragma unroll
+            for (int sb = 0; sa + sb < kSlices; ++sb) {
+              const __nv_bfloat16* xr = xs + (size_t)(sb * 2 + 0) * kCB * 64;
+              const __nv_bfloat16* xi = xs + (size_t)(sb * 2 + 1) * kCB * 64;
               const unsigned br0 = ld_frag(xr, c8 + gq, kk + 2 * t4), br1 = ld_frag(xr, c8 + gq, kk + 2 * t4 + 8);
               const unsigned bi0 = ld_frag(xi, c8 + gq, kk + 2 * t4), bi1 = ld_frag(xi, c8 + gq, kk + 2 * t4 + 8);
-              mma_bf16(ar, fr, br0, br1);    // + Zr Xr
-              mma_bf16(ar, fn, bi0, bi1);    // - Zi Xi
-              mma_bf16(ai, fr, bi0, bi1);    // + Zr Xi
-              mma_bf16(ai, fi, br0, br1);    // + Zi Xr
+              mma_bf16(acc[sa + sb][0], fr, br0, br1);    // + Zr Xr
+              mma_bf16(acc[sa + sb][0], fn, bi0, bi1);    // - Zi Xi
+              mma_bf16(acc[sa + sb][1], fr, bi0, bi1);    // + Zr Xi
+              mma_bf16(acc[sa + sb][1], fi, br0, br1);    // + Zi Xr
             }
-            const int sc = -8 * (sa + sb + 2);
+          }
+        }
+        float hr[4] = {0.f, 0.f, 0.f, 0.f}, lr[4] = {0.f, 0.f, 0.f, 0.f};
+        float hm[4] = {0.f, 0.f, 0.f, 0.f}, lm[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const int row = r16 + gq + (e >= 2 ? 8 : 0), col = c8 + 2 * t4 + (e & 1);
-              if (rowe[row] > -1000 && cole[col] > -1000) {
-                const int ex = rowe[row] + cole[col] + sc;
-                dd_add(hr[e], lr[e], ldexpf(ar[e], ex));
-                dd_add(hm[e], lm[e], ldexpf(ai[e], ex));
-              }
+        for (int e = 0; e < 4; ++e) {
+          const int row = r16 + gq + (e >= 2 ? 8 : 0), col = c8 + 2 * t4 + (e & 1);
+          if (rowe[row] > -1000 && cole[col] > -1000) {
+            const int ex = rowe[row] + cole[col];
+#pragma unroll
+            for (int d = kSlices - 1; d >= 0; --d) {      // smallest weights first
+              const float w = pow2f(ex - 7 * (d + 2));
+              dd_add(hr[e], lr[e], acc[d][0][e] * w);
+              dd_add(hm[e], lm[e], acc[d][1][e] * w);
             }
           }
         }
