@@ -33,6 +33,9 @@ struct BseF64Shared {
   int perm[128];
   int piv;
   double2 pv, oldkk;
+  // (row offset << 8) | column of the triangular part of a right-hand-side
+  // chunk's back substitution, rows 0..nc-2 in order (row d has columns 0..d)
+  unsigned short tri[32 * 31 / 2];
 };
 
 // D = 1 - gamma_W diag(chi~_W(q)) factorised in LU (n x n, row-major; shared
@@ -52,6 +55,11 @@ __device__ __forceinline__ void bse_f64_system(const Dims& dm, int c, int a, int
   for (int i = tid; i < n; i += blockDim.x) {
     xs[i] = chi[((size_t)a * n + i) * N + q];
     sh.perm[i] = i;
+  }
+  for (int e = tid; e < nc * (nc - 1) / 2; e += blockDim.x) {
+    int d = 0;
+    while ((d + 1) * (d + 2) / 2 <= e) ++d;
+    sh.tri[e] = (unsigned short)((d << 8) | (e - d * (d + 1) / 2));
   }
   __syncthreads();
   for (int idx = tid; idx < n * n; idx += blockDim.x) {
@@ -145,10 +153,24 @@ __device__ __forceinline__ void bse_f64_system(const Dims& dm, int c, int a, int
       __syncthreads();
     }
     for (int k = n - 1; k > j0; --k) {          // unit-upper back substitution, rows >= j0 only
+      // column jj needs rows r >= j0 + jj: rows j0 .. j0+w-2 are the triangle
+      // (table), rows from j0+w-1 on take all w columns
       const int m = k - j0;
-      for (int idx = tid; idx < m * w; idx += blockDim.x) {
-        const int r = j0 + idx / w, jj = idx % w;
-        if (j0 + jj <= r) Y[r * nc + jj] = cfms(LU[r * n + k], Y[k * nc + jj], Y[r * nc + jj]);
+      const int tr = m < w - 1 ? m : w - 1;
+      const int ntri = tr * (tr + 1) / 2;
+      const int nrect = m > w - 1 ? (m - (w - 1)) * w : 0;
+      for (int idx = tid; idx < ntri + nrect; idx += blockDim.x) {
+        int r, jj;
+        if (idx < ntri) {
+          const unsigned short e = sh.tri[idx];
+          r = j0 + (e >> 8);
+          jj = e & 0xff;
+        } else {
+          const int i2 = idx - ntri;
+          r = j0 + (w - 1) + i2 / w;
+          jj = i2 % w;
+        }
+        Y[r * nc + jj] = cfms(LU[r * n + k], Y[k * nc + jj], Y[r * nc + jj]);
       }
       __syncthreads();
     }
