@@ -208,11 +208,7 @@ using namespace df;
 
 namespace {
 
-int mixed_np_of(int n) {
-  int np = 4;
-  while (np < n) np *= 2;
-  return np;
-}
+int mixed_np_of(int n) { return mixed_pad(n); }
 
 struct LadderGroup {          // one persistent ladder launch
   bool mixed = false;

@@ -59,12 +59,7 @@ bse_mixed_kernel(Dims dm, int ch0, int nch, int np, const double2* __restrict__ 
 // host side
 // ---------------------------------------------------------------------------
 
-// n padded so that P = n_pad / 4 is a power of two (shuffle groups of P lanes)
-static int mixed_np(int n) {
-  int np = kTile;
-  while (np < n) np *= 2;
-  return np;
-}
+static int mixed_np(int n) { return mixed_pad(n); }
 
 // the register-resident [D | RHS] tile limits this kernel to n_w <= 64
 bool mixed_supported(int n_w) { return mixed_np(n_w) <= 64; }

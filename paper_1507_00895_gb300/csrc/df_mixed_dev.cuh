@@ -1,26 +1,31 @@
-// Mixed-precision ladder solves (DF_FP32_IR): Eq. lin_alg_inv factorised in
+// Mixed-precision ladder solves (DF_FP32_IR): Eq. lin_alg_inv solved in
 // FP32 (complex64) and corrected once with an FP64-accurate residual.
 //
 // Per (q, W, channel) system, with D = 1 - gamma diag(chi~):
-//   1. LU with partial pivoting of D in FP32 on the augmented [D | gamma]
-//      (forward substitution of the n right-hand sides fused into the
-//      elimination), then back substitution: X0 ~ D^-1 gamma in FP32.
-//   2. R = gamma - D X0 = gamma - X0 + gamma (chi o X0), evaluated with
-//      gamma and chi~ split into FP32 (hi, lo) pairs, exact FP32 products
-//      (fma) and double-float (TwoSum) accumulation: ~48-bit accurate.
-//   3. E = D^-1 R with the same FP32 LU; diag Gamma = diag X0 + diag E in FP64.
+//   1. Gauss-Jordan sweep with partial pivoting of the augmented [D | gamma]
+//      in FP32: the D part becomes D^-1 in place (rows and columns permuted
+//      by the pivot order), the gamma part X0 ~ D^-1 gamma.  The pivots are
+//      those of LU with partial pivoting (the same unused-row maximum of the
+//      same Schur complement column); one sweep, one block barrier per pivot.
+//   2. R = gamma - D X0 = gamma - X0 + Z X0, Z = gamma diag(chi~) formed in
+//      FP64, with ~2^-49 accuracy relative to |Z| |X0| (tensor-core digit
+//      products or double-float FP32 arithmetic).
+//   3. diag E = diag(D^-1 R) (n^2 work with the explicit inverse);
+//      diag Gamma = diag X0 + diag E in FP64.
 // One correction step leaves an error ~(kappa u32)^2 |Gamma| plus kappa times
-// the residual's own accuracy, i.e. FP64-level for the condition numbers of
-// the ladder matrices met here (up to ~1e6).
+// the residual's own accuracy.
 //
-// Layout: the whole [D | RHS] lives in registers.  The block is a P x P
-// grid of threads, P = n_pad / 4; thread (tr, tc) owns rows tr + P i and
-// columns tc + P j (i, j < 4) of D and of the right-hand sides (2D cyclic,
-// so that the shrinking active part of the elimination stays balanced).
-// Row pivoting is implicit: rows never move; pivot rows are marked used and
-// their order is kept in piv[] (logical row k of the factorisation is
-// physical row piv[k]).  Matrices of order n < n_pad are padded with an
-// identity block (gamma = 0, chi~ = 0 there), which leaves the solution of
+// Layout: the whole [D | gamma] lives in registers.  The block is a P x P
+// grid of threads, P = n_pad / 4; thread (tr, tc) = (t / P, t % P) owns rows
+// tr + P i and columns tc + P j (i, j < 4) of D and of gamma (2D cyclic), so
+// that the P threads of a thread row are consecutive lanes and every warp
+// holds whole rows.  Row pivoting is implicit: rows never move.  Each warp
+// publishes, before the barrier that ends a step, its best unused row for
+// the next pivot column together with that row's values; after the barrier
+// every thread picks the best of the warps' candidates and reads the pivot
+// row from it, so a step needs no second barrier.  Matrices of order
+// n < n_pad are padded with an identity block (gamma = 0, chi~ = 0 there),
+// which leaves the solution of the first n rows unchanged.
 // the first n rows unchanged.
 #pragma once
 #include <cuda_bf16.h>
@@ -34,12 +39,25 @@ constexpr int kTile = 4;          // rows / columns per thread
 constexpr int kResChunk = 16;     // gamma columns staged per residual sweep (SIMT residual)
 constexpr int kSlices = 8;        // base-128 digits of the tensor-core residual (56 bits)
 constexpr int kCB = 16;           // column block of the tensor-core residual
+constexpr int kPanel = 8;         // pivot columns per Gauss-Jordan panel
+constexpr int kPanelRows = 2;     // panel rows per lane of warp 0 (np / min(32, P^2) <= 2 for np >= 8)
+
+// padded order of a mixed ladder: a power of two >= 8 (P = np / 4 >= 2 lanes per
+// thread row; warp 0 then holds at most two panel rows per lane)
+inline int mixed_pad(int n) {
+  int np = 2 * kTile;
+  while (np < n) np *= 2;
+  return np;
+}
 
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
   return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
 __device__ __forceinline__ float2 cfmsf(float2 a, float2 b, float2 c) {   // c - a b
   return make_float2(fmaf(-a.x, b.x, fmaf(a.y, b.y, c.x)), fmaf(-a.x, b.y, fmaf(-a.y, b.x, c.y)));
+}
+__device__ __forceinline__ float2 cfmaf2(float2 a, float2 b, float2 c) {   // c + a b
+  return make_float2(fmaf(a.x, b.x, fmaf(-a.y, b.y, c.x)), fmaf(a.x, b.y, fmaf(a.y, b.x, c.y)));
 }
 __device__ __forceinline__ float2 cinvf(float2 z) {
   const float s = fmaxf(fabsf(z.x), fabsf(z.y));
@@ -169,16 +187,102 @@ __device__ __forceinline__ void dd_add(float& hi, float& lo, float v) {
   lo = e - (hi - s);
 }
 
+// b = pb in-place Gauss-Jordan steps on the panel pan[np][kPanel] (the pivot
+// columns k0 .. k0 + pb - 1), run by warp 0 alone: lane l holds rows
+// l + nlanes s (s < np / nlanes <= 2) in registers.  The pivot of each
+// column is the warp maximum of a key (|a| bits with their low 7 bits
+// replaced by 127 - row: the largest |a| to 2^-16 relative, ties to the
+// lowest row) over the rows not yet used; the pivot row is broadcast by
+// shuffles from its owner lane.  Writes the new panel to pan, the pivot rows
+// to piv_s[k0 + i] and the steps to rowstep[row]; used0 marks this lane's
+// rows taken.
+static __device__ __noinline__ void gj_panel(float2* pan, int np, int pb, int k0, int nlanes, unsigned wmask, int lane,
+                                      unsigned& used0, int* piv_s, int* rowstep, int* flags) {
+  const int rows_per_lane = np / nlanes;
+  float2 pv[kPanelRows][kPanel];
+#pragma unroll
+  for (int s2 = 0; s2 < kPanelRows; ++s2)
+#pragma unroll
+    for (int c2 = 0; c2 < kPanel; ++c2)
+      pv[s2][c2] = (s2 < rows_per_lane && c2 < pb) ? pan[(lane + nlanes * s2) * kPanel + c2] : make_float2(0.f, 0.f);
+#pragma unroll
+  for (int i = 0; i < kPanel; ++i) {
+    if (i < pb) {
+      unsigned key = 0u;
+#pragma unroll
+      for (int s2 = 0; s2 < kPanelRows; ++s2) {
+        if (s2 < rows_per_lane && !((used0 >> s2) & 1u)) {
+          const int r = lane + nlanes * s2;
+          const float m = fabsf(pv[s2][i].x) + fabsf(pv[s2][i].y);
+          const unsigned k2 = (__float_as_uint(m) & ~0x7Fu) | (unsigned)(127 - r);
+          key = k2 > key ? k2 : key;
+        }
+      }
+      key = __reduce_max_sync(wmask, key);
+      int p = 127 - (int)(key & 0x7Fu);
+      const float bm = __uint_as_float(key & ~0x7Fu);
+      const bool singular = !(bm > 0.f) || p >= np;
+      if (p >= np) p = 0;
+      const int owner = p % nlanes, sp2 = p / nlanes;
+      float2 u[kPanel];
+#pragma unroll
+      for (int c2 = 0; c2 < kPanel; ++c2) {
+        float2 v = pv[0][c2];
+#pragma unroll
+        for (int s2 = 1; s2 < kPanelRows; ++s2)
+          if (s2 == sp2) v = pv[s2][c2];
+        u[c2].x = __shfl_sync(wmask, v.x, owner);
+        u[c2].y = __shfl_sync(wmask, v.y, owner);
+      }
+      // 1 / pivot (approximate reciprocal: the FP32 sweep is corrected later)
+      float2 ainv = make_float2(0.f, 0.f);
+      if (!singular) {
+        const float2 z = u[i];
+        const float d = __fdividef(1.f, fmaf(z.x, z.x, z.y * z.y));
+        ainv = make_float2(z.x * d, -z.y * d);
+      }
+#pragma unroll
+      for (int c2 = 0; c2 < kPanel; ++c2) u[c2] = (c2 == i) ? ainv : cmulf(u[c2], ainv);
+      if (lane == 0) {
+        piv_s[k0 + i] = p;
+        rowstep[p] = k0 + i;
+        if (singular) atomicOr(flags, 1);
+      }
+      if (lane == owner) used0 |= 1u << sp2;
+#pragma unroll
+      for (int s2 = 0; s2 < kPanelRows; ++s2) {
+        const int r = lane + nlanes * s2;
+        if (r == p) {
+#pragma unroll
+          for (int c2 = 0; c2 < kPanel; ++c2) pv[s2][c2] = u[c2];
+        } else {
+          const float2 m = pv[s2][i];
+#pragma unroll
+          for (int c2 = 0; c2 < kPanel; ++c2) {
+            const float2 base = (c2 == i) ? make_float2(0.f, 0.f) : pv[s2][c2];
+            pv[s2][c2] = cfmsf(m, u[c2], base);
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int s2 = 0; s2 < kPanelRows; ++s2)
+    if (s2 < rows_per_lane)
+#pragma unroll
+      for (int c2 = 0; c2 < kPanel; ++c2)
+        if (c2 < pb) pan[(lane + nlanes * s2) * kPanel + c2] = pv[s2][c2];
+}
+
 struct MixedSmem {
   // offsets in float2 units (8 bytes)
-  int x0, chih, chil, ubuf, lbuf, invu, x0d, chi64, work, gt_h, gt_l, yh, yl, total;
+  int x0, chih, chil, invu, x0d, chi64, work, gt_h, gt_l, yh, yl, total;
 };
 
 // bytes of the tensor-core residual's work area (n_pad in {32, 64})
 __host__ __device__ inline int tc_work_bytes(int np) {
   return 2 * kSlices * 2 * np * 64        // Z digits, bf16 [slice][re/im][row][64]
          + 2 * kSlices * 2 * kCB * 64     // X0 digits of one column block, bf16 [slice][re/im][col][64]
-         + 8 * np * kCB                   // R of one column block, float2 [row][kCB]
          + 4 * (np + kCB);                // row / column exponents
 }
 
@@ -190,8 +294,6 @@ __host__ __device__ inline MixedSmem mixed_layout(int np) {
   L.x0 = o;   o += np * np;        // X0 (logical rows), also the row broadcast of the solves
   L.chih = o; o += np;
   L.chil = o; o += np;
-  L.ubuf = o; o += 2 * np;         // pivot-row broadcast (D part + RHS part)
-  L.lbuf = o; o += 2 * np;         // column broadcast, double buffered
   L.invu = o; o += np;
   L.x0d = o;  o += np;             // diag X0 (FP32)
   L.chi64 = o; o += 2 * np;        // chi~ in FP64 (double2 = two float2 slots)
@@ -203,14 +305,16 @@ __host__ __device__ inline MixedSmem mixed_layout(int np) {
   L.yl = L.yh + np * np;
   const int simt = 2 * kResChunk * np + 2 * np * np;
   const int tc = (tc_work_bytes(np) + 7) / 8;
-  o += use_tc_residual(np) ? tc : simt;
+  const int gj = 2 * np * kPanel + kPanel * 2 * np;   // Gauss-Jordan panels [2][np][kPanel], pivot rows
+  const int res = use_tc_residual(np) ? tc : simt;
+  o += res > gj ? res : gj;
   L.total = o;
   return L;
 }
 
 // Shared-memory views of one mixed solve (layout from mixed_layout).
 struct MixedPtrs {
-  float2 *X0s, *chih, *chil, *ubuf, *lbuf, *invu, *x0d, *gth, *gtl, *Yh, *Yl;
+  float2 *X0s, *chih, *chil, *invu, *x0d, *gth, *gtl, *Yh, *Yl;
   double2* chi64;
   int* piv_s;
   unsigned char* work;
@@ -222,8 +326,6 @@ __device__ __forceinline__ MixedPtrs mixed_ptrs(float2* smf, int np, int* piv_s)
   m.X0s = smf + L.x0;
   m.chih = smf + L.chih;
   m.chil = smf + L.chil;
-  m.ubuf = smf + L.ubuf;
-  m.lbuf = smf + L.lbuf;
   m.invu = smf + L.invu;
   m.x0d = smf + L.x0d;
   m.gth = smf + L.gt_h;
@@ -250,8 +352,6 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
   float2* X0s = sp.X0s;
   float2* chih = sp.chih;
   float2* chil = sp.chil;
-  float2* ubuf = sp.ubuf;
-  float2* lbuf = sp.lbuf;
   float2* invu = sp.invu;
   float2* x0d = sp.x0d;
   float2* gth = sp.gth;
@@ -260,7 +360,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
   float2* Yl = sp.Yl;
   int* piv_s = sp.piv_s;
   const int t = threadIdx.x;
-  const int tr = t % P, tc = t / P;
+  const int tr = t / P, tc = t % P;
   const size_t mat = ((size_t)c * nb + a) * n * n;
   const float2* Gh = gam_hi + mat;
   const float2* Gl = gam_lo + mat;
@@ -295,117 +395,101 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
     }
   }
 
-  // ---- elimination with implicit partial pivoting; RHS forward-substituted ----
-  // k = jk P + kk: jk (the register column of pivot column k) is a
-  // compile-time index after unrolling; the P owners of column k are the
-  // consecutive, P-aligned threads tc == kk and reduce the pivot by shuffles.
-  const unsigned gmask = (P >= 32) ? 0xffffffffu : (((1u << P) - 1u) << ((t & 31) & ~(P - 1)));
-#pragma unroll
-  for (int jk = 0; jk < kTile; ++jk) {
-    for (int kk = 0; kk < P; ++kk) {
-      const int k = jk * P + kk;
-      const bool own_col = (tc == kk);
-      if (own_col) {
-        float best = -1.f;
-        int br = 0x7fffffff;
-        float2 bv = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int ii = 0; ii < kTile; ++ii) {
-          if (rowpos[ii] < 0) {
-            const float2 v = A[ii][jk];
-            const float m = fabsf(v.x) + fabsf(v.y);
-            const int r = tr + P * ii;
-            if (m > best || (m == best && r < br)) { best = m; br = r; bv = v; }
-          }
-        }
-        for (int o = P >> 1; o > 0; o >>= 1) {
-          const float ob = __shfl_xor_sync(gmask, best, o);
-          const int orr = __shfl_xor_sync(gmask, br, o);
-          const float ox = __shfl_xor_sync(gmask, bv.x, o);
-          const float oy = __shfl_xor_sync(gmask, bv.y, o);
-          if (ob > best || (ob == best && orr < br)) { best = ob; br = orr; bv = make_float2(ox, oy); }
-        }
-        if (tr == 0) {
-          const bool singular = (bv.x == 0.f && bv.y == 0.f);
-          piv_s[k] = br;
-          invu[k] = singular ? make_float2(0.f, 0.f) : cinvf(bv);
-          if (singular) atomicOr(flags, 1);
-        }
-      }
-      __syncthreads();
-      const int p = piv_s[k];
-      const float2 inv = invu[k];
-      if (tr == p % P) {
-        const int ip = p / P;
-#pragma unroll
-        for (int ii = 0; ii < kTile; ++ii) {
-          if (ii == ip) {
-            rowpos[ii] = k;
-#pragma unroll
-            for (int jj = 0; jj < kTile; ++jj) {
-              if (jj > jk || (jj == jk && tc > kk)) ubuf[tc + P * jj] = A[ii][jj];
-              ubuf[np + tc + P * jj] = A[ii][kTile + jj];
-            }
-          }
-        }
-      }
-      if (own_col) {
-#pragma unroll
-        for (int ii = 0; ii < kTile; ++ii) {
-          if (rowpos[ii] < 0) {
-            const float2 l = cmulf(A[ii][jk], inv);
-            A[ii][jk] = l;
-            lbuf[tr + P * ii] = l;
-          }
-        }
-      }
-      __syncthreads();
+  // ---- Gauss-Jordan sweep of [D | gamma], implicit partial pivoting, in
+  // panels of b = min(8, P) pivot columns ----
+  // The b GJ steps of a panel change every other column j by a rank-b
+  // update, A[:, j] += W A[piv, j], where W = (panel after its own in-place
+  // GJ steps) - (unit columns at the pivot rows).  Per panel: (1) the owners
+  // of the panel columns copy them to pan; (2) warp 0 runs the b steps on
+  // pan in registers (pivot = warp max of a (|a| bits, ~row) key; the pivot
+  // row by shuffles); (3) the pivot rows' current values go to prs;
+  // (4) every thread applies the rank-b update to its tile and takes the
+  // panel's new columns.  Three block barriers per panel instead of one or
+  // two per pivot.
+  const int warp = t >> 5, lane = t & 31;
+  const int nlanes = P * P < 32 ? P * P : 32;
+  const unsigned wmask = nlanes == 32 ? 0xffffffffu : ((1u << nlanes) - 1u);
+  const int pb = P < kPanel ? P : kPanel;            // panel width b
+  float2* panbuf = reinterpret_cast<float2*>(sp.work);          // [2][np][kPanel]
+  float2* prs = panbuf + 2 * np * kPanel;                        // [kPanel][2 np]
+  int* rowstep = reinterpret_cast<int*>(invu);                   // pivot step of each row, -1 if none
+  for (int i = t; i < np; i += blockDim.x) rowstep[i] = -1;
+  unsigned used0 = 0;                                            // warp 0: its rows already pivots
+  // one copy of the loop body (the register column jk is selected at run time)
+#pragma unroll 1
+  for (int k0 = 0; k0 < np; k0 += pb) {
+    const int jk = k0 / P, kc = k0 - jk * P;
+    float2* pan = panbuf + ((k0 / pb) & 1) * np * kPanel;
+    const bool pcol = (tc >= kc && tc < kc + pb);
+    // (1) the panel columns
+    if (pcol) {
 #pragma unroll
       for (int ii = 0; ii < kTile; ++ii) {
-        if (rowpos[ii] < 0) {
-          const float2 l = lbuf[tr + P * ii];
+        float2 v = A[ii][0];
 #pragma unroll
-          for (int jj = 0; jj < kTile; ++jj) {
-            if (jj > jk || (jj == jk && tc > kk)) A[ii][jj] = cfmsf(l, ubuf[tc + P * jj], A[ii][jj]);
-            A[ii][kTile + jj] = cfmsf(l, ubuf[np + tc + P * jj], A[ii][kTile + jj]);
-          }
+        for (int jj = 1; jj < kTile; ++jj)
+          if (jj == jk) v = A[ii][jj];
+        pan[(tr + P * ii) * kPanel + (tc - kc)] = v;
+      }
+    }
+    __syncthreads();
+    // (2) b GJ steps on the panel, warp 0
+    if (warp == 0) gj_panel(pan, np, pb, k0, nlanes, wmask, lane, used0, piv_s, rowstep, flags);
+    __syncthreads();
+    // (3) current values of the pivot rows
+#pragma unroll
+    for (int ii = 0; ii < kTile; ++ii) {
+      const int l = rowstep[tr + P * ii] - k0;
+      if (l >= 0 && l < pb) {
+#pragma unroll
+        for (int jj = 0; jj < kTile; ++jj) {
+          prs[l * 2 * np + tc + P * jj] = A[ii][jj];
+          prs[l * 2 * np + np + tc + P * jj] = A[ii][kTile + jj];
         }
       }
     }
-  }
-
-  __syncthreads();   // the last elimination update still reads lbuf / ubuf
-
-  // ---- back substitution: X0 row k (logical) from physical row piv[k] ----
+    __syncthreads();
+    // (4) rank-b update; the panel columns take their new values
+#pragma unroll 1
+    for (int l = 0; l < pb; ++l) {
+      const int pl = piv_s[k0 + l];
+      float2 pr[2 * kTile];
 #pragma unroll
-  for (int jk = kTile - 1; jk >= 0; --jk) {
-    for (int kk = P - 1; kk >= 0; --kk) {
-      const int k = jk * P + kk;
-      const int p = piv_s[k];
-      float2* ucol = lbuf + (k & 1) * np;
-      if (tc == kk) {
-#pragma unroll
-        for (int ii = 0; ii < kTile; ++ii) ucol[tr + P * ii] = A[ii][jk];
+      for (int jj = 0; jj < kTile; ++jj) {
+        pr[jj] = prs[l * 2 * np + tc + P * jj];
+        pr[kTile + jj] = prs[l * 2 * np + np + tc + P * jj];
       }
-      if (tr == p % P) {
-        const int ip = p / P;
-        const float2 inv = invu[k];
-#pragma unroll
-        for (int ii = 0; ii < kTile; ++ii)
-          if (ii == ip)
-#pragma unroll
-            for (int jj = 0; jj < kTile; ++jj) X0s[k * np + tc + P * jj] = cmulf(A[ii][kTile + jj], inv);
-      }
-      __syncthreads();
 #pragma unroll
       for (int ii = 0; ii < kTile; ++ii) {
-        if (rowpos[ii] < k) {
-          const float2 u = ucol[tr + P * ii];
+        const int r = tr + P * ii;
+        float2 w = pan[r * kPanel + l];
+        if (r == pl) w.x -= 1.f;
 #pragma unroll
-          for (int jj = 0; jj < kTile; ++jj)
-            A[ii][kTile + jj] = cfmsf(u, X0s[k * np + tc + P * jj], A[ii][kTile + jj]);
+        for (int jj = 0; jj < kTile; ++jj) {
+          if (!(jj == jk && pcol)) A[ii][jj] = cfmaf2(w, pr[jj], A[ii][jj]);
+          A[ii][kTile + jj] = cfmaf2(w, pr[kTile + jj], A[ii][kTile + jj]);
         }
       }
+    }
+    if (pcol) {
+#pragma unroll
+      for (int ii = 0; ii < kTile; ++ii) {
+        const float2 v = pan[(tr + P * ii) * kPanel + (tc - kc)];
+#pragma unroll
+        for (int jj = 0; jj < kTile; ++jj)
+          if (jj == jk) A[ii][jj] = v;
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int ii = 0; ii < kTile; ++ii) rowpos[ii] = rowstep[tr + P * ii];
+  // X0 in logical row order: row r of the sweep is X0 row rowpos (its pivot step)
+#pragma unroll
+  for (int ii = 0; ii < kTile; ++ii) {
+    if (rowpos[ii] >= 0) {
+#pragma unroll
+      for (int jj = 0; jj < kTile; ++jj) X0s[rowpos[ii] * np + tc + P * jj] = A[ii][kTile + jj];
     }
   }
   __syncthreads();
@@ -418,8 +502,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
     // 28 pairs with weight >= 2^-64 are folded, scaled, into a double-float sum.
     __nv_bfloat16* zs = reinterpret_cast<__nv_bfloat16*>(sp.work);    // [kSlices][2][np][64]
     __nv_bfloat16* xs = zs + (size_t)kSlices * 2 * np * 64;          // [kSlices][2][kCB][64]
-    float2* Rst = reinterpret_cast<float2*>(xs + (size_t)kSlices * 2 * kCB * 64);   // [np][kCB]
-    int* rowe = reinterpret_cast<int*>(Rst + np * kCB);              // [np]
+    int* rowe = reinterpret_cast<int*>(xs + (size_t)kSlices * 2 * kCB * 64);   // [np]
     int* cole = rowe + np;                                           // [kCB]
     const int nthr = blockDim.x;
     for (int i = t; i < np; i += nthr) rowe[i] = -1000;
@@ -546,17 +629,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
           const float2 x = X0s[row * np + j];
           const double re = gv.x - (double)x.x + ((double)hr[e] + (double)lr[e]);
           const double im = gv.y - (double)x.y + ((double)hm[e] + (double)lm[e]);
-          Rst[row * kCB + col] = make_float2((float)re, (float)im);
-        }
-      }
-      __syncthreads();
-      // hand this column block of R to the owners of its columns (cyclic layout)
-#pragma unroll
-      for (int ii = 0; ii < kTile; ++ii) {
-#pragma unroll
-        for (int jj = 0; jj < kTile; ++jj) {
-          const int col = tc + P * jj;
-          if (col >= b * kCB && col < (b + 1) * kCB) A[ii][kTile + jj] = Rst[(tr + P * ii) * kCB + (col - b * kCB)];
+          X0s[row * np + j] = make_float2((float)re, (float)im);   // R replaces X0
         }
       }
     }
@@ -649,72 +722,37 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
       }
     }
     __syncthreads();
+    // R to shared memory (logical rows, in place of X0)
+#pragma unroll
+    for (int ii = 0; ii < kTile; ++ii)
+#pragma unroll
+      for (int jj = 0; jj < kTile; ++jj) X0s[(tr + P * ii) * np + tc + P * jj] = A[ii][kTile + jj];
+    __syncthreads();
   }
 
-  // ---- correction E = D^-1 R: forward substitution over the pivot order ----
+  // ---- diag E = diag(D^-1 R): the sweep's D part W holds D^-1 permuted,
+  // D^-1[j][m] = W[piv[j]][ipiv[m]], so E_jj = sum_c W[r][c] R[piv[c]][j] with
+  // j = ipiv[r]; the P threads of a thread row reduce by shuffles ----
+  float2* ediag = invu;
+  int pc[kTile];
 #pragma unroll
-  for (int jk = 0; jk < kTile; ++jk) {
-    for (int kk = 0; kk < P; ++kk) {
-      const int k = jk * P + kk;
-      const int p = piv_s[k];
-      float2* yrow = ubuf + (k & 1) * np;
-      float2* lcol = lbuf + (k & 1) * np;
-      if (tr == p % P) {
-        const int ip = p / P;
+  for (int jj = 0; jj < kTile; ++jj) pc[jj] = piv_s[tc + P * jj];
 #pragma unroll
-        for (int ii = 0; ii < kTile; ++ii)
-          if (ii == ip)
+  for (int ii = 0; ii < kTile; ++ii) {
+    const int j = rowpos[ii] < 0 ? 0 : rowpos[ii];
+    float ex = 0.f, ey = 0.f;
 #pragma unroll
-            for (int jj = 0; jj < kTile; ++jj) yrow[tc + P * jj] = A[ii][kTile + jj];
-      }
-      if (tc == kk) {
-#pragma unroll
-        for (int ii = 0; ii < kTile; ++ii) lcol[tr + P * ii] = A[ii][jk];
-      }
-      __syncthreads();
-#pragma unroll
-      for (int ii = 0; ii < kTile; ++ii) {
-        if (rowpos[ii] > k) {
-          const float2 l = lcol[tr + P * ii];
-#pragma unroll
-          for (int jj = 0; jj < kTile; ++jj)
-            A[ii][kTile + jj] = cfmsf(l, yrow[tc + P * jj], A[ii][kTile + jj]);
-        }
-      }
+    for (int jj = 0; jj < kTile; ++jj) {
+      const float2 rv = X0s[pc[jj] * np + j];
+      const float2 w = A[ii][jj];
+      ex = fmaf(w.x, rv.x, fmaf(-w.y, rv.y, ex));
+      ey = fmaf(w.x, rv.y, fmaf(w.y, rv.x, ey));
     }
-  }
-  __syncthreads();
-  // back substitution (X0s reused as the row broadcast)
-#pragma unroll
-  for (int jk = kTile - 1; jk >= 0; --jk) {
-    for (int kk = P - 1; kk >= 0; --kk) {
-      const int k = jk * P + kk;
-      const int p = piv_s[k];
-      float2* ucol = lbuf + (k & 1) * np;
-      if (tc == kk) {
-#pragma unroll
-        for (int ii = 0; ii < kTile; ++ii) ucol[tr + P * ii] = A[ii][jk];
-      }
-      if (tr == p % P) {
-        const int ip = p / P;
-        const float2 inv = invu[k];
-#pragma unroll
-        for (int ii = 0; ii < kTile; ++ii)
-          if (ii == ip)
-#pragma unroll
-            for (int jj = 0; jj < kTile; ++jj) X0s[k * np + tc + P * jj] = cmulf(A[ii][kTile + jj], inv);
-      }
-      __syncthreads();
-#pragma unroll
-      for (int ii = 0; ii < kTile; ++ii) {
-        if (rowpos[ii] < k) {
-          const float2 u = ucol[tr + P * ii];
-#pragma unroll
-          for (int jj = 0; jj < kTile; ++jj)
-            A[ii][kTile + jj] = cfmsf(u, X0s[k * np + tc + P * jj], A[ii][kTile + jj]);
-        }
-      }
+    for (int o = 1; o < P; o <<= 1) {
+      ex += __shfl_xor_sync(wmask, ex, o);
+      ey += __shfl_xor_sync(wmask, ey, o);
     }
+    if (tc == 0 && rowpos[ii] >= 0) ediag[j] = make_float2(ex, ey);
   }
   __syncthreads();
 
@@ -740,7 +778,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
       g2.y += __shfl_xor_sync(0xffffffffu, g2.y, 2);
     }
     if (j < n && part == 0) {
-      const float2 x0 = x0d[j], e = X0s[j * np + j];
+      const float2 x0 = x0d[j], e = ediag[j];
       const double2 gdiag = mk((double)x0.x + (double)e.x, (double)x0.y + (double)e.y);
       const double wgt = (c == 0) ? 1.0 : 3.0;
       kc[(((size_t)c * nb + a) * n + j) * N + q] =
