@@ -168,13 +168,14 @@ batch_bse_f64_kernel(const PointDev* __restrict__ pts, const int* __restrict__ o
   }
 }
 
+template <int NP>
 __global__ void __launch_bounds__(256)
 batch_bse_mixed_kernel(const PointDev* __restrict__ pts, const int* __restrict__ order, const long* __restrict__ start,
-                       int nseg, int np, int chunk, unsigned long long* __restrict__ counter) {
+                       int nseg, int chunk, unsigned long long* __restrict__ counter) {
   extern __shared__ float2 smf[];
   __shared__ int piv_s[128];
   __shared__ unsigned long long item_s;
-  const MixedPtrs sp = mixed_ptrs(smf, np, piv_s);
+  const MixedPtrs sp = mixed_ptrs(smf, NP, piv_s);
   const long total = start[nseg];
   for (;;) {
     if (threadIdx.x == 0) item_s = atomicAdd(counter, (unsigned long long)chunk);
@@ -193,7 +194,7 @@ batch_bse_mixed_kernel(const PointDev* __restrict__ pts, const int* __restrict__
       const int c = (int)(local / per_ch);
       const int rem = (int)(local - (long)c * per_ch);
       const int a = rem / dm.N, q = rem - a * dm.N;
-      bse_mixed_system(dm, c, a, q, np, P.gam, P.gam_hi, P.gam_lo, P.gg, P.chi, P.kc, P.flags, sp);
+      bse_mixed_system<NP>(dm, c, a, q, P.gam, P.gam_hi, P.gam_lo, P.gg, P.chi, P.kc, P.flags, sp);
     }
   }
 }
@@ -209,6 +210,18 @@ using namespace df;
 namespace {
 
 int mixed_np_of(int n) { return mixed_pad(n); }
+
+using MixedKernel = void (*)(const PointDev*, const int*, const long*, int, int, unsigned long long*);
+
+// the ladder kernel instance of a padded order (8, 16, 32 or 64)
+MixedKernel mixed_kernel_of(int np) {
+  switch (np) {
+    case 8: return batch_bse_mixed_kernel<8>;
+    case 16: return batch_bse_mixed_kernel<16>;
+    case 32: return batch_bse_mixed_kernel<32>;
+    default: return batch_bse_mixed_kernel<64>;
+  }
+}
 
 struct LadderGroup {          // one persistent ladder launch
   bool mixed = false;
@@ -295,8 +308,8 @@ df_status record_pass(df_batch* b) {
       batch_bse_f64_kernel<<<g.grid, kBseThreads, g.smem, s>>>(b->d_pts, g.d_order, g.d_start, g.nseg, b->chunk,
                                                                b->d_counters + g.counter_slot, b->ws, b->ws_stride);
     } else {
-      batch_bse_mixed_kernel<<<g.grid, g.threads, g.smem, s>>>(b->d_pts, g.d_order, g.d_start, g.nseg, g.np,
-                                                               b->chunk, b->d_counters + g.counter_slot);
+      mixed_kernel_of(g.np)<<<g.grid, g.threads, g.smem, s>>>(b->d_pts, g.d_order, g.d_start, g.nseg, b->chunk,
+                                                              b->d_counters + g.counter_slot);
     }
     B_CUDA(b, cudaGetLastError(), "batch ladder");
   }
@@ -336,20 +349,16 @@ df_status configure_groups(df_batch* b) {
   // kernel attributes and persistent grids for the current nc / chunk; the
   // mixed classes share one kernel, whose shared-memory limit is set once to
   // the largest class
-  size_t mixed_max = 0;
-  for (auto& g : b->groups)
-    if (g.mixed) mixed_max = std::max(mixed_max, sizeof(float2) * (size_t)mixed_layout(g.np).total);
-  if (mixed_max)
-    B_CUDA(b, cudaFuncSetAttribute((const void*)batch_bse_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)mixed_max),
-           "mixed smem attribute");
   for (auto& g : b->groups) {
     if (g.mixed) {
       const int P = g.np / 4;
       g.threads = P * P;
       g.smem = sizeof(float2) * (size_t)mixed_layout(g.np).total;
+      B_CUDA(b, cudaFuncSetAttribute((const void*)mixed_kernel_of(g.np), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)g.smem),
+             "mixed smem attribute");
       int per = 0;
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_bse_mixed_kernel, g.threads, g.smem);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, mixed_kernel_of(g.np), g.threads, g.smem);
       g.grid = b->sms * std::max(1, per);
     } else {
       size_t sm = 0;

@@ -37,21 +37,22 @@ __global__ void split_gamma_kernel(size_t count, const double2* __restrict__ g, 
   }
 }
 
+template <int NP>
 __global__ void __launch_bounds__(256)
-bse_mixed_kernel(Dims dm, int ch0, int nch, int np, const double2* __restrict__ gam,
+bse_mixed_kernel(Dims dm, int ch0, int nch, const double2* __restrict__ gam,
                  const float2* __restrict__ gam_hi, const float2* __restrict__ gam_lo,
                  const double2* __restrict__ gg, const double2* __restrict__ chi, double2* __restrict__ kc,
                  int* __restrict__ flags) {
   extern __shared__ float2 smf[];
   __shared__ int piv_s[128];
-  const MixedPtrs sp = mixed_ptrs(smf, np, piv_s);
+  const MixedPtrs sp = mixed_ptrs(smf, NP, piv_s);
   const int N = dm.N, nb = dm.nb;
   const long systems = (long)nch * nb * N;
   for (long sys = blockIdx.x; sys < systems; sys += gridDim.x) {
     const int c = ch0 + (int)(sys / ((long)nb * N));
     const int rem = (int)(sys - (long)(c - ch0) * nb * N);
     const int a = rem / N, q = rem - a * N;
-    bse_mixed_system(dm, c, a, q, np, gam, gam_hi, gam_lo, gg, chi, kc, flags, sp);
+    bse_mixed_system<NP>(dm, c, a, q, gam, gam_hi, gam_lo, gg, chi, kc, flags, sp);
   }
 }
 
@@ -76,19 +77,19 @@ cudaError_t launch_split_gamma(df_ctx* c) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_bse_mixed(df_ctx* c, int channel_mask, const double2* gg, int* flags) {
+template <int NP>
+static cudaError_t launch_bse_mixed_np(df_ctx* c, int channel_mask, const double2* gg, int* flags) {
   const Dims& dm = c->dm;
-  const int np = mixed_np(dm.n_w);
-  const int P = np / kTile;
-  const int threads = P * P;
-  const size_t smem = sizeof(float2) * (size_t)mixed_layout(np).total;
-  cudaError_t e = cudaFuncSetAttribute((const void*)bse_mixed_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  constexpr int P = NP / kTile;
+  constexpr int threads = P * P;
+  const size_t smem = sizeof(float2) * (size_t)mixed_layout(NP).total;
+  cudaError_t e = cudaFuncSetAttribute((const void*)bse_mixed_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
   if (c->mixed_grid == 0) {
     int per_sm = 0, sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bse_mixed_kernel, threads, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bse_mixed_kernel<NP>, threads, smem);
     c->mixed_grid = sms * (per_sm < 1 ? 1 : per_sm);
   }
   const size_t count = (size_t)2 * dm.nb * dm.n_w * dm.n_w;
@@ -97,11 +98,21 @@ cudaError_t launch_bse_mixed(df_ctx* c, int channel_mask, const double2* gg, int
     if (!(channel_mask & (1 << ch))) continue;
     const long systems = (long)dm.nb * dm.N;
     const int grid = (int)(systems < c->mixed_grid ? systems : c->mixed_grid);
-    bse_mixed_kernel<<<grid, threads, smem, c->stream>>>(dm, ch, 1, np, c->gam, hi, hi + count, gg, c->chi, c->kc,
-                                                         flags);
+    bse_mixed_kernel<NP><<<grid, threads, smem, c->stream>>>(dm, ch, 1, c->gam, hi, hi + count, gg, c->chi, c->kc,
+                                                             flags);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+cudaError_t launch_bse_mixed(df_ctx* c, int channel_mask, const double2* gg, int* flags) {
+  switch (mixed_np(c->dm.n_w)) {
+    case 8: return launch_bse_mixed_np<8>(c, channel_mask, gg, flags);
+    case 16: return launch_bse_mixed_np<16>(c, channel_mask, gg, flags);
+    case 32: return launch_bse_mixed_np<32>(c, channel_mask, gg, flags);
+    case 64: return launch_bse_mixed_np<64>(c, channel_mask, gg, flags);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 }  // namespace df

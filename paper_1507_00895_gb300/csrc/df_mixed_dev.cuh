@@ -172,7 +172,7 @@ __device__ __forceinline__ unsigned ld_frag(const __nv_bfloat16* base, int row, 
 }
 
 __device__ __forceinline__ void mma_bf16(float* d, const unsigned* a, unsigned b0, unsigned b1) {
-  asm volatile(
+  asm(
       "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
       "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
@@ -196,9 +196,15 @@ __device__ __forceinline__ void dd_add(float& hi, float& lo, float v) {
 // shuffles from its owner lane.  Writes the new panel to pan, the pivot rows
 // to piv_s[k0 + i] and the steps to rowstep[row]; used0 marks this lane's
 // rows taken.
-static __device__ __noinline__ void gj_panel(float2* pan, int np, int pb, int k0, int nlanes, unsigned wmask, int lane,
-                                      unsigned& used0, int* piv_s, int* rowstep, int* flags) {
-  const int rows_per_lane = np / nlanes;
+template <int NP>
+__device__ __forceinline__ void gj_panel(float2* pan, int k0, int lane, unsigned& used0, int* piv_s, int* rowstep,
+                                         int* flags) {
+  constexpr int np = NP, P = NP / kTile;
+  constexpr int nlanes = P * P < 32 ? P * P : 32;
+  constexpr unsigned wmask = nlanes == 32 ? 0xffffffffu : ((1u << nlanes) - 1u);
+  constexpr int pb = P < kPanel ? P : kPanel;
+  constexpr int rows_per_lane = np / nlanes;
+  static_assert(rows_per_lane <= kPanelRows, "panel rows per lane");
   float2 pv[kPanelRows][kPanel];
 #pragma unroll
   for (int s2 = 0; s2 < kPanelRows; ++s2)
@@ -286,7 +292,7 @@ __host__ __device__ inline int tc_work_bytes(int np) {
          + 4 * (np + kCB);                // row / column exponents
 }
 
-__host__ __device__ inline bool use_tc_residual(int np) { return np == 32 || np == 64; }
+__host__ __device__ constexpr bool use_tc_residual(int np) { return np == 32 || np == 64; }
 
 __host__ __device__ inline MixedSmem mixed_layout(int np) {
   MixedSmem L;
@@ -340,7 +346,8 @@ __device__ __forceinline__ MixedPtrs mixed_ptrs(float2* smf, int np, int* piv_s)
 
 // One (q, W, channel) ladder in mixed precision; all P*P threads of the
 // block (P = np / 4) must call it.  Writes kc[c][a][:][q].
-__device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, int q, int np,
+template <int NP>
+__device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, int q,
                                                  const double2* __restrict__ gam,
                                                  const float2* __restrict__ gam_hi,
                                                  const float2* __restrict__ gam_lo,
@@ -348,7 +355,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
                                                  const double2* __restrict__ chi, double2* __restrict__ kc,
                                                  int* __restrict__ flags, const MixedPtrs& sp) {
   const int n = dm.n_w, N = dm.N, nb = dm.nb;
-  const int P = np / kTile;
+  constexpr int np = NP, P = NP / kTile;
   float2* X0s = sp.X0s;
   float2* chih = sp.chih;
   float2* chil = sp.chil;
@@ -407,9 +414,9 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
   // panel's new columns.  Three block barriers per panel instead of one or
   // two per pivot.
   const int warp = t >> 5, lane = t & 31;
-  const int nlanes = P * P < 32 ? P * P : 32;
-  const unsigned wmask = nlanes == 32 ? 0xffffffffu : ((1u << nlanes) - 1u);
-  const int pb = P < kPanel ? P : kPanel;            // panel width b
+  constexpr int nlanes = P * P < 32 ? P * P : 32;
+  constexpr unsigned wmask = nlanes == 32 ? 0xffffffffu : ((1u << nlanes) - 1u);
+  constexpr int pb = P < kPanel ? P : kPanel;        // panel width b
   float2* panbuf = reinterpret_cast<float2*>(sp.work);          // [2][np][kPanel]
   float2* prs = panbuf + 2 * np * kPanel;                        // [kPanel][2 np]
   int* rowstep = reinterpret_cast<int*>(invu);                   // pivot step of each row, -1 if none
@@ -434,7 +441,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
     }
     __syncthreads();
     // (2) b GJ steps on the panel, warp 0
-    if (warp == 0) gj_panel(pan, np, pb, k0, nlanes, wmask, lane, used0, piv_s, rowstep, flags);
+    if (warp == 0) gj_panel<NP>(pan, k0, lane, used0, piv_s, rowstep, flags);
     __syncthreads();
     // (3) current values of the pivot rows
 #pragma unroll
@@ -450,7 +457,6 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
     }
     __syncthreads();
     // (4) rank-b update; the panel columns take their new values
-#pragma unroll 1
     for (int l = 0; l < pb; ++l) {
       const int pl = piv_s[k0 + l];
       float2 pr[2 * kTile];
@@ -494,7 +500,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
   }
   __syncthreads();
   for (int j = t; j < np; j += blockDim.x) x0d[j] = X0s[j * np + j];
-  if (use_tc_residual(np)) {
+  if constexpr (use_tc_residual(NP)) {
     // ---- residual R = gamma - X0 + Z X0 on the tensor cores, Z = gamma diag(chi~) ----
     // Z (FP64 products) and X0 (FP32) are cut into 7 base-256 digits relative to
     // per-row / per-column powers of two; each digit pair's product is exact in
@@ -600,8 +606,8 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
               const unsigned br0 = ld_frag(xr, c8 + gq, kk + 2 * t4), br1 = ld_frag(xr, c8 + gq, kk + 2 * t4 + 8);
               const unsigned bi0 = ld_frag(xi, c8 + gq, kk + 2 * t4), bi1 = ld_frag(xi, c8 + gq, kk + 2 * t4 + 8);
               mma_bf16(acc[sa + sb][0], fr, br0, br1);    // + Zr Xr
-              mma_bf16(acc[sa + sb][0], fn, bi0, bi1);    // - Zi Xi
               mma_bf16(acc[sa + sb][1], fr, bi0, bi1);    // + Zr Xi
+              mma_bf16(acc[sa + sb][0], fn, bi0, bi1);    // - Zi Xi
               mma_bf16(acc[sa + sb][1], fi, br0, br1);    // + Zi Xr
             }
           }
