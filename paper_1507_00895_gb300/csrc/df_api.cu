@@ -66,7 +66,7 @@ df_status upload_inputs(df_ctx* c, const double* g, const double* delta, const d
   DF_CUDA(c, cudaMemcpyAsync(c->gam, gd, sizeof(double2) * nv, k, c->stream), "copy gamma_d");
   DF_CUDA(c, cudaMemcpyAsync(c->gam + nv, gm, sizeof(double2) * nv, k, c->stream), "copy gamma_m");
   DF_CUDA(c, launch_gamma_gt(c), "gamma o gamma^T");
-  if (c->mixed_ws) DF_CUDA(c, launch_split_gamma(c), "gamma -> FP32 (hi, lo)");
+  if (c->mixed_ws) DF_CUDA(c, launch_split_gamma(c, gamma_gt_ptr(c)), "gamma -> FP32 (hi, lo)");
   DF_CUDA(c, launch_init_g0(c), "bare dual propagator (Eq. gd0)");
   DF_CUDA(c, launch_dyson_ifft(c, 0, dm.ne), "Dyson + FFT to real space");
   return DF_OK;

@@ -30,7 +30,7 @@ struct PointDev {
   int active;    // 1 until converged
   double mix, tol, resid;
   double2 *g, *delta, *gam, *gg, *g0, *gk, *gr, *chi, *kc, *prod, *sigma;
-  float2 *gam_hi, *gam_lo;
+  float2 *gam_hi, *gam_lo, *gg_hi, *gg_lo;   // mixed: FP32 (hi, lo) of gam and gg
   double* red;   // [2 n_w + 4]
   int* flags;    // [4]
 };
@@ -115,12 +115,16 @@ __global__ void batch_setup_elem_kernel(const PointDev* __restrict__ pts, int p)
     const int rem = (int)(idx - mat * n * n);
     const int i = rem / n, j = rem - i * n;
     const double2* G = P.gam + mat * n * n;
-    P.gg[idx] = cmul(G[i * n + j], G[j * n + i]);
+    const double2 w = cmul(G[i * n + j], G[j * n + i]);
+    P.gg[idx] = w;
     if (P.gam_hi) {
       const double2 v = P.gam[idx];
-      const float hx = (float)v.x, hy = (float)v.y;
+      float hx = (float)v.x, hy = (float)v.y;
       P.gam_hi[idx] = make_float2(hx, hy);
       P.gam_lo[idx] = make_float2((float)(v.x - (double)hx), (float)(v.y - (double)hy));
+      hx = (float)w.x; hy = (float)w.y;
+      P.gg_hi[idx] = make_float2(hx, hy);
+      P.gg_lo[idx] = make_float2((float)(w.x - (double)hx), (float)(w.y - (double)hy));
     }
   }
 }
@@ -194,7 +198,7 @@ batch_bse_mixed_kernel(const PointDev* __restrict__ pts, const int* __restrict__
       const int c = (int)(local / per_ch);
       const int rem = (int)(local - (long)c * per_ch);
       const int a = rem / dm.N, q = rem - a * dm.N;
-      bse_mixed_system<NP>(dm, c, a, q, P.gam, P.gam_hi, P.gam_lo, P.gg, P.chi, P.kc, P.flags, sp);
+      bse_mixed_system<NP>(dm, c, a, q, P.gam, P.gam_hi, P.gam_lo, P.gg_hi, P.gg_lo, P.chi, P.kc, P.flags, sp);
     }
   }
 }
@@ -468,7 +472,7 @@ df_status df_batch_init(df_batch** out, int npts, const df_point* pts, int preci
     total += align_up(sizeof(double2) * (size_t)dm.n_w * dm.N);  // sigma
     total += align_up(sizeof(double) * (2 * dm.n_w + 4));
     total += align_up(sizeof(int) * 4);
-    if (P.mixed) total += align_up(sizeof(float2) * nv) * 2;      // gam hi, lo
+    if (P.mixed) total += align_up(sizeof(float2) * nv) * 4;      // gam hi, lo; gg hi, lo
   }
   b->arena_bytes = total;
   df_status st = DF_OK;
@@ -503,6 +507,8 @@ df_status df_batch_init(df_batch** out, int npts, const df_point* pts, int preci
     if (P.mixed) {
       P.gam_hi = (float2*)take(sizeof(float2) * nv);
       P.gam_lo = (float2*)take(sizeof(float2) * nv);
+      P.gg_hi = (float2*)take(sizeof(float2) * nv);
+      P.gg_lo = (float2*)take(sizeof(float2) * nv);
     }
     const char* limit = b->arena + (i + 1 < npts ? off[i + 1] : total);
     if (cur > limit) {

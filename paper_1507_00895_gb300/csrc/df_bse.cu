@@ -221,6 +221,7 @@ int bse_default_grid(const Dims& dm, int device) {
 }
 
 static double2* gg_ptr(df_ctx* c) { return (double2*)c->bse_ws; }
+const double2* gamma_gt_ptr(df_ctx* c) { return gg_ptr(c); }
 static int* flag_ptr(df_ctx* c) { return bse_flags(c); }
 static double2* lu_ws_ptr(df_ctx* c) {
   return (double2*)((char*)c->bse_ws + (size_t)2 * c->dm.nb * c->dm.n_w * c->dm.n_w * sizeof(double2));
@@ -239,7 +240,7 @@ cudaError_t launch_bse(df_ctx* c, int channel_mask) {
   const size_t smem = bse_smem_bytes(n);
   cudaError_t e = cudaMemsetAsync(flag_ptr(c), 0, sizeof(int) * 4, c->stream);
   if (e != cudaSuccess) return e;
-  if (c->opts.precision == DF_FP32_IR) return launch_bse_mixed(c, channel_mask, gg_ptr(c), flag_ptr(c));
+  if (c->opts.precision == DF_FP32_IR) return launch_bse_mixed(c, channel_mask, flag_ptr(c));
   for (int ch = 0; ch < 2; ++ch) {
     if (!(channel_mask & (1 << ch))) continue;
     const long systems = (long)dm.nb * dm.N;

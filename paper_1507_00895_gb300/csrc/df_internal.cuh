@@ -206,6 +206,7 @@ int* bse_flags(df_ctx* c);   // [0]: bit 0 zero pivot, bit 1 |lambda| >= 1
 // mixed precision (df_mixed.cu)
 bool mixed_supported(int n_w);
 size_t mixed_workspace_bytes(const Dims& dm);
-cudaError_t launch_split_gamma(df_ctx* c);
-cudaError_t launch_bse_mixed(df_ctx* c, int channel_mask, const double2* gg, int* flags);
+cudaError_t launch_split_gamma(df_ctx* c, const double2* gg);
+const double2* gamma_gt_ptr(df_ctx* c);   // gamma o gamma^T, written by launch_gamma_gt
+cudaError_t launch_bse_mixed(df_ctx* c, int channel_mask, int* flags);
 }  // namespace df

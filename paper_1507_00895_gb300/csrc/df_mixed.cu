@@ -26,14 +26,19 @@
 
 namespace df {
 
-// gamma (FP64) -> (hi, lo) FP32 pairs, same layout
-__global__ void split_gamma_kernel(size_t count, const double2* __restrict__ g, float2* __restrict__ hi,
-                                   float2* __restrict__ lo) {
+// gamma and gamma o gamma^T (FP64) -> (hi, lo) FP32 pairs, same layouts
+__global__ void split_gamma_kernel(size_t count, const double2* __restrict__ g, const double2* __restrict__ gg,
+                                   float2* __restrict__ hi, float2* __restrict__ lo, float2* __restrict__ gg_hi,
+                                   float2* __restrict__ gg_lo) {
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
     const double2 v = g[i];
-    const float hx = (float)v.x, hy = (float)v.y;
+    float hx = (float)v.x, hy = (float)v.y;
     hi[i] = make_float2(hx, hy);
     lo[i] = make_float2((float)(v.x - (double)hx), (float)(v.y - (double)hy));
+    const double2 w = gg[i];
+    hx = (float)w.x; hy = (float)w.y;
+    gg_hi[i] = make_float2(hx, hy);
+    gg_lo[i] = make_float2((float)(w.x - (double)hx), (float)(w.y - (double)hy));
   }
 }
 
@@ -41,7 +46,8 @@ template <int NP>
 __global__ void __launch_bounds__(256)
 bse_mixed_kernel(Dims dm, int ch0, int nch, const double2* __restrict__ gam,
                  const float2* __restrict__ gam_hi, const float2* __restrict__ gam_lo,
-                 const double2* __restrict__ gg, const double2* __restrict__ chi, double2* __restrict__ kc,
+                 const float2* __restrict__ gg_hi, const float2* __restrict__ gg_lo,
+                 const double2* __restrict__ chi, double2* __restrict__ kc,
                  int* __restrict__ flags) {
   extern __shared__ float2 smf[];
   __shared__ int piv_s[128];
@@ -52,7 +58,7 @@ bse_mixed_kernel(Dims dm, int ch0, int nch, const double2* __restrict__ gam,
     const int c = ch0 + (int)(sys / ((long)nb * N));
     const int rem = (int)(sys - (long)(c - ch0) * nb * N);
     const int a = rem / N, q = rem - a * N;
-    bse_mixed_system<NP>(dm, c, a, q, gam, gam_hi, gam_lo, gg, chi, kc, flags, sp);
+    bse_mixed_system<NP>(dm, c, a, q, gam, gam_hi, gam_lo, gg_hi, gg_lo, chi, kc, flags, sp);
   }
 }
 
@@ -66,19 +72,19 @@ static int mixed_np(int n) { return mixed_pad(n); }
 bool mixed_supported(int n_w) { return mixed_np(n_w) <= 64; }
 
 size_t mixed_workspace_bytes(const Dims& dm) {
-  return (size_t)2 * 2 * dm.nb * dm.n_w * dm.n_w * sizeof(float2);   // gamma hi, lo
+  return (size_t)4 * 2 * dm.nb * dm.n_w * dm.n_w * sizeof(float2);   // gamma hi, lo; gamma o gamma^T hi, lo
 }
 
-cudaError_t launch_split_gamma(df_ctx* c) {
+cudaError_t launch_split_gamma(df_ctx* c, const double2* gg) {
   const Dims& dm = c->dm;
   const size_t count = (size_t)2 * dm.nb * dm.n_w * dm.n_w;
   float2* hi = (float2*)c->mixed_ws;
-  split_gamma_kernel<<<256, 256, 0, c->stream>>>(count, c->gam, hi, hi + count);
+  split_gamma_kernel<<<256, 256, 0, c->stream>>>(count, c->gam, gg, hi, hi + count, hi + 2 * count, hi + 3 * count);
   return cudaGetLastError();
 }
 
 template <int NP>
-static cudaError_t launch_bse_mixed_np(df_ctx* c, int channel_mask, const double2* gg, int* flags) {
+static cudaError_t launch_bse_mixed_np(df_ctx* c, int channel_mask, int* flags) {
   const Dims& dm = c->dm;
   constexpr int P = NP / kTile;
   constexpr int threads = P * P;
@@ -98,19 +104,19 @@ static cudaError_t launch_bse_mixed_np(df_ctx* c, int channel_mask, const double
     if (!(channel_mask & (1 << ch))) continue;
     const long systems = (long)dm.nb * dm.N;
     const int grid = (int)(systems < c->mixed_grid ? systems : c->mixed_grid);
-    bse_mixed_kernel<NP><<<grid, threads, smem, c->stream>>>(dm, ch, 1, c->gam, hi, hi + count, gg, c->chi, c->kc,
-                                                             flags);
+    bse_mixed_kernel<NP><<<grid, threads, smem, c->stream>>>(dm, ch, 1, c->gam, hi, hi + count, hi + 2 * count,
+                                                             hi + 3 * count, c->chi, c->kc, flags);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
-cudaError_t launch_bse_mixed(df_ctx* c, int channel_mask, const double2* gg, int* flags) {
+cudaError_t launch_bse_mixed(df_ctx* c, int channel_mask, int* flags) {
   switch (mixed_np(c->dm.n_w)) {
-    case 8: return launch_bse_mixed_np<8>(c, channel_mask, gg, flags);
-    case 16: return launch_bse_mixed_np<16>(c, channel_mask, gg, flags);
-    case 32: return launch_bse_mixed_np<32>(c, channel_mask, gg, flags);
-    case 64: return launch_bse_mixed_np<64>(c, channel_mask, gg, flags);
+    case 8: return launch_bse_mixed_np<8>(c, channel_mask, flags);
+    case 16: return launch_bse_mixed_np<16>(c, channel_mask, flags);
+    case 32: return launch_bse_mixed_np<32>(c, channel_mask, flags);
+    case 64: return launch_bse_mixed_np<64>(c, channel_mask, flags);
     default: return cudaErrorInvalidValue;
   }
 }

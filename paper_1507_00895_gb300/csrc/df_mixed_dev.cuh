@@ -280,6 +280,21 @@ __device__ __forceinline__ void gj_panel(float2* pan, int k0, int lane, unsigned
         if (c2 < pb) pan[(lane + nlanes * s2) * kPanel + c2] = pv[s2][c2];
 }
 
+// (sr + lr, si + li) += (ah + al)(bh + bl) for complex double-float operands:
+// the four leading products exactly (product + fma error), summed by TwoSum
+// into the leading words; their errors and the four cross products go to
+// the trailing words.  ~2^-46 relative to the largest partial sum.
+__device__ __forceinline__ void cdf_fma(float& sr, float& lr, float& si, float& li, float2 ah, float2 al, float2 bh,
+                                        float2 bl) {
+  float p, e;
+  p = ah.x * bh.x; e = fmaf(ah.x, bh.x, -p); df_add(sr, lr, p); lr += e;
+  p = -ah.y * bh.y; e = fmaf(-ah.y, bh.y, -p); df_add(sr, lr, p); lr += e;
+  lr += fmaf(ah.x, bl.x, fmaf(al.x, bh.x, fmaf(-ah.y, bl.y, -al.y * bh.y)));
+  p = ah.x * bh.y; e = fmaf(ah.x, bh.y, -p); df_add(si, li, p); li += e;
+  p = ah.y * bh.x; e = fmaf(ah.y, bh.x, -p); df_add(si, li, p); li += e;
+  li += fmaf(ah.x, bl.y, fmaf(al.x, bh.y, fmaf(ah.y, bl.x, al.y * bh.x)));
+}
+
 struct MixedSmem {
   // offsets in float2 units (8 bytes)
   int x0, chih, chil, invu, x0d, chi64, work, gt_h, gt_l, yh, yl, total;
@@ -351,7 +366,8 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
                                                  const double2* __restrict__ gam,
                                                  const float2* __restrict__ gam_hi,
                                                  const float2* __restrict__ gam_lo,
-                                                 const double2* __restrict__ gg,
+                                                 const float2* __restrict__ gg_hi,
+                                                 const float2* __restrict__ gg_lo,
                                                  const double2* __restrict__ chi, double2* __restrict__ kc,
                                                  int* __restrict__ flags, const MixedPtrs& sp) {
   const int n = dm.n_w, N = dm.N, nb = dm.nb;
@@ -391,14 +407,16 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
 #pragma unroll
     for (int jj = 0; jj < kTile; ++jj) {
       const int col = tc + P * jj;
-      // D = 1 - gamma chi~ formed in FP64 and rounded once: the diagonal
-      // 1 - gamma_ww chi~_w cancels when |gamma chi~| >> |D|, and a product of
-      // FP32-rounded factors would lose those digits
+      // D = 1 - gamma chi~ formed in double-float and rounded once: the
+      // diagonal 1 - gamma_ww chi~_w cancels when |gamma chi~| >> |D|, and a
+      // product of FP32-rounded factors would lose those digits
       const bool in = (r < n && col < n);
-      const double2 g64 = in ? gam[mat + (size_t)r * n + col] : mk(0.0, 0.0);
-      const double2 z = cmul(g64, sp.chi64[col]);
-      A[ii][jj] = make_float2((float)((r == col ? 1.0 : 0.0) - z.x), (float)(-z.y));
-      A[ii][kTile + jj] = in ? Gh[r * n + col] : make_float2(0.f, 0.f);
+      const float2 gh = in ? Gh[r * n + col] : make_float2(0.f, 0.f);
+      const float2 gl = in ? Gl[r * n + col] : make_float2(0.f, 0.f);
+      float sr = (r == col) ? 1.f : 0.f, lr = 0.f, si = 0.f, li = 0.f;
+      cdf_fma(sr, lr, si, li, make_float2(-gh.x, -gh.y), make_float2(-gl.x, -gl.y), chih[col], chil[col]);
+      A[ii][jj] = make_float2(sr + lr, si + li);
+      A[ii][kTile + jj] = gh;
     }
   }
 
@@ -631,11 +649,17 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
         for (int e = 0; e < 4; ++e) {
           const int row = r16 + gq + (e >= 2 ? 8 : 0), col = c8 + 2 * t4 + (e & 1);
           const int j = b * kCB + col;
-          const double2 gv = (row < n && j < n) ? gam[mat + (size_t)row * n + j] : mk(0.0, 0.0);
+          // R = gamma - X0 + S in double-float (it cancels to ~u32 |gamma|)
+          const bool in = (row < n && j < n);
+          const float2 gh = in ? Gh[row * n + j] : make_float2(0.f, 0.f);
+          const float2 gl = in ? Gl[row * n + j] : make_float2(0.f, 0.f);
           const float2 x = X0s[row * np + j];
-          const double re = gv.x - (double)x.x + ((double)hr[e] + (double)lr[e]);
-          const double im = gv.y - (double)x.y + ((double)hm[e] + (double)lm[e]);
-          X0s[row * np + j] = make_float2((float)re, (float)im);   // R replaces X0
+          float re = gh.x, rl = gl.x, im = gh.y, il = gl.y;
+          df_add(re, rl, -x.x);
+          df_add(re, rl, hr[e]);
+          df_add(im, il, -x.y);
+          df_add(im, il, hm[e]);
+          X0s[row * np + j] = make_float2(re + (rl + lr[e]), im + (il + lm[e]));   // R replaces X0
         }
       }
     }
@@ -763,26 +787,32 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
   __syncthreads();
 
   // ---- diag Gamma = diag X0 + diag E (FP64), Gamma^(2), Eq. sd bracket ----
-  const double2* GG = gg + mat;
+  // Gamma^(2)_jj = sum_x (gamma_jx gamma_xj) chi~_x in double-float
+  const float2* GGh = gg_hi + mat;
+  const float2* GGl = gg_lo + mat;
   // four threads per output frequency j (consecutive lanes, shuffle-reduced)
   // when the block has whole warps; one thread per j otherwise
-  const int per_j = (blockDim.x >= 32) ? 4 : 1;
+  constexpr int per_j = (P * P >= 32) ? 4 : 1;
   for (int base = 0; base < per_j * np; base += blockDim.x) {
     const int idx = base + t;
     const int j = idx / per_j, part = idx % per_j;
-    double2 g2 = mk(0.0, 0.0);
+    float sr = 0.f, lr = 0.f, si = 0.f, li = 0.f;
     if (j < n) {
-      for (int x = part; x < n; x += per_j) {
-        const double2 cx = mk((double)chih[x].x + (double)chil[x].x, (double)chih[x].y + (double)chil[x].y);
-        g2 = cfma(GG[(size_t)j * n + x], cx, g2);
-      }
+      for (int x = part; x < n; x += per_j)
+        cdf_fma(sr, lr, si, li, GGh[j * n + x], GGl[j * n + x], chih[x], chil[x]);
     }
     if (per_j == 4) {
-      g2.x += __shfl_xor_sync(0xffffffffu, g2.x, 1);
-      g2.y += __shfl_xor_sync(0xffffffffu, g2.y, 1);
-      g2.x += __shfl_xor_sync(0xffffffffu, g2.x, 2);
-      g2.y += __shfl_xor_sync(0xffffffffu, g2.y, 2);
+#pragma unroll
+      for (int o = 1; o < 4; o <<= 1) {
+        const float osr = __shfl_xor_sync(0xffffffffu, sr, o), olr = __shfl_xor_sync(0xffffffffu, lr, o);
+        const float osi = __shfl_xor_sync(0xffffffffu, si, o), oli = __shfl_xor_sync(0xffffffffu, li, o);
+        df_add(sr, lr, osr);
+        lr += olr;
+        df_add(si, li, osi);
+        li += oli;
+      }
     }
+    const double2 g2 = mk((double)sr + (double)lr, (double)si + (double)li);
     if (j < n && part == 0) {
       const float2 x0 = x0d[j], e = ediag[j];
       const double2 gdiag = mk((double)x0.x + (double)e.x, (double)x0.y + (double)e.y);
