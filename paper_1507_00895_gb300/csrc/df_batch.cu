@@ -31,6 +31,7 @@ struct PointDev {
   double mix, tol, resid;
   double2 *g, *delta, *gam, *gg, *g0, *gk, *gr, *chi, *kc, *prod, *sigma;
   float2 *gam_hi, *gam_lo, *gg_hi, *gg_lo;   // mixed: FP32 (hi, lo) of gam and gg
+  unsigned char* gdig;                         // mixed, n_pad 32 / 64: gamma's digits
   double* red;   // [2 n_w + 4]
   int* flags;    // [4]
 };
@@ -127,6 +128,9 @@ __global__ void batch_setup_elem_kernel(const PointDev* __restrict__ pts, int p)
       P.gg_lo[idx] = make_float2((float)(w.x - (double)hx), (float)(w.y - (double)hy));
     }
   }
+  if (P.gdig)
+    gamma_digits_rows(n, mixed_pad(n), 2 * P.dm.nb, P.gam, P.gdig, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+                      (gridDim.x * blockDim.x) >> 5, threadIdx.x & 31);
 }
 
 __global__ void __launch_bounds__(kFftThreads)
@@ -181,6 +185,7 @@ batch_bse_mixed_kernel(const PointDev* __restrict__ pts, const int* __restrict__
   __shared__ unsigned long long item_s;
   const MixedPtrs sp = mixed_ptrs(smf, NP, piv_s);
   const long total = start[nseg];
+  long cur = -1;                       // (point, channel, W) whose gamma digits are in shared memory
   for (;;) {
     if (threadIdx.x == 0) item_s = atomicAdd(counter, (unsigned long long)chunk);
     __syncthreads();
@@ -198,7 +203,10 @@ batch_bse_mixed_kernel(const PointDev* __restrict__ pts, const int* __restrict__
       const int c = (int)(local / per_ch);
       const int rem = (int)(local - (long)c * per_ch);
       const int a = rem / dm.N, q = rem - a * dm.N;
-      bse_mixed_system<NP>(dm, c, a, q, P.gam, P.gam_hi, P.gam_lo, P.gg_hi, P.gg_lo, P.chi, P.kc, P.flags, sp);
+      const long key = (long)k * 256 + c * dm.nb + a;
+      bse_mixed_system<NP>(dm, c, a, q, P.gam, P.gam_hi, P.gam_lo, P.gg_hi, P.gg_lo, P.chi, P.kc, P.flags, sp,
+                           P.gdig ? P.gdig + (size_t)(c * dm.nb + a) * gdig_bytes(NP) : nullptr, key != cur);
+      cur = key;
     }
   }
 }
@@ -473,6 +481,8 @@ df_status df_batch_init(df_batch** out, int npts, const df_point* pts, int preci
     total += align_up(sizeof(double) * (2 * dm.n_w + 4));
     total += align_up(sizeof(int) * 4);
     if (P.mixed) total += align_up(sizeof(float2) * nv) * 4;      // gam hi, lo; gg hi, lo
+    if (P.mixed && use_tc_residual(mixed_pad(dm.n_w)))
+      total += align_up((size_t)2 * dm.nb * gdig_bytes(mixed_pad(dm.n_w)));   // gamma's digits
   }
   b->arena_bytes = total;
   df_status st = DF_OK;
@@ -509,6 +519,8 @@ df_status df_batch_init(df_batch** out, int npts, const df_point* pts, int preci
       P.gam_lo = (float2*)take(sizeof(float2) * nv);
       P.gg_hi = (float2*)take(sizeof(float2) * nv);
       P.gg_lo = (float2*)take(sizeof(float2) * nv);
+      if (use_tc_residual(mixed_pad(dm.n_w)))
+        P.gdig = (unsigned char*)take((size_t)2 * dm.nb * gdig_bytes(mixed_pad(dm.n_w)));
     }
     const char* limit = b->arena + (i + 1 < npts ? off[i + 1] : total);
     if (cur > limit) {

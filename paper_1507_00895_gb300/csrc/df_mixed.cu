@@ -42,23 +42,38 @@ __global__ void split_gamma_kernel(size_t count, const double2* __restrict__ g, 
   }
 }
 
+// gamma's digits for the tensor-core residual (once per input upload)
+__global__ void gamma_digits_kernel(int n, int np, int count, const double2* __restrict__ gam,
+                                    unsigned char* __restrict__ out) {
+  gamma_digits_rows(n, np, count, gam, out, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+                    (gridDim.x * blockDim.x) >> 5, threadIdx.x & 31);
+}
+
+// One contiguous range of systems per block (so that consecutive systems
+// share (channel, W) and gamma's digits stay in shared memory).
 template <int NP>
 __global__ void __launch_bounds__(256)
 bse_mixed_kernel(Dims dm, int ch0, int nch, const double2* __restrict__ gam,
                  const float2* __restrict__ gam_hi, const float2* __restrict__ gam_lo,
                  const float2* __restrict__ gg_hi, const float2* __restrict__ gg_lo,
                  const double2* __restrict__ chi, double2* __restrict__ kc,
-                 int* __restrict__ flags) {
+                 const unsigned char* __restrict__ gdig, int* __restrict__ flags) {
   extern __shared__ float2 smf[];
   __shared__ int piv_s[128];
   const MixedPtrs sp = mixed_ptrs(smf, NP, piv_s);
   const int N = dm.N, nb = dm.nb;
   const long systems = (long)nch * nb * N;
-  for (long sys = blockIdx.x; sys < systems; sys += gridDim.x) {
+  const long per = (systems + gridDim.x - 1) / gridDim.x;
+  const long s0 = (long)blockIdx.x * per, s1 = s0 + per < systems ? s0 + per : systems;
+  int cur = -1;
+  for (long sys = s0; sys < s1; ++sys) {
     const int c = ch0 + (int)(sys / ((long)nb * N));
     const int rem = (int)(sys - (long)(c - ch0) * nb * N);
     const int a = rem / N, q = rem - a * N;
-    bse_mixed_system<NP>(dm, c, a, q, gam, gam_hi, gam_lo, gg_hi, gg_lo, chi, kc, flags, sp);
+    const int key = c * nb + a;
+    bse_mixed_system<NP>(dm, c, a, q, gam, gam_hi, gam_lo, gg_hi, gg_lo, chi, kc, flags, sp,
+                         gdig ? gdig + (size_t)key * gdig_bytes(NP) : nullptr, key != cur);
+    cur = key;
   }
 }
 
@@ -71,8 +86,17 @@ static int mixed_np(int n) { return mixed_pad(n); }
 // the register-resident [D | RHS] tile limits this kernel to n_w <= 64
 bool mixed_supported(int n_w) { return mixed_np(n_w) <= 64; }
 
+// gamma hi, lo; gamma o gamma^T hi, lo; gamma's digits (tensor-core residual)
 size_t mixed_workspace_bytes(const Dims& dm) {
-  return (size_t)4 * 2 * dm.nb * dm.n_w * dm.n_w * sizeof(float2);   // gamma hi, lo; gamma o gamma^T hi, lo
+  const int np = mixed_np(dm.n_w);
+  const size_t digits = use_tc_residual(np) ? (size_t)2 * dm.nb * gdig_bytes(np) : 0;
+  return (size_t)4 * 2 * dm.nb * dm.n_w * dm.n_w * sizeof(float2) + digits;
+}
+
+static unsigned char* gdig_ptr(df_ctx* c) {
+  const int np = mixed_np(c->dm.n_w);
+  if (!use_tc_residual(np)) return nullptr;
+  return (unsigned char*)c->mixed_ws + (size_t)4 * 2 * c->dm.nb * c->dm.n_w * c->dm.n_w * sizeof(float2);
 }
 
 cudaError_t launch_split_gamma(df_ctx* c, const double2* gg) {
@@ -80,7 +104,14 @@ cudaError_t launch_split_gamma(df_ctx* c, const double2* gg) {
   const size_t count = (size_t)2 * dm.nb * dm.n_w * dm.n_w;
   float2* hi = (float2*)c->mixed_ws;
   split_gamma_kernel<<<256, 256, 0, c->stream>>>(count, c->gam, gg, hi, hi + count, hi + 2 * count, hi + 3 * count);
-  return cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (unsigned char* gd = gdig_ptr(c)) {
+    const int np = mixed_np(dm.n_w), rows = 2 * dm.nb * np;
+    gamma_digits_kernel<<<(rows + 7) / 8, 256, 0, c->stream>>>(dm.n_w, np, 2 * dm.nb, c->gam, gd);
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 template <int NP>
@@ -105,7 +136,7 @@ static cudaError_t launch_bse_mixed_np(df_ctx* c, int channel_mask, int* flags) 
     const long systems = (long)dm.nb * dm.N;
     const int grid = (int)(systems < c->mixed_grid ? systems : c->mixed_grid);
     bse_mixed_kernel<NP><<<grid, threads, smem, c->stream>>>(dm, ch, 1, c->gam, hi, hi + count, hi + 2 * count,
-                                                             hi + 3 * count, c->chi, c->kc, flags);
+                                                             hi + 3 * count, c->chi, c->kc, gdig_ptr(c), flags);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;

@@ -44,7 +44,12 @@ constexpr int kPanelRows = 2;     // panel rows per lane of warp 0 (np / min(32,
 
 // padded order of a mixed ladder: a power of two >= 8 (P = np / 4 >= 2 lanes per
 // thread row; warp 0 then holds at most two panel rows per lane)
-inline int mixed_pad(int n) {
+// bytes of one gamma matrix's digits for the tensor-core residual: 8 slices
+// x (re, im) x np rows of 64 bf16 (swizzled as in shared memory), then the
+// np row exponents (int)
+__host__ __device__ constexpr int gdig_bytes(int np) { return 2 * kSlices * 2 * np * 64 + 4 * np; }
+
+__host__ __device__ inline int mixed_pad(int n) {
   int np = 2 * kTile;
   while (np < n) np *= 2;
   return np;
@@ -295,16 +300,82 @@ __device__ __forceinline__ void cdf_fma(float& sr, float& lr, float& si, float& 
   li += fmaf(ah.x, bl.y, fmaf(al.x, bh.y, fmaf(ah.y, bl.x, al.y * bh.x)));
 }
 
+// bf16 bit pattern of the signed digit (sign16 = 0 or 0x8000, 0 <= d < 256),
+// exact and without a conversion unit: the float 2^23 + d minus 2^23
+__device__ __forceinline__ unsigned bf16_digit(unsigned d, unsigned sign16) {
+  return (__float_as_uint(__uint_as_float(0x4B000000u | d) - 8388608.f) >> 16) | sign16;
+}
+
+// v 2^(56 - e), truncated toward zero, as a signed integer (|v| < 2^e;
+// subnormal v count as 0)
+__device__ __forceinline__ long long fixed56(float v, int e) {
+  const unsigned bits = __float_as_uint(v);
+  const int E = (int)((bits >> 23) & 0xFFu);
+  if (E == 0) return 0;
+  const unsigned long long M = (unsigned long long)((bits & 0x7FFFFFu) | 0x800000u);
+  const int sh = E - 150 + 56 - e;                       // v = M 2^(E - 150), sh <= 32
+  const unsigned long long m = sh >= 0 ? (M << sh) : (-sh >= 64 ? 0ull : (M >> -sh));
+  return (bits >> 31) ? -(long long)m : (long long)m;
+}
+
+// the 8 base-128 digits of hi + lo relative to 2^e as bf16 patterns
+__device__ __forceinline__ void digits_pair(float hi, float lo, int e, unsigned* d) {
+  const long long T = fixed56(hi, e) + fixed56(lo, e);
+  const unsigned sign16 = T < 0 ? 0x8000u : 0u;
+  const unsigned long long m = (unsigned long long)(T < 0 ? -T : T);
+#pragma unroll
+  for (int s2 = 0; s2 < kSlices; ++s2) d[s2] = bf16_digit((unsigned)((m >> (49 - 7 * s2)) & 0x7Full), sign16);
+}
+
+// gamma's digits for the tensor-core residual, `count` n x n matrices (FP64)
+// -> out[count][gdig_bytes(np)]: row i's exponent bound e_i (|gamma_il| < 2^e_i
+// for both parts, -1000 for a zero row) and the 8 digits of each part
+// relative to 2^e_i; rows and columns >= n are zero.  One warp per row.
+__device__ __forceinline__ void gamma_digits_rows(int n, int np, int count, const double2* __restrict__ gam,
+                                                  unsigned char* __restrict__ out, int warp_id, int nwarps,
+                                                  int lane) {
+  for (int w = warp_id; w < count * np; w += nwarps) {
+    const int mtx = w / np, i = w - mtx * np;
+    const double2* G = gam + (size_t)mtx * n * n;
+    unsigned char* O = out + (size_t)mtx * gdig_bytes(np);
+    __nv_bfloat16* dig = reinterpret_cast<__nv_bfloat16*>(O);
+    int* rowe = reinterpret_cast<int*>(O + 2 * kSlices * 2 * np * 64);
+    double m = 0.0;
+    for (int l = lane; l < n; l += 32)
+      if (i < n) m = fmax(m, fmax(fabs(G[(size_t)i * n + l].x), fabs(G[(size_t)i * n + l].y)));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    int e = -1000;
+    if (m > 0.0) frexp(m, &e);                           // m < 2^e
+    if (lane == 0) rowe[i] = e;
+    for (int l = lane; l < 64; l += 32) {
+      float dr[kSlices], di[kSlices];
+      if (i < n && l < n && e > -1000) {
+        digits_f64(G[(size_t)i * n + l].x, e, dr);
+        digits_f64(G[(size_t)i * n + l].y, e, di);
+      } else {
+#pragma unroll
+        for (int s2 = 0; s2 < kSlices; ++s2) dr[s2] = di[s2] = 0.f;
+      }
+      const int o = swz(i, l);
+#pragma unroll
+      for (int s2 = 0; s2 < kSlices; ++s2) {
+        dig[(size_t)(s2 * 2 + 0) * np * 64 + o] = __float2bfloat16_rn(dr[s2]);
+        dig[(size_t)(s2 * 2 + 1) * np * 64 + o] = __float2bfloat16_rn(di[s2]);
+      }
+    }
+  }
+}
+
 struct MixedSmem {
   // offsets in float2 units (8 bytes)
   int x0, chih, chil, invu, x0d, chi64, work, gt_h, gt_l, yh, yl, total;
 };
 
-// bytes of the tensor-core residual's work area (n_pad in {32, 64})
-__host__ __device__ inline int tc_work_bytes(int np) {
-  return 2 * kSlices * 2 * np * 64        // Z digits, bf16 [slice][re/im][row][64]
-         + 2 * kSlices * 2 * kCB * 64     // X0 digits of one column block, bf16 [slice][re/im][col][64]
-         + 4 * (np + kCB);                // row / column exponents
+// bytes of the tensor-core residual's work area (n_pad in {32, 64}): the
+// gamma digits of the current (channel, W) (kept across systems), then the
+// Y digits of one column block and their column exponents
+__host__ __device__ constexpr int tc_work_bytes(int np) {
+  return gdig_bytes(np) + 2 * kSlices * 2 * kCB * 64 + 4 * kCB;
 }
 
 __host__ __device__ constexpr bool use_tc_residual(int np) { return np == 32 || np == 64; }
@@ -326,7 +397,9 @@ __host__ __device__ inline MixedSmem mixed_layout(int np) {
   L.yl = L.yh + np * np;
   const int simt = 2 * kResChunk * np + 2 * np * np;
   const int tc = (tc_work_bytes(np) + 7) / 8;
-  const int gj = 2 * np * kPanel + kPanel * 2 * np;   // Gauss-Jordan panels [2][np][kPanel], pivot rows
+  // Gauss-Jordan panels [2][np][kPanel] and pivot rows [kPanel][2 np]; with
+  // the tensor-core residual they sit in the Y-digit area, past gamma's digits
+  const int gj = (use_tc_residual(np) ? gdig_bytes(np) / 8 : 0) + 2 * np * kPanel + kPanel * 2 * np;
   const int res = use_tc_residual(np) ? tc : simt;
   o += res > gj ? res : gj;
   L.total = o;
@@ -369,7 +442,8 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
                                                  const float2* __restrict__ gg_hi,
                                                  const float2* __restrict__ gg_lo,
                                                  const double2* __restrict__ chi, double2* __restrict__ kc,
-                                                 int* __restrict__ flags, const MixedPtrs& sp) {
+                                                 int* __restrict__ flags, const MixedPtrs& sp,
+                                                 const unsigned char* __restrict__ gdig, bool reload) {
   const int n = dm.n_w, N = dm.N, nb = dm.nb;
   constexpr int np = NP, P = NP / kTile;
   float2* X0s = sp.X0s;
@@ -388,6 +462,14 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
   const float2* Gh = gam_hi + mat;
   const float2* Gl = gam_lo + mat;
 
+  if constexpr (use_tc_residual(NP)) {
+    // gamma's digits of this (channel, W), kept in shared memory across systems
+    if (reload) {
+      const uint4* src = reinterpret_cast<const uint4*>(gdig);
+      uint4* dst = reinterpret_cast<uint4*>(sp.work);
+      for (int i = t; i < gdig_bytes(NP) / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+    }
+  }
   for (int i = t; i < np; i += blockDim.x) {
     double2 x = (i < n) ? chi[((size_t)a * n + i) * N + q] : mk(0.0, 0.0);
     const float hx = (float)x.x, hy = (float)x.y;
@@ -435,7 +517,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
   constexpr int nlanes = P * P < 32 ? P * P : 32;
   constexpr unsigned wmask = nlanes == 32 ? 0xffffffffu : ((1u << nlanes) - 1u);
   constexpr int pb = P < kPanel ? P : kPanel;        // panel width b
-  float2* panbuf = reinterpret_cast<float2*>(sp.work);          // [2][np][kPanel]
+  float2* panbuf = reinterpret_cast<float2*>(sp.work + (use_tc_residual(NP) ? gdig_bytes(NP) : 0));   // [2][np][kPanel]
   float2* prs = panbuf + 2 * np * kPanel;                        // [kPanel][2 np]
   int* rowstep = reinterpret_cast<int*>(invu);                   // pivot step of each row, -1 if none
   for (int i = t; i < np; i += blockDim.x) rowstep[i] = -1;
@@ -519,46 +601,19 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
   __syncthreads();
   for (int j = t; j < np; j += blockDim.x) x0d[j] = X0s[j * np + j];
   if constexpr (use_tc_residual(NP)) {
-    // ---- residual R = gamma - X0 + Z X0 on the tensor cores, Z = gamma diag(chi~) ----
-    // Z (FP64 products) and X0 (FP32) are cut into 7 base-256 digits relative to
-    // per-row / per-column powers of two; each digit pair's product is exact in
-    // the FP32 accumulator (|d| <= 255, 64 terms, two products: < 2^23), and the
-    // 28 pairs with weight >= 2^-64 are folded, scaled, into a double-float sum.
-    __nv_bfloat16* zs = reinterpret_cast<__nv_bfloat16*>(sp.work);    // [kSlices][2][np][64]
-    __nv_bfloat16* xs = zs + (size_t)kSlices * 2 * np * 64;          // [kSlices][2][kCB][64]
-    int* rowe = reinterpret_cast<int*>(xs + (size_t)kSlices * 2 * kCB * 64);   // [np]
-    int* cole = rowe + np;                                           // [kCB]
+    // ---- residual R = gamma - X0 + gamma Y on the tensor cores, Y = diag(chi~) X0 ----
+    // gamma's digits (cut once per input upload: 8 signed base-128 digits
+    // relative to per-row powers of two) are in zs / rowe; Y is formed in
+    // double-float and cut the same way relative to per-column powers of two,
+    // kCB columns at a time.  Each digit pair's product is exact in the FP32
+    // accumulator of its weight, and the 36 pairs with weight >= 2^-63 are
+    // folded, scaled, into a double-float sum.
+    __nv_bfloat16* zs = reinterpret_cast<__nv_bfloat16*>(sp.work);                       // [kSlices][2][np][64]
+    const int* rowe = reinterpret_cast<const int*>(zs + (size_t)kSlices * 2 * np * 64);   // [np]
+    __nv_bfloat16* xs = reinterpret_cast<__nv_bfloat16*>(sp.work + gdig_bytes(NP));      // [kSlices][2][kCB][64]
+    int* cole = reinterpret_cast<int*>(xs + (size_t)kSlices * 2 * kCB * 64);             // [kCB]
+    unsigned* xw = reinterpret_cast<unsigned*>(xs);
     const int nthr = blockDim.x;
-    for (int i = t; i < np; i += nthr) rowe[i] = -1000;
-    __syncthreads();
-    for (int idx = t; idx < np * np; idx += nthr) {
-      const int i = idx / np, l = idx - i * np;
-      if (i < n && l < n) {
-        const float2 gg2 = Gh[i * n + l];
-        const float2 xx = chih[l];
-        const float u = (fabsf(gg2.x) + fabsf(gg2.y)) * (fabsf(xx.x) + fabsf(xx.y)) * 1.0001f;
-        if (u > 0.f) atomicMax(&rowe[i], exp_bound_f32(u));
-      }
-    }
-    __syncthreads();
-    for (int idx = t; idx < np * np; idx += nthr) {
-      const int i = idx / np, l = idx - i * np;
-      float dr[kSlices], di[kSlices];
-      if (i < n && l < n && rowe[i] > -1000) {
-        const double2 z = cmul(gam[mat + (size_t)i * n + l], sp.chi64[l]);
-        digits_f64(z.x, rowe[i], dr);
-        digits_f64(z.y, rowe[i], di);
-      } else {
-#pragma unroll
-        for (int q2 = 0; q2 < kSlices; ++q2) dr[q2] = di[q2] = 0.f;
-      }
-      const int o = swz(i, l);
-#pragma unroll
-      for (int q2 = 0; q2 < kSlices; ++q2) {
-        zs[(size_t)(q2 * 2 + 0) * np * 64 + o] = __float2bfloat16_rn(dr[q2]);
-        zs[(size_t)(q2 * 2 + 1) * np * 64 + o] = __float2bfloat16_rn(di[q2]);
-      }
-    }
     const int warp = t >> 5, lane = t & 31, gq = lane >> 2, t4 = lane & 3;
     const int nwarp = nthr >> 5;
     const int tiles = (np / 16) * (kCB / 8);
@@ -569,26 +624,37 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
       for (int idx = t; idx < kCB * np; idx += nthr) {
         const int c2 = idx / np, l = idx - c2 * np;
         const float2 x = X0s[l * np + b * kCB + c2];
-        const float m = fmaxf(fabsf(x.x), fabsf(x.y));
+        float yr = 0.f, ylr = 0.f, yi = 0.f, yli = 0.f;
+        cdf_fma(yr, ylr, yi, yli, chih[l], chil[l], x, make_float2(0.f, 0.f));
+        const float m = fmaxf(fabsf(yr), fabsf(yi)) * 1.0001f;
         if (m > 0.f) atomicMax(&cole[c2], exp_bound_f32(m));
       }
       __syncthreads();
-      for (int idx = t; idx < kCB * np; idx += nthr) {
-        const int c2 = idx / np, l = idx - c2 * np;
-        const float2 x = X0s[l * np + b * kCB + c2];
-        float dr[kSlices], di[kSlices];
-        if (cole[c2] > -1000) {
-          digits_f32(x.x, cole[c2], dr);
-          digits_f32(x.y, cole[c2], di);
-        } else {
+      // two consecutive l per thread: one 32-bit word per slice and part
+      for (int idx = t; idx < kCB * np / 2; idx += nthr) {
+        const int c2 = idx / (np / 2), l = 2 * (idx - c2 * (np / 2));
+        unsigned w0[kSlices], w1[kSlices], v0[kSlices], v1[kSlices];
+        const int e = cole[c2];
 #pragma unroll
-          for (int q2 = 0; q2 < kSlices; ++q2) dr[q2] = di[q2] = 0.f;
+        for (int h = 0; h < 2; ++h) {
+          const float2 x = X0s[(l + h) * np + b * kCB + c2];
+          float yr = 0.f, ylr = 0.f, yi = 0.f, yli = 0.f;
+          cdf_fma(yr, ylr, yi, yli, chih[l + h], chil[l + h], x, make_float2(0.f, 0.f));
+          unsigned* dr = h ? v0 : w0;
+          unsigned* di = h ? v1 : w1;
+          if (e > -1000) {
+            digits_pair(yr, ylr, e, dr);
+            digits_pair(yi, yli, e, di);
+          } else {
+#pragma unroll
+            for (int s2 = 0; s2 < kSlices; ++s2) dr[s2] = di[s2] = 0u;
+          }
         }
-        const int o = swz(c2, l);
+        const int wo = swz(c2, l) >> 1;
 #pragma unroll
-        for (int q2 = 0; q2 < kSlices; ++q2) {
-          xs[(size_t)(q2 * 2 + 0) * kCB * 64 + o] = __float2bfloat16_rn(dr[q2]);
-          xs[(size_t)(q2 * 2 + 1) * kCB * 64 + o] = __float2bfloat16_rn(di[q2]);
+        for (int s2 = 0; s2 < kSlices; ++s2) {
+          xw[(s2 * 2 + 0) * kCB * 32 + wo] = w0[s2] | (v0[s2] << 16);
+          xw[(s2 * 2 + 1) * kCB * 32 + wo] = w1[s2] | (v1[s2] << 16);
         }
       }
       __syncthreads();
