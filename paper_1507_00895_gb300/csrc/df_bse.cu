@@ -54,10 +54,12 @@ bse_f64_kernel(Dims dm, int ch0, int nch, int nc, const double2* __restrict__ ga
 // leading eigenvalue of A = gamma_W diag(chi~_W(q)): power iteration with a
 // Rayleigh-quotient estimate, first in FP32 (gamma staged in shared memory
 // as complex64) until the estimate settles to FP32 precision, then polished
-// in FP64 from that vector (gamma read in FP64 through L1/L2).  The
-// reported value and its converged flag are those of the FP64 phase.  One
-// CTA handles kEigQ systems that share (channel, W); each thread owns
-// (row, system) pairs of y = A v.
+// from that vector with FP64 vectors and Rayleigh quotients, the products
+// gamma (chi~ o v) in double-float FP32 (gamma staged as (hi, lo) pairs;
+// ~2^-46 relative, far below the 1e-12 stopping tolerance).  The reported
+// value and its converged flag are those of the polish.  One CTA handles
+// kEigQ systems that share (channel, W); each thread owns (row, system)
+// pairs of y = A v.
 // ---------------------------------------------------------------------------
 constexpr int kEigQ = 8;
 constexpr int kEigThreads = 256;
@@ -88,7 +90,7 @@ __device__ __forceinline__ void eig_rayleigh(int n, int warp, int lane, const C*
 }
 
 __global__ void __launch_bounds__(kEigThreads)
-lambda_kernel(Dims dm, int ch0, int a0, int na, int unused, double tol, const double2* __restrict__ gam,
+lambda_kernel(Dims dm, int ch0, int a0, int na, double tol, const double2* __restrict__ gam,
               const double2* __restrict__ chi, double2* __restrict__ lam, int* __restrict__ ok,
               int* __restrict__ flags) {
   extern __shared__ double2 sm[];
@@ -97,7 +99,8 @@ lambda_kernel(Dims dm, int ch0, int a0, int na, int unused, double tol, const do
   double2* xq = v + n * kEigQ;
   double2* y = xq + n * kEigQ;
   float2* G32 = (float2*)(y + n * kEigQ);  // [n][n]
-  float2* v32 = G32 + n * n;
+  float2* G32l = G32 + n * n;              // [n][n], gamma - G32
+  float2* v32 = G32l + n * n;
   float2* x32 = v32 + n * kEigQ;
   float2* y32 = x32 + n * kEigQ;
   __shared__ double2 lam_old[kEigQ], lam_new[kEigQ];
@@ -107,9 +110,8 @@ lambda_kernel(Dims dm, int ch0, int a0, int na, int unused, double tol, const do
   __shared__ int done[kEigQ];
   const int qtiles = (N + kEigQ - 1) / kEigQ;
   const int tile = blockIdx.x % qtiles;
-  const int a = a0 + blockIdx.x / qtiles;
-  const int c = ch0;
-  if (a >= a0 + na) return;
+  const int a = a0 + (blockIdx.x / qtiles) % na;
+  const int c = ch0 + blockIdx.x / (qtiles * na);
   const int q0 = tile * kEigQ;
   const int nq = min(kEigQ, N - q0);
   const double2* Gg = gam + ((size_t)c * nb + a) * n * n;
@@ -117,7 +119,9 @@ lambda_kernel(Dims dm, int ch0, int a0, int na, int unused, double tol, const do
 
   for (int idx = tid; idx < n * n; idx += blockDim.x) {
     const double2 g = Gg[idx];
-    G32[idx] = make_float2((float)g.x, (float)g.y);
+    const float hx = (float)g.x, hy = (float)g.y;
+    G32[idx] = make_float2(hx, hy);
+    G32l[idx] = make_float2((float)(g.x - (double)hx), (float)(g.y - (double)hy));
   }
   for (int idx = tid; idx < n * kEigQ; idx += blockDim.x) {
     const int j = idx / kEigQ, t = idx % kEigQ;
@@ -161,12 +165,22 @@ lambda_kernel(Dims dm, int ch0, int a0, int na, int unused, double tol, const do
   for (int idx = tid; idx < n * kEigQ; idx += blockDim.x) v[idx] = mk((double)v32[idx].x, (double)v32[idx].y);
   if (tid < kEigQ) done[tid] = (tid < nq) ? 0 : 1;
   __syncthreads();
+  float2* wh = x32;                        // chi~ o v as (hi, lo) pairs; x32, y32 are free now
+  float2* wl = y32;
   for (int it = 0; it < kEigIter64; ++it) {
+    for (int idx = tid; idx < n * kEigQ; idx += blockDim.x) {
+      const double2 w = cmul(xq[idx], v[idx]);
+      const float hx = (float)w.x, hy = (float)w.y;
+      wh[idx] = make_float2(hx, hy);
+      wl[idx] = make_float2((float)(w.x - (double)hx), (float)(w.y - (double)hy));
+    }
+    __syncthreads();
     for (int p = tid; p < n * kEigQ; p += blockDim.x) {
       const int i = p / kEigQ, t = p % kEigQ;
-      double2 acc = mk(0.0, 0.0);
-      for (int j = 0; j < n; ++j) acc = cfma(Gg[(size_t)i * n + j], cmul(xq[j * kEigQ + t], v[j * kEigQ + t]), acc);
-      y[p] = acc;
+      float sr = 0.f, lr = 0.f, si = 0.f, li = 0.f;
+      for (int j = 0; j < n; ++j)
+        cdf_fma(sr, lr, si, li, G32[i * n + j], G32l[i * n + j], wh[j * kEigQ + t], wl[j * kEigQ + t]);
+      y[p] = mk((double)sr + (double)lr, (double)si + (double)li);
     }
     __syncthreads();
     eig_rayleigh<double2, double>(n, warp, lane, v, y, lam_new, nrm);
@@ -263,19 +277,18 @@ cudaError_t launch_lambda(df_ctx* c, int channel_mask) {
   const int a0 = (c->opts.eig_mode == 1) ? dm.m_max : 0;
   const int na = (c->opts.eig_mode == 1) ? 1 : dm.nb;
   const int qtiles = (dm.N + kEigQ - 1) / kEigQ;
-  const int g_in_smem = 0;
   const size_t smem = sizeof(double2) * 3 * dm.n_w * kEigQ +
-                      sizeof(float2) * ((size_t)dm.n_w * dm.n_w + 3 * dm.n_w * kEigQ);
+                      sizeof(float2) * ((size_t)2 * dm.n_w * dm.n_w + 3 * dm.n_w * kEigQ);
   cudaError_t e = cudaFuncSetAttribute((const void*)lambda_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  for (int ch = 0; ch < 2; ++ch) {
-    if (!(channel_mask & (1 << ch))) continue;
-    lambda_kernel<<<qtiles * na, kEigThreads, smem, c->stream>>>(dm, ch, a0, na, g_in_smem, 1e-12, c->gam,
-                                                                 c->chi, c->lam, c->lam_ok, flag_ptr(c));
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  // both channels in one launch when both are asked for
+  const int ch0 = (channel_mask & 1) ? 0 : 1;
+  const int nch = (channel_mask & 1) && (channel_mask & 2) ? 2 : 1;
+  if (!(channel_mask & 3)) return cudaSuccess;
+  lambda_kernel<<<nch * na * qtiles, kEigThreads, smem, c->stream>>>(dm, ch0, a0, na, 1e-12, c->gam, c->chi, c->lam,
+                                                                     c->lam_ok, flag_ptr(c));
+  return cudaGetLastError();
 }
 
 }  // namespace df

@@ -71,19 +71,6 @@ __device__ __forceinline__ float2 cinvf(float2 z) {
   return make_float2(a * d, -b * d);
 }
 
-// double-float helpers (value = hi + lo, |lo| <= ulp(hi)/2 after renormalisation)
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = a + b;
-  const float bb = s - a;
-  e = (a - (s - bb)) + (b - bb);
-}
-// acc (hi, lo) += p exactly-ish: hi absorbs p with its rounding error moved to lo
-__device__ __forceinline__ void df_add(float& hi, float& lo, float p) {
-  float s, e;
-  two_sum(hi, p, s, e);
-  hi = s;
-  lo += e;
-}
 // (hi, lo) += a * b with a renormalised double-float accumulator: the exact
 // product p + pe (fma), TwoSum into hi, the error and lo folded back by
 // FastTwoSum, so that |lo| <= ulp(hi)/2 after every step and the running
@@ -283,21 +270,6 @@ __device__ __forceinline__ void gj_panel(float2* pan, int k0, int lane, unsigned
 #pragma unroll
       for (int c2 = 0; c2 < kPanel; ++c2)
         if (c2 < pb) pan[(lane + nlanes * s2) * kPanel + c2] = pv[s2][c2];
-}
-
-// (sr + lr, si + li) += (ah + al)(bh + bl) for complex double-float operands:
-// the four leading products exactly (product + fma error), summed by TwoSum
-// into the leading words; their errors and the four cross products go to
-// the trailing words.  ~2^-46 relative to the largest partial sum.
-__device__ __forceinline__ void cdf_fma(float& sr, float& lr, float& si, float& li, float2 ah, float2 al, float2 bh,
-                                        float2 bl) {
-  float p, e;
-  p = ah.x * bh.x; e = fmaf(ah.x, bh.x, -p); df_add(sr, lr, p); lr += e;
-  p = -ah.y * bh.y; e = fmaf(-ah.y, bh.y, -p); df_add(sr, lr, p); lr += e;
-  lr += fmaf(ah.x, bl.x, fmaf(al.x, bh.x, fmaf(-ah.y, bl.y, -al.y * bh.y)));
-  p = ah.x * bh.y; e = fmaf(ah.x, bh.y, -p); df_add(si, li, p); li += e;
-  p = ah.y * bh.x; e = fmaf(ah.y, bh.x, -p); df_add(si, li, p); li += e;
-  li += fmaf(ah.x, bl.y, fmaf(al.x, bh.y, fmaf(ah.y, bl.x, al.y * bh.x)));
 }
 
 // bf16 bit pattern of the signed digit (sign16 = 0 or 0x8000, 0 <= d < 256),
