@@ -46,7 +46,7 @@ FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07
 FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) per launch of the ladder kernel from one ncu capture
 # of that kernel on this workload (None once the kernel changes)
-NCU_TRAFFIC = {"bse_f64_kernel": 17729536, "bse_mixed_kernel": 18327040}
+NCU_TRAFFIC = {"bse_f64_kernel": None, "bse_mixed_kernel": None}
 
 
 def dist_env():
@@ -413,16 +413,17 @@ def run_ours(args):
                                    "1.20 TF/s measured by an FMA loop)",
                     "flop_per_launch": systems_per_launch * flop, "launch_ms": bse_avg_s * 1e3}
         else:
-            # FP32: LU n^3/3 + forward n^3/2 + back n^3/2 + correction forward and back n^3
-            # complex MACs; plus the n^3 complex MACs of the double-float residual
-            flop = 8.0 * (7.0 / 3.0) * n ** 3 + 8.0 * n ** 3
+            # FP32 Gauss-Jordan sweep of [D | gamma] (2 n^3 complex MACs) plus the
+            # residual product gamma Y (n^3 complex MACs, on the tensor cores)
+            flop = 8.0 * 2.0 * n ** 3 + 8.0 * n ** 3
             achieved = systems_per_launch * flop / bse_avg_s / 1e9
             roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_GFLOPS, "unit": "GFLOP/s",
                     "frac": achieved / FP32_PEAK_GFLOPS, "traffic": NCU_TRAFFIC.get("bse_mixed_kernel"),
                     "kernel": "bse_mixed_kernel",
                     "peak_source": "FP32 CUDA cores: 152 SM x 128 FMA/clk x 2 flop x 2.07 GHz "
-                                   "(75.2 TF/s measured by an FMA loop); the residual's double-float flops "
-                                   "count once each here but cost ~11 FP32 instructions",
+                                   "(75.2 TF/s measured by an FMA loop); the residual's n^3 complex MACs "
+                                   "count once each here but run as 36 bf16 digit-pair products on the "
+                                   "tensor cores (mma.sync)",
                     "flop_per_launch": systems_per_launch * flop, "launch_ms": bse_avg_s * 1e3}
         res = {"value": world * points / (ms * 1e-3), "ms_per_step": ms, "roofline": roof,
                "gpu_launches": sum(v[1] for v in timing.values()),

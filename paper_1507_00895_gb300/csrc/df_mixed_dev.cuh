@@ -40,6 +40,7 @@ constexpr int kResChunk = 16;     // gamma columns staged per residual sweep (SI
 constexpr int kSlices = 8;        // base-128 digits of the tensor-core residual (56 bits)
 constexpr int kCB = 16;           // column block of the tensor-core residual
 constexpr int kPanel = 8;         // pivot columns per Gauss-Jordan panel
+constexpr int kPanelLd = kPanel + 1;   // panel row stride (float2): conflict-free lane-per-row access
 constexpr int kPanelRows = 2;     // panel rows per lane of warp 0 (np / min(32, P^2) <= 2 for np >= 8)
 
 // padded order of a mixed ladder: a power of two >= 8 (P = np / 4 >= 2 lanes per
@@ -179,7 +180,7 @@ __device__ __forceinline__ void dd_add(float& hi, float& lo, float v) {
   lo = e - (hi - s);
 }
 
-// b = pb in-place Gauss-Jordan steps on the panel pan[np][kPanel] (the pivot
+// b = pb in-place Gauss-Jordan steps on the panel pan[np][kPanelLd] (the pivot
 // columns k0 .. k0 + pb - 1), run by warp 0 alone: lane l holds rows
 // l + nlanes s (s < np / nlanes <= 2) in registers.  The pivot of each
 // column is the warp maximum of a key (|a| bits with their low 7 bits
@@ -202,7 +203,7 @@ __device__ __forceinline__ void gj_panel(float2* pan, int k0, int lane, unsigned
   for (int s2 = 0; s2 < kPanelRows; ++s2)
 #pragma unroll
     for (int c2 = 0; c2 < kPanel; ++c2)
-      pv[s2][c2] = (s2 < rows_per_lane && c2 < pb) ? pan[(lane + nlanes * s2) * kPanel + c2] : make_float2(0.f, 0.f);
+      pv[s2][c2] = (s2 < rows_per_lane && c2 < pb) ? pan[(lane + nlanes * s2) * kPanelLd + c2] : make_float2(0.f, 0.f);
 #pragma unroll
   for (int i = 0; i < kPanel; ++i) {
     if (i < pb) {
@@ -269,7 +270,7 @@ __device__ __forceinline__ void gj_panel(float2* pan, int k0, int lane, unsigned
     if (s2 < rows_per_lane)
 #pragma unroll
       for (int c2 = 0; c2 < kPanel; ++c2)
-        if (c2 < pb) pan[(lane + nlanes * s2) * kPanel + c2] = pv[s2][c2];
+        if (c2 < pb) pan[(lane + nlanes * s2) * kPanelLd + c2] = pv[s2][c2];
 }
 
 // bf16 bit pattern of the signed digit (sign16 = 0 or 0x8000, 0 <= d < 256),
@@ -369,9 +370,9 @@ __host__ __device__ inline MixedSmem mixed_layout(int np) {
   L.yl = L.yh + np * np;
   const int simt = 2 * kResChunk * np + 2 * np * np;
   const int tc = (tc_work_bytes(np) + 7) / 8;
-  // Gauss-Jordan panels [2][np][kPanel] and pivot rows [kPanel][2 np]; with
+  // Gauss-Jordan panels [2][np][kPanelLd] and pivot rows [kPanel][2 np]; with
   // the tensor-core residual they sit in the Y-digit area, past gamma's digits
-  const int gj = (use_tc_residual(np) ? gdig_bytes(np) / 8 : 0) + 2 * np * kPanel + kPanel * 2 * np;
+  const int gj = (use_tc_residual(np) ? gdig_bytes(np) / 8 : 0) + 2 * np * kPanelLd + kPanel * 2 * np;
   const int res = use_tc_residual(np) ? tc : simt;
   o += res > gj ? res : gj;
   L.total = o;
@@ -489,8 +490,8 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
   constexpr int nlanes = P * P < 32 ? P * P : 32;
   constexpr unsigned wmask = nlanes == 32 ? 0xffffffffu : ((1u << nlanes) - 1u);
   constexpr int pb = P < kPanel ? P : kPanel;        // panel width b
-  float2* panbuf = reinterpret_cast<float2*>(sp.work + (use_tc_residual(NP) ? gdig_bytes(NP) : 0));   // [2][np][kPanel]
-  float2* prs = panbuf + 2 * np * kPanel;                        // [kPanel][2 np]
+  float2* panbuf = reinterpret_cast<float2*>(sp.work + (use_tc_residual(NP) ? gdig_bytes(NP) : 0));   // [2][np][kPanelLd]
+  float2* prs = panbuf + 2 * np * kPanelLd;                      // [kPanel][2 np]
   int* rowstep = reinterpret_cast<int*>(invu);                   // pivot step of each row, -1 if none
   for (int i = t; i < np; i += blockDim.x) rowstep[i] = -1;
   unsigned used0 = 0;                                            // warp 0: its rows already pivots
@@ -498,7 +499,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
 #pragma unroll 1
   for (int k0 = 0; k0 < np; k0 += pb) {
     const int jk = k0 / P, kc = k0 - jk * P;
-    float2* pan = panbuf + ((k0 / pb) & 1) * np * kPanel;
+    float2* pan = panbuf + ((k0 / pb) & 1) * np * kPanelLd;
     const bool pcol = (tc >= kc && tc < kc + pb);
     // (1) the panel columns
     if (pcol) {
@@ -508,7 +509,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
 #pragma unroll
         for (int jj = 1; jj < kTile; ++jj)
           if (jj == jk) v = A[ii][jj];
-        pan[(tr + P * ii) * kPanel + (tc - kc)] = v;
+        pan[(tr + P * ii) * kPanelLd + (tc - kc)] = v;
       }
     }
     __syncthreads();
@@ -540,7 +541,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
 #pragma unroll
       for (int ii = 0; ii < kTile; ++ii) {
         const int r = tr + P * ii;
-        float2 w = pan[r * kPanel + l];
+        float2 w = pan[r * kPanelLd + l];
         if (r == pl) w.x -= 1.f;
 #pragma unroll
         for (int jj = 0; jj < kTile; ++jj) {
@@ -552,7 +553,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
     if (pcol) {
 #pragma unroll
       for (int ii = 0; ii < kTile; ++ii) {
-        const float2 v = pan[(tr + P * ii) * kPanel + (tc - kc)];
+        const float2 v = pan[(tr + P * ii) * kPanelLd + (tc - kc)];
 #pragma unroll
         for (int jj = 0; jj < kTile; ++jj)
           if (jj == jk) A[ii][jj] = v;
@@ -593,8 +594,9 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
       __syncthreads();
       for (int c2 = t; c2 < kCB; c2 += nthr) cole[c2] = -1000;
       __syncthreads();
+      // lanes take consecutive columns of a row of X0 (no bank conflicts)
       for (int idx = t; idx < kCB * np; idx += nthr) {
-        const int c2 = idx / np, l = idx - c2 * np;
+        const int l = idx / kCB, c2 = idx - l * kCB;
         const float2 x = X0s[l * np + b * kCB + c2];
         float yr = 0.f, ylr = 0.f, yi = 0.f, yli = 0.f;
         cdf_fma(yr, ylr, yi, yli, chih[l], chil[l], x, make_float2(0.f, 0.f));
@@ -604,7 +606,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
       __syncthreads();
       // two consecutive l per thread: one 32-bit word per slice and part
       for (int idx = t; idx < kCB * np / 2; idx += nthr) {
-        const int c2 = idx / (np / 2), l = 2 * (idx - c2 * (np / 2));
+        const int l = 2 * (idx / kCB), c2 = idx - (l / 2) * kCB;
         unsigned w0[kSlices], w1[kSlices], v0[kSlices], v1[kSlices];
         const int e = cole[c2];
 #pragma unroll
