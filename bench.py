@@ -294,6 +294,42 @@ def batch_bench(df, I, torch, full: bool, passes: int = 3):
     return out
 
 
+def example_i_bench(df):
+    """The paper's Example I sweeps (N_W, N_w, N_k^D) on the FP64 path: passes and wall
+    time to r <= 1e-12 from Sigma~ = 0, and Eq. deltag against the extrapolated limit."""
+    from paper_1507_00895_gb300 import sweeps as S
+    out = S.example_i(df, df.DF_FP64)
+    slowest = max((p for sw in out.values() for p in sw["points"]), key=lambda p: p["seconds"])
+    out["slowest_point"] = {k: slowest[k] for k in ("n_w", "N_W", "N_k", "passes", "seconds")}
+    out["paper_context"] = "the paper's slowest point of these sweeps took about 2 min on a laptop CPU"
+    return out
+
+
+def observables_bench(df, I, torch, reps: int = 20):
+    """Eq. sigma_lat and Eq. glat on the bench workload after one pass (device outputs)."""
+    w = I.workload(WORKLOAD)
+    stream = torch.cuda.current_stream()
+    with df.DualFermion.from_workload(w, stream=stream.cuda_stream) as d:
+        d.iterate(1)
+        so = torch.empty((w.n_w, w.N), dtype=torch.complex128, device="cuda")
+        go = torch.empty_like(so)
+        for _ in range(3):
+            d.lattice_observables(so, go)
+        d.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for _ in range(reps):
+            d.lattice_observables(so, go)
+        t1.record(stream)
+        t1.synchronize()
+        ms = t0.elapsed_time(t1) / reps
+    nbytes = 16 * w.n_w * w.N * 4          # G0~ and Sigma~ in, Sigma_lat and G_lat out
+    return {"kernel": "lattice_kernel", "ms": ms, "algorithmic_bytes": nbytes,
+            "GB_per_s": nbytes / (ms * 1e-3) / 1e9,
+            "note": "one elementwise pass over [n_w][N]; at this size launch latency dominates"}
+
+
 def warmstart_bench(df, I, torch, n_train=2000, n_test=200, steps=3000):
     """Learned warm start: train the 4x512 network (own BF16 kernels) on
     converged Sigma~ of n_train points of the warm-start family (2D 16^2,
@@ -491,6 +527,12 @@ def run_ours(args):
     batch = None
     if rank == 0 and not args.no_batch:
         batch = batch_bench(df, I, torch, args.batch_full)
+    sweeps = None
+    if rank == 0 and not args.no_sweeps:
+        sweeps = example_i_bench(df)
+    obs = None
+    if rank == 0:
+        obs = observables_bench(df, I, torch)
     warm = None
     if rank == 0 and not args.no_warmstart:
         warm = warmstart_bench(df, I, torch)
@@ -516,7 +558,8 @@ def run_ours(args):
             "gpu_launches": main["gpu_launches"], "kernel_ms_per_step": main["kernel_ms_per_step"],
             "err_vs_fp64_first_pass": main.get("err_vs_fp64_first_pass"),
             "plain_fp64": plain if prec != df.DF_FP64 else None,
-            "time_to_converged": ttc, "batch": batch, "warm_start": warm, "clocks": main["clocks"]}
+            "time_to_converged": ttc, "batch": batch, "warm_start": warm, "example_i": sweeps,
+            "observables": obs, "clocks": main["clocks"]}
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -529,13 +572,13 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--precision", choices=["fp64", "fp32ir"], default="fp64")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttc", action="store_true", help="skip the time-to-converged comparison")
     ap.add_argument("--no-batch", action="store_true", help="skip the uneven-batch throughput")
     ap.add_argument("--batch-full", action="store_true", help="uneven batch at the recipe's full sizes")
     ap.add_argument("--no-warmstart", action="store_true", help="skip the learned warm-start measurement")
+    ap.add_argument("--no-sweeps", action="store_true", help="skip the paper's Example I sweeps")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)       # at least 3 untimed warm-up steps
     if args.impl == "reference":

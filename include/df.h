@@ -159,6 +159,20 @@ df_status df_iterate(df_ctx* c, int max_iter, double tol, int* iters_done, doubl
 df_status df_get_sigma(df_ctx* c, double* out, int out_is_device);
 df_status df_set_sigma(df_ctx* c, const double* in, int in_is_device);
 df_status df_get_gtilde(df_ctx* c, double* out, int out_is_device);
+
+/* Lattice observables of the current Sigma~ (section "Resulting observables"),
+ * each [n_w][N] complex (the box frequencies, k flattened like Sigma~):
+ *   Eq. sigma_lat: Sigma_lat = Sigma~ / (1 + g Sigma~) + Sigma^DMFT,
+ *                  Sigma^DMFT = i w + mu - Delta - 1/g;
+ *   Eq. glat:      G_lat = A + A g^-1 G~ g^-1 A,  A = (Delta - eps_k)^-1,
+ *                  G~ = 1 / (1/G0~ - Sigma~) (Eq. gd0, Eq. dyson).
+ * The printed Eq. sigma_lat has "1 - g Sigma" in the denominator; the sign
+ * used is the one for which the two observables obey the Dyson relation
+ * G_lat^-1 = i w + mu - eps_k - Sigma_lat that the paper states.  Either
+ * output may be NULL.  Device outputs are written asynchronously on the
+ * handle's stream; host outputs are complete on return.
+ * Errors: DF_ERR_ARG (no handle), DF_ERR_CUDA. */
+df_status df_lattice_observables(df_ctx* c, double* sigma_lat, double* g_lat, int out_is_device);
 df_status df_get_chi(df_ctx* c, double* out, int out_is_device);
 df_status df_get_kernel(df_ctx* c, double* out, int out_is_device);
 /* lambda [2][N_W][N] complex; ok [2][N_W][N] ints: 1 converged, 0 not

@@ -38,6 +38,8 @@ Status of each function's parity pin (tests/test_oracle_pins.py):
                                               by the first-order closed form of Sigma~)
   ladder_gamma_* / hand LU .................. pinned (LAPACK, geometric series)
   second_order_diag ......................... pinned (second-order diagram, direct sum)
+  lattice_observables ....................... pinned (G = G_DMFT at Sigma~ = 0; the Dyson relation
+                                              between Eq. sigma_lat and Eq. glat)
   dual_sigma_* .............................. pinned (first/second order in gamma by
                                               Richardson extrapolation vs closed form /
                                               direct diagram; point-group, conjugation,
@@ -101,6 +103,38 @@ def dual_g(g0_ext: np.ndarray, sigma_box: np.ndarray, n_w: int, m_max: int) -> n
     gt = g0_ext.copy()
     gt[m_max:m_max + n_w] = dyson(g0_ext[m_max:m_max + n_w], sigma_box)
     return gt
+
+
+# ---------------------------------------------------------------------------
+# Section "Resulting observables": Eq. sigma_lat and Eq. glat
+# ---------------------------------------------------------------------------
+
+def matsubara_box(n_w: int, beta: float) -> np.ndarray:
+    """Fermionic frequencies of the box, w_n = (2n + 1) pi / beta, n in [-n_w/2, n_w/2)."""
+    n = np.arange(-(n_w // 2), n_w // 2)
+    return (2 * n + 1) * math.pi / beta
+
+
+def lattice_observables(g_ext: np.ndarray, delta_ext: np.ndarray, eps: np.ndarray,
+                        sigma_box: np.ndarray, n_w: int, m_max: int, beta: float, mu: float):
+    """Lattice self-energy and Green's function of the box frequencies, [n_w][N] each.
+
+    Eq. sigma_lat: Sigma = Sigma~ / (1 + g Sigma~) + Sigma^DMFT, Sigma^DMFT = i w + mu - Delta - 1/g;
+    Eq. glat:      G = A + A g^-1 G~ g^-1 A, A = (Delta - eps_k)^-1, G~ from Eq. gd0 and Eq. dyson.
+    Reading: the printed denominator "1 - g Sigma" is taken as 1 + g Sigma~, the sign for which the
+    two observables obey the Dyson relation G^-1 = i w + mu - eps_k - Sigma that the paper states
+    (pinned in tests/test_oracle_pins.py).
+    """
+    box = slice(m_max, m_max + n_w)
+    g = g_ext[box][:, None]
+    delta = delta_ext[box][:, None]
+    iw = 1j * matsubara_box(n_w, beta)[:, None]
+    gt = dyson(bare_dual_g(g_ext[box], delta_ext[box], eps), sigma_box)
+    a = 1.0 / (delta - eps[None, :])
+    g_lat = a + a * (1.0 / g) * gt * (1.0 / g) * a
+    sigma_dmft = iw + mu - delta - 1.0 / g
+    sigma_lat = sigma_box / (1.0 + g * sigma_box) + sigma_dmft
+    return sigma_lat, g_lat
 
 
 # ---------------------------------------------------------------------------

@@ -191,6 +191,7 @@ void df_destroy(df_ctx* c) {
   cudaFree(c->kc);
   cudaFree(c->prod);
   cudaFree(c->sigma);
+  cudaFree(c->lat);
   cudaFree(c->lam);
   cudaFree(c->lam_ok);
   cudaFree(c->red);
@@ -274,6 +275,7 @@ df_status df_init(df_ctx** out, const df_lattice* lat, double beta, double mu, d
   ALLOC(c->kc, 2 * nchi);
   ALLOC(c->prod, nchi);
   ALLOC(c->sigma, (size_t)dm.n_w * dm.N);
+  ALLOC(c->lat, (size_t)2 * dm.n_w * dm.N);
   ALLOC(c->lam, (size_t)2 * dm.nb * dm.N);
   ALLOC(c->lam_ok, (size_t)2 * dm.nb * dm.N);
   ALLOC(c->red, (size_t)2 * dm.n_w + 4);
@@ -397,6 +399,21 @@ df_status df_set_sigma(df_ctx* c, const double* in, int is_device) {
           "df_set_sigma");
   DF_CUDA(c, launch_dyson_ifft(c, c->dm.m_max, c->dm.n_w), "Dyson + FFT to real space");
   if (!is_device) DF_CUDA(c, cudaStreamSynchronize(c->stream), "df_set_sigma");
+  return DF_OK;
+}
+
+df_status df_lattice_observables(df_ctx* c, double* sigma_lat, double* g_lat, int is_device) {
+  if (!c) return DF_ERR_ARG;
+  const size_t cnt = (size_t)c->dm.n_w * c->dm.N;
+  double2* so = is_device ? (double2*)sigma_lat : (sigma_lat ? c->lat : nullptr);
+  double2* go = is_device ? (double2*)g_lat : (g_lat ? c->lat + cnt : nullptr);
+  DF_CUDA(c, launch_lattice(c, so, go), "lattice observables (Eqs. sigma_lat, glat)");
+  if (!is_device) {
+    df_status s = DF_OK;
+    if (sigma_lat) s = copy_out(c, sigma_lat, c->lat, sizeof(double2) * cnt, 0, "df_lattice_observables");
+    if (s == DF_OK && g_lat) s = copy_out(c, g_lat, c->lat + cnt, sizeof(double2) * cnt, 0, "df_lattice_observables");
+    return s;
+  }
   return DF_OK;
 }
 

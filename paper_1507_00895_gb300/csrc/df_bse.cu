@@ -90,7 +90,7 @@ __device__ __forceinline__ void eig_rayleigh(int n, int warp, int lane, const C*
 }
 
 __global__ void __launch_bounds__(kEigThreads)
-lambda_kernel(Dims dm, int ch0, int a0, int na, double tol, const double2* __restrict__ gam,
+lambda_kernel(Dims dm, int ch0, int a0, int na, int lo_in_smem, double tol, const double2* __restrict__ gam,
               const double2* __restrict__ chi, double2* __restrict__ lam, int* __restrict__ ok,
               int* __restrict__ flags) {
   extern __shared__ double2 sm[];
@@ -99,8 +99,8 @@ lambda_kernel(Dims dm, int ch0, int a0, int na, double tol, const double2* __res
   double2* xq = v + n * kEigQ;
   double2* y = xq + n * kEigQ;
   float2* G32 = (float2*)(y + n * kEigQ);  // [n][n]
-  float2* G32l = G32 + n * n;              // [n][n], gamma - G32
-  float2* v32 = G32l + n * n;
+  float2* G32l = G32 + n * n;              // [n][n], gamma - G32 (when it fits; else formed on the fly)
+  float2* v32 = G32l + (lo_in_smem ? n * n : 0);
   float2* x32 = v32 + n * kEigQ;
   float2* y32 = x32 + n * kEigQ;
   __shared__ double2 lam_old[kEigQ], lam_new[kEigQ];
@@ -121,7 +121,7 @@ lambda_kernel(Dims dm, int ch0, int a0, int na, double tol, const double2* __res
     const double2 g = Gg[idx];
     const float hx = (float)g.x, hy = (float)g.y;
     G32[idx] = make_float2(hx, hy);
-    G32l[idx] = make_float2((float)(g.x - (double)hx), (float)(g.y - (double)hy));
+    if (lo_in_smem) G32l[idx] = make_float2((float)(g.x - (double)hx), (float)(g.y - (double)hy));
   }
   for (int idx = tid; idx < n * kEigQ; idx += blockDim.x) {
     const int j = idx / kEigQ, t = idx % kEigQ;
@@ -178,8 +178,17 @@ lambda_kernel(Dims dm, int ch0, int a0, int na, double tol, const double2* __res
     for (int p = tid; p < n * kEigQ; p += blockDim.x) {
       const int i = p / kEigQ, t = p % kEigQ;
       float sr = 0.f, lr = 0.f, si = 0.f, li = 0.f;
-      for (int j = 0; j < n; ++j)
-        cdf_fma(sr, lr, si, li, G32[i * n + j], G32l[i * n + j], wh[j * kEigQ + t], wl[j * kEigQ + t]);
+      for (int j = 0; j < n; ++j) {
+        const float2 gh = G32[i * n + j];
+        float2 gl;
+        if (lo_in_smem) {
+          gl = G32l[i * n + j];
+        } else {
+          const double2 g = Gg[(size_t)i * n + j];
+          gl = make_float2((float)(g.x - (double)gh.x), (float)(g.y - (double)gh.y));
+        }
+        cdf_fma(sr, lr, si, li, gh, gl, wh[j * kEigQ + t], wl[j * kEigQ + t]);
+      }
       y[p] = mk((double)sr + (double)lr, (double)si + (double)li);
     }
     __syncthreads();
@@ -277,8 +286,11 @@ cudaError_t launch_lambda(df_ctx* c, int channel_mask) {
   const int a0 = (c->opts.eig_mode == 1) ? dm.m_max : 0;
   const int na = (c->opts.eig_mode == 1) ? 1 : dm.nb;
   const int qtiles = (dm.N + kEigQ - 1) / kEigQ;
-  const size_t smem = sizeof(double2) * 3 * dm.n_w * kEigQ +
-                      sizeof(float2) * ((size_t)2 * dm.n_w * dm.n_w + 3 * dm.n_w * kEigQ);
+  // gamma's (hi, lo) FP32 pairs in shared memory when they fit (n_w <= 96), the
+  // lo parts formed from FP64 gamma on the fly above that
+  const size_t base = sizeof(double2) * 3 * dm.n_w * kEigQ + sizeof(float2) * ((size_t)dm.n_w * dm.n_w + 3 * dm.n_w * kEigQ);
+  const int lo_in_smem = base + sizeof(float2) * (size_t)dm.n_w * dm.n_w <= (size_t)200 * 1024 ? 1 : 0;
+  const size_t smem = base + (lo_in_smem ? sizeof(float2) * (size_t)dm.n_w * dm.n_w : 0);
   cudaError_t e = cudaFuncSetAttribute((const void*)lambda_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
@@ -286,8 +298,8 @@ cudaError_t launch_lambda(df_ctx* c, int channel_mask) {
   const int ch0 = (channel_mask & 1) ? 0 : 1;
   const int nch = (channel_mask & 1) && (channel_mask & 2) ? 2 : 1;
   if (!(channel_mask & 3)) return cudaSuccess;
-  lambda_kernel<<<nch * na * qtiles, kEigThreads, smem, c->stream>>>(dm, ch0, a0, na, 1e-12, c->gam, c->chi, c->lam,
-                                                                     c->lam_ok, flag_ptr(c));
+  lambda_kernel<<<nch * na * qtiles, kEigThreads, smem, c->stream>>>(dm, ch0, a0, na, lo_in_smem, 1e-12, c->gam,
+                                                                     c->chi, c->lam, c->lam_ok, flag_ptr(c));
   return cudaGetLastError();
 }
 

@@ -6,6 +6,8 @@
 // Every momentum sum over the N = N_k^D grid is a cyclic correlation and is
 // done exactly with D-dimensional FFTs held in shared memory: one CTA per
 // (frequency, frequency) plane, N <= 4096 points (64 KB in complex128).
+#include <math_constants.h>
+
 #include "df_fft_dev.cuh"
 
 namespace df {
@@ -49,6 +51,33 @@ sigma_dyson_kernel(Dims dm, double mix, const double2* __restrict__ prod, const 
                     sm + dm.nk / 2 + dm.N, red_sm);
 }
 
+// Section "Resulting observables", per box element (w, k): Eq. sigma_lat
+// (denominator 1 + g Sigma~) and Eq. glat, with G~ from Eq. dyson.
+__global__ void lattice_kernel(Dims dm, const double2* __restrict__ g, const double2* __restrict__ delta,
+                               const double2* __restrict__ g0, const double2* __restrict__ sigma,
+                               double2* __restrict__ s_out, double2* __restrict__ g_out) {
+  const int total = dm.n_w * dm.N;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    const int i = idx / dm.N, r = idx - i * dm.N, e = i + dm.m_max;
+    const double2 ge = g[e], de = delta[e], st = sigma[idx];
+    const double2 gi = cinv(ge);
+    if (g_out) {
+      const double eps = eps_of(r, dm.D, dm.p, dm.t, dm.tp);
+      const double2 y = cinv(g0[(size_t)e * dm.N + r]);
+      const double2 gt = cinv(mk(y.x - st.x, y.y - st.y));
+      const double2 a = cinv(mk(de.x - eps, de.y));
+      const double2 v = cmul(cmul(a, gi), cmul(gt, cmul(gi, a)));
+      g_out[idx] = mk(a.x + v.x, a.y + v.y);
+    }
+    if (s_out) {
+      const double2 den = cmul(ge, st);
+      const double2 f = cmul(st, cinv(mk(1.0 + den.x, den.y)));
+      const double w = (double)(2 * (i - dm.n_w / 2) + 1) * CUDART_PI * dm.T;
+      s_out[idx] = mk(f.x + dm.mu - de.x - gi.x, f.y + w - de.y - gi.y);
+    }
+  }
+}
+
 __global__ void residual_reduce_kernel(int n, double* red) {
   __shared__ double red_sm[32];
   residual_reduce_block(n, red, red_sm);
@@ -83,6 +112,13 @@ cudaError_t launch_bubble(df_ctx* c) {
   cudaError_t e = set_smem((const void*)bubble_kernel, sm);
   if (e != cudaSuccess) return e;
   bubble_kernel<<<dm.nb * dm.n_w, kFftThreads, sm, c->stream>>>(dm, c->gr, c->chi);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lattice(df_ctx* c, double2* s_out, double2* g_out) {
+  const Dims& dm = c->dm;
+  const int total = dm.n_w * dm.N;
+  lattice_kernel<<<(total + 255) / 256, 256, 0, c->stream>>>(dm, c->g, c->delta, c->g0, c->sigma, s_out, g_out);
   return cudaGetLastError();
 }
 

@@ -198,6 +198,7 @@ struct df_ctx {
   double2* kc = nullptr;       // [2][nb][n_w][N] Eq. sd bracket per channel (weights 1, 3)
   double2* prod = nullptr;     // [nb][n_w][N] K(-r) G~_{w+W}(r)
   double2* sigma = nullptr;    // [n_w][N]
+  double2* lat = nullptr;      // [2][n_w][N] lattice observables staged for host copies
   double2* lam = nullptr;      // [2][nb][N] leading eigenvalue of gamma chi
   int* lam_ok = nullptr;       // [2][nb][N] power iteration converged flag
   double* red = nullptr;       // [2 n_w] residual partials, [2] final, [2] solve flags (ints)
@@ -236,6 +237,7 @@ int* bse_flags(df_ctx* c);   // [0]: bit 0 zero pivot, bit 1 |lambda| >= 1
 bool mixed_supported(int n_w);
 size_t mixed_workspace_bytes(const Dims& dm);
 cudaError_t launch_split_gamma(df_ctx* c, const double2* gg);
+cudaError_t launch_lattice(df_ctx* c, double2* s_out, double2* g_out);
 const double2* gamma_gt_ptr(df_ctx* c);   // gamma o gamma^T, written by launch_gamma_gt
 cudaError_t launch_bse_mixed(df_ctx* c, int channel_mask, int* flags);
 }  // namespace df

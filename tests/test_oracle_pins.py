@@ -399,3 +399,77 @@ def test_cubic_workload_sits_at_lambda_098():
     q = 8 * 256 + 8 * 16 + 8
     lam = O.ladder_lambda(gm, chi, 0, q)
     assert abs(lam - 0.98) < 1e-9
+
+
+# ---------------------------------------------------------------------------
+# section "Resulting observables": Eq. sigma_lat, Eq. glat
+# ---------------------------------------------------------------------------
+
+def _obs_inputs(seed=7, dim=2, nk=4, n_w=6, m_max=1):
+    w = I.random_nonsymmetric(n_w, m_max, dim, nk, seed=seed, beta=1.7)
+    eps = O.dispersion(dim, nk, 1.0, 0.0)
+    return w, eps
+
+
+def test_lattice_observables_dmft_limit():
+    # Sigma~ = 0: G_lat is the DMFT lattice Green's function 1/(1/g + Delta - eps)
+    # (a different formula from Eq. glat) and Sigma_lat = Sigma^DMFT
+    w, eps = _obs_inputs()
+    zero = np.zeros((w.n_w, w.N), complex)
+    s_lat, g_lat = O.lattice_observables(w.g, w.delta, eps, zero, w.n_w, w.m_max, w.beta, w.mu)
+    box = slice(w.m_max, w.m_max + w.n_w)
+    g, d = w.g[box][:, None], w.delta[box][:, None]
+    g_dmft = 1.0 / (1.0 / g + d - eps[None, :])
+    assert np.max(np.abs(g_lat - g_dmft)) / np.max(np.abs(g_dmft)) < 1e-13
+    iw = 1j * O.matsubara_box(w.n_w, w.beta)[:, None]
+    assert np.max(np.abs(s_lat - (iw + w.mu - d - 1.0 / g))) < 1e-12
+
+
+def test_lattice_observables_obey_dyson():
+    # the paper: Eqs. sigma_lat and glat are related by a Dyson equation for G and
+    # Sigma, G^-1 = i w + mu - eps_k - Sigma, for any Sigma~
+    w, eps = _obs_inputs(seed=11)
+    rng = np.random.default_rng(3)
+    sig = 0.3 * (rng.normal(size=(w.n_w, w.N)) + 1j * rng.normal(size=(w.n_w, w.N)))
+    s_lat, g_lat = O.lattice_observables(w.g, w.delta, eps, sig, w.n_w, w.m_max, w.beta, w.mu)
+    iw = 1j * O.matsubara_box(w.n_w, w.beta)[:, None]
+    lhs = 1.0 / g_lat
+    rhs = iw + w.mu - eps[None, :] - s_lat
+    assert np.max(np.abs(lhs - rhs)) / np.max(np.abs(rhs)) < 1e-12
+
+
+def test_printed_sigma_lat_sign_breaks_dyson(monkeypatch):
+    # the printed denominator 1 - g Sigma~ (planted in the oracle) violates the
+    # Dyson relation: the reading 1 + g Sigma~ is forced
+    w, eps = _obs_inputs(seed=13)
+    rng = np.random.default_rng(5)
+    sig = 0.3 * (rng.normal(size=(w.n_w, w.N)) + 1j * rng.normal(size=(w.n_w, w.N)))
+    orig = O.lattice_observables
+
+    def planted(g_ext, delta_ext, eps_, sigma_box, n_w, m_max, beta, mu):
+        s_lat, g_lat = orig(g_ext, delta_ext, eps_, sigma_box, n_w, m_max, beta, mu)
+        g = g_ext[m_max:m_max + n_w][:, None]
+        s_lat = s_lat - sigma_box / (1.0 + g * sigma_box) + sigma_box / (1.0 - g * sigma_box)
+        return s_lat, g_lat
+
+    monkeypatch.setattr(O, "lattice_observables", planted)
+    s_lat, g_lat = O.lattice_observables(w.g, w.delta, eps, sig, w.n_w, w.m_max, w.beta, w.mu)
+    iw = 1j * O.matsubara_box(w.n_w, w.beta)[:, None]
+    rhs = iw + w.mu - eps[None, :] - s_lat
+    assert np.max(np.abs(1.0 / g_lat - rhs)) / np.max(np.abs(rhs)) > 1e-3
+
+
+def test_example_i_extrapolation_recovers_the_limit():
+    # the N_x -> infinity extrapolation of the Example I sweeps: exact for
+    # g(N) = g_inf + b / N, and delta_g follows Eq. deltag
+    from paper_1507_00895_gb300 import sweeps as S
+    ns = [8, 16, 24, 32, 48]
+    g_inf = 0.3 - 0.7j
+    gs = [g_inf + (0.2 + 0.1j) / n for n in ns]
+    assert abs(S.extrapolate(ns, gs) - g_inf) < 1e-14
+    d = S.delta_g(gs, g_inf)
+    assert all(abs(d[i] - abs(0.2 + 0.1j) / ns[i] / abs(g_inf)) < 1e-14 for i in range(len(ns)))
+    gt = np.zeros((10, 4), complex)
+    gt[1 + 4, 0] = 2 + 3j      # m_max = 1, n_w = 8: box index n_w/2 is the first w > 0
+    assert S.control_value(gt, 8, 1) == 2 + 3j
+    assert abs(O.matsubara_box(8, 1.0)[4] - np.pi) < 1e-15

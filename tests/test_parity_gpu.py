@@ -230,3 +230,74 @@ def test_device_pointers_and_set_inputs(df):
         d.get_sigma(out)
         torch.cuda.synchronize()
         assert nrel(out.cpu().numpy(), st.sigma) < TOL64
+
+
+@pytest.mark.parametrize("name,kw", [("paper_u20", dict(nk=8, n_w=6, m_max=2)),
+                                     ("square32_tp", dict(nk=16, n_w=34, m_max=1)),
+                                     ("cubic16_crit", dict(nk=4, n_w=8, m_max=1))])
+def test_lattice_observables(df, name, kw):
+    # section "Resulting observables" after one pass, host and device outputs
+    import torch
+    w = I.workload(name, **kw)
+    st, gd, gm = oracle_first_pass(w)
+    eps = O.dispersion(w.dim, w.nk, w.t, w.tp)
+    s_ref, g_ref = O.lattice_observables(w.g, w.delta, eps, st.sigma, w.n_w, w.m_max, w.beta, w.mu)
+    with df.DualFermion.from_workload(w) as d:
+        d.iterate(1)
+        s_lat, g_lat = d.lattice_observables()
+        assert nrel(s_lat, s_ref) < TOL64
+        assert nrel(g_lat, g_ref) < TOL64
+        sd = torch.empty((w.n_w, w.N), dtype=torch.complex128, device="cuda")
+        gdv = torch.empty_like(sd)
+        d.lattice_observables(sd, gdv)
+        torch.cuda.synchronize()
+        assert nrel(sd.cpu().numpy(), s_ref) < TOL64 and nrel(gdv.cpu().numpy(), g_ref) < TOL64
+
+
+def test_lattice_observables_converged_paper_workload(df):
+    w = I.workload("paper_u20", nk=16, n_w=16, m_max=1)
+    st = O.run_workload(w, n_iter=30, tol=1e-13)
+    eps = O.dispersion(w.dim, w.nk, w.t, w.tp)
+    s_ref, g_ref = O.lattice_observables(w.g, w.delta, eps, st.sigma, w.n_w, w.m_max, w.beta, w.mu)
+    with df.DualFermion.from_workload(w) as d:
+        d.iterate(30, tol=1e-13)
+        s_lat, g_lat = d.lattice_observables()
+    assert nrel(s_lat, s_ref) < TOL64 and nrel(g_lat, g_ref) < TOL64
+
+
+def test_example_i_sweep_point_matches_oracle(df):
+    # one point of the paper's Example I sweeps: converged g = G~(i pi/beta, k=0)
+    from paper_1507_00895_gb300 import sweeps as S
+    for n_w, m_max, nk in ((8, 1, 4), (12, 0, 8)):
+        p = S.run_point(df, n_w, m_max, nk, df.DF_FP64, tol=1e-12)
+        w = I.workload("paper_u20", nk=nk, n_w=n_w, m_max=m_max)
+        st = O.run_workload(w, n_iter=80, tol=1e-12)
+        gt = O.dual_g(st.g0_ext, st.sigma, n_w, m_max)
+        g_ref = S.control_value(gt, n_w, m_max)
+        assert p["converged"]
+        assert abs(complex(*p["g"]) - g_ref) <= 1e-10 * abs(g_ref)
+
+
+@pytest.mark.parametrize("n_w", [98, 128])
+def test_largest_ladder_orders(df, n_w):
+    # n_w > 96: the FP64 LU in global scratch, the eigenvalue polish with gamma's
+    # lo parts formed on the fly; kernel, Sigma~ and lambda against the oracle
+    w = I.workload("paper_u20", nk=4, n_w=n_w, m_max=0)
+    st, gd, gm = oracle_first_pass(w)
+    with df.DualFermion.from_workload(w, eig_mode=1) as d:
+        d.bubble()
+        d.bse(3)
+        assert nrel(d.get_kernel(), kernel_channels(st, gd, gm)) < TOL64
+        lam, ok = d.get_lambda()
+        d.sigma()
+        assert nrel(d.get_sigma(), st.sigma) < TOL64
+    n_ok = 0
+    for c, gx in enumerate((gd, gm)):
+        for q in range(w.N):
+            ev = np.linalg.eigvals(gx[0] * st.chi[0, :, q][None, :])
+            srt = np.sort(np.abs(ev))[::-1]
+            if srt[1] < 0.5 * srt[0]:
+                lead = ev[np.argmax(np.abs(ev))]
+                assert ok[c, 0, q] == 1 and abs(lam[c, 0, q] - lead) < 1e-8 * abs(lead)
+                n_ok += 1
+    assert n_ok > 0
