@@ -173,6 +173,22 @@ df_status df_get_gtilde(df_ctx* c, double* out, int out_is_device);
  * handle's stream; host outputs are complete on return.
  * Errors: DF_ERR_ARG (no handle), DF_ERR_CUDA. */
 df_status df_lattice_observables(df_ctx* c, double* sigma_lat, double* g_lat, int out_is_device);
+
+/* Charge and spin susceptibilities of the current Sigma~ (section "Resulting
+ * observables"), out [2][N_W][N] complex (0: chi^ch with Gamma^d, 1: chi^sp
+ * with Gamma^m):
+ *   chi(W, q) = -(T/N) sum_{w,k} G_{w,k} G_{w+W,k+q}
+ *             + sum_{w,w'} L_{W,w}(q) Gamma_{W,w,w'}(q) L_{W,w'}(q),
+ *   L_{W,w}(q) = -(T/N) sum_k frakG_{w,k} frakG_{w+W,k+q},
+ *   frakG = G~ (G0~ + g) / G0~,
+ * G from Eq. glat, Gamma = (1 - gamma chi~)^-1 gamma (Eq. lin_alg_inv, FP64
+ * LU with partial pivoting) with chi~ the dual bubble of the current G~
+ * (recomputed here; df_get_chi returns it afterwards), w over the box.  The
+ * printed k sums lack 1/N; both carry it here (per-site normalisation).
+ * Synchronous.  Errors: DF_ERR_ARG (no handle or NULL out), DF_ERR_OOM (the
+ * first call allocates its buffers), DF_ERR_SINGULAR (an exactly zero pivot),
+ * DF_ERR_CUDA. */
+df_status df_susceptibility(df_ctx* c, double* out, int out_is_device);
 df_status df_get_chi(df_ctx* c, double* out, int out_is_device);
 df_status df_get_kernel(df_ctx* c, double* out, int out_is_device);
 /* lambda [2][N_W][N] complex; ok [2][N_W][N] ints: 1 converged, 0 not

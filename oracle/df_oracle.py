@@ -40,6 +40,9 @@ Status of each function's parity pin (tests/test_oracle_pins.py):
   second_order_diag ......................... pinned (second-order diagram, direct sum)
   lattice_observables ....................... pinned (G = G_DMFT at Sigma~ = 0; the Dyson relation
                                               between Eq. sigma_lat and Eq. glat)
+  susceptibilities .......................... pinned (flat-band closed form of the bare term; frakG = G
+                                              at Sigma~ = 0; gamma = 0; brute-force L Gamma L; first
+                                              order in a scaled vertex; conjugation symmetry)
   dual_sigma_* .............................. pinned (first/second order in gamma by
                                               Richardson extrapolation vs closed form /
                                               direct diagram; point-group, conjugation,
@@ -135,6 +138,18 @@ def lattice_observables(g_ext: np.ndarray, delta_ext: np.ndarray, eps: np.ndarra
     sigma_dmft = iw + mu - delta - 1.0 / g
     sigma_lat = sigma_box / (1.0 + g * sigma_box) + sigma_dmft
     return sigma_lat, g_lat
+
+
+def lattice_planes_ext(g_ext, delta_ext, eps, sigma_box, n_w, m_max):
+    """G (Eq. glat) and frakG = G~ (G0~ + g) / G0~ on the extended grid, [n_e][N] each
+    (Sigma~ = 0 outside the box, so G~ = G0~ there)."""
+    g0 = bare_dual_g(g_ext, delta_ext, eps)
+    gt = dual_g(g0, sigma_box, n_w, m_max)
+    g = g_ext[:, None]
+    a = 1.0 / (delta_ext[:, None] - eps[None, :])
+    g_lat = a + a * (1.0 / g) * gt * (1.0 / g) * a
+    frak = gt * (g0 + g) / g0
+    return g_lat, frak
 
 
 # ---------------------------------------------------------------------------
@@ -301,6 +316,36 @@ def leading_eigenvalue(gamma_W: np.ndarray, chi_Wq: np.ndarray) -> complex:
 # ---------------------------------------------------------------------------
 # Eq. sd
 # ---------------------------------------------------------------------------
+
+def susceptibilities(g_ext, delta_ext, eps, sigma_box, gamma_d, gamma_m, n_w, m_max,
+                     beta, dim, nk) -> np.ndarray:
+    """Charge and spin susceptibilities (section "Resulting observables"), [2][N_W][N]
+    (index 0 = ch with Gamma^d, 1 = sp with Gamma^m):
+
+      chi(W, q) = -(T/N) sum_{w,k} G_{w,k} G_{w+W,k+q}
+                  + sum_{w,w'} L_{W,w}(q) Gamma_{W,w,w'}(q) L_{W,w'}(q),
+      L_{W,w}(q) = -(T/N) sum_k frakG_{w,k} frakG_{w+W,k+q},
+
+    G from Eq. glat, frakG = G~ (G0~ + g) / G0~, Gamma = (1 - gamma chi~)^-1 gamma
+    (Eq. lin_alg_inv) with chi~ the dual bubble of the same G~, w over the box.
+    Reading: the printed k sums lack 1/N; both carry it here (per-site normalisation,
+    pinned by the flat-band limit in tests/test_oracle_pins.py).
+    """
+    g_lat, frak = lattice_planes_ext(g_ext, delta_ext, eps, sigma_box, n_w, m_max)
+    gt = dual_g(bare_dual_g(g_ext, delta_ext, eps), sigma_box, n_w, m_max)
+    chi0 = dual_bubble_fft(g_lat, n_w, m_max, beta, dim, nk).sum(axis=1)     # [N_W][N]
+    L = dual_bubble_fft(frak, n_w, m_max, beta, dim, nk)                     # [N_W][n_w][N]
+    chi_t = dual_bubble_fft(gt, n_w, m_max, beta, dim, nk)
+    nb, N = chi0.shape
+    out = np.empty((2, nb, N), dtype=np.complex128)
+    for c, gam in enumerate((gamma_d, gamma_m)):
+        for a in range(nb):
+            for q in range(N):
+                Gam = ladder_gamma_full(gam[a], chi_t[a, :, q])
+                lv = L[a, :, q]
+                out[c, a, q] = chi0[a, q] + lv @ Gam @ lv
+    return out
+
 
 def sd_kernel(gd_diag, gd2_diag, gm_diag, gm2_diag) -> np.ndarray:
     """The bracket of Eq. sd: 3 [Gm - Gm^(2)/2] + Gd - Gd^(2)/2, [N_W][n][N]."""

@@ -192,6 +192,7 @@ void df_destroy(df_ctx* c) {
   cudaFree(c->prod);
   cudaFree(c->sigma);
   cudaFree(c->lat);
+  cudaFree(c->sus);
   cudaFree(c->lam);
   cudaFree(c->lam_ok);
   cudaFree(c->red);
@@ -414,6 +415,36 @@ df_status df_lattice_observables(df_ctx* c, double* sigma_lat, double* g_lat, in
     if (s == DF_OK && g_lat) s = copy_out(c, g_lat, c->lat + cnt, sizeof(double2) * cnt, 0, "df_lattice_observables");
     return s;
   }
+  return DF_OK;
+}
+
+df_status df_susceptibility(df_ctx* c, double* out, int is_device) {
+  if (!c) return DF_ERR_ARG;
+  if (!out) return fail(c, DF_ERR_ARG, "output pointer is NULL");
+  const Dims& dm = c->dm;
+  const size_t plane = (size_t)dm.ne * dm.N, pw = (size_t)dm.nb * dm.n_w * dm.N, pq = (size_t)dm.nb * dm.N;
+  if (!c->sus) {
+    const cudaError_t e = cudaMalloc((void**)&c->sus, sizeof(double2) * (4 * plane + 2 * pw + 3 * pq));
+    if (e != cudaSuccess) {
+      c->sus = nullptr;
+      return fail(c, DF_ERR_OOM, "susceptibility buffers", e);
+    }
+  }
+  double2* planes = c->sus;
+  double2* P = planes + 4 * plane;
+  double2* L = P + pw;
+  double2* chi0 = L + pw;
+  double2* res = chi0 + pq;
+  DF_CUDA(c, launch_bubble(c), "dual bubble (Eq. dual_bubble)");
+  DF_CUDA(c, launch_obs_bubbles(c, planes, P, L, chi0), "susceptibility bubbles");
+  DF_CUDA(c, cudaMemsetAsync(bse_flags(c), 0, sizeof(int) * 4, c->stream), "flags");
+  DF_CUDA(c, launch_chi_ladder(c, L, chi0, is_device ? (double2*)out : res), "susceptibility ladders");
+  int fl[4] = {0, 0, 0, 0};
+  DF_CUDA(c, cudaMemcpyAsync(fl, bse_flags(c), sizeof fl, cudaMemcpyDeviceToHost, c->stream), "flags");
+  if (!is_device)
+    DF_CUDA(c, cudaMemcpyAsync(out, res, sizeof(double2) * 2 * pq, cudaMemcpyDeviceToHost, c->stream), "copy out");
+  DF_CUDA(c, cudaStreamSynchronize(c->stream), "df_susceptibility");
+  if (fl[0] & 1) return fail(c, DF_ERR_SINGULAR, "exactly zero pivot in a susceptibility ladder");
   return DF_OK;
 }
 

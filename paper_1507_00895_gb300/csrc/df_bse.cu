@@ -50,6 +50,75 @@ bse_f64_kernel(Dims dm, int ch0, int nch, int nc, const double2* __restrict__ ga
   }
 }
 
+// The ladder term of the susceptibilities (section "Resulting observables"):
+// for one (q, W, channel), sum_{w,w'} L_w Gamma_{w,w'} L_w' with
+// Gamma = D^-1 gamma (Eq. lin_alg_inv) = L . x, D x = gamma L, D in LU
+// (bse_f64_factor, FP64); out = chi0 + L . x.  Y holds [n][2]: the permuted
+// right-hand side, then L.
+__device__ __forceinline__ void chi_ladder_system(const Dims& dm, int c, int a, int q,
+                                                  const double2* __restrict__ gam, const double2* __restrict__ chi,
+                                                  const double2* __restrict__ Lb, const double2* __restrict__ chi0,
+                                                  double2* __restrict__ out, double2* LU, double2* Y, double2* xs,
+                                                  double2* invu, BseF64Shared& sh, int* __restrict__ flags) {
+  const int n = dm.n_w, N = dm.N, nb = dm.nb;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const double2* G = gam + ((size_t)c * nb + a) * n * n;
+  double2* y = Y;
+  double2* lv = Y + n;
+  bse_f64_factor(dm, c, a, q, gam, chi, LU, xs, invu, sh, flags);
+  for (int i = tid; i < n; i += blockDim.x) lv[i] = Lb[((size_t)a * n + i) * N + q];
+  __syncthreads();
+  for (int r = tid; r < n; r += blockDim.x) {      // y = P (gamma L)
+    const double2* gr = G + (size_t)sh.perm[r] * n;
+    double2 b = mk(0.0, 0.0);
+    for (int j = 0; j < n; ++j) b = cfma(gr[j], lv[j], b);
+    y[r] = b;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    for (int k = 0; k < n - 1; ++k) {              // unit-lower forward substitution
+      const double2 yk = y[k];
+      for (int r = k + 1 + lane; r < n; r += 32) y[r] = cfms(LU[r * n + k], yk, y[r]);
+      __syncwarp();
+    }
+    for (int k = n - 1; k > 0; --k) {              // unit-upper back substitution (V = U diag(1/U_kk))
+      const double2 yk = y[k];
+      for (int r = lane; r < k; r += 32) y[r] = cfms(LU[r * n + k], yk, y[r]);
+      __syncwarp();
+    }
+    double2 s2 = mk(0.0, 0.0);                     // L . x, x = y / U_kk
+    for (int i = lane; i < n; i += 32) s2 = cfma(lv[i], cmul(y[i], invu[i]), s2);
+    for (int o = 16; o > 0; o >>= 1) {
+      s2.x += __shfl_xor_sync(0xffffffffu, s2.x, o);
+      s2.y += __shfl_xor_sync(0xffffffffu, s2.y, o);
+    }
+    if (lane == 0) {
+      const double2 c0 = chi0[(size_t)a * N + q];
+      out[((size_t)c * nb + a) * N + q] = mk(c0.x + s2.x, c0.y + s2.y);
+    }
+  }
+  __syncthreads();
+}
+
+template <bool LU_SMEM>
+__global__ void __launch_bounds__(kBseThreads)
+chi_ladder_kernel(Dims dm, const double2* __restrict__ gam, const double2* __restrict__ chi,
+                  const double2* __restrict__ Lb, const double2* __restrict__ chi0, double2* __restrict__ out,
+                  double2* __restrict__ ws, int* __restrict__ flags) {
+  extern __shared__ double2 sm[];
+  __shared__ BseF64Shared sh;
+  const int n = dm.n_w, N = dm.N, nb = dm.nb;
+  const BseSmem L = bse_layout(n, 2, LU_SMEM);
+  double2* LU = LU_SMEM ? sm + L.lu : ws + (size_t)blockIdx.x * n * n;
+  const long systems = 2L * nb * N;
+  for (long sys = blockIdx.x; sys < systems; sys += gridDim.x) {
+    const int c = (int)(sys / ((long)nb * N));
+    const int rem = (int)(sys - (long)c * nb * N);
+    const int a = rem / N, q = rem - a * N;
+    chi_ladder_system(dm, c, a, q, gam, chi, Lb, chi0, out, LU, sm + L.y, sm + L.xs, sm + L.invu, sh, flags);
+  }
+}
+
 // ---------------------------------------------------------------------------
 // leading eigenvalue of A = gamma_W diag(chi~_W(q)): power iteration with a
 // Rayleigh-quotient estimate, first in FP32 (gamma staged in shared memory
@@ -278,6 +347,27 @@ cudaError_t launch_bse(df_ctx* c, int channel_mask) {
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+// the ladder term of the susceptibilities for both channels (FP64); the
+// persistent grid and LU scratch of the FP64 ladder kernel
+cudaError_t launch_chi_ladder(df_ctx* c, const double2* Lb, const double2* chi0, double2* out) {
+  const Dims& dm = c->dm;
+  const int n = dm.n_w;
+  const bool in_smem = bse_lu_in_smem(n);
+  const size_t smem = sizeof(double2) * (size_t)bse_layout(n, 2, in_smem).total;
+  const void* fn = in_smem ? (const void*)chi_ladder_kernel<true> : (const void*)chi_ladder_kernel<false>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const long systems = 2L * dm.nb * dm.N;
+  const int grid = (int)(systems < c->bse_grid ? systems : c->bse_grid);
+  if (in_smem)
+    chi_ladder_kernel<true><<<grid, kBseThreads, smem, c->stream>>>(dm, c->gam, c->chi, Lb, chi0, out, nullptr,
+                                                                    flag_ptr(c));
+  else
+    chi_ladder_kernel<false><<<grid, kBseThreads, smem, c->stream>>>(dm, c->gam, c->chi, Lb, chi0, out,
+                                                                     lu_ws_ptr(c), flag_ptr(c));
+  return cudaGetLastError();
 }
 
 cudaError_t launch_lambda(df_ctx* c, int channel_mask) {

@@ -38,28 +38,23 @@ struct BseF64Shared {
   unsigned short tri[32 * 31 / 2];
 };
 
-// D = 1 - gamma_W diag(chi~_W(q)) factorised in LU (n x n, row-major; shared
-// or global memory), right-hand sides P gamma in chunks of nc columns in Y,
-// writes kc[c][a][:][q] = w_c (Gamma_jj - Gamma^(2)_jj / 2).
-__device__ __forceinline__ void bse_f64_system(const Dims& dm, int c, int a, int q, int nc,
-                                               const double2* __restrict__ gam, const double2* __restrict__ gg,
-                                               const double2* __restrict__ chi, double2* __restrict__ kc,
-                                               double2* LU, double2* Y, double2* xs, double2* invu,
-                                               BseF64Shared& sh, int* __restrict__ flags) {
+// D = 1 - gamma_W diag(chi~_W(q)) (Eq. lin_alg_inv) factorised in place in LU
+// (n x n, row-major; shared or global memory) with partial pivoting:
+// P D = L U, L unit lower (the multipliers), U's strictly upper columns
+// scaled by 1/U_kk (so D = P^T L V diag(U_kk) with V unit upper), 1/U_kk in
+// invu, the row order in sh.perm, chi~_W(q) in xs.  Zero pivots set flags bit 0.
+__device__ __forceinline__ void bse_f64_factor(const Dims& dm, int c, int a, int q,
+                                               const double2* __restrict__ gam, const double2* __restrict__ chi,
+                                               double2* LU, double2* xs, double2* invu, BseF64Shared& sh,
+                                               int* __restrict__ flags) {
   const int n = dm.n_w, N = dm.N, nb = dm.nb;
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const double2* G = gam + ((size_t)c * nb + a) * n * n;
-  const double2* GG = gg + ((size_t)c * nb + a) * n * n;
 
   for (int i = tid; i < n; i += blockDim.x) {
     xs[i] = chi[((size_t)a * n + i) * N + q];
     sh.perm[i] = i;
-  }
-  for (int e = tid; e < nc * (nc - 1) / 2; e += blockDim.x) {
-    int d = 0;
-    while ((d + 1) * (d + 2) / 2 <= e) ++d;
-    sh.tri[e] = (unsigned short)((d << 8) | (e - d * (d + 1) / 2));
   }
   __syncthreads();
   for (int idx = tid; idx < n * n; idx += blockDim.x) {
@@ -69,7 +64,6 @@ __device__ __forceinline__ void bse_f64_system(const Dims& dm, int c, int a, int
     LU[idx] = v;
   }
   __syncthreads();
-
   // ---- LU with partial pivoting ----
   for (int k = 0; k < n; ++k) {
     if (warp == 0) {
@@ -135,6 +129,27 @@ __device__ __forceinline__ void bse_f64_system(const Dims& dm, int c, int a, int
     if (r < col) LU[idx] = cmul(LU[idx], invu[col]);
   }
   __syncthreads();
+}
+
+// D = 1 - gamma_W diag(chi~_W(q)) factorised in LU (n x n, row-major; shared
+// or global memory), right-hand sides P gamma in chunks of nc columns in Y,
+// writes kc[c][a][:][q] = w_c (Gamma_jj - Gamma^(2)_jj / 2).
+__device__ __forceinline__ void bse_f64_system(const Dims& dm, int c, int a, int q, int nc,
+                                               const double2* __restrict__ gam, const double2* __restrict__ gg,
+                                               const double2* __restrict__ chi, double2* __restrict__ kc,
+                                               double2* LU, double2* Y, double2* xs, double2* invu,
+                                               BseF64Shared& sh, int* __restrict__ flags) {
+  const int n = dm.n_w, N = dm.N, nb = dm.nb;
+  const int tid = threadIdx.x;
+  const double2* G = gam + ((size_t)c * nb + a) * n * n;
+  const double2* GG = gg + ((size_t)c * nb + a) * n * n;
+
+  for (int e = tid; e < nc * (nc - 1) / 2; e += blockDim.x) {
+    int d = 0;
+    while ((d + 1) * (d + 2) / 2 <= e) ++d;
+    sh.tri[e] = (unsigned short)((d << 8) | (e - d * (d + 1) / 2));
+  }
+  bse_f64_factor(dm, c, a, q, gam, chi, LU, xs, invu, sh, flags);
 
   // ---- diag(Gamma) by chunks of nc right-hand sides ----
   for (int j0 = 0; j0 < n; j0 += nc) {

@@ -78,6 +78,43 @@ __global__ void lattice_kernel(Dims dm, const double2* __restrict__ g, const dou
   }
 }
 
+// Planes of the susceptibilities (section "Resulting observables") on the
+// extended grid: G (Eq. glat) and frakG = G~ (G0~ + g) / G0~, with G~ from
+// Eq. dyson inside the box and G0~ outside.
+__global__ void obs_planes_kernel(Dims dm, const double2* __restrict__ g, const double2* __restrict__ delta,
+                                  const double2* __restrict__ g0, const double2* __restrict__ sigma,
+                                  double2* __restrict__ Gk, double2* __restrict__ Fk) {
+  const int total = dm.ne * dm.N;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    const int e = idx / dm.N, r = idx - e * dm.N, i = e - dm.m_max;
+    const double2 ge = g[e], de = delta[e], g0v = g0[idx];
+    double2 gt = g0v;
+    if (i >= 0 && i < dm.n_w) {
+      const double2 y = cinv(g0v), st = sigma[(size_t)i * dm.N + r];
+      gt = cinv(mk(y.x - st.x, y.y - st.y));
+    }
+    const double eps = eps_of(r, dm.D, dm.p, dm.t, dm.tp);
+    const double2 a = cinv(mk(de.x - eps, de.y)), gi = cinv(ge);
+    const double2 v = cmul(cmul(a, gi), cmul(gt, cmul(gi, a)));
+    Gk[idx] = mk(a.x + v.x, a.y + v.y);
+    Fk[idx] = cmul(gt, cmul(mk(g0v.x + ge.x, g0v.y + ge.y), cinv(g0v)));
+  }
+}
+
+// chi0[a][q] = sum_i P[a][i][q] (the bare term's sum over the box frequencies)
+__global__ void sum_w_kernel(Dims dm, const double2* __restrict__ P, double2* __restrict__ chi0) {
+  const int total = dm.nb * dm.N;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+    const int a = idx / dm.N, q = idx - a * dm.N;
+    double2 s = mk(0.0, 0.0);
+    for (int i = 0; i < dm.n_w; ++i) {
+      const double2 v = P[((size_t)a * dm.n_w + i) * dm.N + q];
+      s = mk(s.x + v.x, s.y + v.y);
+    }
+    chi0[idx] = s;
+  }
+}
+
 __global__ void residual_reduce_kernel(int n, double* red) {
   __shared__ double red_sm[32];
   residual_reduce_block(n, red, red_sm);
@@ -119,6 +156,33 @@ cudaError_t launch_lattice(df_ctx* c, double2* s_out, double2* g_out) {
   const Dims& dm = c->dm;
   const int total = dm.n_w * dm.N;
   lattice_kernel<<<(total + 255) / 256, 256, 0, c->stream>>>(dm, c->g, c->delta, c->g0, c->sigma, s_out, g_out);
+  return cudaGetLastError();
+}
+
+// The lattice parts of the susceptibilities: G and frakG planes (planes[0..1],
+// k space), to real space (planes[2..3]), their bubbles; writes
+// L [N_W][n_w][N] and chi0 [N_W][N], P [N_W][n_w][N] is scratch.
+cudaError_t launch_obs_bubbles(df_ctx* c, double2* planes, double2* P, double2* L, double2* chi0) {
+  const Dims& dm = c->dm;
+  const size_t plane = (size_t)dm.ne * dm.N;
+  double2* Gp = planes;
+  double2* Fp = planes + plane;
+  double2* Gr = planes + 2 * plane;
+  double2* Fr = planes + 3 * plane;
+  const int total = dm.ne * dm.N;
+  obs_planes_kernel<<<(total + 255) / 256, 256, 0, c->stream>>>(dm, c->g, c->delta, c->g0, c->sigma, Gp, Fp);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  size_t sm = fft_smem(dm, 1);
+  if ((e = set_smem((const void*)dyson_ifft_kernel, sm)) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)bubble_kernel, sm)) != cudaSuccess) return e;
+  dyson_ifft_kernel<<<dm.ne, kFftThreads, sm, c->stream>>>(dm, 0, Gp, nullptr, nullptr, Gr);
+  dyson_ifft_kernel<<<dm.ne, kFftThreads, sm, c->stream>>>(dm, 0, Fp, nullptr, nullptr, Fr);
+  bubble_kernel<<<dm.nb * dm.n_w, kFftThreads, sm, c->stream>>>(dm, Gr, P);
+  bubble_kernel<<<dm.nb * dm.n_w, kFftThreads, sm, c->stream>>>(dm, Fr, L);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int nq = dm.nb * dm.N;
+  sum_w_kernel<<<(nq + 255) / 256, 256, 0, c->stream>>>(dm, P, chi0);
   return cudaGetLastError();
 }
 

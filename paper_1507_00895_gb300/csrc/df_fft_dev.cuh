@@ -39,7 +39,8 @@ __device__ __forceinline__ void init_g0_elem(const Dims& dm, int idx, const doub
 }
 
 // Plane e: G~(k) = Dyson(G0~, Sigma~) inside the box (G0~ outside), then
-// G~(r) = (1/N) sum_k exp(ik.r) G~(k).
+// G~(r) = (1/N) sum_k exp(ik.r) G~(k).  With sigma == nullptr the plane is
+// transformed as given; with gk == nullptr the k-space copy is skipped.
 __device__ __forceinline__ void dyson_ifft_plane(const Dims& dm, int e, const double2* __restrict__ g0,
                                                  const double2* __restrict__ sigma, double2* __restrict__ gk,
                                                  double2* __restrict__ gr, double2* tw, double2* s) {
@@ -48,8 +49,8 @@ __device__ __forceinline__ void dyson_ifft_plane(const Dims& dm, int e, const do
   load_twiddles(tw, dm.nk);
   for (int r = threadIdx.x; r < dm.N; r += blockDim.x) {
     double2 v = g0[(size_t)e * dm.N + r];
-    if (in_box) v = cinv(cinv(v) - sigma[(size_t)i * dm.N + r]);
-    gk[(size_t)e * dm.N + r] = v;
+    if (in_box && sigma) v = cinv(cinv(v) - sigma[(size_t)i * dm.N + r]);
+    if (gk) gk[(size_t)e * dm.N + r] = v;
     s[bitrev_axes(r, dm.D, dm.p)] = v;
   }
   __syncthreads();

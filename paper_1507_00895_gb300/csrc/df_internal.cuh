@@ -199,6 +199,7 @@ struct df_ctx {
   double2* prod = nullptr;     // [nb][n_w][N] K(-r) G~_{w+W}(r)
   double2* sigma = nullptr;    // [n_w][N]
   double2* lat = nullptr;      // [2][n_w][N] lattice observables staged for host copies
+  double2* sus = nullptr;      // susceptibility buffers, allocated by the first df_susceptibility
   double2* lam = nullptr;      // [2][nb][N] leading eigenvalue of gamma chi
   int* lam_ok = nullptr;       // [2][nb][N] power iteration converged flag
   double* red = nullptr;       // [2 n_w] residual partials, [2] final, [2] solve flags (ints)
@@ -238,6 +239,8 @@ bool mixed_supported(int n_w);
 size_t mixed_workspace_bytes(const Dims& dm);
 cudaError_t launch_split_gamma(df_ctx* c, const double2* gg);
 cudaError_t launch_lattice(df_ctx* c, double2* s_out, double2* g_out);
+cudaError_t launch_obs_bubbles(df_ctx* c, double2* planes, double2* P, double2* L, double2* chi0);
+cudaError_t launch_chi_ladder(df_ctx* c, const double2* Lb, const double2* chi0, double2* out);
 const double2* gamma_gt_ptr(df_ctx* c);   // gamma o gamma^T, written by launch_gamma_gt
 cudaError_t launch_bse_mixed(df_ctx* c, int channel_mask, int* flags);
 }  // namespace df

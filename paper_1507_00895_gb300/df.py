@@ -36,7 +36,7 @@ DF_FP32_IR = 1
 # every symbol include/df.h declares (checked by the CPU tests)
 EXPORTS = (
     "df_default_opts", "df_init", "df_set_inputs", "df_vertex_from_spin", "df_bubble", "df_bse",
-    "df_sigma", "df_iterate", "df_get_sigma", "df_set_sigma", "df_get_gtilde", "df_lattice_observables", "df_get_chi",
+    "df_sigma", "df_iterate", "df_get_sigma", "df_set_sigma", "df_get_gtilde", "df_lattice_observables", "df_susceptibility", "df_get_chi",
     "df_get_kernel", "df_get_lambda", "df_get_sizes", "df_set_timing", "df_get_timing",
     "df_synchronize", "df_bse_noalloc", "df_batch_init", "df_batch_iterate", "df_batch_get_sigma",
     "df_batch_reset", "df_batch_autotune", "df_batch_last_error", "df_batch_destroy", "df_mlp_create",
@@ -96,6 +96,7 @@ def load(path: str = LIB_PATH):
         "df_set_sigma": [P, P, C.c_int],
         "df_get_gtilde": [P, P, C.c_int],
         "df_lattice_observables": [P, P, P, C.c_int],
+        "df_susceptibility": [P, P, C.c_int],
         "df_get_chi": [P, P, C.c_int],
         "df_get_kernel": [P, P, C.c_int],
         "df_get_lambda": [P, P, P, C.c_int],
@@ -289,6 +290,10 @@ class DualFermion:
 
     def get_gtilde(self, out=None):
         return self._get(self.lib.df_get_gtilde, (self.ne, self.N), out)
+
+    def susceptibility(self, out=None):
+        """chi^{ch/sp}(W, q) of the current Sigma~, [2][N_W][N] (0: charge, 1: spin)."""
+        return self._get(self.lib.df_susceptibility, (2, 2 * self.m_max + 1, self.N), out)
 
     def lattice_observables(self, sigma_out=None, g_out=None):
         """(Sigma_lat, G_lat) of the current Sigma~, each [n_w][N] (Eq. sigma_lat, Eq. glat)."""

@@ -473,3 +473,88 @@ def test_example_i_extrapolation_recovers_the_limit():
     gt[1 + 4, 0] = 2 + 3j      # m_max = 1, n_w = 8: box index n_w/2 is the first w > 0
     assert S.control_value(gt, 8, 1) == 2 + 3j
     assert abs(O.matsubara_box(8, 1.0)[4] - np.pi) < 1e-15
+
+
+# ---------------------------------------------------------------------------
+# section "Resulting observables": charge and spin susceptibilities
+# ---------------------------------------------------------------------------
+
+def _sus(w, eps, sigma, gd, gm):
+    return O.susceptibilities(w.g, w.delta, eps, sigma, gd, gm, w.n_w, w.m_max, w.beta, w.dim, w.nk)
+
+
+@pytest.mark.parametrize("nk", [2, 4])
+def test_susceptibility_flat_band_closed_form(nk):
+    # t = 0: G_lat = 1/(1/g + Delta) for every k, so the bare term is the atom's
+    # -T sum_w G_w G_{w+W}, independent of q and of N (an extensive sum would not be)
+    w = I.workload("paper_u20", nk=nk, n_w=8, m_max=2)
+    eps = np.zeros(w.N)
+    zero_g = np.zeros_like(O.channel_vertices(w.gamma_uu, w.gamma_ud)[0])
+    chi = _sus(w, eps, np.zeros((w.n_w, w.N), complex), zero_g, zero_g)
+    gl = 1.0 / (1.0 / w.g + w.delta)
+    T = 1.0 / w.beta
+    for a in range(w.n_bos):
+        ref = -T * sum(gl[i + w.m_max] * gl[i + a] for i in range(w.n_w))
+        assert np.max(np.abs(chi[:, a, :] - ref)) < 1e-11 * abs(ref)
+
+
+def test_frak_g_is_lattice_g_at_zero_dual_self_energy():
+    w = I.random_nonsymmetric(6, 1, 2, 4, seed=21)
+    eps = O.dispersion(2, 4, 1.0, 0.0)
+    g_lat, frak = O.lattice_planes_ext(w.g, w.delta, eps, np.zeros((6, 16), complex), 6, 1)
+    g_dmft = 1.0 / (1.0 / w.g[:, None] + w.delta[:, None] - eps[None, :])
+    assert np.max(np.abs(frak - g_dmft)) < 1e-12 * np.max(np.abs(g_dmft))
+    assert np.max(np.abs(g_lat - g_dmft)) < 1e-12 * np.max(np.abs(g_dmft))
+
+
+def test_susceptibility_brute_force_and_zero_vertex():
+    # non-symmetric inputs, tiny grid: L and the bare term by explicit k sums,
+    # Gamma by an explicit inverse, L Gamma L by a double loop
+    w = I.random_nonsymmetric(4, 1, 2, 2, seed=23, scale=0.2)
+    eps = O.dispersion(2, 2, 1.0, 0.0)
+    rng = np.random.default_rng(9)
+    sig = 0.2 * (rng.normal(size=(4, 4)) + 1j * rng.normal(size=(4, 4)))
+    gd, gm = O.channel_vertices(w.gamma_uu, w.gamma_ud)
+    chi = _sus(w, eps, sig, gd, gm)
+    g_lat, frak = O.lattice_planes_ext(w.g, w.delta, eps, sig, 4, 1)
+    gt = O.dual_g(O.bare_dual_g(w.g, w.delta, eps), sig, 4, 1)
+    chi0 = O.dual_bubble_direct(g_lat, 4, 1, w.beta, 2, 2).sum(axis=1)
+    L = O.dual_bubble_direct(frak, 4, 1, w.beta, 2, 2)
+    ct = O.dual_bubble_direct(gt, 4, 1, w.beta, 2, 2)
+    for c, gam in enumerate((gd, gm)):
+        for a in range(3):
+            for q in range(4):
+                Gam = np.linalg.inv(np.eye(4) - gam[a] * ct[a, :, q][None, :]) @ gam[a]
+                s = sum(L[a, i, q] * Gam[i, j] * L[a, j, q] for i in range(4) for j in range(4))
+                assert abs(chi[c, a, q] - (chi0[a, q] + s)) < 1e-12 * max(1.0, abs(chi[c, a, q]))
+    zero = np.zeros_like(gd)
+    chi_z = _sus(w, eps, sig, zero, zero)
+    assert np.max(np.abs(chi_z[0] - chi0)) < 1e-13 and np.max(np.abs(chi_z[1] - chi0)) < 1e-13
+
+
+def test_susceptibility_first_order_in_the_vertex():
+    # chi(e gamma) = chi0 + e L^T gamma L + O(e^2): the ladder enters as gamma at first order
+    w = I.workload("paper_u20", nk=4, n_w=4, m_max=1)
+    eps = O.dispersion(2, 4, 1.0, 0.0)
+    sig = np.zeros((4, 16), complex)
+    gd, gm = O.channel_vertices(w.gamma_uu, w.gamma_ud)
+    base = _sus(w, eps, sig, 0 * gd, 0 * gm)
+    e1, e2 = 1e-4, 2e-4
+    d1 = (_sus(w, eps, sig, e1 * gd, e1 * gm) - base) / e1
+    d2 = (_sus(w, eps, sig, e2 * gd, e2 * gm) - base) / e2
+    first = 2 * d1 - d2                                   # Richardson: O(e^2) removed
+    _, frak = O.lattice_planes_ext(w.g, w.delta, eps, sig, 4, 1)
+    L = O.dual_bubble_direct(frak, 4, 1, w.beta, 2, 4)
+    for c, gam in enumerate((gd, gm)):
+        ref = np.einsum("aiq,aij,ajq->aq", L, gam, L)
+        assert np.max(np.abs(first[c] - ref)) < 1e-6 * np.max(np.abs(ref))
+
+
+def test_susceptibility_conjugation_symmetry():
+    # symmetric atom inputs: chi(-W, q) = chi(W, q)*
+    w = I.workload("paper_u20", nk=4, n_w=6, m_max=2)
+    eps = O.dispersion(2, 4, 1.0, 0.0)
+    gd, gm = O.channel_vertices(w.gamma_uu, w.gamma_ud)
+    st = O.run_workload(w, n_iter=3)
+    chi = _sus(w, eps, st.sigma, gd, gm)
+    assert np.max(np.abs(chi[:, ::-1, :] - np.conj(chi))) < 1e-11 * np.max(np.abs(chi))

@@ -301,3 +301,24 @@ def test_largest_ladder_orders(df, n_w):
                 assert ok[c, 0, q] == 1 and abs(lam[c, 0, q] - lead) < 1e-8 * abs(lead)
                 n_ok += 1
     assert n_ok > 0
+
+
+@pytest.mark.parametrize("name,kw", [("paper_u20", dict(nk=4, n_w=6, m_max=1)),
+                                     ("square32_tp", dict(nk=8, n_w=10, m_max=2)),
+                                     ("cubic16_crit", dict(nk=4, n_w=8, m_max=1)),
+                                     ("paper_u20", dict(nk=2, n_w=98, m_max=0))])   # LU in global memory
+def test_susceptibility(df, name, kw):
+    # section "Resulting observables": chi^{ch/sp} after two passes, host and device outputs
+    import torch
+    w = I.workload(name, **kw)
+    st = O.run_workload(w, n_iter=2)
+    eps = O.dispersion(w.dim, w.nk, w.t, w.tp)
+    gd, gm = O.channel_vertices(w.gamma_uu, w.gamma_ud)
+    ref = O.susceptibilities(w.g, w.delta, eps, st.sigma, gd, gm, w.n_w, w.m_max, w.beta, w.dim, w.nk)
+    with df.DualFermion.from_workload(w) as d:
+        d.iterate(2)
+        chi = d.susceptibility()
+        assert nrel(chi, ref) < TOL64
+        dev = torch.empty(chi.shape, dtype=torch.complex128, device="cuda")
+        d.susceptibility(dev)
+        assert nrel(dev.cpu().numpy(), ref) < TOL64
