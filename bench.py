@@ -280,9 +280,11 @@ def batch_bench(df, I, torch, full: bool, passes: int = 3):
     pts = sum(w.n_bos * w.N for w in ws)
     out = {"workload": desc, "points_per_pass": pts, "ladders_per_pass": 2 * pts}
     cache = os.path.join(tempfile.gettempdir(), "df_batch_tune.txt")
+    if full:
+        passes = 1         # ~20 TFLOP of ladders per pass: one warm and one timed pass, default tiles
     for name, prec in (("fp64", df.DF_FP64), ("fp32ir", df.DF_FP32_IR)):
         with df.DualFermionBatch(ws, precision=prec) as b:
-            nc, ch, cached = b.autotune(cache)
+            nc, ch, cached = b.autotune(cache) if not full else (None, None, None)
             b.iterate(1)
             b.reset()
             torch.cuda.synchronize()
@@ -306,7 +308,8 @@ def example_i_bench(df):
 
 
 def observables_bench(df, I, torch, reps: int = 20):
-    """Eq. sigma_lat and Eq. glat on the bench workload after one pass (device outputs)."""
+    """Eq. sigma_lat and Eq. glat (device outputs) and the susceptibilities on the bench
+    workload after one pass."""
     w = I.workload(WORKLOAD)
     stream = torch.cuda.current_stream()
     with df.DualFermion.from_workload(w, stream=stream.cuda_stream) as d:
@@ -324,10 +327,25 @@ def observables_bench(df, I, torch, reps: int = 20):
         t1.record(stream)
         t1.synchronize()
         ms = t0.elapsed_time(t1) / reps
+        # susceptibilities: both channels' ladders factorised (FP64 LU, n^3/3 complex MACs)
+        # and solved for one right-hand side, plus the lattice bubbles
+        d.susceptibility()
+        t_sus = []
+        for _ in range(3):
+            d.synchronize()
+            t0h = time.perf_counter()
+            d.susceptibility()
+            t_sus.append(time.perf_counter() - t0h)
+        sus_s = min(t_sus)
     nbytes = 16 * w.n_w * w.N * 4          # G0~ and Sigma~ in, Sigma_lat and G_lat out
-    return {"kernel": "lattice_kernel", "ms": ms, "algorithmic_bytes": nbytes,
-            "GB_per_s": nbytes / (ms * 1e-3) / 1e9,
-            "note": "one elementwise pass over [n_w][N]; at this size launch latency dominates"}
+    lu_flop = 2 * w.n_bos * w.N * 8.0 * w.n_w ** 3 / 3.0
+    return {"lattice": {"kernel": "lattice_kernel", "ms": ms, "algorithmic_bytes": nbytes,
+                        "GB_per_s": nbytes / (ms * 1e-3) / 1e9,
+                        "note": "one elementwise pass over [n_w][N]; at this size launch latency dominates"},
+            "susceptibility": {"ms_per_call": sus_s * 1e3, "ladders": 2 * w.n_bos * w.N,
+                               "lu_flop": lu_flop, "lu_GFLOP_per_s": lu_flop / sus_s / 1e9,
+                               "note": "df_susceptibility wall time (synchronous call): dual bubble, G and frakG "
+                                       "planes, two lattice bubbles, 2 x N_W x N FP64 LU + solve"}}
 
 
 def warmstart_bench(df, I, torch, n_train=2000, n_test=200, steps=3000):

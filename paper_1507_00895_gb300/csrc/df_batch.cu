@@ -167,7 +167,7 @@ batch_bse_f64_kernel(const PointDev* __restrict__ pts, const int* __restrict__ o
       const int c = (int)(local / per_ch);
       const int rem = (int)(local - (long)c * per_ch);
       const int a = rem / dm.N, q = rem - a * dm.N;
-      const bool lu_smem = dm.n_w <= 96;
+      const bool lu_smem = dm.n_w <= kLuSmemOrder;
       const BseSmem L = bse_layout(dm.n_w, P.nc, lu_smem);
       double2* LU = lu_smem ? sm + L.lu : ws + blockIdx.x * ws_stride;
       bse_f64_system(dm, c, a, q, P.nc, P.gam, P.gg, P.chi, P.kc, LU, sm + L.y, sm + L.xs, sm + L.invu, sh,
@@ -305,7 +305,7 @@ int default_nc(int n) { return n <= 32 ? n : (n <= 64 ? 32 : 16); }
 
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
-constexpr int kLuScratchPerSm = 4;   // global LU slices per SM (FP64 ladders of order > 96)
+constexpr int kLuScratchPerSm = 4;   // global LU slices per SM (FP64 ladders of order > kLuSmemOrder)
 
 // the pass: all stages, captured into b->graph
 df_status record_pass(df_batch* b) {
@@ -377,7 +377,7 @@ df_status configure_groups(df_batch* b) {
       for (int p : g.order) {
         PointDev& P = b->host_pts[p];
         P.nc = b->nc_override ? std::min(b->nc_override, P.dm.n_w) : default_nc(P.dm.n_w);
-        sm = std::max(sm, sizeof(double2) * (size_t)bse_layout(P.dm.n_w, P.nc, P.dm.n_w <= 96).total);
+        sm = std::max(sm, sizeof(double2) * (size_t)bse_layout(P.dm.n_w, P.nc, P.dm.n_w <= kLuSmemOrder).total);
       }
       g.smem = sm;
       g.threads = kBseThreads;
@@ -636,11 +636,12 @@ df_status df_batch_init(df_batch** out, int npts, const df_point* pts, int preci
       cudaMemcpy(g.d_order, g.order.data(), sizeof(int) * g.nseg, cudaMemcpyHostToDevice);
     }
     BALLOC(b->d_counters, sizeof(unsigned long long) * std::max<size_t>(1, b->groups.size()), "counters");
-    // global LU scratch for FP64 ladders of order > 96
+    // global LU scratch for FP64 ladders of order > kLuSmemOrder
     int big = 0;
     for (auto& g : b->groups)
       if (!g.mixed)
-        for (int p : g.order) big = std::max(big, b->host_pts[p].dm.n_w > 96 ? b->host_pts[p].dm.n_w : 0);
+        for (int p : g.order)
+          big = std::max(big, b->host_pts[p].dm.n_w > kLuSmemOrder ? b->host_pts[p].dm.n_w : 0);
     if (big) {
       b->ws_stride = (size_t)big * big;
       BALLOC(b->ws, sizeof(double2) * b->ws_stride * (size_t)b->sms * kLuScratchPerSm, "LU scratch");

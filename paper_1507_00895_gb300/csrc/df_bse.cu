@@ -288,7 +288,8 @@ lambda_kernel(Dims dm, int ch0, int a0, int na, int lo_in_smem, double tol, cons
 // ---------------------------------------------------------------------------
 
 static int bse_chunk(int n) { return n <= 32 ? n : (n <= 64 ? 32 : 16); }
-static bool bse_lu_in_smem(int n) { return n <= 96; }
+static bool bse_lu_in_smem(int n) { return n <= kLuSmemOrder; }
+static bool bse_lu_fits_smem(int n) { return n <= 96; }   // the allocation-free entry point's limit
 
 size_t bse_workspace_bytes(const Dims& dm, int grid) {
   size_t b = (size_t)2 * dm.nb * dm.n_w * dm.n_w * sizeof(double2);      // gamma o gamma^T
@@ -408,10 +409,16 @@ cudaError_t launch_gamma_gt_raw(int n, int count, const double2* gam, double2* g
 
 cudaError_t launch_bse_both_raw(const Dims& dm, const double2* gam, const double2* gg, const double2* chi,
                                 double2* kc, int* flags, int device, cudaStream_t stream) {
-  if (!bse_lu_in_smem(dm.n_w)) return cudaErrorInvalidValue;
+  if (!bse_lu_fits_smem(dm.n_w)) return cudaErrorInvalidValue;
   const int nc = bse_chunk(dm.n_w);
-  const size_t smem = bse_smem_bytes(dm.n_w);
-  const int grid_max = bse_default_grid(dm, device);   // sets the shared-memory attribute
+  const size_t smem = sizeof(double2) * (size_t)bse_layout(dm.n_w, nc, true).total;
+  int sms = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  cudaError_t e = cudaFuncSetAttribute((const void*)bse_f64_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bse_f64_kernel<true>, kBseThreads, smem);
+  const int grid_max = sms * (per_sm < 1 ? 1 : per_sm);
   const long systems = 2L * dm.nb * dm.N;
   const int grid = (int)(systems < grid_max ? systems : grid_max);
   bse_f64_kernel<true><<<grid, kBseThreads, smem, stream>>>(dm, 0, 2, nc, gam, gg, chi, kc, nullptr, flags);
