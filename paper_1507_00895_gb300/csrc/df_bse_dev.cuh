@@ -9,11 +9,12 @@ namespace df {
 
 constexpr int kBseThreads = 256;
 // FP64 ladders of order <= kLuSmemOrder factorise in shared memory, larger ones
-// in a per-block slice of global (L2-resident) scratch: above order 64 the
-// shared-memory LU leaves room for one block per SM, the global one for
-// several, which hides the per-pivot barrier latency better (order 96:
-// 57% vs order 128: 84% of the FP64 peak measured with these placements)
-constexpr int kLuSmemOrder = 64;
+// in a per-block slice of global (L2-resident) scratch: the shared-memory LU
+// limits the blocks per SM (one at order 96, two at 64), the global one
+// leaves room for several, which hides the per-pivot barrier latency better.
+// Measured fractions of the FP64 peak (shared / global): order 40 64.6 / 63.8%,
+// 48 67.4 / 70.2%, 64 71.4 / 78.4%, 96 57 / 83%.
+constexpr int kLuSmemOrder = 40;
 
 struct BseSmem {
   // offsets in double2 units inside the dynamic shared block
