@@ -95,6 +95,13 @@ typedef struct df_opts {
   int eig_mode;       /* leading eigenvalue of gamma chi~: 0 off, 1 at W = 0 (default), 2 all W */
   int ir_max_steps;   /* DF_FP32_IR: maximum refinement steps (default 8) */
   double ir_tol;      /* DF_FP32_IR: relative correction size that stops refinement (default 1e-13) */
+  int radius_order;   /* the convergence-radius extension (the remark after Eq. lin_alg_inv): 0 off
+                       * (default: Eq. lin_alg_inv is solved regardless and |lambda| >= 1 raises
+                       * DF_WARN_LADDER_RADIUS); K >= 1: every (q, W, channel) whose leading
+                       * eigenvalue of gamma chi~ has |lambda| >= 1 takes the low-order iterative
+                       * evaluation Gamma <- gamma + gamma chi~ Gamma, K times from Gamma = gamma
+                       * (the Neumann series to order K), the others the inversion; decided anew
+                       * every pass.  K in [0, 16]; K >= 1 needs DF_FP64 and eig_mode 2. */
 } df_opts;
 
 /* Fill *o with the defaults above (n_w, m_max set to 0: the caller sets them). */

@@ -40,6 +40,9 @@ Status of each function's parity pin (tests/test_oracle_pins.py):
   second_order_diag ......................... pinned (second-order diagram, direct sum)
   lattice_observables ....................... pinned (G = G_DMFT at Sigma~ = 0; the Dyson relation
                                               between Eq. sigma_lat and Eq. glat)
+  ladder_gamma_diag(radius_order=K) ......... pinned (the order-K evaluation equals the truncated
+                                              Neumann series sum_j (gamma chi~)^j gamma by explicit
+                                              matrix powers; inside the radius it is the solve)
   susceptibilities .......................... pinned (flat-band closed form of the bare term; frakG = G
                                               at Sigma~ = 0; gamma = 0; brute-force L Gamma L; first
                                               order in a scaled vertex; conjugation symmetry)
@@ -250,10 +253,14 @@ def ladder_gamma_full(gamma_W: np.ndarray, chi_Wq: np.ndarray) -> np.ndarray:
     return np.linalg.solve(ladder_matrix(gamma_W, chi_Wq), gamma_W)
 
 
-def ladder_gamma_diag(gamma: np.ndarray, chi: np.ndarray) -> np.ndarray:
+def ladder_gamma_diag(gamma: np.ndarray, chi: np.ndarray, radius_order: int = 0) -> np.ndarray:
     """diag Gamma for every (W, q): gamma [N_W][n][n], chi [N_W][n][N] -> [N_W][n][N].
 
-    One LAPACK solve per (q, W) with all n right-hand sides (batched over q)."""
+    One LAPACK solve per (q, W) with all n right-hand sides (batched over q).
+    radius_order K > 0: the convergence-radius extension (the remark after
+    Eq. lin_alg_inv): where the largest-modulus eigenvalue of gamma chi~
+    (LAPACK zgeev) has |lambda| >= 1, Gamma is the low-order iterative
+    evaluation Gamma <- gamma + gamma chi~ Gamma, K times from Gamma = gamma."""
     nb, n, N = chi.shape
     out = np.empty((nb, n, N), dtype=np.complex128)
     eye = np.eye(n, dtype=np.complex128)
@@ -262,6 +269,14 @@ def ladder_gamma_diag(gamma: np.ndarray, chi: np.ndarray) -> np.ndarray:
         d = eye[None, :, :] - ga[None, :, :] * chi[a].T[:, None, :]     # [N][n][n]
         sol = np.linalg.solve(d, np.broadcast_to(ga, (N, n, n)))
         out[a] = np.diagonal(sol, axis1=1, axis2=2).T
+        if radius_order > 0:
+            for q in range(N):
+                A = ga * chi[a, :, q][None, :]
+                if np.max(np.abs(np.linalg.eigvals(A))) >= 1.0:
+                    G = ga.copy()
+                    for _ in range(radius_order):
+                        G = ga + A @ G
+                    out[a, :, q] = np.diagonal(G)
     return out
 
 
@@ -402,15 +417,15 @@ class LoopState:
 
 
 def one_iteration(state: LoopState, gamma_d, gamma_m, n_w, m_max, beta, dim, nk,
-                  mix: float = 1.0, bubble=dual_bubble_fft, sigma_fn=dual_sigma_fft):
+                  mix: float = 1.0, bubble=dual_bubble_fft, sigma_fn=dual_sigma_fft, radius_order: int = 0):
     """One pass of the loop: Dyson -> bubble -> ladder (both channels) -> Sigma~.
 
     Returns the new Sigma~ (mixed: mix * new + (1 - mix) * old) and
     r = max|Sigma_new - Sigma_old| / max|Sigma_new|."""
     gt = dual_g(state.g0_ext, state.sigma, n_w, m_max)
     chi = bubble(gt, n_w, m_max, beta, dim, nk)
-    gd = ladder_gamma_diag(gamma_d, chi)
-    gm = ladder_gamma_diag(gamma_m, chi)
+    gd = ladder_gamma_diag(gamma_d, chi, radius_order)
+    gm = ladder_gamma_diag(gamma_m, chi, radius_order)
     kern = sd_kernel(gd, second_order_diag(gamma_d, chi), gm, second_order_diag(gamma_m, chi))
     sig_new = sigma_fn(kern, gt, n_w, m_max, beta, dim, nk)
     sig_new = mix * sig_new + (1.0 - mix) * state.sigma
@@ -426,7 +441,7 @@ def one_iteration(state: LoopState, gamma_d, gamma_m, n_w, m_max, beta, dim, nk,
 
 def df_loop(g, delta, gamma_uu, gamma_ud, *, dim, nk, t, tp, beta, n_w, m_max,
             n_iter: int, mix: float = 1.0, tol: float = 0.0,
-            sigma0: Optional[np.ndarray] = None) -> LoopState:
+            sigma0: Optional[np.ndarray] = None, radius_order: int = 0) -> LoopState:
     """The ladder dual-fermion self-consistency loop, n_iter passes (or until r <= tol)."""
     eps = dispersion(dim, nk, t, tp)
     g0 = bare_dual_g(np.asarray(g), np.asarray(delta), eps)
@@ -434,19 +449,19 @@ def df_loop(g, delta, gamma_uu, gamma_ud, *, dim, nk, t, tp, beta, n_w, m_max,
     sigma = np.zeros((n_w, nk ** dim), np.complex128) if sigma0 is None else np.array(sigma0)
     st = LoopState(g0_ext=g0, sigma=sigma)
     for _ in range(n_iter):
-        _, r = one_iteration(st, gamma_d, gamma_m, n_w, m_max, beta, dim, nk, mix)
+        _, r = one_iteration(st, gamma_d, gamma_m, n_w, m_max, beta, dim, nk, mix, radius_order=radius_order)
         if r <= tol:
             break
     return st
 
 
 def run_workload(w, n_iter: Optional[int] = None, mix: float = 1.0, tol: float = 0.0,
-                 sigma0=None) -> LoopState:
+                 sigma0=None, radius_order: int = 0) -> LoopState:
     """df_loop on an ``inputs.Workload``-like object (duck typed)."""
     return df_loop(w.g, w.delta, w.gamma_uu, w.gamma_ud, dim=w.dim, nk=w.nk, t=w.t,
                    tp=w.tp, beta=w.beta, n_w=w.n_w, m_max=w.m_max,
                    n_iter=w.n_iter if n_iter is None else n_iter, mix=mix, tol=tol,
-                   sigma0=sigma0)
+                   sigma0=sigma0, radius_order=radius_order)
 
 
 def ladder_lambda(gamma, chi, a: int, q: int) -> complex:

@@ -120,6 +120,18 @@ cudaError_t run_lambda(df_ctx* c, int mask) {
   Timed t(c, DF_T_LAMBDA, n_channels(mask));
   return launch_lambda(c, mask);
 }
+// both ladder stages of a pass: the solves and the leading eigenvalue; with the
+// radius extension the eigenvalue goes first (the solves read it)
+cudaError_t run_ladders(df_ctx* c, int mask) {
+  cudaError_t e = cudaMemsetAsync(bse_flags(c), 0, sizeof(int) * 4, c->stream);
+  if (e != cudaSuccess) return e;
+  if (c->opts.radius_order > 0) {
+    if ((e = run_lambda(c, mask)) != cudaSuccess) return e;
+    return run_bse(c, mask);
+  }
+  if ((e = run_bse(c, mask)) != cudaSuccess) return e;
+  return run_lambda(c, mask);
+}
 cudaError_t run_sigma(df_ctx* c) {
   Timed t(c, DF_T_SIGMA, 3);
   return launch_sigma(c, c->opts.mix);
@@ -149,6 +161,7 @@ df_status df_default_opts(df_opts* o) {
   o->eig_mode = 1;
   o->ir_max_steps = 8;
   o->ir_tol = 1e-13;
+  o->radius_order = 0;
   return DF_OK;
 }
 
@@ -222,6 +235,8 @@ df_status df_init(df_ctx** out, const df_lattice* lat, double beta, double mu, d
   if (!(beta > 0.0) || !(opts->mix > 0.0 && opts->mix <= 1.0)) return DF_ERR_ARG;
   if (opts->precision != DF_FP64 && opts->precision != DF_FP32_IR) return DF_ERR_ARG;
   if (opts->eig_mode < 0 || opts->eig_mode > 2) return DF_ERR_ARG;
+  if (opts->radius_order < 0 || opts->radius_order > 16) return DF_ERR_ARG;
+  if (opts->radius_order > 0 && (opts->precision != DF_FP64 || opts->eig_mode != 2)) return DF_ERR_ARG;
   if (opts->precision == DF_FP32_IR && !mixed_supported(opts->n_w)) {
     fprintf(stderr, "libdf: DF_FP32_IR supports n_w <= 64\n");
     return DF_ERR_ARG;
@@ -336,8 +351,7 @@ df_status df_bubble(df_ctx* c) {
 df_status df_bse(df_ctx* c, int channel_mask) {
   if (!c) return DF_ERR_ARG;
   if (channel_mask < 1 || channel_mask > 3) return fail(c, DF_ERR_ARG, "channel_mask must be 1, 2 or 3");
-  DF_CUDA(c, run_bse(c, channel_mask), "ladder solve (Eq. lin_alg_inv)");
-  DF_CUDA(c, run_lambda(c, channel_mask), "leading eigenvalue of gamma chi");
+  DF_CUDA(c, run_ladders(c, channel_mask), "ladder solve (Eq. lin_alg_inv) and leading eigenvalue");
   return DF_OK;
 }
 
@@ -363,8 +377,7 @@ df_status df_iterate(df_ctx* c, int max_iter, double tol, int* iters_done, doubl
   int it = 0, flags = 0;
   for (; it < max_iter; ++it) {
     DF_CUDA(c, run_bubble(c), "dual bubble (Eq. dual_bubble)");
-    DF_CUDA(c, run_bse(c, 3), "ladder solve (Eq. lin_alg_inv)");
-    DF_CUDA(c, run_lambda(c, 3), "leading eigenvalue of gamma chi");
+    DF_CUDA(c, run_ladders(c, 3), "ladder solve (Eq. lin_alg_inv) and leading eigenvalue");
     DF_CUDA(c, run_sigma(c), "dual self-energy (Eq. sd) + Dyson");
     ++c->iter_done;
     if (tol > 0.0 || it == max_iter - 1) {

@@ -35,7 +35,8 @@ template <bool LU_SMEM>
 __global__ void __launch_bounds__(kBseThreads)
 bse_f64_kernel(Dims dm, int ch0, int nch, int nc, const double2* __restrict__ gam,
                const double2* __restrict__ gg, const double2* __restrict__ chi,
-               double2* __restrict__ kc, double2* __restrict__ ws, int* __restrict__ flags) {
+               double2* __restrict__ kc, double2* __restrict__ ws, int* __restrict__ flags, int radius_K,
+               const double2* __restrict__ lam) {
   extern __shared__ double2 sm[];
   __shared__ BseF64Shared sh;
   const int n = dm.n_w, N = dm.N, nb = dm.nb;
@@ -46,7 +47,8 @@ bse_f64_kernel(Dims dm, int ch0, int nch, int nc, const double2* __restrict__ ga
     const int c = ch0 + (int)(sys / ((long)nb * N));
     const int rem = (int)(sys - (long)(c - ch0) * nb * N);
     const int a = rem / N, q = rem - a * N;
-    bse_f64_system(dm, c, a, q, nc, gam, gg, chi, kc, LU, sm + L.y, sm + L.xs, sm + L.invu, sh, flags);
+    bse_f64_system(dm, c, a, q, nc, gam, gg, chi, kc, LU, sm + L.y, sm + L.xs, sm + L.invu, sh, flags, radius_K,
+                   lam);
   }
 }
 
@@ -331,19 +333,20 @@ cudaError_t launch_bse(df_ctx* c, int channel_mask) {
   const int n = dm.n_w;
   const int nc = bse_chunk(n);
   const size_t smem = bse_smem_bytes(n);
-  cudaError_t e = cudaMemsetAsync(flag_ptr(c), 0, sizeof(int) * 4, c->stream);
-  if (e != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
   if (c->opts.precision == DF_FP32_IR) return launch_bse_mixed(c, channel_mask, flag_ptr(c));
+  const int K = c->opts.radius_order;
+  const double2* lam = K > 0 ? c->lam : nullptr;
   for (int ch = 0; ch < 2; ++ch) {
     if (!(channel_mask & (1 << ch))) continue;
     const long systems = (long)dm.nb * dm.N;
     const int grid = (int)(systems < c->bse_grid ? systems : c->bse_grid);
     if (bse_lu_in_smem(n)) {
       bse_f64_kernel<true><<<grid, kBseThreads, smem, c->stream>>>(dm, ch, 1, nc, c->gam, gg_ptr(c), c->chi,
-                                                                   c->kc, nullptr, flag_ptr(c));
+                                                                   c->kc, nullptr, flag_ptr(c), K, lam);
     } else {
       bse_f64_kernel<false><<<grid, kBseThreads, smem, c->stream>>>(dm, ch, 1, nc, c->gam, gg_ptr(c), c->chi,
-                                                                    c->kc, lu_ws_ptr(c), flag_ptr(c));
+                                                                    c->kc, lu_ws_ptr(c), flag_ptr(c), K, lam);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -421,7 +424,8 @@ cudaError_t launch_bse_both_raw(const Dims& dm, const double2* gam, const double
   const int grid_max = sms * (per_sm < 1 ? 1 : per_sm);
   const long systems = 2L * dm.nb * dm.N;
   const int grid = (int)(systems < grid_max ? systems : grid_max);
-  bse_f64_kernel<true><<<grid, kBseThreads, smem, stream>>>(dm, 0, 2, nc, gam, gg, chi, kc, nullptr, flags);
+  bse_f64_kernel<true><<<grid, kBseThreads, smem, stream>>>(dm, 0, 2, nc, gam, gg, chi, kc, nullptr, flags, 0,
+                                                            nullptr);
   return cudaGetLastError();
 }
 

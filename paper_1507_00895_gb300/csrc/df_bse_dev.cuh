@@ -140,27 +140,62 @@ __device__ __forceinline__ void bse_f64_factor(const Dims& dm, int c, int a, int
 
 // D = 1 - gamma_W diag(chi~_W(q)) factorised in LU (n x n, row-major; shared
 // or global memory), right-hand sides P gamma in chunks of nc columns in Y,
-// writes kc[c][a][:][q] = w_c (Gamma_jj - Gamma^(2)_jj / 2).
+// writes kc[c][a][:][q] = w_c (Gamma_jj - Gamma^(2)_jj / 2).  With radius_K > 0
+// and |lam[c][a][q]| >= 1 (outside the ladder's convergence radius) Gamma is
+// instead the low-order iterative evaluation Gamma <- gamma + gamma chi~ Gamma,
+// radius_K times from Gamma = gamma (the LU buffer holds the product).
 __device__ __forceinline__ void bse_f64_system(const Dims& dm, int c, int a, int q, int nc,
                                                const double2* __restrict__ gam, const double2* __restrict__ gg,
                                                const double2* __restrict__ chi, double2* __restrict__ kc,
                                                double2* LU, double2* Y, double2* xs, double2* invu,
-                                               BseF64Shared& sh, int* __restrict__ flags) {
+                                               BseF64Shared& sh, int* __restrict__ flags, int radius_K = 0,
+                                               const double2* __restrict__ lam = nullptr) {
   const int n = dm.n_w, N = dm.N, nb = dm.nb;
   const int tid = threadIdx.x;
   const double2* G = gam + ((size_t)c * nb + a) * n * n;
   const double2* GG = gg + ((size_t)c * nb + a) * n * n;
 
-  for (int e = tid; e < nc * (nc - 1) / 2; e += blockDim.x) {
-    int d = 0;
-    while ((d + 1) * (d + 2) / 2 <= e) ++d;
-    sh.tri[e] = (unsigned short)((d << 8) | (e - d * (d + 1) / 2));
+  bool series = false;
+  if (radius_K > 0) {
+    const double2 l = lam[((size_t)c * nb + a) * N + q];
+    series = (l.x * l.x + l.y * l.y >= 1.0);
   }
-  bse_f64_factor(dm, c, a, q, gam, chi, LU, xs, invu, sh, flags);
+  if (series) {
+    for (int i = tid; i < n; i += blockDim.x) xs[i] = chi[((size_t)a * n + i) * N + q];
+    __syncthreads();
+  } else {
+    for (int e = tid; e < nc * (nc - 1) / 2; e += blockDim.x) {
+      int d = 0;
+      while ((d + 1) * (d + 2) / 2 <= e) ++d;
+      sh.tri[e] = (unsigned short)((d << 8) | (e - d * (d + 1) / 2));
+    }
+    bse_f64_factor(dm, c, a, q, gam, chi, LU, xs, invu, sh, flags);
+  }
 
   // ---- diag(Gamma) by chunks of nc right-hand sides ----
   for (int j0 = 0; j0 < n; j0 += nc) {
     const int w = min(nc, n - j0);
+    if (series) {
+      for (int idx = tid; idx < n * w; idx += blockDim.x) {
+        const int r = idx / w, jj = idx - r * w;
+        Y[r * nc + jj] = G[(size_t)r * n + j0 + jj];
+      }
+      __syncthreads();
+      for (int it = 0; it < radius_K; ++it) {
+        for (int idx = tid; idx < n * w; idx += blockDim.x) {
+          const int r = idx / w, jj = idx - r * w;
+          double2 t = G[(size_t)r * n + j0 + jj];
+          for (int k = 0; k < n; ++k) t = cfma(cmul(G[(size_t)r * n + k], xs[k]), Y[k * nc + jj], t);
+          LU[r * nc + jj] = t;
+        }
+        __syncthreads();
+        for (int idx = tid; idx < n * w; idx += blockDim.x) {
+          const int r = idx / w, jj = idx - r * w;
+          Y[r * nc + jj] = LU[r * nc + jj];
+        }
+        __syncthreads();
+      }
+    } else {
     for (int idx = tid; idx < n * w; idx += blockDim.x) {
       const int r = idx / w, jj = idx - r * w;
       Y[r * nc + jj] = G[(size_t)sh.perm[r] * n + j0 + jj];
@@ -196,9 +231,10 @@ __device__ __forceinline__ void bse_f64_system(const Dims& dm, int c, int a, int
       }
       __syncthreads();
     }
+    }
     for (int jj = tid; jj < w; jj += blockDim.x) {
       const int j = j0 + jj;
-      const double2 gdiag = cmul(Y[j * nc + jj], invu[j]);
+      const double2 gdiag = series ? Y[j * nc + jj] : cmul(Y[j * nc + jj], invu[j]);
       double2 g2 = mk(0.0, 0.0);
       for (int x = 0; x < n; ++x) g2 = cfma(GG[(size_t)j * n + x], xs[x], g2);
       const double wgt = (c == 0) ? 1.0 : 3.0;

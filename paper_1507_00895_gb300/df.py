@@ -64,7 +64,8 @@ class df_point(C.Structure):
 
 class df_opts(C.Structure):
     _fields_ = [("n_w", C.c_int), ("m_max", C.c_int), ("mix", C.c_double), ("precision", C.c_int),
-                ("eig_mode", C.c_int), ("ir_max_steps", C.c_int), ("ir_tol", C.c_double)]
+                ("eig_mode", C.c_int), ("ir_max_steps", C.c_int), ("ir_tol", C.c_double),
+                ("radius_order", C.c_int)]
 
 
 _lib = None
@@ -181,7 +182,7 @@ class DualFermion:
     def __init__(self, *, dim: int, nk: int, t: float, tp: float, beta: float, mu: float,
                  n_w: int, m_max: int, g, delta, gamma_d, gamma_m, mix: float = 1.0,
                  precision: int = DF_FP64, eig_mode: int = 1, ir_max_steps: int = 8,
-                 ir_tol: float = 1e-13, stream: Optional[int] = None):
+                 ir_tol: float = 1e-13, radius_order: int = 0, stream: Optional[int] = None):
         self.lib = load()
         self.dim, self.nk, self.n_w, self.m_max = dim, nk, n_w, m_max
         self.N = nk ** dim
@@ -192,6 +193,7 @@ class DualFermion:
         self.lib.df_default_opts(C.byref(opts))
         opts.n_w, opts.m_max, opts.mix, opts.precision = n_w, m_max, mix, precision
         opts.eig_mode, opts.ir_max_steps, opts.ir_tol = eig_mode, ir_max_steps, ir_tol
+        opts.radius_order = radius_order
         g, delta = _c128(g), _c128(delta)
         gd, gm = _c128(gamma_d), _c128(gamma_m)
         if g.shape != (self.ne,) or delta.shape != (self.ne,):

@@ -64,6 +64,13 @@ def test_bad_sizes_are_rejected_before_any_device_call(lib):
     assert lib.df_init(C.byref(h), C.byref(lat), 1.0, 0.0, 1.0, p, p, p, p, C.byref(opts), None) == 1
     lat = df.df_lattice(3, 4, -0.2)              # t' only in 2D
     assert lib.df_init(C.byref(h), C.byref(lat), 1.0, 0.0, 1.0, p, p, p, p, C.byref(opts), None) == 1
+    lat = df.df_lattice(2, 4, 0.0)
+    opts.radius_order = 1                        # the radius extension needs eig_mode 2 ...
+    assert lib.df_init(C.byref(h), C.byref(lat), 1.0, 0.0, 1.0, p, p, p, p, C.byref(opts), None) == 1
+    opts.eig_mode, opts.precision = 2, df.DF_FP32_IR   # ... and the FP64 path
+    assert lib.df_init(C.byref(h), C.byref(lat), 1.0, 0.0, 1.0, p, p, p, p, C.byref(opts), None) == 1
+    opts.precision, opts.radius_order = df.DF_FP64, 17
+    assert lib.df_init(C.byref(h), C.byref(lat), 1.0, 0.0, 1.0, p, p, p, p, C.byref(opts), None) == 1
 
 
 def test_no_gpu_fails_loudly(lib):

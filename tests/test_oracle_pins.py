@@ -558,3 +558,37 @@ def test_susceptibility_conjugation_symmetry():
     st = O.run_workload(w, n_iter=3)
     chi = _sus(w, eps, st.sigma, gd, gm)
     assert np.max(np.abs(chi[:, ::-1, :] - np.conj(chi))) < 1e-11 * np.max(np.abs(chi))
+
+
+# ---------------------------------------------------------------------------
+# the convergence-radius extension (the remark after Eq. lin_alg_inv)
+# ---------------------------------------------------------------------------
+
+def test_radius_extension_is_the_truncated_series_outside_the_radius():
+    # config-1-like inputs far outside the radius: every flagged system takes
+    # sum_{j <= K} (gamma chi~)^j gamma (explicit matrix powers), the rest the solve
+    w = I.workload("square16_b5", nk=4, n_w=8, m_max=2)
+    st = O.run_workload(w, n_iter=1)
+    gd, _ = O.channel_vertices(w.gamma_uu, w.gamma_ud)
+    chi = st.chi
+    plain = O.ladder_gamma_diag(gd, chi)
+    for K in (1, 3):
+        ext = O.ladder_gamma_diag(gd, chi, radius_order=K)
+        n_out = 0
+        for a in range(w.n_bos):
+            for q in range(w.N):
+                A = gd[a] * chi[a, :, q][None, :]
+                if np.max(np.abs(np.linalg.eigvals(A))) >= 1.0:
+                    ref = sum(np.linalg.matrix_power(A, j) @ gd[a] for j in range(K + 1))
+                    assert np.max(np.abs(ext[a, :, q] - np.diagonal(ref))) < 1e-10 * np.max(np.abs(ref))
+                    n_out += 1
+                else:
+                    assert np.max(np.abs(ext[a, :, q] - plain[a, :, q])) == 0.0
+        assert 0 < n_out < w.n_bos * w.N        # both kinds present
+
+
+def test_radius_extension_changes_nothing_inside_the_radius():
+    w = I.workload("paper_u20", nk=4, n_w=6, m_max=1)
+    a = O.run_workload(w, n_iter=3)
+    b = O.run_workload(w, n_iter=3, radius_order=2)
+    assert np.array_equal(a.sigma, b.sigma)

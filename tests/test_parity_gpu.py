@@ -322,3 +322,22 @@ def test_susceptibility(df, name, kw):
         dev = torch.empty(chi.shape, dtype=torch.complex128, device="cuda")
         d.susceptibility(dev)
         assert nrel(dev.cpu().numpy(), ref) < TOL64
+
+
+@pytest.mark.parametrize("K", [1, 3])
+def test_radius_extension(df, K):
+    # outside the ladder radius (|lambda| up to 25): flagged systems take the
+    # order-K iterative evaluation; each pass teacher-forced from the oracle's
+    # previous Sigma~ (the decisions are >= 0.12 away from |lambda| = 1 here)
+    w = I.workload("square16_b5", nk=4, n_w=8, m_max=2)
+    st = O.run_workload(w, n_iter=3, radius_order=K)
+    prev = np.zeros((w.n_w, w.N), complex)
+    with df.DualFermion.from_workload(w, eig_mode=2, radius_order=K) as d:
+        for p in range(3):
+            d.set_sigma(prev)
+            d.iterate(1)
+            assert nrel(d.get_sigma(), st.sigmas[p]) < TOL64
+            prev = st.sigmas[p]
+    # the plain inversion differs: the extension is active
+    plain = O.run_workload(w, n_iter=1)
+    assert nrel(st.sigmas[0], plain.sigmas[0]) > 1e-3
