@@ -348,6 +348,28 @@ def observables_bench(df, I, torch, reps: int = 20):
                                        "planes, two lattice bubbles, 2 x N_W x N FP64 LU + solve"}}
 
 
+def radius_bench(df, I, torch, passes: int = 10):
+    """The convergence-radius extension on the 16x16, n_w = 32 workload (outside the radius):
+    ms per pass with eigenvalues at every W, plain inversion vs order-1 and order-3 evaluation
+    of the flagged ladders, and the share of ladders flagged on the first pass."""
+    import numpy as np
+    w = I.workload("square16_b5")
+    out = {"workload": "2D 16x16, U=2, beta=5, n_w=32, N_W=1, Delta = V^2/(i w)"}
+    stream = torch.cuda.current_stream()
+    for name, K in (("plain", 0), ("order_1", 1), ("order_3", 3)):
+        with df.DualFermion.from_workload(w, eig_mode=2, radius_order=K, stream=stream.cuda_stream) as d:
+            d.iterate(1)
+            lam, _ = d.get_lambda()
+            d.set_sigma(np.zeros((w.n_w, w.N), np.complex128))
+            d.synchronize()
+            t0 = time.perf_counter()
+            d.iterate(passes)
+            d.synchronize()
+            out[name] = {"ms_per_pass": (time.perf_counter() - t0) / passes * 1e3}
+        out["flagged_share_first_pass"] = float(np.mean(np.abs(lam) >= 1.0))
+    return out
+
+
 def warmstart_bench(df, I, torch, n_train=2000, n_test=200, steps=3000):
     """Learned warm start: train the 4x512 network (own BF16 kernels) on
     converged Sigma~ of n_train points of the warm-start family (2D 16^2,
@@ -551,6 +573,7 @@ def run_ours(args):
     obs = None
     if rank == 0:
         obs = observables_bench(df, I, torch)
+        obs["radius_extension"] = radius_bench(df, I, torch)
     warm = None
     if rank == 0 and not args.no_warmstart:
         warm = warmstart_bench(df, I, torch)
