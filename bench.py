@@ -46,7 +46,7 @@ FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07
 FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) per launch of the ladder kernel from one ncu capture
 # of that kernel on this workload (None once the kernel changes)
-NCU_TRAFFIC = {"bse_f64_kernel": None, "bse_mixed_kernel": 19773952}
+NCU_TRAFFIC = {"bse_f64_kernel": 33274112, "bse_mixed_kernel": 19773952}
 
 
 def dist_env():
@@ -571,7 +571,7 @@ def run_ours(args):
     if rank == 0 and not args.no_sweeps:
         sweeps = example_i_bench(df)
     obs = None
-    if rank == 0:
+    if rank == 0 and not args.no_observables:
         obs = observables_bench(df, I, torch)
         obs["radius_extension"] = radius_bench(df, I, torch)
     warm = None
@@ -620,6 +620,8 @@ def main():
     ap.add_argument("--batch-full", action="store_true", help="uneven batch at the recipe's full sizes")
     ap.add_argument("--no-warmstart", action="store_true", help="skip the learned warm-start measurement")
     ap.add_argument("--no-sweeps", action="store_true", help="skip the paper's Example I sweeps")
+    ap.add_argument("--no-observables", action="store_true",
+                    help="skip the lattice-observable, susceptibility and radius-extension timings")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)       # at least 3 untimed warm-up steps
     if args.impl == "reference":
