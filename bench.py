@@ -56,6 +56,21 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """The largest of the ranks' values (the slowest rank's time); x itself on one rank."""
+    if world <= 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(points_per_rank: int, world: int, seconds: float) -> float:
+    """Whole-job throughput of `world` replicas that each processed points_per_rank in at most `seconds`."""
+    return world * points_per_rank / seconds
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -472,11 +487,7 @@ def run_ours(args):
         timing = d.get_timing()
         d.set_timing(False)
         step_ms = [s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)]
-        ms = sum(step_ms) / len(step_ms)
-        if world > 1:
-            t = torch.tensor([ms], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(sum(step_ms) / len(step_ms), world)
         bse_ms, bse_launches = timing["bse"]
         bse_avg_s = bse_ms / max(1, bse_launches) * 1e-3
         if prec == df.DF_FP64:
@@ -501,7 +512,7 @@ def run_ours(args):
                                    "count once each here but run as 36 bf16 digit-pair products on the "
                                    "tensor cores (mma.sync)",
                     "flop_per_launch": systems_per_launch * flop, "launch_ms": bse_avg_s * 1e3}
-        res = {"value": world * points / (ms * 1e-3), "ms_per_step": ms, "roofline": roof,
+        res = {"value": whole_job_rate(points, world, ms * 1e-3), "ms_per_step": ms, "roofline": roof,
                "gpu_launches": sum(v[1] for v in timing.values()),
                "kernel_ms_per_step": {k: v[0] / args.steps for k, v in timing.items()},
                "clocks": clk}
@@ -553,12 +564,8 @@ def run_ours(args):
             step()
             d.get_sigma(h_out)
         torch.cuda.synchronize()
-        e2e_s = (time.perf_counter() - t0) / args.steps
-        if world > 1:
-            t = torch.tensor([e2e_s], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": world * points / e2e_s, "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, world)
+        e2e = {"value": whole_job_rate(points, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
                "ms_per_step": e2e_s * 1e3}
     d.close()
     ttc = None
