@@ -183,12 +183,13 @@ __device__ __forceinline__ void dd_add(float& hi, float& lo, float v) {
 // b = pb in-place Gauss-Jordan steps on the panel pan[np][kPanelLd] (the pivot
 // columns k0 .. k0 + pb - 1), run by warp 0 alone: lane l holds rows
 // l + nlanes s (s < np / nlanes <= 2) in registers.  The pivot of each
-// column is the warp maximum of a key (|a| bits with their low 7 bits
-// replaced by 127 - row: the largest |a| to 2^-16 relative, ties to the
-// lowest row) over the rows not yet used; the pivot row is broadcast by
-// shuffles from its owner lane.  Writes the new panel to pan, the pivot rows
-// to piv_s[k0 + i] and the steps to rowstep[row]; used0 marks this lane's
-// rows taken.
+// column is the warp maximum of a key (|re| + |im| bits with their low 7 bits
+// replaced by 127 - row: the largest to 2^-16 relative, ties to the lowest
+// row) over the rows not yet used; the pivot row is broadcast by shuffles
+// from its owner lane.  The elimination is branch-free (the pivot row takes
+// the scaled row by a select).  Writes the new panel to pan, after the pb
+// steps the pivot rows to piv_s[k0 + i] and the steps to rowstep[row];
+// used0 marks this lane's rows taken.
 template <int NP>
 __device__ __forceinline__ void gj_panel(float2* pan, int k0, int lane, unsigned& used0, int* piv_s, int* rowstep,
                                          int* flags) {
@@ -204,18 +205,18 @@ __device__ __forceinline__ void gj_panel(float2* pan, int k0, int lane, unsigned
 #pragma unroll
     for (int c2 = 0; c2 < kPanel; ++c2)
       pv[s2][c2] = (s2 < rows_per_lane && c2 < pb) ? pan[(lane + nlanes * s2) * kPanelLd + c2] : make_float2(0.f, 0.f);
+  int pivs[kPanel];
+  bool sing = false;
 #pragma unroll
   for (int i = 0; i < kPanel; ++i) {
     if (i < pb) {
       unsigned key = 0u;
 #pragma unroll
-      for (int s2 = 0; s2 < kPanelRows; ++s2) {
-        if (s2 < rows_per_lane && !((used0 >> s2) & 1u)) {
-          const int r = lane + nlanes * s2;
-          const float m = fabsf(pv[s2][i].x) + fabsf(pv[s2][i].y);
-          const unsigned k2 = (__float_as_uint(m) & ~0x7Fu) | (unsigned)(127 - r);
-          key = k2 > key ? k2 : key;
-        }
+      for (int s2 = 0; s2 < rows_per_lane; ++s2) {
+        const int r = lane + nlanes * s2;
+        const float m = fabsf(pv[s2][i].x) + fabsf(pv[s2][i].y);
+        const unsigned k2 = ((used0 >> s2) & 1u) ? 0u : ((__float_as_uint(m) & ~0x7Fu) | (unsigned)(127 - r));
+        key = k2 > key ? k2 : key;
       }
       key = __reduce_max_sync(wmask, key);
       int p = 127 - (int)(key & 0x7Fu);
@@ -228,7 +229,7 @@ __device__ __forceinline__ void gj_panel(float2* pan, int k0, int lane, unsigned
       for (int c2 = 0; c2 < kPanel; ++c2) {
         float2 v = pv[0][c2];
 #pragma unroll
-        for (int s2 = 1; s2 < kPanelRows; ++s2)
+        for (int s2 = 1; s2 < rows_per_lane; ++s2)
           if (s2 == sp2) v = pv[s2][c2];
         u[c2].x = __shfl_sync(wmask, v.x, owner);
         u[c2].y = __shfl_sync(wmask, v.y, owner);
@@ -242,35 +243,111 @@ __device__ __forceinline__ void gj_panel(float2* pan, int k0, int lane, unsigned
       }
 #pragma unroll
       for (int c2 = 0; c2 < kPanel; ++c2) u[c2] = (c2 == i) ? ainv : cmulf(u[c2], ainv);
-      if (lane == 0) {
-        piv_s[k0 + i] = p;
-        rowstep[p] = k0 + i;
-        if (singular) atomicOr(flags, 1);
-      }
-      if (lane == owner) used0 |= 1u << sp2;
+      pivs[i] = p;
+      sing |= singular;
+      used0 |= (lane == owner) ? (1u << sp2) : 0u;
 #pragma unroll
-      for (int s2 = 0; s2 < kPanelRows; ++s2) {
-        const int r = lane + nlanes * s2;
-        if (r == p) {
+      for (int s2 = 0; s2 < rows_per_lane; ++s2) {
+        const bool isp = (lane + nlanes * s2 == p);
+        const float2 m = pv[s2][i];
 #pragma unroll
-          for (int c2 = 0; c2 < kPanel; ++c2) pv[s2][c2] = u[c2];
-        } else {
-          const float2 m = pv[s2][i];
-#pragma unroll
-          for (int c2 = 0; c2 < kPanel; ++c2) {
-            const float2 base = (c2 == i) ? make_float2(0.f, 0.f) : pv[s2][c2];
-            pv[s2][c2] = cfmsf(m, u[c2], base);
-          }
+        for (int c2 = 0; c2 < kPanel; ++c2) {
+          const float2 base = (c2 == i) ? make_float2(0.f, 0.f) : pv[s2][c2];
+          const float2 e = cfmsf(m, u[c2], base);
+          pv[s2][c2] = isp ? u[c2] : e;
         }
       }
     }
   }
 #pragma unroll
-  for (int s2 = 0; s2 < kPanelRows; ++s2)
-    if (s2 < rows_per_lane)
+  for (int s2 = 0; s2 < rows_per_lane; ++s2)
 #pragma unroll
-      for (int c2 = 0; c2 < kPanel; ++c2)
-        if (c2 < pb) pan[(lane + nlanes * s2) * kPanelLd + c2] = pv[s2][c2];
+    for (int c2 = 0; c2 < kPanel; ++c2)
+      if (c2 < pb) pan[(lane + nlanes * s2) * kPanelLd + c2] = pv[s2][c2];
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < kPanel; ++i) {
+      if (i < pb) {
+        piv_s[k0 + i] = pivs[i];
+        rowstep[pivs[i]] = k0 + i;
+      }
+    }
+    if (sing) atomicOr(flags, 1);
+  }
+}
+
+// The same b = 8 steps for np = 64 on two warps (threads 0..63), one row per
+// lane: each warp's best unused row (its warp max) goes to cand / ckey, a
+// 64-thread named barrier, then both warps take the better of the two.  The
+// candidate slots alternate between steps, so one barrier per step suffices.
+__device__ __forceinline__ void gj_panel2(float2* pan, int k0, int w, int lane, unsigned& used0, int* piv_s,
+                                          int* rowstep, int* flags, float4* cand, unsigned* ckey) {
+  constexpr int np = 64;
+  const int r = 32 * w + lane;
+  float2 pv[kPanel];
+#pragma unroll
+  for (int c2 = 0; c2 < kPanel; ++c2) pv[c2] = pan[r * kPanelLd + c2];
+  int pivs[kPanel];
+  bool sing = false;
+#pragma unroll
+  for (int i = 0; i < kPanel; ++i) {
+    const float m0 = fabsf(pv[i].x) + fabsf(pv[i].y);
+    const unsigned key = (used0 & 1u) ? 0u : ((__float_as_uint(m0) & ~0x7Fu) | (unsigned)(127 - r));
+    const unsigned kw = __reduce_max_sync(0xffffffffu, key);
+    const int par = i & 1;
+    if (key == kw && kw != 0u) {
+      float4* cs = cand + (par * 2 + w) * (kPanel / 2);
+#pragma unroll
+      for (int c4 = 0; c4 < kPanel / 2; ++c4)
+        cs[c4] = make_float4(pv[2 * c4].x, pv[2 * c4].y, pv[2 * c4 + 1].x, pv[2 * c4 + 1].y);
+    }
+    if (lane == 0) ckey[par * 2 + w] = kw;
+    asm volatile("bar.sync 1, 64;" ::: "memory");
+    const unsigned ka = ckey[par * 2], kb = ckey[par * 2 + 1];
+    const int wb = kb > ka ? 1 : 0;
+    const unsigned kbest = kb > ka ? kb : ka;
+    int p = 127 - (int)(kbest & 0x7Fu);
+    const float bm = __uint_as_float(kbest & ~0x7Fu);
+    const bool singular = !(bm > 0.f) || p >= np;
+    if (p >= np) p = 0;
+    const float4* cb = cand + (par * 2 + wb) * (kPanel / 2);
+    float2 u[kPanel];
+#pragma unroll
+    for (int c4 = 0; c4 < kPanel / 2; ++c4) {
+      const float4 q = cb[c4];
+      u[2 * c4] = make_float2(q.x, q.y);
+      u[2 * c4 + 1] = make_float2(q.z, q.w);
+    }
+    float2 ainv = make_float2(0.f, 0.f);
+    if (!singular) {
+      const float2 z = u[i];
+      const float d = __fdividef(1.f, fmaf(z.x, z.x, z.y * z.y));
+      ainv = make_float2(z.x * d, -z.y * d);
+    }
+#pragma unroll
+    for (int c2 = 0; c2 < kPanel; ++c2) u[c2] = (c2 == i) ? ainv : cmulf(u[c2], ainv);
+    pivs[i] = p;
+    sing |= singular;
+    const bool isp = (r == p);
+    used0 |= isp ? 1u : 0u;
+    const float2 m = pv[i];
+#pragma unroll
+    for (int c2 = 0; c2 < kPanel; ++c2) {
+      const float2 base = (c2 == i) ? make_float2(0.f, 0.f) : pv[c2];
+      const float2 e = cfmsf(m, u[c2], base);
+      pv[c2] = isp ? u[c2] : e;
+    }
+  }
+#pragma unroll
+  for (int c2 = 0; c2 < kPanel; ++c2) pan[r * kPanelLd + c2] = pv[c2];
+  if (w == 0 && lane == 0) {
+#pragma unroll
+    for (int i = 0; i < kPanel; ++i) {
+      piv_s[k0 + i] = pivs[i];
+      rowstep[pivs[i]] = k0 + i;
+    }
+    if (sing) atomicOr(flags, 1);
+  }
 }
 
 // bf16 bit pattern of the signed digit (sign16 = 0 or 0x8000, 0 <= d < 256),
@@ -372,7 +449,8 @@ __host__ __device__ inline MixedSmem mixed_layout(int np) {
   const int tc = (tc_work_bytes(np) + 7) / 8;
   // Gauss-Jordan panels [2][np][kPanelLd] and pivot rows [kPanel][2 np]; with
   // the tensor-core residual they sit in the Y-digit area, past gamma's digits
-  const int gj = (use_tc_residual(np) ? gdig_bytes(np) / 8 : 0) + 2 * np * kPanelLd + kPanel * 2 * np;
+  const int gj = (use_tc_residual(np) ? gdig_bytes(np) / 8 : 0) + 2 * np * kPanelLd + kPanel * 2 * np +
+                 2 * 2 * kPanel + 2;   // + the two-warp panel's candidate rows and keys
   const int res = use_tc_residual(np) ? tc : simt;
   o += res > gj ? res : gj;
   L.total = o;
@@ -480,21 +558,24 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
   // The b GJ steps of a panel change every other column j by a rank-b
   // update, A[:, j] += W A[piv, j], where W = (panel after its own in-place
   // GJ steps) - (unit columns at the pivot rows).  Per panel: (1) the owners
-  // of the panel columns copy them to pan; (2) warp 0 runs the b steps on
-  // pan in registers (pivot = warp max of a (|a| bits, ~row) key; the pivot
-  // row by shuffles); (3) the pivot rows' current values go to prs;
-  // (4) every thread applies the rank-b update to its tile and takes the
-  // panel's new columns.  Three block barriers per panel instead of one or
-  // two per pivot.
+  // of the panel columns copy them to pan; (2) warp 0 (warps 0 and 1 for
+  // np = 64, one row per lane) runs the b steps on pan in registers (pivot =
+  // max of a (|a| bits, ~row) key); (3) the pivot rows' current values go to
+  // prs; (4) every thread applies the rank-b update to its whole tile, then
+  // the panel columns take the panel's new values (their updated ones are
+  // dropped: no per-column test in the update).  Three block barriers per
+  // panel instead of one or two per pivot.
   const int warp = t >> 5, lane = t & 31;
   constexpr int nlanes = P * P < 32 ? P * P : 32;
   constexpr unsigned wmask = nlanes == 32 ? 0xffffffffu : ((1u << nlanes) - 1u);
   constexpr int pb = P < kPanel ? P : kPanel;        // panel width b
   float2* panbuf = reinterpret_cast<float2*>(sp.work + (use_tc_residual(NP) ? gdig_bytes(NP) : 0));   // [2][np][kPanelLd]
   float2* prs = panbuf + 2 * np * kPanelLd;                      // [kPanel][2 np]
+  float4* cand = reinterpret_cast<float4*>(prs + kPanel * 2 * np);  // two-warp panel: [2][2][kPanel / 2]
+  unsigned* ckey = reinterpret_cast<unsigned*>(cand + 2 * kPanel);   // [2][2]
   int* rowstep = reinterpret_cast<int*>(invu);                   // pivot step of each row, -1 if none
   for (int i = t; i < np; i += blockDim.x) rowstep[i] = -1;
-  unsigned used0 = 0;                                            // warp 0: its rows already pivots
+  unsigned used0 = 0;                                            // panel warps: their rows already pivots
   // one copy of the loop body (the register column jk is selected at run time)
 #pragma unroll 1
   for (int k0 = 0; k0 < np; k0 += pb) {
@@ -513,8 +594,12 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
       }
     }
     __syncthreads();
-    // (2) b GJ steps on the panel, warp 0
-    if (warp == 0) gj_panel<NP>(pan, k0, lane, used0, piv_s, rowstep, flags);
+    // (2) b GJ steps on the panel: warps 0 and 1 for np = 64, else warp 0
+    if constexpr (NP == 64) {
+      if (warp < 2) gj_panel2(pan, k0, warp, lane, used0, piv_s, rowstep, flags, cand, ckey);
+    } else {
+      if (warp == 0) gj_panel<NP>(pan, k0, lane, used0, piv_s, rowstep, flags);
+    }
     __syncthreads();
     // (3) current values of the pivot rows
 #pragma unroll
@@ -529,7 +614,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
       }
     }
     __syncthreads();
-    // (4) rank-b update; the panel columns take their new values
+    // (4) rank-b update (the panel columns too: they take their new values after)
     for (int l = 0; l < pb; ++l) {
       const int pl = piv_s[k0 + l];
       float2 pr[2 * kTile];
@@ -545,7 +630,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
         if (r == pl) w.x -= 1.f;
 #pragma unroll
         for (int jj = 0; jj < kTile; ++jj) {
-          if (!(jj == jk && pcol)) A[ii][jj] = cfmaf2(w, pr[jj], A[ii][jj]);
+          A[ii][jj] = cfmaf2(w, pr[jj], A[ii][jj]);
           A[ii][kTile + jj] = cfmaf2(w, pr[kTile + jj], A[ii][kTile + jj]);
         }
       }
