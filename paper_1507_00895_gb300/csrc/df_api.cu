@@ -355,6 +355,16 @@ df_status df_bse(df_ctx* c, int channel_mask) {
   return DF_OK;
 }
 
+// errors carried in the ladder kernels' flags word
+static df_status flag_error(df_ctx* c, int flags) {
+  if (flags & kFlagSingular) return fail(c, DF_ERR_SINGULAR, "exactly zero pivot in a ladder solve");
+  if (flags & kFlagTcTimeout)
+    return fail(c, DF_ERR_TIMEOUT, "a tensor-core completion wait in the mixed ladder kernel gave up");
+  if (flags & kFlagTcLayout)
+    return fail(c, DF_ERR_CUDA, "mixed ladder kernel: shared-memory operands not 1024-byte aligned");
+  return DF_OK;
+}
+
 df_status df_sigma(df_ctx* c, double* resid) {
   if (!c) return DF_ERR_ARG;
   DF_CUDA(c, run_sigma(c), "dual self-energy (Eq. sd) + Dyson");
@@ -364,8 +374,8 @@ df_status df_sigma(df_ctx* c, double* resid) {
     df_status s = read_scalars(c, resid, &flags);
     if (s != DF_OK) return s;
     c->last_resid = *resid;
-    if (flags & 1) return fail(c, DF_ERR_SINGULAR, "exactly zero pivot in a ladder solve");
-    if (flags & 2) return DF_WARN_LADDER_RADIUS;
+    if ((s = flag_error(c, flags)) != DF_OK) return s;
+    if (flags & kFlagRadius) return DF_WARN_LADDER_RADIUS;
   }
   return DF_OK;
 }
@@ -383,9 +393,9 @@ df_status df_iterate(df_ctx* c, int max_iter, double tol, int* iters_done, doubl
     if (tol > 0.0 || it == max_iter - 1) {
       df_status s = read_scalars(c, &r, &flags);
       if (s != DF_OK) return s;
-      if (flags & 1) {
+      if ((s = flag_error(c, flags)) != DF_OK) {
         if (iters_done) *iters_done = it + 1;
-        return fail(c, DF_ERR_SINGULAR, "exactly zero pivot in a ladder solve");
+        return s;
       }
       if (tol > 0.0 && r <= tol) {
         ++it;
@@ -397,7 +407,7 @@ df_status df_iterate(df_ctx* c, int max_iter, double tol, int* iters_done, doubl
   if (resid) *resid = r;
   c->last_resid = r;
   if (tol > 0.0 && !(r <= tol)) return DF_ERR_NOT_CONVERGED;
-  if (flags & 2) return DF_WARN_LADDER_RADIUS;
+  if (flags & kFlagRadius) return DF_WARN_LADDER_RADIUS;
   return DF_OK;
 }
 
@@ -457,7 +467,7 @@ df_status df_susceptibility(df_ctx* c, double* out, int is_device) {
   if (!is_device)
     DF_CUDA(c, cudaMemcpyAsync(out, res, sizeof(double2) * 2 * pq, cudaMemcpyDeviceToHost, c->stream), "copy out");
   DF_CUDA(c, cudaStreamSynchronize(c->stream), "df_susceptibility");
-  if (fl[0] & 1) return fail(c, DF_ERR_SINGULAR, "exactly zero pivot in a susceptibility ladder");
+  if (fl[0] & kFlagSingular) return fail(c, DF_ERR_SINGULAR, "exactly zero pivot in a susceptibility ladder");
   return DF_OK;
 }
 

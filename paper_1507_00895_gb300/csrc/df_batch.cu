@@ -177,13 +177,24 @@ batch_bse_f64_kernel(const PointDev* __restrict__ pts, const int* __restrict__ o
 }
 
 template <int NP>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, use_umma_residual(NP) ? 1 : 0)
 batch_bse_mixed_kernel(const PointDev* __restrict__ pts, const int* __restrict__ order, const long* __restrict__ start,
                        int nseg, int chunk, unsigned long long* __restrict__ counter) {
-  extern __shared__ float2 smf[];
+  extern __shared__ __align__(1024) float2 smf[];
   __shared__ int piv_s[128];
   __shared__ unsigned long long item_s;
+  __shared__ uint64_t mbar_s;
+  __shared__ unsigned tslot_s;
   const MixedPtrs sp = mixed_ptrs(smf, NP, piv_s);
+  Tc05 tc{};
+  if constexpr (use_umma_residual(NP)) {
+    // the swizzled operand tiles need a 1024-aligned work area
+    if (smem_u32(sp.work) & 1023u) {
+      if (threadIdx.x == 0) atomicOr(pts[0].flags, kFlagTcLayout);
+      return;
+    }
+    tc05_setup(tc, &mbar_s, &tslot_s);
+  }
   const long total = start[nseg];
   long cur = -1;                       // (point, channel, W) whose gamma digits are in shared memory
   for (;;) {
@@ -205,10 +216,11 @@ batch_bse_mixed_kernel(const PointDev* __restrict__ pts, const int* __restrict__
       const int a = rem / dm.N, q = rem - a * dm.N;
       const long key = (long)k * 256 + c * dm.nb + a;
       bse_mixed_system<NP>(dm, c, a, q, P.gam, P.gam_hi, P.gam_lo, P.gg_hi, P.gg_lo, P.chi, P.kc, P.flags, sp,
-                           P.gdig ? P.gdig + (size_t)(c * dm.nb + a) * gdig_bytes(NP) : nullptr, key != cur);
+                           P.gdig ? P.gdig + (size_t)(c * dm.nb + a) * gdig_bytes(NP) : nullptr, key != cur, &tc);
       cur = key;
     }
   }
+  if constexpr (use_umma_residual(NP)) tc05_teardown(tc);
 }
 
 }  // namespace df
@@ -690,14 +702,17 @@ df_status df_batch_iterate(df_batch* b, int max_iter, int* passes_done, double* 
     for (int i = 0; i < b->npts; ++i) any |= (b->h_out[3 * i + 1] != 0.0);
     ++b->passes;
   }
-  int sing = 0;
+  int fl = 0;
   for (int i = 0; i < b->npts; ++i) {
     if (resid) resid[i] = b->h_out[3 * i];
     if (active) active[i] = (int)b->h_out[3 * i + 1];
-    sing |= (int)b->h_out[3 * i + 2] & 1;
+    fl |= (int)b->h_out[3 * i + 2];
   }
   if (passes_done) *passes_done = it;
-  if (sing) return bfail(b, DF_ERR_SINGULAR, "exactly zero pivot in a ladder solve");
+  if (fl & kFlagSingular) return bfail(b, DF_ERR_SINGULAR, "exactly zero pivot in a ladder solve");
+  if (fl & kFlagTcTimeout)
+    return bfail(b, DF_ERR_TIMEOUT, "a tensor-core completion wait in the mixed ladder kernel gave up");
+  if (fl & kFlagTcLayout) return bfail(b, DF_ERR_CUDA, "mixed ladder kernel: shared-memory operands not 1024-byte aligned");
   return any ? DF_ERR_NOT_CONVERGED : DF_OK;
 }
 

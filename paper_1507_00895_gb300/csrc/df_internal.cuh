@@ -13,6 +13,12 @@
 
 namespace df {
 
+// bits of the ladder kernels' flags word
+constexpr int kFlagSingular = 1;    // an exactly zero pivot
+constexpr int kFlagRadius = 2;      // a ladder outside the radius of convergence
+constexpr int kFlagTcTimeout = 4;   // a bounded tensor-core completion wait gave up
+constexpr int kFlagTcLayout = 8;    // tensor-core operands not 1024-byte aligned (no MMA issued)
+
 // ---------------------------------------------------------------------------
 // complex arithmetic on double2 / float2 (x = real, y = imag)
 // ---------------------------------------------------------------------------

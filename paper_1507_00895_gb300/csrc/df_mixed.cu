@@ -52,15 +52,26 @@ __global__ void gamma_digits_kernel(int n, int np, int count, const double2* __r
 // One contiguous range of systems per block (so that consecutive systems
 // share (channel, W) and gamma's digits stay in shared memory).
 template <int NP>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, use_umma_residual(NP) ? 1 : 0)
 bse_mixed_kernel(Dims dm, int ch0, int nch, const double2* __restrict__ gam,
                  const float2* __restrict__ gam_hi, const float2* __restrict__ gam_lo,
                  const float2* __restrict__ gg_hi, const float2* __restrict__ gg_lo,
                  const double2* __restrict__ chi, double2* __restrict__ kc,
                  const unsigned char* __restrict__ gdig, int* __restrict__ flags) {
-  extern __shared__ float2 smf[];
+  extern __shared__ __align__(1024) float2 smf[];
   __shared__ int piv_s[128];
+  __shared__ uint64_t mbar_s;
+  __shared__ unsigned tslot_s;
   const MixedPtrs sp = mixed_ptrs(smf, NP, piv_s);
+  Tc05 tc{};
+  if constexpr (use_umma_residual(NP)) {
+    // the swizzled operand tiles need a 1024-aligned work area
+    if (smem_u32(sp.work) & 1023u) {
+      if (threadIdx.x == 0) atomicOr(flags, kFlagTcLayout);
+      return;
+    }
+    tc05_setup(tc, &mbar_s, &tslot_s);
+  }
   const int N = dm.N, nb = dm.nb;
   const long systems = (long)nch * nb * N;
   const long per = (systems + gridDim.x - 1) / gridDim.x;
@@ -72,9 +83,10 @@ bse_mixed_kernel(Dims dm, int ch0, int nch, const double2* __restrict__ gam,
     const int a = rem / N, q = rem - a * N;
     const int key = c * nb + a;
     bse_mixed_system<NP>(dm, c, a, q, gam, gam_hi, gam_lo, gg_hi, gg_lo, chi, kc, flags, sp,
-                         gdig ? gdig + (size_t)key * gdig_bytes(NP) : nullptr, key != cur);
+                         gdig ? gdig + (size_t)key * gdig_bytes(NP) : nullptr, key != cur, &tc);
     cur = key;
   }
+  if constexpr (use_umma_residual(NP)) tc05_teardown(tc);
 }
 
 // ---------------------------------------------------------------------------

@@ -29,6 +29,7 @@
 // the first n rows unchanged.
 #pragma once
 #include <cuda_bf16.h>
+#include <cstdint>
 
 #include "df_internal.cuh"
 
@@ -170,6 +171,102 @@ __device__ __forceinline__ void mma_bf16(float* d, const unsigned* a, unsigned b
       "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
       : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// ---- tcgen05 (5th-generation tensor core) helpers for the np = 64 residual ----
+// Operands are K-major bf16 tiles in shared memory with 128-byte rows in the
+// 128-byte swizzle (16-byte chunk c of row r at chunk c ^ (r & 7); 8-row groups
+// 1024 bytes apart, group base 1024-aligned) -- the layout swz() writes.  The
+// FP32 accumulators live in tensor memory (TMEM): row i of D in TMEM lane i,
+// column j in TMEM column (base + j).
+constexpr int kTmemCols = 256;      // 8 weight groups x 32 columns
+constexpr unsigned kMbarSpin = 1u << 22;   // try_wait rounds before giving up
+
+struct Tc05 {
+  unsigned tmem;        // TMEM base address (lane 0, first allocated column)
+  uint64_t* mbar;       // completion barrier of the MMA batches
+  unsigned phase;       // parity of the next completion (the same in every thread)
+};
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t umma_desc_sw128(unsigned saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// instruction descriptor, kind::f16: bf16 A and B (K-major), FP32 D, M x N
+__host__ __device__ constexpr unsigned umma_idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
+}
+__device__ __forceinline__ void umma_bf16(unsigned dtmem, uint64_t a, uint64_t b, unsigned idesc, unsigned acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// arrive on mbar once every MMA issued so far by this thread has completed
+__device__ __forceinline__ void umma_commit(uint64_t* mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
+               : "memory");
+}
+// bounded wait for the completion of the given parity; false if it gave up
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, unsigned parity) {
+  const unsigned a = smem_u32(mbar);
+  for (unsigned it = 0; it < kMbarSpin; ++it) {
+    unsigned done;
+    asm volatile(
+        "{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void tc05_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc05_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// generic-proxy shared-memory writes -> visible to the tensor core's reads
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+// 16 consecutive FP32 columns of this thread's TMEM lane (warp w reads lanes 32 (w % 4) ..)
+__device__ __forceinline__ void tmem_ld16(unsigned taddr, float* v) {
+  unsigned r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+// block-level set-up / tear-down (all threads call; warp 0 owns the TMEM allocation)
+__device__ __forceinline__ void tc05_setup(Tc05& tc, uint64_t* mbar, unsigned* tslot) {
+  if ((threadIdx.x >> 5) == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "n"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc05_fence_before();
+  __syncthreads();
+  tc05_fence_after();
+  tc.tmem = *tslot;
+  tc.mbar = mbar;
+  tc.phase = 0;
+}
+__device__ __forceinline__ void tc05_teardown(const Tc05& tc) {
+  tc05_fence_before();
+  __syncthreads();
+  tc05_fence_after();
+  if ((threadIdx.x >> 5) == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tc.tmem), "n"(kTmemCols) : "memory");
 }
 
 __device__ __forceinline__ void dd_add(float& hi, float& lo, float v) {
@@ -421,14 +518,19 @@ struct MixedSmem {
   int x0, chih, chil, invu, x0d, chi64, work, gt_h, gt_l, yh, yl, total;
 };
 
+__host__ __device__ constexpr bool use_tc_residual(int np) { return np == 32 || np == 64; }
+// np = 64: the digit products run as tcgen05 MMAs (M = 128 = [Zr; Zi] rows)
+__host__ __device__ constexpr bool use_umma_residual(int np) { return np == 64; }
+// offset of the Y digits in the work area (1024-aligned for the tcgen05 operands)
+__host__ __device__ constexpr int xs_offset(int np) {
+  return use_umma_residual(np) ? ((gdig_bytes(np) + 1023) & ~1023) : gdig_bytes(np);
+}
 // bytes of the tensor-core residual's work area (n_pad in {32, 64}): the
 // gamma digits of the current (channel, W) (kept across systems), then the
 // Y digits of one column block and their column exponents
 __host__ __device__ constexpr int tc_work_bytes(int np) {
-  return gdig_bytes(np) + 2 * kSlices * 2 * kCB * 64 + 4 * kCB;
+  return xs_offset(np) + 2 * kSlices * 2 * kCB * 64 + 4 * kCB;
 }
-
-__host__ __device__ constexpr bool use_tc_residual(int np) { return np == 32 || np == 64; }
 
 __host__ __device__ inline MixedSmem mixed_layout(int np) {
   MixedSmem L;
@@ -494,7 +596,8 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
                                                  const float2* __restrict__ gg_lo,
                                                  const double2* __restrict__ chi, double2* __restrict__ kc,
                                                  int* __restrict__ flags, const MixedPtrs& sp,
-                                                 const unsigned char* __restrict__ gdig, bool reload) {
+                                                 const unsigned char* __restrict__ gdig, bool reload,
+                                                 Tc05* umma) {
   const int n = dm.n_w, N = dm.N, nb = dm.nb;
   constexpr int np = NP, P = NP / kTile;
   float2* X0s = sp.X0s;
@@ -519,6 +622,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
       const uint4* src = reinterpret_cast<const uint4*>(gdig);
       uint4* dst = reinterpret_cast<uint4*>(sp.work);
       for (int i = t; i < gdig_bytes(NP) / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+      if constexpr (use_umma_residual(NP)) fence_async_smem();
     }
   }
   for (int i = t; i < np; i += blockDim.x) {
@@ -668,7 +772,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
     // folded, scaled, into a double-float sum.
     __nv_bfloat16* zs = reinterpret_cast<__nv_bfloat16*>(sp.work);                       // [kSlices][2][np][64]
     const int* rowe = reinterpret_cast<const int*>(zs + (size_t)kSlices * 2 * np * 64);   // [np]
-    __nv_bfloat16* xs = reinterpret_cast<__nv_bfloat16*>(sp.work + gdig_bytes(NP));      // [kSlices][2][kCB][64]
+    __nv_bfloat16* xs = reinterpret_cast<__nv_bfloat16*>(sp.work + xs_offset(NP));       // [kSlices][2][kCB][64]
     int* cole = reinterpret_cast<int*>(xs + (size_t)kSlices * 2 * kCB * 64);             // [kCB]
     unsigned* xw = reinterpret_cast<unsigned*>(xs);
     const int nthr = blockDim.x;
@@ -716,6 +820,98 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
           xw[(s2 * 2 + 1) * kCB * 32 + wo] = w1[s2] | (v1[s2] << 16);
         }
       }
+      if constexpr (use_umma_residual(NP)) {
+        // ---- tcgen05: for each gamma slice sa one MMA per K step of 16,
+        // A = [Zr; Zi] of slice sa (M = 128), B = the Y slices 0 .. 7 - sa
+        // stacked along N (32 rows each: Yr then Yi columns), D at TMEM column
+        // 32 sa: Y slice sb lands in accumulator d = sa + sb (weight 2^-7(d+2)),
+        // columns 32 d .. 32 d + 31 = [Yr | Yi]; lanes 0-63 hold the Zr rows,
+        // 64-127 the Zi rows.  Each accumulator is exact (<= 8 pairs x 64 x 127^2 < 2^23).
+        fence_async_smem();
+        __syncthreads();
+        if (t == 0) {
+          tc05_fence_after();
+          const unsigned za = smem_u32(zs), xa = smem_u32(xs);
+#pragma unroll 1
+          for (int sa = 0; sa < kSlices; ++sa) {
+            const unsigned idesc = umma_idesc_bf16(128, 32 * (kSlices - sa));
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks)
+              umma_bf16(umma->tmem + 32 * sa, umma_desc_sw128(za + sa * (2 * np * 128) + 32 * ks),
+                        umma_desc_sw128(xa + 32 * ks), idesc, (sa > 0 || ks > 0) ? 1u : 0u);
+          }
+          umma_commit(umma->mbar);
+        }
+        if (!mbar_wait(umma->mbar, umma->phase) && t == 0) atomicOr(flags, kFlagTcTimeout);
+        umma->phase ^= 1;
+        tc05_fence_after();
+        // fold: warp w reads lane quadrant q = w % 4 (gamma row i, Zr or Zi) and
+        // column half h = w / 4 (Yr or Yi) of the 8 accumulators, smallest
+        // weight first, into double-float
+        const int qd = warp & 3, h = warp >> 2;
+        const int i = ((qd & 1) << 5) + lane;
+        const bool zi = qd >= 2;
+        float fh[kCB], fl[kCB];
+#pragma unroll
+        for (int c2 = 0; c2 < kCB; ++c2) fh[c2] = fl[c2] = 0.f;
+        const unsigned tl = umma->tmem + ((unsigned)(32 * qd) << 16) + (unsigned)(16 * h);
+#pragma unroll
+        for (int d = kSlices - 1; d >= 0; --d) {
+          float v[kCB];
+          tmem_ld16(tl + 32 * d, v);
+          const float sc = __int_as_float((127 - 7 * d) << 23);     // 2^-7d
+#pragma unroll
+          for (int c2 = 0; c2 < kCB; ++c2) dd_add(fh[c2], fl[c2], v[c2] * sc);
+        }
+        tc05_fence_before();
+        // scale by 2^(e_i + e_j - 14); the Zi rows' parts go to E first (ZiYi
+        // negated: it enters the real part with a minus), then the Zr rows add
+        // theirs: E[0] = S real, E[1] = S imaginary, row stride kCB + 1
+        float2* E = reinterpret_cast<float2*>(xs);
+        const int ei = rowe[i];
+#pragma unroll
+        for (int c2 = 0; c2 < kCB; ++c2) {
+          const int ej = cole[c2];
+          const float w = (ei > -1000 && ej > -1000) ? pow2f(ei + ej - 14) : 0.f;
+          fh[c2] *= w;
+          fl[c2] *= w;
+        }
+        if (zi) {
+          const float sg = h ? -1.f : 1.f;
+          float2* Eo = E + (1 - h) * np * (kCB + 1) + i * (kCB + 1);   // ZiYr -> imaginary, ZiYi -> real
+#pragma unroll
+          for (int c2 = 0; c2 < kCB; ++c2) Eo[c2] = make_float2(sg * fh[c2], sg * fl[c2]);
+        }
+        __syncthreads();
+        if (!zi) {
+          float2* Eo = E + h * np * (kCB + 1) + i * (kCB + 1);         // ZrYr -> real, ZrYi -> imaginary
+#pragma unroll
+          for (int c2 = 0; c2 < kCB; ++c2) {
+            const float2 o = Eo[c2];
+            float sh, se;
+            two_sum(fh[c2], o.x, sh, se);
+            Eo[c2] = make_float2(sh, se + (fl[c2] + o.y));
+          }
+        }
+        __syncthreads();
+        // R = gamma - X0 + S in double-float (it cancels to ~u32 |gamma|);
+        // consecutive threads take consecutive columns of a row
+        for (int idx = t; idx < np * kCB; idx += nthr) {
+          const int row = idx / kCB, col = idx - row * kCB;
+          const int j = b * kCB + col;
+          const bool in = (row < n && j < n);
+          const float2 gh = in ? Gh[row * n + j] : make_float2(0.f, 0.f);
+          const float2 gl = in ? Gl[row * n + j] : make_float2(0.f, 0.f);
+          const float2 x = X0s[row * np + j];
+          const float2 sr = E[row * (kCB + 1) + col], si = E[np * (kCB + 1) + row * (kCB + 1) + col];
+          float re = gh.x, rl = gl.x, im = gh.y, il = gl.y;
+          df_add(re, rl, -x.x);
+          df_add(re, rl, sr.x);
+          df_add(im, il, -x.y);
+          df_add(im, il, si.x);
+          X0s[row * np + j] = make_float2(re + (rl + sr.y), im + (il + si.y));   // R replaces X0
+        }
+      } else {
       __syncthreads();
       for (int tile = warp; tile < tiles; tile += nwarp) {
         const int r16 = (tile / (kCB / 8)) * 16, c8 = (tile % (kCB / 8)) * 8;
@@ -786,6 +982,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
           df_add(im, il, hm[e]);
           X0s[row * np + j] = make_float2(re + (rl + lr[e]), im + (il + lm[e]));   // R replaces X0
         }
+      }
       }
     }
     __syncthreads();
