@@ -179,7 +179,7 @@ __device__ __forceinline__ void mma_bf16(float* d, const unsigned* a, unsigned b
 // 1024 bytes apart, group base 1024-aligned) -- the layout swz() writes.  The
 // FP32 accumulators live in tensor memory (TMEM): row i of D in TMEM lane i,
 // column j in TMEM column (base + j).
-constexpr int kTmemCols = 256;      // 8 weight groups x 32 columns
+constexpr int kTmemCols = 512;      // two buffers of 8 weight groups x 32 columns
 constexpr unsigned kMbarSpin = 1u << 22;   // try_wait rounds before giving up
 
 struct Tc05 {
@@ -529,7 +529,10 @@ __host__ __device__ constexpr int xs_offset(int np) {
 // gamma digits of the current (channel, W) (kept across systems), then the
 // Y digits of one column block and their column exponents
 __host__ __device__ constexpr int tc_work_bytes(int np) {
-  return xs_offset(np) + 2 * kSlices * 2 * kCB * 64 + 4 * kCB;
+  // np = 64 adds a second column-exponent slot, the re/im exchange
+  // [2][np][kCB + 1] (double-float) and per-warp column exponents [8][kCB]
+  return xs_offset(np) + 2 * kSlices * 2 * kCB * 64 + 4 * kCB +
+         (use_umma_residual(np) ? 4 * kCB + 2 * np * (kCB + 1) * 8 + 4 * 8 * kCB : 0);
 }
 
 __host__ __device__ inline MixedSmem mixed_layout(int np) {
@@ -762,7 +765,184 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
   }
   __syncthreads();
   for (int j = t; j < np; j += blockDim.x) x0d[j] = X0s[j * np + j];
-  if constexpr (use_tc_residual(NP)) {
+  if constexpr (use_umma_residual(NP)) {
+    // ---- residual R = gamma - X0 + gamma Y with tcgen05, Y = diag(chi~) X0 ----
+    // gamma's digits (8 signed base-128 digits relative to per-row powers of
+    // two, cut once per input upload) are in zs / rowe; Y is formed in
+    // double-float and cut the same way relative to per-column powers of two,
+    // kCB columns at a time.  For each gamma slice sa one MMA per K step of
+    // 16: A = [Zr; Zi] of slice sa (M = 128), B = the Y slices 0 .. 7 - sa
+    // stacked along N (32 rows each: the block's Yr then Yi columns), D at
+    // TMEM column 32 sa, so that Y slice sb lands in accumulator d = sa + sb
+    // (weight 2^-7(d+2)), columns 32 d .. 32 d + 31 = [Yr | Yi]; lanes 0-63
+    // hold the Zr rows, 64-127 the Zi rows.  Every accumulator is exact (<= 8
+    // pairs x 64 x 127^2 < 2^23), and the pairs with weight < 2^-63 are never
+    // formed.  Column block b's MMAs run in TMEM buffer b & 1 while block
+    // b - 1 is folded and assembled.
+    __nv_bfloat16* zs = reinterpret_cast<__nv_bfloat16*>(sp.work);                       // [kSlices][2][np][64]
+    const int* rowe = reinterpret_cast<const int*>(zs + (size_t)kSlices * 2 * np * 64);   // [np]
+    __nv_bfloat16* xs = reinterpret_cast<__nv_bfloat16*>(sp.work + xs_offset(NP));       // [kSlices][2][kCB][64]
+    int* cole2 = reinterpret_cast<int*>(xs + (size_t)kSlices * 2 * kCB * 64);            // [2][kCB]
+    float2* E = reinterpret_cast<float2*>(cole2 + 2 * kCB);                              // [2][np][kCB + 1]
+    int* cw = reinterpret_cast<int*>(E + 2 * np * (kCB + 1));                            // [8][kCB]
+    unsigned* xw = reinterpret_cast<unsigned*>(xs);
+    const int warp = t >> 5, lane = t & 31;
+    const int yc = t & (kCB - 1), yp = t >> 4;          // Y map: column yc, rows 2 yp (+1) (+32)
+    // fold of column block bb (TMEM buffer bb & 1) and R = gamma - X0 + S for it
+    auto finish = [&](int bb) {
+      const int* ce = cole2 + (bb & 1) * kCB;
+      // gamma (hi, lo) of this thread's four R entries, loaded ahead of the fold
+      float2 ghv[4], glv[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int row = yp + 16 * k, j = bb * kCB + yc;
+        const bool in = (row < n && j < n);
+        ghv[k] = in ? Gh[row * n + j] : make_float2(0.f, 0.f);
+        glv[k] = in ? Gl[row * n + j] : make_float2(0.f, 0.f);
+      }
+      // warp w reads lane quadrant q = w % 4 (gamma row i; Zr or Zi) and column
+      // half h = w / 4 (Yr or Yi) of the 8 accumulators.  Weights 2^-7d for
+      // d = 4..7 are summed in FP32 (Horner; their sum is < 2^-4.9 of the
+      // d = 0 scale, rounding error < 2^-27 of it), d = 0..3 in double-float.
+      const int qd = warp & 3, h = warp >> 2;
+      const int i = ((qd & 1) << 5) + lane;
+      const bool zi = qd >= 2;
+      const unsigned tl = umma->tmem + ((unsigned)(32 * qd) << 16) + (unsigned)(256 * (bb & 1) + 16 * h);
+      float fh[kCB], fl[kCB];
+      {
+        float v[kCB];
+        tmem_ld16(tl + 32 * 7, fh);
+#pragma unroll
+        for (int d = 6; d >= 4; --d) {
+          tmem_ld16(tl + 32 * d, v);
+#pragma unroll
+          for (int c2 = 0; c2 < kCB; ++c2) fh[c2] = fmaf(fh[c2], 0.0078125f, v[c2]);
+        }
+#pragma unroll
+        for (int c2 = 0; c2 < kCB; ++c2) {
+          fh[c2] *= 3.7252902984619141e-09f;      // 2^-28
+          fl[c2] = 0.f;
+        }
+#pragma unroll
+        for (int d = 3; d >= 0; --d) {
+          tmem_ld16(tl + 32 * d, v);
+          const float sc = __int_as_float((127 - 7 * d) << 23);     // 2^-7d
+#pragma unroll
+          for (int c2 = 0; c2 < kCB; ++c2) dd_add(fh[c2], fl[c2], v[c2] * sc);
+        }
+      }
+      tc05_fence_before();
+      // scale by 2^(e_i + e_j - 14); the Zi rows' parts go to E first (ZiYi
+      // negated: it enters the real part with a minus), then the Zr rows add
+      // theirs: E[0] = S real, E[1] = S imaginary, row stride kCB + 1
+      const int ei = rowe[i];
+#pragma unroll
+      for (int c2 = 0; c2 < kCB; ++c2) {
+        const int ej = ce[c2];
+        const float w = (ei > -1000 && ej > -1000) ? pow2f(ei + ej - 14) : 0.f;
+        fh[c2] *= w;
+        fl[c2] *= w;
+      }
+      if (zi) {
+        const float sg = h ? -1.f : 1.f;
+        float2* Eo = E + (1 - h) * np * (kCB + 1) + i * (kCB + 1);   // ZiYr -> imaginary, ZiYi -> real
+#pragma unroll
+        for (int c2 = 0; c2 < kCB; ++c2) Eo[c2] = make_float2(sg * fh[c2], sg * fl[c2]);
+      }
+      __syncthreads();
+      if (!zi) {
+        float2* Eo = E + h * np * (kCB + 1) + i * (kCB + 1);         // ZrYr -> real, ZrYi -> imaginary
+#pragma unroll
+        for (int c2 = 0; c2 < kCB; ++c2) {
+          const float2 o = Eo[c2];
+          float sh, se;
+          two_sum(fh[c2], o.x, sh, se);
+          Eo[c2] = make_float2(sh, se + (fl[c2] + o.y));
+        }
+      }
+      __syncthreads();
+      // R = gamma - X0 + S in double-float (it cancels to ~u32 |gamma|)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int row = yp + 16 * k, j = bb * kCB + yc;
+        const float2 x = X0s[row * np + j];
+        const float2 sr = E[row * (kCB + 1) + yc], si = E[np * (kCB + 1) + row * (kCB + 1) + yc];
+        float re = ghv[k].x, rl = glv[k].x, im = ghv[k].y, il = glv[k].y;
+        df_add(re, rl, -x.x);
+        df_add(re, rl, sr.x);
+        df_add(im, il, -x.y);
+        df_add(im, il, si.x);
+        X0s[row * np + j] = make_float2(re + (rl + sr.y), im + (il + si.y));   // R replaces X0
+      }
+    };
+    for (int b = 0; b < np / kCB; ++b) {
+      __syncthreads();
+      // Y = chi~ o X0 in double-float for rows 2 yp, 2 yp + 1, 2 yp + 32, 2 yp + 33
+      // of column yc; its column exponent e (|Y| < 2^e, -1000 for a zero
+      // column): the thread's max, the warp's two row groups, the 8 warps
+      float y[4][4];
+      float m = 0.f;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int l = 2 * yp + (k & 1) + 32 * (k >> 1);
+        const float2 x = X0s[l * np + b * kCB + yc];
+        y[k][0] = y[k][1] = y[k][2] = y[k][3] = 0.f;
+        cdf_fma(y[k][0], y[k][1], y[k][2], y[k][3], chih[l], chil[l], x, make_float2(0.f, 0.f));
+        m = fmaxf(m, fmaxf(fabsf(y[k][0]), fabsf(y[k][2])));
+      }
+      m *= 1.0001f;
+      int e = m > 0.f ? exp_bound_f32(m) : -1000;
+      e = max(e, __shfl_xor_sync(0xffffffffu, e, 16));
+      if (lane < kCB) cw[warp * kCB + lane] = e;
+      __syncthreads();
+      int ecol = cw[yc];
+#pragma unroll
+      for (int w2 = 1; w2 < 8; ++w2) ecol = max(ecol, cw[w2 * kCB + yc]);
+      if (t < kCB) cole2[(b & 1) * kCB + t] = ecol;
+      // digits of the two row pairs, two rows per 32-bit word
+#pragma unroll
+      for (int pr = 0; pr < 2; ++pr) {
+        unsigned w0[kSlices], w1[kSlices], v0[kSlices], v1[kSlices];
+        if (ecol > -1000) {
+          digits_pair(y[2 * pr][0], y[2 * pr][1], ecol, w0);
+          digits_pair(y[2 * pr][2], y[2 * pr][3], ecol, w1);
+          digits_pair(y[2 * pr + 1][0], y[2 * pr + 1][1], ecol, v0);
+          digits_pair(y[2 * pr + 1][2], y[2 * pr + 1][3], ecol, v1);
+        } else {
+#pragma unroll
+          for (int s2 = 0; s2 < kSlices; ++s2) w0[s2] = w1[s2] = v0[s2] = v1[s2] = 0u;
+        }
+        const int wo = swz(yc, 2 * yp + 32 * pr) >> 1;
+#pragma unroll
+        for (int s2 = 0; s2 < kSlices; ++s2) {
+          xw[(s2 * 2 + 0) * kCB * 32 + wo] = w0[s2] | (v0[s2] << 16);
+          xw[(s2 * 2 + 1) * kCB * 32 + wo] = w1[s2] | (v1[s2] << 16);
+        }
+      }
+      fence_async_smem();
+      __syncthreads();
+      if (t == 0) {
+        tc05_fence_after();
+        const unsigned za = smem_u32(zs), xa = smem_u32(xs);
+        const unsigned dt = umma->tmem + (unsigned)(256 * (b & 1));
+#pragma unroll 1
+        for (int sa = 0; sa < kSlices; ++sa) {
+          const unsigned idesc = umma_idesc_bf16(128, 32 * (kSlices - sa));
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks)
+            umma_bf16(dt + 32 * sa, umma_desc_sw128(za + sa * (2 * np * 128) + 32 * ks),
+                      umma_desc_sw128(xa + 32 * ks), idesc, (sa > 0 || ks > 0) ? 1u : 0u);
+        }
+        umma_commit(umma->mbar);
+      }
+      if (b > 0) finish(b - 1);
+      if (!mbar_wait(umma->mbar, umma->phase) && t == 0) atomicOr(flags, kFlagTcTimeout);
+      umma->phase ^= 1;
+      tc05_fence_after();
+    }
+    finish(np / kCB - 1);
+    __syncthreads();
+  } else if constexpr (use_tc_residual(NP)) {
     // ---- residual R = gamma - X0 + gamma Y on the tensor cores, Y = diag(chi~) X0 ----
     // gamma's digits (cut once per input upload: 8 signed base-128 digits
     // relative to per-row powers of two) are in zs / rowe; Y is formed in
@@ -820,98 +1000,6 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
           xw[(s2 * 2 + 1) * kCB * 32 + wo] = w1[s2] | (v1[s2] << 16);
         }
       }
-      if constexpr (use_umma_residual(NP)) {
-        // ---- tcgen05: for each gamma slice sa one MMA per K step of 16,
-        // A = [Zr; Zi] of slice sa (M = 128), B = the Y slices 0 .. 7 - sa
-        // stacked along N (32 rows each: Yr then Yi columns), D at TMEM column
-        // 32 sa: Y slice sb lands in accumulator d = sa + sb (weight 2^-7(d+2)),
-        // columns 32 d .. 32 d + 31 = [Yr | Yi]; lanes 0-63 hold the Zr rows,
-        // 64-127 the Zi rows.  Each accumulator is exact (<= 8 pairs x 64 x 127^2 < 2^23).
-        fence_async_smem();
-        __syncthreads();
-        if (t == 0) {
-          tc05_fence_after();
-          const unsigned za = smem_u32(zs), xa = smem_u32(xs);
-#pragma unroll 1
-          for (int sa = 0; sa < kSlices; ++sa) {
-            const unsigned idesc = umma_idesc_bf16(128, 32 * (kSlices - sa));
-#pragma unroll
-            for (int ks = 0; ks < 4; ++ks)
-              umma_bf16(umma->tmem + 32 * sa, umma_desc_sw128(za + sa * (2 * np * 128) + 32 * ks),
-                        umma_desc_sw128(xa + 32 * ks), idesc, (sa > 0 || ks > 0) ? 1u : 0u);
-          }
-          umma_commit(umma->mbar);
-        }
-        if (!mbar_wait(umma->mbar, umma->phase) && t == 0) atomicOr(flags, kFlagTcTimeout);
-        umma->phase ^= 1;
-        tc05_fence_after();
-        // fold: warp w reads lane quadrant q = w % 4 (gamma row i, Zr or Zi) and
-        // column half h = w / 4 (Yr or Yi) of the 8 accumulators, smallest
-        // weight first, into double-float
-        const int qd = warp & 3, h = warp >> 2;
-        const int i = ((qd & 1) << 5) + lane;
-        const bool zi = qd >= 2;
-        float fh[kCB], fl[kCB];
-#pragma unroll
-        for (int c2 = 0; c2 < kCB; ++c2) fh[c2] = fl[c2] = 0.f;
-        const unsigned tl = umma->tmem + ((unsigned)(32 * qd) << 16) + (unsigned)(16 * h);
-#pragma unroll
-        for (int d = kSlices - 1; d >= 0; --d) {
-          float v[kCB];
-          tmem_ld16(tl + 32 * d, v);
-          const float sc = __int_as_float((127 - 7 * d) << 23);     // 2^-7d
-#pragma unroll
-          for (int c2 = 0; c2 < kCB; ++c2) dd_add(fh[c2], fl[c2], v[c2] * sc);
-        }
-        tc05_fence_before();
-        // scale by 2^(e_i + e_j - 14); the Zi rows' parts go to E first (ZiYi
-        // negated: it enters the real part with a minus), then the Zr rows add
-        // theirs: E[0] = S real, E[1] = S imaginary, row stride kCB + 1
-        float2* E = reinterpret_cast<float2*>(xs);
-        const int ei = rowe[i];
-#pragma unroll
-        for (int c2 = 0; c2 < kCB; ++c2) {
-          const int ej = cole[c2];
-          const float w = (ei > -1000 && ej > -1000) ? pow2f(ei + ej - 14) : 0.f;
-          fh[c2] *= w;
-          fl[c2] *= w;
-        }
-        if (zi) {
-          const float sg = h ? -1.f : 1.f;
-          float2* Eo = E + (1 - h) * np * (kCB + 1) + i * (kCB + 1);   // ZiYr -> imaginary, ZiYi -> real
-#pragma unroll
-          for (int c2 = 0; c2 < kCB; ++c2) Eo[c2] = make_float2(sg * fh[c2], sg * fl[c2]);
-        }
-        __syncthreads();
-        if (!zi) {
-          float2* Eo = E + h * np * (kCB + 1) + i * (kCB + 1);         // ZrYr -> real, ZrYi -> imaginary
-#pragma unroll
-          for (int c2 = 0; c2 < kCB; ++c2) {
-            const float2 o = Eo[c2];
-            float sh, se;
-            two_sum(fh[c2], o.x, sh, se);
-            Eo[c2] = make_float2(sh, se + (fl[c2] + o.y));
-          }
-        }
-        __syncthreads();
-        // R = gamma - X0 + S in double-float (it cancels to ~u32 |gamma|);
-        // consecutive threads take consecutive columns of a row
-        for (int idx = t; idx < np * kCB; idx += nthr) {
-          const int row = idx / kCB, col = idx - row * kCB;
-          const int j = b * kCB + col;
-          const bool in = (row < n && j < n);
-          const float2 gh = in ? Gh[row * n + j] : make_float2(0.f, 0.f);
-          const float2 gl = in ? Gl[row * n + j] : make_float2(0.f, 0.f);
-          const float2 x = X0s[row * np + j];
-          const float2 sr = E[row * (kCB + 1) + col], si = E[np * (kCB + 1) + row * (kCB + 1) + col];
-          float re = gh.x, rl = gl.x, im = gh.y, il = gl.y;
-          df_add(re, rl, -x.x);
-          df_add(re, rl, sr.x);
-          df_add(im, il, -x.y);
-          df_add(im, il, si.x);
-          X0s[row * np + j] = make_float2(re + (rl + sr.y), im + (il + si.y));   // R replaces X0
-        }
-      } else {
       __syncthreads();
       for (int tile = warp; tile < tiles; tile += nwarp) {
         const int r16 = (tile / (kCB / 8)) * 16, c8 = (tile % (kCB / 8)) * 8;
@@ -982,7 +1070,6 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
           df_add(im, il, hm[e]);
           X0s[row * np + j] = make_float2(re + (rl + lr[e]), im + (il + lm[e]));   // R replaces X0
         }
-      }
       }
     }
     __syncthreads();
