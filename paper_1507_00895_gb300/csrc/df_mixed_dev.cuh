@@ -535,15 +535,20 @@ __host__ __device__ constexpr int tc_work_bytes(int np) {
          (use_umma_residual(np) ? 4 * kCB + 2 * np * (kCB + 1) * 8 + 4 * 8 * kCB : 0);
 }
 
+// row stride of X0 / R in shared memory (float2): np + 1 spreads a column
+// read (16 rows, one column) over 16 banks
+__host__ __device__ constexpr int x0_ld(int np) { return np + 1; }
+
 __host__ __device__ inline MixedSmem mixed_layout(int np) {
   MixedSmem L;
   int o = 0;
-  L.x0 = o;   o += np * np;        // X0 (logical rows), also the row broadcast of the solves
+  L.x0 = o;   o += np * x0_ld(np); // X0 (logical rows), then R in its place
   L.chih = o; o += np;
   L.chil = o; o += np;
   L.invu = o; o += np;
   L.x0d = o;  o += np;             // diag X0 (FP32)
   L.chi64 = o; o += 2 * np;        // chi~ in FP64 (double2 = two float2 slots)
+  if (use_umma_residual(np)) o = (o + 127) & ~127;   // tcgen05 operand tiles: 1024-byte aligned
   L.work = o;                      // residual work area (one of the two layouts below)
   // SIMT residual: gamma tiles and Y = chi o X0 as double-float
   L.gt_h = o;
@@ -603,6 +608,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
                                                  Tc05* umma) {
   const int n = dm.n_w, N = dm.N, nb = dm.nb;
   constexpr int np = NP, P = NP / kTile;
+  constexpr int ld = x0_ld(NP);
   float2* X0s = sp.X0s;
   float2* chih = sp.chih;
   float2* chil = sp.chil;
@@ -760,11 +766,11 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
   for (int ii = 0; ii < kTile; ++ii) {
     if (rowpos[ii] >= 0) {
 #pragma unroll
-      for (int jj = 0; jj < kTile; ++jj) X0s[rowpos[ii] * np + tc + P * jj] = A[ii][kTile + jj];
+      for (int jj = 0; jj < kTile; ++jj) X0s[rowpos[ii] * ld + tc + P * jj] = A[ii][kTile + jj];
     }
   }
   __syncthreads();
-  for (int j = t; j < np; j += blockDim.x) x0d[j] = X0s[j * np + j];
+  for (int j = t; j < np; j += blockDim.x) x0d[j] = X0s[j * ld + j];
   if constexpr (use_umma_residual(NP)) {
     // ---- residual R = gamma - X0 + gamma Y with tcgen05, Y = diag(chi~) X0 ----
     // gamma's digits (8 signed base-128 digits relative to per-row powers of
@@ -865,14 +871,14 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const int row = yp + 16 * k, j = bb * kCB + yc;
-        const float2 x = X0s[row * np + j];
+        const float2 x = X0s[row * ld + j];
         const float2 sr = E[row * (kCB + 1) + yc], si = E[np * (kCB + 1) + row * (kCB + 1) + yc];
         float re = ghv[k].x, rl = glv[k].x, im = ghv[k].y, il = glv[k].y;
         df_add(re, rl, -x.x);
         df_add(re, rl, sr.x);
         df_add(im, il, -x.y);
         df_add(im, il, si.x);
-        X0s[row * np + j] = make_float2(re + (rl + sr.y), im + (il + si.y));   // R replaces X0
+        X0s[row * ld + j] = make_float2(re + (rl + sr.y), im + (il + si.y));   // R replaces X0
       }
     };
     for (int b = 0; b < np / kCB; ++b) {
@@ -885,7 +891,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const int l = 2 * yp + (k & 1) + 32 * (k >> 1);
-        const float2 x = X0s[l * np + b * kCB + yc];
+        const float2 x = X0s[l * ld + b * kCB + yc];
         y[k][0] = y[k][1] = y[k][2] = y[k][3] = 0.f;
         cdf_fma(y[k][0], y[k][1], y[k][2], y[k][3], chih[l], chil[l], x, make_float2(0.f, 0.f));
         m = fmaxf(m, fmaxf(fabsf(y[k][0]), fabsf(y[k][2])));
@@ -966,7 +972,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
       // lanes take consecutive columns of a row of X0 (no bank conflicts)
       for (int idx = t; idx < kCB * np; idx += nthr) {
         const int l = idx / kCB, c2 = idx - l * kCB;
-        const float2 x = X0s[l * np + b * kCB + c2];
+        const float2 x = X0s[l * ld + b * kCB + c2];
         float yr = 0.f, ylr = 0.f, yi = 0.f, yli = 0.f;
         cdf_fma(yr, ylr, yi, yli, chih[l], chil[l], x, make_float2(0.f, 0.f));
         const float m = fmaxf(fabsf(yr), fabsf(yi)) * 1.0001f;
@@ -980,7 +986,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
         const int e = cole[c2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const float2 x = X0s[(l + h) * np + b * kCB + c2];
+          const float2 x = X0s[(l + h) * ld + b * kCB + c2];
           float yr = 0.f, ylr = 0.f, yi = 0.f, yli = 0.f;
           cdf_fma(yr, ylr, yi, yli, chih[l + h], chil[l + h], x, make_float2(0.f, 0.f));
           unsigned* dr = h ? v0 : w0;
@@ -1062,13 +1068,13 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
           const bool in = (row < n && j < n);
           const float2 gh = in ? Gh[row * n + j] : make_float2(0.f, 0.f);
           const float2 gl = in ? Gl[row * n + j] : make_float2(0.f, 0.f);
-          const float2 x = X0s[row * np + j];
+          const float2 x = X0s[row * ld + j];
           float re = gh.x, rl = gl.x, im = gh.y, il = gl.y;
           df_add(re, rl, -x.x);
           df_add(re, rl, hr[e]);
           df_add(im, il, -x.y);
           df_add(im, il, hm[e]);
-          X0s[row * np + j] = make_float2(re + (rl + lr[e]), im + (il + lm[e]));   // R replaces X0
+          X0s[row * ld + j] = make_float2(re + (rl + lr[e]), im + (il + lm[e]));   // R replaces X0
         }
       }
     }
@@ -1078,7 +1084,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
     for (int idx = t; idx < np * np; idx += blockDim.x) {
       const int l = idx / np;
       const float2 xh = chih[l], xl = chil[l];
-      const float2 x = X0s[idx];
+      const float2 x = X0s[l * ld + (idx - l * np)];
       float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
       df_fma(rh, rl, xh.x, x.x);
       df_fma(rh, rl, -xh.y, x.y);
@@ -1153,7 +1159,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
         for (int jj = 0; jj < kTile; ++jj) {
           const int col = tc + P * jj;
           double2 g = (r < n && col < n) ? gam[mat + (size_t)r * n + col] : mk(0.0, 0.0);
-          const float2 x = X0s[r * np + col];
+          const float2 x = X0s[r * ld + col];
           const double re = g.x - (double)x.x + (((double)acc[i2][jj][0] + (double)acc[i2][jj][1]) + (double)acc[i2][jj][4]);
           const double im = g.y - (double)x.y + (((double)acc[i2][jj][2] + (double)acc[i2][jj][3]) + (double)acc[i2][jj][5]);
           A[ii][kTile + jj] = make_float2((float)re, (float)im);
@@ -1165,9 +1171,28 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
 #pragma unroll
     for (int ii = 0; ii < kTile; ++ii)
 #pragma unroll
-      for (int jj = 0; jj < kTile; ++jj) X0s[(tr + P * ii) * np + tc + P * jj] = A[ii][kTile + jj];
+      for (int jj = 0; jj < kTile; ++jj) X0s[(tr + P * ii) * ld + tc + P * jj] = A[ii][kTile + jj];
     __syncthreads();
   }
+
+  // gamma o gamma^T (hi, lo) of this thread's first pass of the Gamma^(2)
+  // sums below, loaded now so that their latency overlaps the diag correction
+  constexpr int per_j = (P * P >= 32) ? 4 : 1;      // threads per output frequency j
+  constexpr int nxj = (np + per_j - 1) / per_j;     // terms per thread
+  const float2* GGh = gg_hi + mat;
+  const float2* GGl = gg_lo + mat;
+  float2 pgh[nxj], pgl[nxj];
+  auto load_gg = [&](int idx) {
+    const int j = idx / per_j, part = idx % per_j;
+#pragma unroll
+    for (int k = 0; k < nxj; ++k) {
+      const int x = part + per_j * k;
+      const bool ok = j < n && x < n;
+      pgh[k] = ok ? GGh[j * n + x] : make_float2(0.f, 0.f);
+      pgl[k] = ok ? GGl[j * n + x] : make_float2(0.f, 0.f);
+    }
+  };
+  load_gg(t);
 
   // ---- diag E = diag(D^-1 R): the sweep's D part W holds D^-1 permuted,
   // D^-1[j][m] = W[piv[j]][ipiv[m]], so E_jj = sum_c W[r][c] R[piv[c]][j] with
@@ -1182,7 +1207,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
     float ex = 0.f, ey = 0.f;
 #pragma unroll
     for (int jj = 0; jj < kTile; ++jj) {
-      const float2 rv = X0s[pc[jj] * np + j];
+      const float2 rv = X0s[pc[jj] * ld + j];
       const float2 w = A[ii][jj];
       ex = fmaf(w.x, rv.x, fmaf(-w.y, rv.y, ex));
       ey = fmaf(w.x, rv.y, fmaf(w.y, rv.x, ey));
@@ -1196,19 +1221,18 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
   __syncthreads();
 
   // ---- diag Gamma = diag X0 + diag E (FP64), Gamma^(2), Eq. sd bracket ----
-  // Gamma^(2)_jj = sum_x (gamma_jx gamma_xj) chi~_x in double-float
-  const float2* GGh = gg_hi + mat;
-  const float2* GGl = gg_lo + mat;
-  // four threads per output frequency j (consecutive lanes, shuffle-reduced)
-  // when the block has whole warps; one thread per j otherwise
-  constexpr int per_j = (P * P >= 32) ? 4 : 1;
+  // Gamma^(2)_jj = sum_x (gamma_jx gamma_xj) chi~_x in double-float; four
+  // threads per output frequency j (consecutive lanes, shuffle-reduced) when
+  // the block has whole warps, one thread per j otherwise
   for (int base = 0; base < per_j * np; base += blockDim.x) {
     const int idx = base + t;
     const int j = idx / per_j, part = idx % per_j;
+    if (base > 0) load_gg(idx);
     float sr = 0.f, lr = 0.f, si = 0.f, li = 0.f;
-    if (j < n) {
-      for (int x = part; x < n; x += per_j)
-        cdf_fma(sr, lr, si, li, GGh[j * n + x], GGl[j * n + x], chih[x], chil[x]);
+#pragma unroll
+    for (int k = 0; k < nxj; ++k) {
+      const int x = part + per_j * k;
+      if (x < n) cdf_fma(sr, lr, si, li, pgh[k], pgl[k], chih[x], chil[x]);
     }
     if (per_j == 4) {
 #pragma unroll
