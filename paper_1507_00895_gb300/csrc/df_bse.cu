@@ -128,7 +128,11 @@ chi_ladder_kernel(Dims dm, const double2* __restrict__ gam, const double2* __res
 // from that vector with FP64 vectors and Rayleigh quotients, the products
 // gamma (chi~ o v) in double-float FP32 (gamma staged as (hi, lo) pairs;
 // ~2^-46 relative, far below the 1e-12 stopping tolerance).  The reported
-// value and its converged flag are those of the polish.  One CTA handles
+// value and its converged flag are those of the polish.  The polish runs only
+// for the systems whose FP32 phase settled: one that still changes by more
+// than 2e-6 per step after 64 steps converges at a geometric rate above 0.81,
+// so 24 more steps cannot reach 1e-12; it reports its FP32 estimate, flagged
+// not converged (a block whose systems all are skips the polish).  One CTA handles
 // kEigQ systems that share (channel, W); each thread owns (row, system)
 // pairs of y = A v.
 // ---------------------------------------------------------------------------
@@ -179,6 +183,7 @@ lambda_kernel(Dims dm, int ch0, int a0, int na, int lo_in_smem, double tol, cons
   __shared__ double nrm[kEigQ];
   __shared__ float nrm32[kEigQ];
   __shared__ int done[kEigQ];
+  __shared__ int conv[kEigQ];            // FP32 phase converged (the polish runs for these only)
   const int qtiles = (N + kEigQ - 1) / kEigQ;
   const int tile = blockIdx.x % qtiles;
   const int a = a0 + (blockIdx.x / qtiles) % na;
@@ -234,11 +239,18 @@ lambda_kernel(Dims dm, int ch0, int a0, int na, int lo_in_smem, double tol, cons
   }
   // ---- FP64 polish from the FP32 vector ----
   for (int idx = tid; idx < n * kEigQ; idx += blockDim.x) v[idx] = mk((double)v32[idx].x, (double)v32[idx].y);
-  if (tid < kEigQ) done[tid] = (tid < nq) ? 0 : 1;
+  // a system whose FP32 phase did not settle keeps its FP32 estimate (not converged)
+  if (tid < kEigQ) {
+    conv[tid] = tid < nq && done[tid];
+    done[tid] = conv[tid] ? 0 : 1;
+  }
   __syncthreads();
+  int any = 0;
+#pragma unroll
+  for (int t = 0; t < kEigQ; ++t) any |= conv[t];
   float2* wh = x32;                        // chi~ o v as (hi, lo) pairs; x32, y32 are free now
   float2* wl = y32;
-  for (int it = 0; it < kEigIter64; ++it) {
+  for (int it = 0; it < (any ? kEigIter64 : 0); ++it) {
     for (int idx = tid; idx < n * kEigQ; idx += blockDim.x) {
       const double2 w = cmul(xq[idx], v[idx]);
       const float hx = (float)w.x, hy = (float)w.y;
@@ -279,9 +291,310 @@ lambda_kernel(Dims dm, int ch0, int a0, int na, int lo_in_smem, double tol, cons
   }
   if (tid < nq) {
     const size_t o = ((size_t)c * nb + a) * N + q0 + tid;
-    lam[o] = lam_new[tid];
-    ok[o] = done[tid];
-    if (cabs2(lam_new[tid]) >= 1.0) atomicOr(flags, 2);
+    const double2 l = conv[tid] ? lam_new[tid] : mk((double)l32_new[tid].x, (double)l32_new[tid].y);
+    lam[o] = l;
+    ok[o] = conv[tid] && done[tid];
+    if (cabs2(l) >= 1.0) atomicOr(flags, 2);
+  }
+}
+
+// The same power iteration and polish for n_w <= 64 with gamma in registers:
+// thread (i, jb) = (tid / 4, tid % 4) holds row i, columns 16 jb .. 16 jb + 15
+// of gamma's hi parts (the lo parts, polish only, in shared memory as
+// [jb][k][i]), reads u = chi~ o v (all kEigQ systems) as broadcast 16-byte
+// loads, and the four column blocks of a row (consecutive lanes) are summed
+// by shuffles.  Thread (i, jb) owns systems 2 jb, 2 jb + 1 of row i.  The
+// polish keeps its vectors in double-float (FP32 pairs: the FP64 pipe is
+// slow); only the per-system scalars (Rayleigh quotient, norm, stopping test)
+// are FP64, in 8 threads.  Same stopping rules and outputs as lambda_kernel.
+constexpr int kEigRegN = 64;                      // largest n_w of this kernel
+constexpr int kEigUStride = 16 * kEigQ + 2;       // u block stride (float2): the 4 column blocks in distinct banks
+constexpr int kEigLoStride = 16 * kEigRegN + 8;   // gamma-lo block stride (float2): a warp's 4 blocks in 2 wavefronts
+
+// y = gamma u for the kEigQ systems (FP32, this thread's 16 columns), then
+// summed over the 4 column blocks of the row (consecutive lanes)
+__device__ __forceinline__ void eig_gemv32(const float2 (&gh)[16], const float2* __restrict__ ub2,
+                                           float2 (&y)[kEigQ]) {
+#pragma unroll
+  for (int t = 0; t < kEigQ; ++t) y[t] = make_float2(0.f, 0.f);
+  const float4* ub = reinterpret_cast<const float4*>(ub2);
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+#pragma unroll
+    for (int tp = 0; tp < kEigQ / 2; ++tp) {
+      const float4 q = ub[(k * kEigQ) / 2 + tp];
+      y[2 * tp] = cfma(gh[k], make_float2(q.x, q.y), y[2 * tp]);
+      y[2 * tp + 1] = cfma(gh[k], make_float2(q.z, q.w), y[2 * tp + 1]);
+    }
+  }
+#pragma unroll
+  for (int o = 1; o < 4; o <<= 1)
+#pragma unroll
+    for (int t = 0; t < kEigQ; ++t) {
+      y[t].x += __shfl_xor_sync(0xffffffffu, y[t].x, o);
+      y[t].y += __shfl_xor_sync(0xffffffffu, y[t].y, o);
+    }
+}
+
+template <typename T, int M>
+__device__ __forceinline__ T pick2(const T (&a)[M], int jb, int k) {   // a[2 jb + k], jb < 4
+  T r = a[k];
+#pragma unroll
+  for (int q = 1; q < 4; ++q)
+    if (q == jb) r = a[2 * q + k];
+  return r;
+}
+
+// (hi, lo) * s for a double-float real s = (sh, sl): leading product exact
+__device__ __forceinline__ void df_scale(float& hi, float& lo, float sh, float sl) {
+  const float p = hi * sh;
+  const float e = fmaf(hi, sh, -p);
+  const float l = fmaf(hi, sl, fmaf(lo, sh, e));
+  hi = p + l;
+  lo = l - (hi - p);
+}
+
+__global__ void __launch_bounds__(256, 2)
+lambda_reg_kernel(Dims dm, int ch0, int a0, int na, double tol, const double2* __restrict__ gam,
+                  const double2* __restrict__ chi, double2* __restrict__ lam, int* __restrict__ ok,
+                  int* __restrict__ flags) {
+  static_assert(kEigQ == 8, "two systems per thread of a row");
+  extern __shared__ float2 glo[];                // [4][16][kEigRegN], block stride kEigLoStride
+  __shared__ __align__(16) float2 uh[4 * kEigUStride], ul[4 * kEigUStride];
+  __shared__ float2 xh[kEigRegN][kEigQ], xl[kEigRegN][kEigQ];   // chi~ as (hi, lo) pairs
+  __shared__ float redf[8][kEigQ][6];            // per warp: Rayleigh quotient (re, im) and |y|^2 (df pairs)
+  __shared__ float2 scal[kEigQ];                 // per system: 1 / |y| as a double-float (hi, lo)
+  __shared__ double2 lold_s[kEigQ];              // previous (current, at the end) Rayleigh quotients
+  __shared__ int done_s[kEigQ];
+  __shared__ int conv_s[kEigQ];                  // FP32 phase converged (the polish runs for these only)
+  const int n = dm.n_w, N = dm.N, nb = dm.nb;
+  const int qtiles = (N + kEigQ - 1) / kEigQ;
+  const int tile = blockIdx.x % qtiles;
+  const int a = a0 + (blockIdx.x / qtiles) % na;
+  const int c = ch0 + blockIdx.x / (qtiles * na);
+  const int q0 = tile * kEigQ;
+  const int nq = min(kEigQ, N - q0);
+  const double2* Gg = gam + ((size_t)c * nb + a) * n * n;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int i = tid >> 2, jb = tid & 3;
+  const int uo = (i >> 4) * kEigUStride + (i & 15) * kEigQ + 2 * jb;   // this thread's u slot (row i, t = 2 jb)
+  float2 gh[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int j = 16 * jb + k;
+    const double2 g = (i < n && j < n) ? Gg[(size_t)i * n + j] : mk(0.0, 0.0);
+    gh[k] = make_float2((float)g.x, (float)g.y);
+  }
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int t = 2 * jb + k;
+    const double2 x = (i < n && t < nq) ? chi[((size_t)a * n + i) * N + q0 + t] : mk(0.0, 0.0);
+    const float2 h = make_float2((float)x.x, (float)x.y);
+    xh[i][t] = h;
+    xl[i][t] = make_float2((float)(x.x - (double)h.x), (float)(x.y - (double)h.y));
+  }
+  if (tid < kEigQ) {
+    done_s[tid] = tid < nq ? 0 : 1;
+    lold_s[tid] = mk(0.0, 0.0);
+  }
+
+  // ---- FP32 phase ----
+  float2 v32[2];
+  const float v0 = i < n ? rsqrtf((float)n) : 0.f;
+  v32[0] = v32[1] = make_float2(v0, 0.f);
+  for (int it = 0; it < kEigIter32; ++it) {
+    {
+      const float2 u0 = cmul(xh[i][2 * jb], v32[0]), u1 = cmul(xh[i][2 * jb + 1], v32[1]);
+      *reinterpret_cast<float4*>(uh + uo) = make_float4(u0.x, u0.y, u1.x, u1.y);
+    }
+    __syncthreads();
+    float2 y[kEigQ];
+    eig_gemv32(gh, uh + jb * kEigUStride, y);
+    float2 yo[2];
+    float pt[2][3];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      yo[k] = pick2(y, jb, k);
+      const float2 rq = cmul(cconj(v32[k]), yo[k]);
+      pt[k][0] = rq.x;
+      pt[k][1] = rq.y;
+      pt[k][2] = cabs2(yo[k]);
+#pragma unroll
+      for (int m = 0; m < 3; ++m)
+#pragma unroll
+        for (int o = 4; o < 32; o <<= 1) pt[k][m] += __shfl_xor_sync(0xffffffffu, pt[k][m], o);
+    }
+    if (lane < 4) {
+#pragma unroll
+      for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int m = 0; m < 3; ++m) redf[warp][2 * jb + k][m] = pt[k][m];
+    }
+    __syncthreads();
+    if (tid < kEigQ) {
+      float r0 = 0.f, r1 = 0.f, yy = 0.f;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) {
+        r0 += redf[w][tid][0];
+        r1 += redf[w][tid][1];
+        yy += redf[w][tid][2];
+      }
+      scal[tid] = make_float2(yy > 0.f ? 1.f / sqrtf(yy) : 0.f, 0.f);
+      const float2 ln = make_float2(r0, r1);
+      const float2 lo = make_float2((float)lold_s[tid].x, (float)lold_s[tid].y);
+      if (!done_s[tid]) {
+        const float2 d = ln - lo;
+        if (sqrtf(cabs2(d)) <= 2e-6f * sqrtf(cabs2(ln))) done_s[tid] = 1;
+      }
+      lold_s[tid] = mk((double)ln.x, (double)ln.y);
+    }
+    __syncthreads();
+    int all = 1;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) v32[k] = cscale(yo[k], scal[2 * jb + k].x);
+#pragma unroll
+    for (int t = 0; t < kEigQ; ++t) all &= done_s[t];
+    if (all) break;
+  }
+  // ---- double-float polish from the FP32 vector ----
+  float2* glt = glo + jb * kEigLoStride + i;     // this thread's lo parts, stride kEigRegN
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    const int j = 16 * jb + k;
+    const double2 g = (i < n && j < n) ? Gg[(size_t)i * n + j] : mk(0.0, 0.0);
+    glt[k * kEigRegN] = make_float2((float)(g.x - (double)gh[k].x), (float)(g.y - (double)gh[k].y));
+  }
+  float2 vh[2] = {v32[0], v32[1]}, vl[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+  __syncthreads();
+  // a system whose FP32 phase did not settle keeps its FP32 estimate (not converged)
+  if (tid < kEigQ) {
+    conv_s[tid] = tid < nq && done_s[tid];
+    done_s[tid] = conv_s[tid] ? 0 : 1;
+    if (conv_s[tid]) lold_s[tid] = mk(0.0, 0.0);
+  }
+  __syncthreads();
+  int any = 0;
+#pragma unroll
+  for (int t = 0; t < kEigQ; ++t) any |= conv_s[t];
+  for (int it = 0; it < (any ? kEigIter64 : 0); ++it) {
+    {
+      // w = chi~ o v in double-float
+      float4 wh4, wl4;
+      float* whp = &wh4.x;
+      float* wlp = &wl4.x;
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        float sr = 0.f, lr = 0.f, si = 0.f, li = 0.f;
+        cdf_fma(sr, lr, si, li, xh[i][2 * jb + k], xl[i][2 * jb + k], vh[k], vl[k]);
+        whp[2 * k] = sr + lr;
+        wlp[2 * k] = lr - (whp[2 * k] - sr);
+        whp[2 * k + 1] = si + li;
+        wlp[2 * k + 1] = li - (whp[2 * k + 1] - si);
+      }
+      *reinterpret_cast<float4*>(uh + uo) = wh4;
+      *reinterpret_cast<float4*>(ul + uo) = wl4;
+    }
+    __syncthreads();
+    // y = gamma w in double-float, two systems at a time (register pressure);
+    // systems 2 h2, 2 h2 + 1 belong to the threads with jb == h2
+    float ys[2][4];                                   // this thread's two systems: sr, lr, si, li
+#pragma unroll
+    for (int h2 = 0; h2 < 4; ++h2) {
+      float sr[2], lr[2], si[2], li[2];
+#pragma unroll
+      for (int t = 0; t < 2; ++t) sr[t] = lr[t] = si[t] = li[t] = 0.f;
+      const float4* bh = reinterpret_cast<const float4*>(uh + jb * kEigUStride) + h2;
+      const float4* bl = reinterpret_cast<const float4*>(ul + jb * kEigUStride) + h2;
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const float4 h = bh[(k * kEigQ) / 2], l = bl[(k * kEigQ) / 2];
+        const float2 gk = glt[k * kEigRegN];
+        cdf_fma(sr[0], lr[0], si[0], li[0], gh[k], gk, make_float2(h.x, h.y), make_float2(l.x, l.y));
+        cdf_fma(sr[1], lr[1], si[1], li[1], gh[k], gk, make_float2(h.z, h.w), make_float2(l.z, l.w));
+      }
+#pragma unroll
+      for (int o = 1; o < 4; o <<= 1)
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          const float a1 = __shfl_xor_sync(0xffffffffu, sr[t], o), a2 = __shfl_xor_sync(0xffffffffu, lr[t], o);
+          const float b1 = __shfl_xor_sync(0xffffffffu, si[t], o), b2 = __shfl_xor_sync(0xffffffffu, li[t], o);
+          df_add(sr[t], lr[t], a1);
+          lr[t] += a2;
+          df_add(si[t], li[t], b1);
+          li[t] += b2;
+        }
+      if (jb == h2) {
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          ys[k][0] = sr[k];
+          ys[k][1] = lr[k];
+          ys[k][2] = si[k];
+          ys[k][3] = li[k];
+        }
+      }
+    }
+    // row sums of conj(v) y and |y|^2 in double-float
+    float pt[2][6];
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const float2 yh = make_float2(ys[k][0], ys[k][2]), yl = make_float2(ys[k][1], ys[k][3]);
+      float a1 = 0.f, a2 = 0.f, a3 = 0.f, a4 = 0.f;
+      cdf_fma(a1, a2, a3, a4, cconj(vh[k]), cconj(vl[k]), yh, yl);
+      float b1 = 0.f, b2 = 0.f, b3 = 0.f, b4 = 0.f;
+      cdf_fma(b1, b2, b3, b4, cconj(yh), cconj(yl), yh, yl);
+      pt[k][0] = a1; pt[k][1] = a2; pt[k][2] = a3; pt[k][3] = a4; pt[k][4] = b1; pt[k][5] = b2;
+#pragma unroll
+      for (int o = 4; o < 32; o <<= 1)
+#pragma unroll
+        for (int m = 0; m < 6; m += 2) {
+          const float oh = __shfl_xor_sync(0xffffffffu, pt[k][m], o), ol = __shfl_xor_sync(0xffffffffu, pt[k][m + 1], o);
+          df_add(pt[k][m], pt[k][m + 1], oh);
+          pt[k][m + 1] += ol;
+        }
+    }
+    if (lane < 4) {
+#pragma unroll
+      for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int m = 0; m < 6; ++m) redf[warp][2 * jb + k][m] = pt[k][m];
+    }
+    __syncthreads();
+    if (tid < kEigQ) {
+      double r[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+      for (int w = 0; w < 8; ++w)
+#pragma unroll
+        for (int m = 0; m < 3; ++m) r[m] += (double)redf[w][tid][2 * m] + (double)redf[w][tid][2 * m + 1];
+      const double nrm = r[2] > 0.0 ? 1.0 / sqrt(r[2]) : 0.0;
+      const float nh = (float)nrm;
+      scal[tid] = make_float2(nh, (float)(nrm - (double)nh));
+      const double2 ln = mk(r[0], r[1]);
+      if (!done_s[tid]) {
+        const double2 d = ln - lold_s[tid];
+        if (it > 0 && sqrt(cabs2(d)) <= tol * sqrt(cabs2(ln))) done_s[tid] = 1;
+        lold_s[tid] = ln;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const float2 sc = scal[2 * jb + k];
+      float a1 = ys[k][0], a2 = ys[k][1], a3 = ys[k][2], a4 = ys[k][3];
+      df_scale(a1, a2, sc.x, sc.y);
+      df_scale(a3, a4, sc.x, sc.y);
+      vh[k] = make_float2(a1, a3);
+      vl[k] = make_float2(a2, a4);
+    }
+    int all = 1;
+#pragma unroll
+    for (int t = 0; t < kEigQ; ++t) all &= done_s[t];
+    if (all) break;
+  }
+  if (tid < nq) {
+    const size_t o = ((size_t)c * nb + a) * N + q0 + tid;
+    lam[o] = lold_s[tid];
+    ok[o] = conv_s[tid] && done_s[tid];
+    if (cabs2(lold_s[tid]) >= 1.0) atomicOr(flags, 2);
   }
 }
 
@@ -380,6 +693,18 @@ cudaError_t launch_lambda(df_ctx* c, int channel_mask) {
   const int a0 = (c->opts.eig_mode == 1) ? dm.m_max : 0;
   const int na = (c->opts.eig_mode == 1) ? 1 : dm.nb;
   const int qtiles = (dm.N + kEigQ - 1) / kEigQ;
+  const int ch0 = (channel_mask & 1) ? 0 : 1;
+  const int nch = (channel_mask & 1) && (channel_mask & 2) ? 2 : 1;
+  if (!(channel_mask & 3)) return cudaSuccess;
+  if (dm.n_w <= kEigRegN) {
+    const size_t lsm = sizeof(float2) * 4 * kEigLoStride;
+    cudaError_t e = cudaFuncSetAttribute((const void*)lambda_reg_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)lsm);
+    if (e != cudaSuccess) return e;
+    lambda_reg_kernel<<<nch * na * qtiles, 256, lsm, c->stream>>>(dm, ch0, a0, na, 1e-12, c->gam, c->chi, c->lam,
+                                                                  c->lam_ok, flag_ptr(c));
+    return cudaGetLastError();
+  }
   // gamma's (hi, lo) FP32 pairs in shared memory when they fit (n_w <= 96), the
   // lo parts formed from FP64 gamma on the fly above that
   const size_t base = sizeof(double2) * 3 * dm.n_w * kEigQ + sizeof(float2) * ((size_t)dm.n_w * dm.n_w + 3 * dm.n_w * kEigQ);
@@ -389,9 +714,6 @@ cudaError_t launch_lambda(df_ctx* c, int channel_mask) {
                                        (int)smem);
   if (e != cudaSuccess) return e;
   // both channels in one launch when both are asked for
-  const int ch0 = (channel_mask & 1) ? 0 : 1;
-  const int nch = (channel_mask & 1) && (channel_mask & 2) ? 2 : 1;
-  if (!(channel_mask & 3)) return cudaSuccess;
   lambda_kernel<<<nch * na * qtiles, kEigThreads, smem, c->stream>>>(dm, ch0, a0, na, lo_in_smem, 1e-12, c->gam,
                                                                      c->chi, c->lam, c->lam_ok, flag_ptr(c));
   return cudaGetLastError();
