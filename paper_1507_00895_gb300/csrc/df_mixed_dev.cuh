@@ -474,6 +474,34 @@ __device__ __forceinline__ void digits_pair(float hi, float lo, int e, unsigned*
   for (int s2 = 0; s2 < kSlices; ++s2) d[s2] = bf16_digit((unsigned)((m >> (49 - 7 * s2)) & 0x7Full), sign16);
 }
 
+// The same 8 digits as float bit patterns of the signed digit (+-d, d < 128,
+// exact), for packing two rows' bf16 halves with one byte permute.  Digit s =
+// bits [49 - 7s, 55 - 7s] of |T|, taken from the 32-bit word that holds it.
+__device__ __forceinline__ unsigned bfe7(unsigned x, unsigned pos) {
+  unsigned r;
+  asm("bfe.u32 %0, %1, %2, 7;" : "=r"(r) : "r"(x), "r"(pos));
+  return r;
+}
+__device__ __forceinline__ void digits_pair_f(float hi, float lo, int e, unsigned* f) {
+  const long long T = fixed56(hi, e) + fixed56(lo, e);
+  const unsigned sgn = T < 0 ? 0x80000000u : 0u;
+  const unsigned long long m = (unsigned long long)(T < 0 ? -T : T);
+  const unsigned mh = (unsigned)(m >> 32), ml = (unsigned)m;
+  unsigned d[kSlices];
+  d[0] = bfe7(mh, 17);
+  d[1] = bfe7(mh, 10);
+  d[2] = bfe7(mh, 3);
+  d[3] = __funnelshift_r(ml, mh, 28) & 0x7Fu;
+  d[4] = bfe7(ml, 21);
+  d[5] = bfe7(ml, 14);
+  d[6] = bfe7(ml, 7);
+  d[7] = ml & 0x7Fu;
+#pragma unroll
+  for (int s2 = 0; s2 < kSlices; ++s2) f[s2] = __float_as_uint(__uint_as_float(0x4B000000u | d[s2]) - 8388608.f) | sgn;
+}
+// {bf16 of row l (low half), bf16 of row l + 1 (high half)} from their float patterns
+__device__ __forceinline__ unsigned pack_bf16_hi(unsigned f0, unsigned f1) { return __byte_perm(f0, f1, 0x7632); }
+
 // gamma's digits for the tensor-core residual, `count` n x n matrices (FP64)
 // -> out[count][gdig_bytes(np)]: row i's exponent bound e_i (|gamma_il| < 2^e_i
 // for both parts, -1000 for a zero row) and the 8 digits of each part
@@ -910,10 +938,10 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
       for (int pr = 0; pr < 2; ++pr) {
         unsigned w0[kSlices], w1[kSlices], v0[kSlices], v1[kSlices];
         if (ecol > -1000) {
-          digits_pair(y[2 * pr][0], y[2 * pr][1], ecol, w0);
-          digits_pair(y[2 * pr][2], y[2 * pr][3], ecol, w1);
-          digits_pair(y[2 * pr + 1][0], y[2 * pr + 1][1], ecol, v0);
-          digits_pair(y[2 * pr + 1][2], y[2 * pr + 1][3], ecol, v1);
+          digits_pair_f(y[2 * pr][0], y[2 * pr][1], ecol, w0);
+          digits_pair_f(y[2 * pr][2], y[2 * pr][3], ecol, w1);
+          digits_pair_f(y[2 * pr + 1][0], y[2 * pr + 1][1], ecol, v0);
+          digits_pair_f(y[2 * pr + 1][2], y[2 * pr + 1][3], ecol, v1);
         } else {
 #pragma unroll
           for (int s2 = 0; s2 < kSlices; ++s2) w0[s2] = w1[s2] = v0[s2] = v1[s2] = 0u;
@@ -921,8 +949,8 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
         const int wo = swz(yc, 2 * yp + 32 * pr) >> 1;
 #pragma unroll
         for (int s2 = 0; s2 < kSlices; ++s2) {
-          xw[(s2 * 2 + 0) * kCB * 32 + wo] = w0[s2] | (v0[s2] << 16);
-          xw[(s2 * 2 + 1) * kCB * 32 + wo] = w1[s2] | (v1[s2] << 16);
+          xw[(s2 * 2 + 0) * kCB * 32 + wo] = pack_bf16_hi(w0[s2], v0[s2]);
+          xw[(s2 * 2 + 1) * kCB * 32 + wo] = pack_bf16_hi(w1[s2], v1[s2]);
         }
       }
       fence_async_smem();
