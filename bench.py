@@ -46,7 +46,7 @@ FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07
 FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) per launch of the ladder kernel from one ncu capture
 # of that kernel on this workload (None once the kernel changes)
-NCU_TRAFFIC = {"bse_f64_kernel": 33274112, "bse_mixed_kernel": 19764480}
+NCU_TRAFFIC = {"bse_f64_kernel": 33274112, "bse_mixed_kernel": 19809024}
 
 
 def dist_env():
@@ -510,7 +510,7 @@ def run_ours(args):
                     "peak_source": "FP32 CUDA cores: 152 SM x 128 FMA/clk x 2 flop x 2.07 GHz "
                                    "(75.2 TF/s measured by an FMA loop); the residual's n^3 complex MACs "
                                    "count once each here but run as 36 bf16 digit-pair products on the "
-                                   "tensor cores (mma.sync)",
+                                   "tensor cores (tcgen05, TMEM accumulators)",
                     "flop_per_launch": systems_per_launch * flop, "launch_ms": bse_avg_s * 1e3}
         res = {"value": whole_job_rate(points, world, ms * 1e-3), "ms_per_step": ms, "roofline": roof,
                "gpu_launches": sum(v[1] for v in timing.values()),
