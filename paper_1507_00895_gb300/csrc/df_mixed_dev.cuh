@@ -6,10 +6,12 @@
 //      in FP32: the D part becomes D^-1 in place (rows and columns permuted
 //      by the pivot order), the gamma part X0 ~ D^-1 gamma.  The pivots are
 //      those of LU with partial pivoting (the same unused-row maximum of the
-//      same Schur complement column); one sweep, one block barrier per pivot.
+//      same Schur complement column); one sweep, three block barriers per
+//      panel of 8 pivots.
 //   2. R = gamma - D X0 = gamma - X0 + Z X0, Z = gamma diag(chi~) formed in
-//      FP64, with ~2^-49 accuracy relative to |Z| |X0| (tensor-core digit
-//      products or double-float FP32 arithmetic).
+//      FP64, with ~2^-49 accuracy relative to |Z| |X0| (exact BF16 digit
+//      products on the tensor cores: tcgen05 with TMEM accumulators at
+//      n_pad = 64, mma.sync at 32; double-float FP32 arithmetic below).
 //   3. diag E = diag(D^-1 R) (n^2 work with the explicit inverse);
 //      diag Gamma = diag X0 + diag E in FP64.
 // One correction step leaves an error ~(kappa u32)^2 |Gamma| plus kappa times
@@ -19,14 +21,11 @@
 // grid of threads, P = n_pad / 4; thread (tr, tc) = (t / P, t % P) owns rows
 // tr + P i and columns tc + P j (i, j < 4) of D and of gamma (2D cyclic), so
 // that the P threads of a thread row are consecutive lanes and every warp
-// holds whole rows.  Row pivoting is implicit: rows never move.  Each warp
-// publishes, before the barrier that ends a step, its best unused row for
-// the next pivot column together with that row's values; after the barrier
-// every thread picks the best of the warps' candidates and reads the pivot
-// row from it, so a step needs no second barrier.  Matrices of order
-// n < n_pad are padded with an identity block (gamma = 0, chi~ = 0 there),
-// which leaves the solution of the first n rows unchanged.
-// the first n rows unchanged.
+// holds whole rows.  Row pivoting is implicit: rows never move.  The sweep
+// goes by panels of 8 pivot columns factored by one or two warps (see the
+// sweep below).  Matrices of order n < n_pad are padded with an identity
+// block (gamma = 0, chi~ = 0 there), which leaves the solution of the first
+// n rows unchanged.
 #pragma once
 #include <cuda_bf16.h>
 #include <cstdint>
