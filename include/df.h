@@ -332,6 +332,16 @@ df_status df_warmstart_sigma(df_ctx* c, const float* y, const float* mean, const
 df_status df_bse_noalloc(const double* gamma, const double* chi, int n_w, int n_bos, int n_k_total,
                          double* kernel, void* stream);
 
+/* Self-test of the bounded device-side wait used by the tensor-core
+ * residual of the mixed path (n_w 33-64): a one-warp kernel on the current
+ * device initialises a shared-memory barrier, completes it only when
+ * arrive != 0, and waits for it with a limit of `spins` polls.  Returns
+ * DF_ERR_TIMEOUT when the wait gave up (arrive = 0), DF_OK when it saw the
+ * barrier complete; the device stays usable either way.  Needs no handle.
+ * Synchronous.  Errors: DF_ERR_ARG (spins < 1; no CUDA call is made),
+ * DF_ERR_CUDA. */
+df_status df_selftest_wait(int arrive, int spins);
+
 const char* df_last_error(const df_ctx* c);
 const char* df_status_string(df_status s);
 void df_destroy(df_ctx* c);

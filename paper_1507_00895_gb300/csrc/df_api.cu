@@ -365,6 +365,19 @@ static df_status flag_error(df_ctx* c, int flags) {
   return DF_OK;
 }
 
+df_status df_selftest_wait(int arrive, int spins) {
+  if (spins < 1) return DF_ERR_ARG;
+  int* d = nullptr;
+  if (cudaMalloc(&d, sizeof(int)) != cudaSuccess) return DF_ERR_CUDA;
+  int h = 0;
+  cudaError_t e = cudaMemset(d, 0, sizeof(int));
+  if (e == cudaSuccess) e = df::launch_wait_selftest(arrive ? 1 : 0, (unsigned)spins, d, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return DF_ERR_CUDA;
+  return (h & kFlagTcTimeout) ? DF_ERR_TIMEOUT : DF_OK;
+}
+
 df_status df_sigma(df_ctx* c, double* resid) {
   if (!c) return DF_ERR_ARG;
   DF_CUDA(c, run_sigma(c), "dual self-energy (Eq. sd) + Dyson");

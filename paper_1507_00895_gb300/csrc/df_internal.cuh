@@ -231,6 +231,7 @@ struct df_ctx {
 // host-side launchers (kernels live in df_fft.cu and df_bse.cu)
 namespace df {
 cudaError_t launch_init_g0(df_ctx* c);
+cudaError_t launch_wait_selftest(int arrive, unsigned spins, int* flags, cudaStream_t stream);
 cudaError_t launch_dyson_ifft(df_ctx* c, int first_plane, int n_planes);
 cudaError_t launch_bubble(df_ctx* c);
 cudaError_t launch_sigma(df_ctx* c, double mix);

@@ -89,9 +89,32 @@ bse_mixed_kernel(Dims dm, int ch0, int nch, const double2* __restrict__ gam,
   if constexpr (use_umma_residual(NP)) tc05_teardown(tc);
 }
 
+// Self-test of the bounded wait the tensor-core residual uses: one warp
+// initialises an mbarrier (one arrival expected), arrives on it only when
+// `arrive` is set, and waits for its first phase with a limit of `spins`
+// polls; a wait that gives up sets kFlagTcTimeout.  Nothing else runs.
+__global__ void wait_selftest_kernel(int arrive, unsigned spins, int* __restrict__ flags) {
+  __shared__ uint64_t mbar;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (arrive && threadIdx.x == 0) {
+    unsigned long long state;
+    asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(smem_u32(&mbar)) : "memory");
+  }
+  if (!mbar_wait(&mbar, 0, spins) && threadIdx.x == 0) atomicOr(flags, kFlagTcTimeout);
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
+
+cudaError_t launch_wait_selftest(int arrive, unsigned spins, int* flags, cudaStream_t stream) {
+  wait_selftest_kernel<<<1, 32, 0, stream>>>(arrive, spins, flags);
+  return cudaGetLastError();
+}
 
 static int mixed_np(int n) { return mixed_pad(n); }
 

@@ -211,9 +211,10 @@ __device__ __forceinline__ void umma_commit(uint64_t* mbar) {
                : "memory");
 }
 // bounded wait for the completion of the given parity; false if it gave up
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, unsigned parity) {
+// after `spins` polls
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, unsigned parity, unsigned spins = kMbarSpin) {
   const unsigned a = smem_u32(mbar);
-  for (unsigned it = 0; it < kMbarSpin; ++it) {
+  for (unsigned it = 0; it < spins; ++it) {
     unsigned done;
     asm volatile(
         "{\n.reg .pred q;\nmbarrier.try_wait.parity.shared::cta.b64 q, [%1], %2;\nselp.u32 %0, 1, 0, q;\n}\n"

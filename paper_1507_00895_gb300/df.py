@@ -42,7 +42,7 @@ EXPORTS = (
     "df_batch_reset", "df_batch_autotune", "df_batch_last_error", "df_batch_destroy", "df_mlp_create",
     "df_mlp_param_count", "df_mlp_forward", "df_mlp_gradients", "df_mlp_adam_step", "df_mlp_train_step",
     "df_mlp_params", "df_mlp_grads", "df_mlp_last_error", "df_mlp_destroy", "df_warmstart_sigma", "df_last_error",
-    "df_status_string", "df_destroy",
+    "df_status_string", "df_destroy", "df_selftest_wait",
 )
 
 
@@ -106,6 +106,7 @@ def load(path: str = LIB_PATH):
         "df_get_timing": [P, D, I, C.c_int],
         "df_synchronize": [P],
         "df_bse_noalloc": [P, P, C.c_int, C.c_int, C.c_int, P, P],
+        "df_selftest_wait": [C.c_int, C.c_int],
         "df_batch_init": [C.POINTER(P), C.c_int, C.c_void_p, C.c_int, C.c_double, C.c_double, P],
         "df_batch_iterate": [P, C.c_int, I, D, I],
         "df_batch_get_sigma": [P, C.c_int, P, C.c_int],
