@@ -101,8 +101,7 @@ __global__ void wait_selftest_kernel(int arrive, unsigned spins, int* __restrict
   }
   __syncthreads();
   if (arrive && threadIdx.x == 0) {
-    unsigned long long state;
-    asm volatile("mbarrier.arrive.shared::cta.b64 %0, [%1];" : "=l"(state) : "r"(smem_u32(&mbar)) : "memory");
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&mbar)) : "memory");
   }
   if (!mbar_wait(&mbar, 0, spins) && threadIdx.x == 0) atomicOr(flags, kFlagTcTimeout);
 }
