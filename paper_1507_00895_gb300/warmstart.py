@@ -8,7 +8,7 @@ Pipeline (every numerical step on the GPU through libdf):
      inputs and targets standardised per component;
   3. use: predict, expand to the whole grid (df_warmstart_sigma), iterate
      from there; the plain iteration from Sigma~ = 0 is the fallback and the
-     judge of the prediction's error.
+     yardstick for the prediction's error.
 Host code here only builds feature vectors and index maps.
 """
 from __future__ import annotations
