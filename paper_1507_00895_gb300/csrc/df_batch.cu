@@ -177,7 +177,7 @@ batch_bse_f64_kernel(const PointDev* __restrict__ pts, const int* __restrict__ o
 }
 
 template <int NP>
-__global__ void __launch_bounds__(256, use_umma_residual(NP) ? 1 : 0)
+__global__ void __launch_bounds__(mixed_block_threads(NP), use_umma_residual(NP) ? 1 : 0)
 batch_bse_mixed_kernel(const PointDev* __restrict__ pts, const int* __restrict__ order, const long* __restrict__ start,
                        int nseg, int chunk, unsigned long long* __restrict__ counter) {
   extern __shared__ __align__(1024) float2 smf[];
@@ -215,8 +215,11 @@ batch_bse_mixed_kernel(const PointDev* __restrict__ pts, const int* __restrict__
       const int rem = (int)(local - (long)c * per_ch);
       const int a = rem / dm.N, q = rem - a * dm.N;
       const long key = (long)k * 256 + c * dm.nb + a;
-      bse_mixed_system<NP>(dm, c, a, q, P.gam, P.gam_hi, P.gam_lo, P.gg_hi, P.gg_lo, P.chi, P.kc, P.flags, sp,
-                           P.gdig ? P.gdig + (size_t)(c * dm.nb + a) * gdig_bytes(NP) : nullptr, key != cur, &tc);
+      if (use_umma_residual(NP) && (threadIdx.x >> 5) == mixed_compute_threads(NP) / 32)
+        mixed_producer(sp, &tc);                      // warp 8: the tensor-core MMAs
+      else
+        bse_mixed_system<NP>(dm, c, a, q, P.gam, P.gam_hi, P.gam_lo, P.gg_hi, P.gg_lo, P.chi, P.kc, P.flags, sp,
+                             P.gdig ? P.gdig + (size_t)(c * dm.nb + a) * gdig_bytes(NP) : nullptr, key != cur, &tc);
       cur = key;
     }
   }
@@ -375,8 +378,7 @@ df_status configure_groups(df_batch* b) {
   // the largest class
   for (auto& g : b->groups) {
     if (g.mixed) {
-      const int P = g.np / 4;
-      g.threads = P * P;
+      g.threads = mixed_block_threads(g.np);
       g.smem = sizeof(float2) * (size_t)mixed_layout(g.np).total;
       B_CUDA(b, cudaFuncSetAttribute((const void*)mixed_kernel_of(g.np), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)g.smem),

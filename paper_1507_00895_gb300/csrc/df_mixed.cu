@@ -52,7 +52,7 @@ __global__ void gamma_digits_kernel(int n, int np, int count, const double2* __r
 // One contiguous range of systems per block (so that consecutive systems
 // share (channel, W) and gamma's digits stay in shared memory).
 template <int NP>
-__global__ void __launch_bounds__(256, use_umma_residual(NP) ? 1 : 0)
+__global__ void __launch_bounds__(mixed_block_threads(NP), use_umma_residual(NP) ? 1 : 0)
 bse_mixed_kernel(Dims dm, int ch0, int nch, const double2* __restrict__ gam,
                  const float2* __restrict__ gam_hi, const float2* __restrict__ gam_lo,
                  const float2* __restrict__ gg_hi, const float2* __restrict__ gg_lo,
@@ -82,8 +82,11 @@ bse_mixed_kernel(Dims dm, int ch0, int nch, const double2* __restrict__ gam,
     const int rem = (int)(sys - (long)(c - ch0) * nb * N);
     const int a = rem / N, q = rem - a * N;
     const int key = c * nb + a;
-    bse_mixed_system<NP>(dm, c, a, q, gam, gam_hi, gam_lo, gg_hi, gg_lo, chi, kc, flags, sp,
-                         gdig ? gdig + (size_t)key * gdig_bytes(NP) : nullptr, key != cur, &tc);
+    if (use_umma_residual(NP) && (threadIdx.x >> 5) == mixed_compute_threads(NP) / 32)
+      mixed_producer(sp, &tc);                        // warp 8: the tensor-core MMAs
+    else
+      bse_mixed_system<NP>(dm, c, a, q, gam, gam_hi, gam_lo, gg_hi, gg_lo, chi, kc, flags, sp,
+                           gdig ? gdig + (size_t)key * gdig_bytes(NP) : nullptr, key != cur, &tc);
     cur = key;
   }
   if constexpr (use_umma_residual(NP)) tc05_teardown(tc);
@@ -151,8 +154,7 @@ cudaError_t launch_split_gamma(df_ctx* c, const double2* gg) {
 template <int NP>
 static cudaError_t launch_bse_mixed_np(df_ctx* c, int channel_mask, int* flags) {
   const Dims& dm = c->dm;
-  constexpr int P = NP / kTile;
-  constexpr int threads = P * P;
+  constexpr int threads = mixed_block_threads(NP);   // + the producer warp at n_pad = 64
   const size_t smem = sizeof(float2) * (size_t)mixed_layout(NP).total;
   cudaError_t e = cudaFuncSetAttribute((const void*)bse_mixed_kernel<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);

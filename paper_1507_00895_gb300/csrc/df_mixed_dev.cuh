@@ -621,6 +621,31 @@ __device__ __forceinline__ MixedPtrs mixed_ptrs(float2* smf, int np, int* piv_s)
   return m;
 }
 
+// n_pad = 64 runs 9 warps: warps 0-7 compute (their own 256-thread barrier),
+// warp 8 issues the tensor-core MMAs.  Per column block the compute warps
+// arrive on barrier kBarHandoff once the block's Y digits are in shared
+// memory; the producer waits there, issues the block's MMAs and commits them
+// to the mbarrier the compute warps wait on before they read TMEM.
+constexpr int kBarCompute = 2;    // named barrier of the 256 compute threads
+constexpr int kBarHandoff = 3;    // compute warps -> producer warp (288 threads)
+__host__ __device__ constexpr int mixed_compute_threads(int np) { return (np / kTile) * (np / kTile); }
+__host__ __device__ constexpr int mixed_block_threads(int np) {
+  return mixed_compute_threads(np) + (use_umma_residual(np) ? 32 : 0);
+}
+template <int NP>
+__device__ __forceinline__ void block_sync() {
+  if constexpr (use_umma_residual(NP))
+    asm volatile("bar.sync %0, %1;" ::"n"(kBarCompute), "n"(mixed_compute_threads(NP)) : "memory");
+  else
+    __syncthreads();
+}
+__device__ __forceinline__ void handoff_arrive() {
+  asm volatile("bar.arrive %0, %1;" ::"n"(kBarHandoff), "n"(mixed_compute_threads(64) + 32) : "memory");
+}
+__device__ __forceinline__ void handoff_wait() {
+  asm volatile("bar.sync %0, %1;" ::"n"(kBarHandoff), "n"(mixed_compute_threads(64) + 32) : "memory");
+}
+
 // One (q, W, channel) ladder in mixed precision; all P*P threads of the
 // block (P = np / 4) must call it.  Writes kc[c][a][:][q].
 template <int NP>
@@ -636,6 +661,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
                                                  Tc05* umma) {
   const int n = dm.n_w, N = dm.N, nb = dm.nb;
   constexpr int np = NP, P = NP / kTile;
+  constexpr int kThr = mixed_compute_threads(NP);       // threads taking part (the producer warp does not)
   constexpr int ld = x0_ld(NP);
   float2* X0s = sp.X0s;
   float2* chih = sp.chih;
@@ -658,18 +684,18 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
     if (reload) {
       const uint4* src = reinterpret_cast<const uint4*>(gdig);
       uint4* dst = reinterpret_cast<uint4*>(sp.work);
-      for (int i = t; i < gdig_bytes(NP) / 16; i += blockDim.x) dst[i] = __ldg(src + i);
+      for (int i = t; i < gdig_bytes(NP) / 16; i += kThr) dst[i] = __ldg(src + i);
       if constexpr (use_umma_residual(NP)) fence_async_smem();
     }
   }
-  for (int i = t; i < np; i += blockDim.x) {
+  for (int i = t; i < np; i += kThr) {
     double2 x = (i < n) ? chi[((size_t)a * n + i) * N + q] : mk(0.0, 0.0);
     const float hx = (float)x.x, hy = (float)x.y;
     chih[i] = make_float2(hx, hy);
     chil[i] = make_float2((float)(x.x - (double)hx), (float)(x.y - (double)hy));
     sp.chi64[i] = x;
   }
-  __syncthreads();
+  block_sync<NP>();
 
   // ---- load [D | gamma] (FP32) into registers ----
   float2 A[kTile][2 * kTile];
@@ -715,7 +741,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
   float4* cand = reinterpret_cast<float4*>(prs + kPanel * 2 * np);  // two-warp panel: [2][2][kPanel / 2]
   unsigned* ckey = reinterpret_cast<unsigned*>(cand + 2 * kPanel);   // [2][2]
   int* rowstep = reinterpret_cast<int*>(invu);                   // pivot step of each row, -1 if none
-  for (int i = t; i < np; i += blockDim.x) rowstep[i] = -1;
+  for (int i = t; i < np; i += kThr) rowstep[i] = -1;
   unsigned used0 = 0;                                            // panel warps: their rows already pivots
   // one copy of the loop body (the register column jk is selected at run time)
 #pragma unroll 1
@@ -734,14 +760,14 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
         pan[(tr + P * ii) * kPanelLd + (tc - kc)] = v;
       }
     }
-    __syncthreads();
+    block_sync<NP>();
     // (2) b GJ steps on the panel: warps 0 and 1 for np = 64, else warp 0
     if constexpr (NP == 64) {
       if (warp < 2) gj_panel2(pan, k0, warp, lane, used0, piv_s, rowstep, flags, cand, ckey);
     } else {
       if (warp == 0) gj_panel<NP>(pan, k0, lane, used0, piv_s, rowstep, flags);
     }
-    __syncthreads();
+    block_sync<NP>();
     // (3) current values of the pivot rows
 #pragma unroll
     for (int ii = 0; ii < kTile; ++ii) {
@@ -754,7 +780,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
         }
       }
     }
-    __syncthreads();
+    block_sync<NP>();
     // (4) rank-b update (the panel columns too: they take their new values after)
     for (int l = 0; l < pb; ++l) {
       const int pl = piv_s[k0 + l];
@@ -786,7 +812,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
       }
     }
   }
-  __syncthreads();
+  block_sync<NP>();
 #pragma unroll
   for (int ii = 0; ii < kTile; ++ii) rowpos[ii] = rowstep[tr + P * ii];
   // X0 in logical row order: row r of the sweep is X0 row rowpos (its pivot step)
@@ -797,8 +823,8 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
       for (int jj = 0; jj < kTile; ++jj) X0s[rowpos[ii] * ld + tc + P * jj] = A[ii][kTile + jj];
     }
   }
-  __syncthreads();
-  for (int j = t; j < np; j += blockDim.x) x0d[j] = X0s[j * ld + j];
+  block_sync<NP>();
+  for (int j = t; j < np; j += kThr) x0d[j] = X0s[j * ld + j];
   if constexpr (use_umma_residual(NP)) {
     // ---- residual R = gamma - X0 + gamma Y with tcgen05, Y = diag(chi~) X0 ----
     // gamma's digits (8 signed base-128 digits relative to per-row powers of
@@ -883,7 +909,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
 #pragma unroll
         for (int c2 = 0; c2 < kCB; ++c2) Eo[c2] = make_float2(sg * fh[c2], sg * fl[c2]);
       }
-      __syncthreads();
+      block_sync<NP>();
       if (!zi) {
         float2* Eo = E + h * np * (kCB + 1) + i * (kCB + 1);         // ZrYr -> real, ZrYi -> imaginary
 #pragma unroll
@@ -894,7 +920,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
           Eo[c2] = make_float2(sh, se + (fl[c2] + o.y));
         }
       }
-      __syncthreads();
+      block_sync<NP>();
       // R = gamma - X0 + S in double-float (it cancels to ~u32 |gamma|)
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
@@ -910,7 +936,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
       }
     };
     for (int b = 0; b < np / kCB; ++b) {
-      __syncthreads();
+      block_sync<NP>();
       // Y = chi~ o X0 in double-float for rows 2 yp, 2 yp + 1, 2 yp + 32, 2 yp + 33
       // of column yc; its column exponent e (|Y| < 2^e, -1000 for a zero
       // column): the thread's max, the warp's two row groups, the 8 warps
@@ -928,7 +954,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
       int e = m > 0.f ? exp_bound_f32(m) : -1000;
       e = max(e, __shfl_xor_sync(0xffffffffu, e, 16));
       if (lane < kCB) cw[warp * kCB + lane] = e;
-      __syncthreads();
+      block_sync<NP>();
       int ecol = cw[yc];
 #pragma unroll
       for (int w2 = 1; w2 < 8; ++w2) ecol = max(ecol, cw[w2 * kCB + yc]);
@@ -954,28 +980,15 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
         }
       }
       fence_async_smem();
-      __syncthreads();
-      if (t == 0) {
-        tc05_fence_after();
-        const unsigned za = smem_u32(zs), xa = smem_u32(xs);
-        const unsigned dt = umma->tmem + (unsigned)(256 * (b & 1));
-#pragma unroll 1
-        for (int sa = 0; sa < kSlices; ++sa) {
-          const unsigned idesc = umma_idesc_bf16(128, 32 * (kSlices - sa));
-#pragma unroll
-          for (int ks = 0; ks < 4; ++ks)
-            umma_bf16(dt + 32 * sa, umma_desc_sw128(za + sa * (2 * np * 128) + 32 * ks),
-                      umma_desc_sw128(xa + 32 * ks), idesc, (sa > 0 || ks > 0) ? 1u : 0u);
-        }
-        umma_commit(umma->mbar);
-      }
+      tc05_fence_before();
+      handoff_arrive();                                 // the producer warp issues block b's MMAs
       if (b > 0) finish(b - 1);
       if (!mbar_wait(umma->mbar, umma->phase) && t == 0) atomicOr(flags, kFlagTcTimeout);
       umma->phase ^= 1;
       tc05_fence_after();
     }
     finish(np / kCB - 1);
-    __syncthreads();
+    block_sync<NP>();
   } else if constexpr (use_tc_residual(NP)) {
     // ---- residual R = gamma - X0 + gamma Y on the tensor cores, Y = diag(chi~) X0 ----
     // gamma's digits (cut once per input upload: 8 signed base-128 digits
@@ -989,14 +1002,14 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
     __nv_bfloat16* xs = reinterpret_cast<__nv_bfloat16*>(sp.work + xs_offset(NP));       // [kSlices][2][kCB][64]
     int* cole = reinterpret_cast<int*>(xs + (size_t)kSlices * 2 * kCB * 64);             // [kCB]
     unsigned* xw = reinterpret_cast<unsigned*>(xs);
-    const int nthr = blockDim.x;
+    const int nthr = kThr;
     const int warp = t >> 5, lane = t & 31, gq = lane >> 2, t4 = lane & 3;
     const int nwarp = nthr >> 5;
     const int tiles = (np / 16) * (kCB / 8);
     for (int b = 0; b < np / kCB; ++b) {
-      __syncthreads();
+      block_sync<NP>();
       for (int c2 = t; c2 < kCB; c2 += nthr) cole[c2] = -1000;
-      __syncthreads();
+      block_sync<NP>();
       // lanes take consecutive columns of a row of X0 (no bank conflicts)
       for (int idx = t; idx < kCB * np; idx += nthr) {
         const int l = idx / kCB, c2 = idx - l * kCB;
@@ -1006,7 +1019,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
         const float m = fmaxf(fabsf(yr), fabsf(yi)) * 1.0001f;
         if (m > 0.f) atomicMax(&cole[c2], exp_bound_f32(m));
       }
-      __syncthreads();
+      block_sync<NP>();
       // two consecutive l per thread: one 32-bit word per slice and part
       for (int idx = t; idx < kCB * np / 2; idx += nthr) {
         const int l = 2 * (idx / kCB), c2 = idx - (l / 2) * kCB;
@@ -1034,7 +1047,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
           xw[(s2 * 2 + 1) * kCB * 32 + wo] = w1[s2] | (v1[s2] << 16);
         }
       }
-      __syncthreads();
+      block_sync<NP>();
       for (int tile = warp; tile < tiles; tile += nwarp) {
         const int r16 = (tile / (kCB / 8)) * 16, c8 = (tile % (kCB / 8)) * 8;
         // acc[d][0 / 1][.]: re / im of all digit pairs with sa + sb = d (one
@@ -1106,10 +1119,10 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
         }
       }
     }
-    __syncthreads();
+    block_sync<NP>();
   } else {
     // Y = chi o X0 as double-float pairs, once per system
-    for (int idx = t; idx < np * np; idx += blockDim.x) {
+    for (int idx = t; idx < np * np; idx += kThr) {
       const int l = idx / np;
       const float2 xh = chih[l], xl = chil[l];
       const float2 x = X0s[l * ld + (idx - l * np)];
@@ -1140,15 +1153,15 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
   #pragma unroll
           for (int e = 0; e < 6; ++e) acc[i2][jj][e] = 0.f;
       for (int l0 = 0; l0 < np; l0 += lc) {
-        __syncthreads();
-        for (int idx = t; idx < lc * np; idx += blockDim.x) {
+        block_sync<NP>();
+        for (int idx = t; idx < lc * np; idx += kThr) {
           const int r = idx / lc, ll = idx - r * lc;
           const int l = l0 + ll;
           const bool in = (r < n && l < n);
           gth[ll * np + r] = in ? Gh[r * n + l] : make_float2(0.f, 0.f);
           gtl[ll * np + r] = in ? Gl[r * n + l] : make_float2(0.f, 0.f);
         }
-        __syncthreads();
+        block_sync<NP>();
         for (int ll = 0; ll < lc; ++ll) {
           const int l = l0 + ll;
           float2 yh[kTile], yl[kTile];
@@ -1194,13 +1207,13 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
         }
       }
     }
-    __syncthreads();
+    block_sync<NP>();
     // R to shared memory (logical rows, in place of X0)
 #pragma unroll
     for (int ii = 0; ii < kTile; ++ii)
 #pragma unroll
       for (int jj = 0; jj < kTile; ++jj) X0s[(tr + P * ii) * ld + tc + P * jj] = A[ii][kTile + jj];
-    __syncthreads();
+    block_sync<NP>();
   }
 
   // gamma o gamma^T (hi, lo) of this thread's first pass of the Gamma^(2)
@@ -1246,13 +1259,13 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
     }
     if (tc == 0 && rowpos[ii] >= 0) ediag[j] = make_float2(ex, ey);
   }
-  __syncthreads();
+  block_sync<NP>();
 
   // ---- diag Gamma = diag X0 + diag E (FP64), Gamma^(2), Eq. sd bracket ----
   // Gamma^(2)_jj = sum_x (gamma_jx gamma_xj) chi~_x in double-float; four
   // threads per output frequency j (consecutive lanes, shuffle-reduced) when
   // the block has whole warps, one thread per j otherwise
-  for (int base = 0; base < per_j * np; base += blockDim.x) {
+  for (int base = 0; base < per_j * np; base += kThr) {
     const int idx = base + t;
     const int j = idx / per_j, part = idx % per_j;
     if (base > 0) load_gg(idx);
@@ -1282,7 +1295,34 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
           mk(wgt * (gdiag.x - 0.5 * g2.x), wgt * (gdiag.y - 0.5 * g2.y));
     }
   }
-  __syncthreads();
+  block_sync<NP>();
+}
+
+// The producer warp's side of bse_mixed_system<64> for one system: per
+// column block, wait for the compute warps' handoff, then (lane 0) issue the
+// 32 MMAs (gamma slice sa: A = [Zr; Zi] of slice sa, B = the Y slices 0 .. 7 - sa
+// stacked along N, D at TMEM buffer b & 1, column 32 sa) and commit them.
+__device__ __forceinline__ void mixed_producer(const MixedPtrs& sp, const Tc05* umma) {
+  constexpr int np = 64;
+  const unsigned za = smem_u32(sp.work), xa = smem_u32(sp.work + xs_offset(np));
+  const int lane = threadIdx.x & 31;
+  for (int b = 0; b < np / kCB; ++b) {
+    handoff_wait();
+    if (lane == 0) {
+      tc05_fence_after();
+      const unsigned dt = umma->tmem + (unsigned)(256 * (b & 1));
+#pragma unroll 1
+      for (int sa = 0; sa < kSlices; ++sa) {
+        const unsigned idesc = umma_idesc_bf16(128, 32 * (kSlices - sa));
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks)
+          umma_bf16(dt + 32 * sa, umma_desc_sw128(za + sa * (2 * np * 128) + 32 * ks), umma_desc_sw128(xa + 32 * ks),
+                    idesc, (sa > 0 || ks > 0) ? 1u : 0u);
+      }
+      umma_commit(umma->mbar);
+    }
+    __syncwarp();
+  }
 }
 
 }  // namespace df
