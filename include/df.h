@@ -198,7 +198,10 @@ df_status df_lattice_observables(df_ctx* c, double* sigma_lat, double* g_lat, in
 df_status df_susceptibility(df_ctx* c, double* out, int out_is_device);
 df_status df_get_chi(df_ctx* c, double* out, int out_is_device);
 df_status df_get_kernel(df_ctx* c, double* out, int out_is_device);
-/* lambda [2][N_W][N] complex; ok [2][N_W][N] ints: 1 converged, 0 not
+/* lambda [2][N_W][N] complex; ok [2][N_W][N] ints: 1 converged (to 1e-12),
+ * 2 (n_w <= 64) the two largest moduli are equal (a complex-conjugate pair:
+ * one power-iteration vector cannot settle) and lambda is the pair's member
+ * of larger imaginary part, to FP32 accuracy (~1e-5 relative), 0 not
  * converged, -1 not computed (eig_mode).  ok may be NULL. */
 df_status df_get_lambda(df_ctx* c, double* lambda, int* ok, int out_is_device);
 

@@ -362,7 +362,12 @@ lambda_reg_kernel(Dims dm, int ch0, int a0, int na, double tol, const double2* _
   extern __shared__ float2 glo[];                // [4][16][kEigRegN], block stride kEigLoStride
   __shared__ __align__(16) float2 uh[4 * kEigUStride], ul[4 * kEigUStride];
   __shared__ float2 xh[kEigRegN][kEigQ], xl[kEigRegN][kEigQ];   // chi~ as (hi, lo) pairs
-  __shared__ float redf[8][kEigQ][6];            // per warp: Rayleigh quotient (re, im) and |y|^2 (df pairs)
+  __shared__ float redf[8][kEigQ][7];            // per warp: FP32 phase: u^H y, |y|^2, u_prev^H y, u_prev^H u;
+                                                 // polish: u^H y and |y|^2 as df pairs
+  __shared__ float2 pair_s[kEigQ][2];            // FP32 phase: the dominant pair's two estimates
+  __shared__ float cprev_s[kEigQ];               // FP32 phase: |A u_prev|
+  __shared__ int pconv_s[kEigQ];                 // FP32 phase: the pair estimate settled
+  __shared__ int phave_s[kEigQ];                 // FP32 phase: pair_s holds an accepted estimate
   __shared__ float2 scal[kEigQ];                 // per system: 1 / |y| as a double-float (hi, lo)
   __shared__ double2 lold_s[kEigQ];              // previous (current, at the end) Rayleigh quotients
   __shared__ int done_s[kEigQ];
@@ -396,10 +401,20 @@ lambda_reg_kernel(Dims dm, int ch0, int a0, int na, double tol, const double2* _
   if (tid < kEigQ) {
     done_s[tid] = tid < nq ? 0 : 1;
     lold_s[tid] = mk(0.0, 0.0);
+    pair_s[tid][0] = pair_s[tid][1] = make_float2(0.f, 0.f);
+    cprev_s[tid] = 0.f;
+    pconv_s[tid] = 0;
+    phave_s[tid] = 0;
   }
 
   // ---- FP32 phase ----
-  float2 v32[2];
+  // Alongside the Rayleigh quotient, the span of the last two iterates gives
+  // the dominant pair when two eigenvalues share the largest modulus (a
+  // complex-conjugate pair, where one vector cannot settle): with u_k = A
+  // u_{k-1} / c, fit A u_k ~ alpha u_k + beta u_{k-1} (least squares); on that
+  // span A acts as [[0, beta], [c, alpha]], whose eigenvalues solve
+  // l^2 - alpha l - beta c = 0.
+  float2 v32[2], vprev[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
   const float v0 = i < n ? rsqrtf((float)n) : 0.f;
   v32[0] = v32[1] = make_float2(v0, 0.f);
   for (int it = 0; it < kEigIter32; ++it) {
@@ -411,16 +426,22 @@ lambda_reg_kernel(Dims dm, int ch0, int a0, int na, double tol, const double2* _
     float2 y[kEigQ];
     eig_gemv32(gh, uh + jb * kEigUStride, y);
     float2 yo[2];
-    float pt[2][3];
+    float pt[2][7];
 #pragma unroll
     for (int k = 0; k < 2; ++k) {
       yo[k] = pick2(y, jb, k);
       const float2 rq = cmul(cconj(v32[k]), yo[k]);
+      const float2 g = cmul(cconj(vprev[k]), yo[k]);
+      const float2 h = cmul(cconj(vprev[k]), v32[k]);
       pt[k][0] = rq.x;
       pt[k][1] = rq.y;
       pt[k][2] = cabs2(yo[k]);
+      pt[k][3] = g.x;
+      pt[k][4] = g.y;
+      pt[k][5] = h.x;
+      pt[k][6] = h.y;
 #pragma unroll
-      for (int m = 0; m < 3; ++m)
+      for (int m = 0; m < 7; ++m)
 #pragma unroll
         for (int o = 4; o < 32; o <<= 1) pt[k][m] += __shfl_xor_sync(0xffffffffu, pt[k][m], o);
     }
@@ -428,32 +449,62 @@ lambda_reg_kernel(Dims dm, int ch0, int a0, int na, double tol, const double2* _
 #pragma unroll
       for (int k = 0; k < 2; ++k)
 #pragma unroll
-        for (int m = 0; m < 3; ++m) redf[warp][2 * jb + k][m] = pt[k][m];
+        for (int m = 0; m < 7; ++m) redf[warp][2 * jb + k][m] = pt[k][m];
     }
     __syncthreads();
     if (tid < kEigQ) {
-      float r0 = 0.f, r1 = 0.f, yy = 0.f;
+      float r[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-      for (int w = 0; w < 8; ++w) {
-        r0 += redf[w][tid][0];
-        r1 += redf[w][tid][1];
-        yy += redf[w][tid][2];
-      }
+      for (int w = 0; w < 8; ++w)
+#pragma unroll
+        for (int m = 0; m < 7; ++m) r[m] += redf[w][tid][m];
+      const float yy = r[2];
       scal[tid] = make_float2(yy > 0.f ? 1.f / sqrtf(yy) : 0.f, 0.f);
-      const float2 ln = make_float2(r0, r1);
+      const float2 ln = make_float2(r[0], r[1]);
       const float2 lo = make_float2((float)lold_s[tid].x, (float)lold_s[tid].y);
       if (!done_s[tid]) {
         const float2 d = ln - lo;
         if (sqrtf(cabs2(d)) <= 2e-6f * sqrtf(cabs2(ln))) done_s[tid] = 1;
       }
       lold_s[tid] = mk((double)ln.x, (double)ln.y);
+      // the pair from span{u_prev, u}: Gram [[1, conj h], [h, 1]], right side
+      // (u^H y, u_prev^H y).  For a pair the two iterates' overlap oscillates;
+      // a fit counts only when the Gram matrix is well conditioned (det > 0.1:
+      // FP32 rounding amplified <= 10x), and is compared with the previous
+      // counted fit (settled: both roots within 1e-4); ill-conditioned steps
+      // leave the estimate as it was
+      const float c = cprev_s[tid];
+      const float2 g = make_float2(r[3], r[4]), h = make_float2(r[5], r[6]);
+      const float det = 1.f - cabs2(h);
+      if (it > 0 && c > 0.f && det > 0.1f) {
+        const float2 al = cscale(ln - cmul(cconj(h), g), 1.f / det);
+        const float2 be = cscale(g - cmul(h, ln), 1.f / det);
+        const float2 disc = cmul(al, al) + cscale(be, 4.f * c);
+        const float dm = sqrtf(cabs2(disc));
+        float2 sq = make_float2(sqrtf(fmaxf(0.5f * (dm + disc.x), 0.f)), sqrtf(fmaxf(0.5f * (dm - disc.x), 0.f)));
+        if (disc.y < 0.f) sq.y = -sq.y;
+        const float2 l1 = cscale(al + sq, 0.5f), l2 = cscale(al - sq, 0.5f);
+        // match the new roots to the previous ones (their order may swap)
+        const float2 o1 = pair_s[tid][0], o2 = pair_s[tid][1];
+        const bool sw = cabs2(l1 - o2) + cabs2(l2 - o1) < cabs2(l1 - o1) + cabs2(l2 - o2);
+        const float2 d1 = (sw ? l2 : l1) - o1, d2 = (sw ? l1 : l2) - o2;
+        const float sc = fmaxf(sqrtf(cabs2(l1)), sqrtf(cabs2(l2)));
+        pconv_s[tid] = phave_s[tid] && sqrtf(cabs2(d1)) <= 1e-4f * sc && sqrtf(cabs2(d2)) <= 1e-4f * sc;
+        pair_s[tid][0] = l1;
+        pair_s[tid][1] = l2;
+        phave_s[tid] = 1;
+      }
+      cprev_s[tid] = sqrtf(yy);
     }
     __syncthreads();
     int all = 1;
 #pragma unroll
-    for (int k = 0; k < 2; ++k) v32[k] = cscale(yo[k], scal[2 * jb + k].x);
+    for (int k = 0; k < 2; ++k) {
+      vprev[k] = v32[k];
+      v32[k] = cscale(yo[k], scal[2 * jb + k].x);
+    }
 #pragma unroll
-    for (int t = 0; t < kEigQ; ++t) all &= done_s[t];
+    for (int t = 0; t < kEigQ; ++t) all &= done_s[t];   // the pair is for systems that never settle
     if (all) break;
   }
   // ---- double-float polish from the FP32 vector ----
@@ -592,9 +643,21 @@ lambda_reg_kernel(Dims dm, int ch0, int a0, int na, double tol, const double2* _
   }
   if (tid < nq) {
     const size_t o = ((size_t)c * nb + a) * N + q0 + tid;
-    lam[o] = lold_s[tid];
-    ok[o] = conv_s[tid] && done_s[tid];
-    if (cabs2(lold_s[tid]) >= 1.0) atomicOr(flags, 2);
+    double2 l = lold_s[tid];
+    int okv = conv_s[tid] && done_s[tid];
+    if (!conv_s[tid] && pconv_s[tid]) {
+      // a settled dominant pair: the root of larger modulus (of equal moduli,
+      // the one with the larger imaginary part), to FP32 accuracy
+      const float2 l1 = pair_s[tid][0], l2 = pair_s[tid][1];
+      const float m1 = cabs2(l1), m2 = cabs2(l2);
+      const bool first = m1 > m2 * (1.f + 1e-5f) || (m2 <= m1 * (1.f + 1e-5f) && l1.y >= l2.y);
+      const float2 lp = first ? l1 : l2;
+      l = mk((double)lp.x, (double)lp.y);
+      okv = 2;
+    }
+    lam[o] = l;
+    ok[o] = okv;
+    if (cabs2(l) >= 1.0) atomicOr(flags, 2);
   }
 }
 

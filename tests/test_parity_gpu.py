@@ -193,6 +193,31 @@ def test_lambda_matches_eigvals_where_converged(df):
     assert n_ok > 0
 
 
+def test_lambda_dominant_pairs(df):
+    # where the two largest moduli tie (complex-conjugate pairs: a single power
+    # vector cannot settle), the FP32 phase's fit on the last two iterates gives
+    # the pair: ok = 2 and lambda within 1e-4 of the pair's member, to LAPACK
+    w = I.workload("square32_tp", nk=8, n_w=12, m_max=2)
+    st, gd, gm = oracle_first_pass(w)
+    with df.DualFermion.from_workload(w, eig_mode=2) as d:
+        d.bubble()
+        d.bse(3)
+        lam, ok = d.get_lambda()
+    n_pair = 0
+    for c, gx in enumerate((gd, gm)):
+        for a in range(w.n_bos):
+            for q in range(w.N):
+                ev = np.linalg.eigvals(gx[a] * st.chi[a, :, q][None, :])
+                order = np.argsort(-np.abs(ev))
+                s0, s1, s2 = np.abs(ev[order[:3]])
+                if s0 - s1 < 1e-9 * s0 and s2 < 0.5 * s0:
+                    assert ok[c, a, q] == 2, (c, a, q, ok[c, a, q])
+                    assert min(abs(lam[c, a, q] - ev[order[0]]), abs(lam[c, a, q] - ev[order[1]])) < 1e-4 * s0
+                    assert lam[c, a, q].imag >= -1e-4 * s0       # the member of larger imaginary part
+                    n_pair += 1
+    assert n_pair > 0
+
+
 def test_set_and_get_sigma_roundtrip(df):
     w = I.workload("paper_u20", nk=8, n_w=8, m_max=1)
     rng = np.random.default_rng(9)
