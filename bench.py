@@ -352,6 +352,17 @@ def observables_bench(df, I, torch, reps: int = 20):
             d.susceptibility()
             t_sus.append(time.perf_counter() - t0h)
         sus_s = min(t_sus)
+    # the same under DF_FP32_IR: FP32 LU + FP64 refinement, FP64 LU for the systems handed back
+    with df.DualFermion.from_workload(w, precision=df.DF_FP32_IR, stream=stream.cuda_stream) as d:
+        d.iterate(1)
+        d.susceptibility()
+        t_ir = []
+        for _ in range(3):
+            d.synchronize()
+            t0h = time.perf_counter()
+            d.susceptibility()
+            t_ir.append(time.perf_counter() - t0h)
+        ir_s = min(t_ir)
     nbytes = 16 * w.n_w * w.N * 4          # G0~ and Sigma~ in, Sigma_lat and G_lat out
     lu_flop = 2 * w.n_bos * w.N * 8.0 * w.n_w ** 3 / 3.0
     return {"lattice": {"kernel": "lattice_kernel", "ms": ms, "algorithmic_bytes": nbytes,
@@ -360,7 +371,12 @@ def observables_bench(df, I, torch, reps: int = 20):
             "susceptibility": {"ms_per_call": sus_s * 1e3, "ladders": 2 * w.n_bos * w.N,
                                "lu_flop": lu_flop, "lu_GFLOP_per_s": lu_flop / sus_s / 1e9,
                                "note": "df_susceptibility wall time (synchronous call): dual bubble, G and frakG "
-                                       "planes, two lattice bubbles, 2 x N_W x N FP64 LU + solve"}}
+                                       "planes, two lattice bubbles, 2 x N_W x N FP64 LU + solve"},
+            "susceptibility_fp32_ir": {"ms_per_call": ir_s * 1e3, "ladders": 2 * w.n_bos * w.N,
+                                       "lu_flop_fp64_equivalent": lu_flop,
+                                       "fp64_equivalent_GFLOP_per_s": lu_flop / ir_s / 1e9,
+                                       "note": "the same call under DF_FP32_IR: FP32 LU + FP64 refinement "
+                                               "(chi_ladder_ir_kernel), FP64 LU for the systems handed back"}}
 
 
 def radius_bench(df, I, torch, passes: int = 10):

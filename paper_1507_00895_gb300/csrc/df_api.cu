@@ -236,6 +236,8 @@ df_status df_init(df_ctx** out, const df_lattice* lat, double beta, double mu, d
   if (opts->precision != DF_FP64 && opts->precision != DF_FP32_IR) return DF_ERR_ARG;
   if (opts->eig_mode < 0 || opts->eig_mode > 2) return DF_ERR_ARG;
   if (opts->radius_order < 0 || opts->radius_order > 16) return DF_ERR_ARG;
+  if (opts->ir_max_steps < 1 || opts->ir_max_steps > 64 || !(opts->ir_tol > 0.0 && opts->ir_tol < 1.0))
+    return DF_ERR_ARG;
   if (opts->radius_order > 0 && (opts->precision != DF_FP64 || opts->eig_mode != 2)) return DF_ERR_ARG;
   if (opts->precision == DF_FP32_IR && !mixed_supported(opts->n_w)) {
     fprintf(stderr, "libdf: DF_FP32_IR supports n_w <= 64\n");
@@ -460,7 +462,9 @@ df_status df_susceptibility(df_ctx* c, double* out, int is_device) {
   const Dims& dm = c->dm;
   const size_t plane = (size_t)dm.ne * dm.N, pw = (size_t)dm.nb * dm.n_w * dm.N, pq = (size_t)dm.nb * dm.N;
   if (!c->sus) {
-    const cudaError_t e = cudaMalloc((void**)&c->sus, sizeof(double2) * (4 * plane + 2 * pw + 3 * pq));
+    // the planes, P, L, chi0, the result, then the refinement's hand-back list
+    const cudaError_t e =
+        cudaMalloc((void**)&c->sus, sizeof(double2) * (4 * plane + 2 * pw + 3 * pq) + sizeof(int) * (2 * pq + 4));
     if (e != cudaSuccess) {
       c->sus = nullptr;
       return fail(c, DF_ERR_OOM, "susceptibility buffers", e);
@@ -471,10 +475,11 @@ df_status df_susceptibility(df_ctx* c, double* out, int is_device) {
   double2* L = P + pw;
   double2* chi0 = L + pw;
   double2* res = chi0 + pq;
+  int* redo = (int*)(res + 2 * pq);
   DF_CUDA(c, launch_bubble(c), "dual bubble (Eq. dual_bubble)");
   DF_CUDA(c, launch_obs_bubbles(c, planes, P, L, chi0), "susceptibility bubbles");
   DF_CUDA(c, cudaMemsetAsync(bse_flags(c), 0, sizeof(int) * 4, c->stream), "flags");
-  DF_CUDA(c, launch_chi_ladder(c, L, chi0, is_device ? (double2*)out : res), "susceptibility ladders");
+  DF_CUDA(c, launch_chi_ladder(c, L, chi0, is_device ? (double2*)out : res, redo), "susceptibility ladders");
   int fl[4] = {0, 0, 0, 0};
   DF_CUDA(c, cudaMemcpyAsync(fl, bse_flags(c), sizeof fl, cudaMemcpyDeviceToHost, c->stream), "flags");
   if (!is_device)

@@ -102,22 +102,263 @@ __device__ __forceinline__ void chi_ladder_system(const Dims& dm, int c, int a, 
   __syncthreads();
 }
 
+// All 2 nb N systems, or with `list` non-null the list[0] systems whose
+// indices follow it (the ones the refinement kernel below handed back).
 template <bool LU_SMEM>
 __global__ void __launch_bounds__(kBseThreads)
 chi_ladder_kernel(Dims dm, const double2* __restrict__ gam, const double2* __restrict__ chi,
                   const double2* __restrict__ Lb, const double2* __restrict__ chi0, double2* __restrict__ out,
-                  double2* __restrict__ ws, int* __restrict__ flags) {
+                  double2* __restrict__ ws, int* __restrict__ flags, const int* __restrict__ list) {
   extern __shared__ double2 sm[];
   __shared__ BseF64Shared sh;
   const int n = dm.n_w, N = dm.N, nb = dm.nb;
   const BseSmem L = bse_layout(n, 2, LU_SMEM);
   double2* LU = LU_SMEM ? sm + L.lu : ws + (size_t)blockIdx.x * n * n;
+  const long systems = list ? (long)list[0] : 2L * nb * N;
+  for (long s = blockIdx.x; s < systems; s += gridDim.x) {
+    const long sys = list ? (long)list[1 + s] : s;
+    const int c = (int)(sys / ((long)nb * N));
+    const int rem = (int)(sys - (long)c * nb * N);
+    const int a = rem / N, q = rem - a * N;
+    chi_ladder_system(dm, c, a, q, gam, chi, Lb, chi0, out, LU, sm + L.y, sm + L.xs, sm + L.invu, sh, flags);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The same ladder term under DF_FP32_IR (n_w <= 64): x = D^-1 gamma L by
+// mixed-precision iterative refinement.  D = 1 - gamma_W diag(chi~_W(q)) is
+// factorised once in FP32 (complex64 in shared memory, row stride n + 1,
+// partial pivoting on |re| + |im|); then, from x = 0 and r = gamma L,
+//     D d = r / |r|   (the FP32 factors),   x += |r| d,   r = gamma L - D x
+// with x, r and the products gamma v in FP64 (D x = x - gamma (chi~ o x)).
+// Each step shrinks the error by about cond(D) 2^-24.  A system stops when
+// its correction d is below ir_tol |x| (max norms of |re| + |im|), or when
+// d times its ratio to the previous correction is (the error left after a
+// contracting step); it is handed back to the FP64 LU kernel (appended to
+// `redo`, count in redo[0], output not written here) on an exactly zero FP32
+// pivot, a non-finite value, a correction that did not halve, or after
+// max_steps solves.  128 threads: warp 0 searches pivots and runs the FP32
+// triangular solves (two rows per lane in registers), all threads the
+// rank-1 updates (one column each, rows split in 128 / n groups) and the
+// FP64 row products (128 / n rounded down to a power of two lanes per row).
+// ---------------------------------------------------------------------------
+constexpr int kChiIrThreads = 128;
+constexpr int kChiIrMaxN = 64;
+
+struct ChiIrShared {
+  int perm[kChiIrMaxN];
+  double2 xs[kChiIrMaxN], lv[kChiIrMaxN], b[kChiIrMaxN], x[kChiIrMaxN], v[kChiIrMaxN], r[kChiIrMaxN];
+  float2 invd[kChiIrMaxN];
+  float2 pv, oldkk;
+  int piv, bad, state;
+};
+
+// sum_j gamma_ij v_j for row i by `tpr` adjacent lanes (lane part of them
+// takes j = part mod tpr); every lane of the warp must call it, rows i >= n
+// contribute nothing.  The sum is complete in every lane of the group.
+__device__ __forceinline__ double2 chi_ir_rowdot(const double2* __restrict__ G, const double2* v, int n, int i,
+                                                 int part, int tpr) {
+  double2 s0 = mk(0.0, 0.0), s1 = mk(0.0, 0.0);
+  if (i < n) {
+    const double2* g = G + (size_t)i * n;
+    int j = part;
+    for (; j + tpr < n; j += 2 * tpr) {
+      s0 = cfma(__ldg(g + j), v[j], s0);
+      s1 = cfma(__ldg(g + j + tpr), v[j + tpr], s1);
+    }
+    if (j < n) s0 = cfma(__ldg(g + j), v[j], s0);
+  }
+  s0 = s0 + s1;
+  for (int o = tpr >> 1; o > 0; o >>= 1) {
+    s0.x += __shfl_xor_sync(0xffffffffu, s0.x, o);
+    s0.y += __shfl_xor_sync(0xffffffffu, s0.y, o);
+  }
+  return s0;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__global__ void __launch_bounds__(kChiIrThreads, 4)
+chi_ladder_ir_kernel(Dims dm, const double2* __restrict__ gam, const double2* __restrict__ chi,
+                     const double2* __restrict__ Lb, const double2* __restrict__ chi0, double2* __restrict__ out,
+                     int* __restrict__ redo, int max_steps, double tol) {
+  extern __shared__ float2 A[];        // [n][n + 1]
+  __shared__ ChiIrShared sh;
+  const int n = dm.n_w, N = dm.N, nb = dm.nb, ld = n + 1;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // rank-1 update / build map: column j, row group i0 of rpp
+  const int rpp = kChiIrThreads / n, j = tid % n, i0 = tid / n;
+  // row-product map: tpr lanes per row
+  int tpr = 1;
+  while (tpr < 32 && 2 * tpr * n <= kChiIrThreads) tpr *= 2;
+  const int ri = tid / tpr, rpart = tid % tpr;
   const long systems = 2L * nb * N;
   for (long sys = blockIdx.x; sys < systems; sys += gridDim.x) {
     const int c = (int)(sys / ((long)nb * N));
     const int rem = (int)(sys - (long)c * nb * N);
     const int a = rem / N, q = rem - a * N;
-    chi_ladder_system(dm, c, a, q, gam, chi, Lb, chi0, out, LU, sm + L.y, sm + L.xs, sm + L.invu, sh, flags);
+    const double2* G = gam + ((size_t)c * nb + a) * n * n;
+    for (int i = tid; i < n; i += kChiIrThreads) {
+      sh.xs[i] = chi[((size_t)a * n + i) * N + q];
+      sh.lv[i] = Lb[((size_t)a * n + i) * N + q];
+      sh.perm[i] = i;
+    }
+    if (tid == 0) sh.bad = 0;
+    __syncthreads();
+    if (i0 < rpp) {
+      for (int i = i0; i < n; i += rpp) {
+        const double2 t = cmul(__ldg(G + (size_t)i * n + j), sh.xs[j]);
+        A[i * ld + j] = make_float2((float)((i == j ? 1.0 : 0.0) - t.x), (float)(-t.y));
+      }
+    }
+    {   // b = gamma L, the first residual
+      const double2 s = chi_ir_rowdot(G, sh.lv, n, ri, rpart, tpr);
+      if (rpart == 0 && ri < n) {
+        sh.b[ri] = s;
+        sh.r[ri] = s;
+        sh.x[ri] = mk(0.0, 0.0);
+      }
+    }
+    __syncthreads();
+    // ---- FP32 LU with partial pivoting ----
+    for (int k = 0; k < n; ++k) {
+      if (warp == 0) {
+        float best = -1.f;
+        int bi = k;
+        for (int r = k + lane; r < n; r += 32) {
+          const float v = cabs1(A[r * ld + k]);
+          if (v > best) { best = v; bi = r; }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          const float ov = __shfl_xor_sync(0xffffffffu, best, o);
+          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+          if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+        }
+        if (lane == 0) {
+          const float2 pv = A[bi * ld + k];
+          sh.piv = bi;
+          sh.pv = pv;
+          sh.oldkk = A[k * ld + k];
+          if (pv.x == 0.f && pv.y == 0.f) {
+            sh.bad = 1;
+            sh.invd[k] = make_float2(0.f, 0.f);
+          } else {
+            sh.invd[k] = cinv(pv);
+          }
+          if (bi != k) { const int t = sh.perm[k]; sh.perm[k] = sh.perm[bi]; sh.perm[bi] = t; }
+        }
+      }
+      __syncthreads();
+      const int p = sh.piv;
+      const float2 inv = sh.invd[k];
+      // rows k and p exchanged (column k: pivot on the diagonal, the old A_kk
+      // scaled into row p), the other multipliers of column k scaled
+      if (p != k && tid < n) {
+        if (tid == k) {
+          A[k * ld + k] = sh.pv;
+          A[p * ld + k] = cmul(sh.oldkk, inv);
+        } else {
+          const float2 t = A[k * ld + tid];
+          A[k * ld + tid] = A[p * ld + tid];
+          A[p * ld + tid] = t;
+        }
+      }
+      if (tid > k && tid < n && tid != p) A[tid * ld + k] = cmul(A[tid * ld + k], inv);
+      __syncthreads();
+      if (i0 < rpp && j > k) {
+        const float2 u = A[k * ld + j];
+        for (int r = k + 1 + i0; r < n; r += rpp) A[r * ld + j] = cfms(A[r * ld + k], u, A[r * ld + j]);
+      }
+      __syncthreads();
+    }
+    // ---- refinement: state 0 going on, 1 converged, 2 handed back; every
+    // thread reads the state right after the barrier that follows its write,
+    // and warp 0 writes it again only after the next barrier ----
+    int state = sh.bad ? 2 : 0;
+    double dprev = 0.0;
+    for (int it = 0; state == 0; ++it) {
+      if (warp == 0) {
+        const bool h0 = lane < n, h1 = lane + 32 < n;
+        double rm = fmax(h0 ? cabs1(sh.r[sh.perm[lane]]) : 0.0, h1 ? cabs1(sh.r[sh.perm[lane + 32]]) : 0.0);
+        rm = warp_max(rm);
+        const double sc = rm > 0.0 ? 1.0 / rm : 0.0;
+        float2 y0 = make_float2(0.f, 0.f), y1 = y0;
+        if (h0) { const double2 t = sh.r[sh.perm[lane]]; y0 = make_float2((float)(t.x * sc), (float)(t.y * sc)); }
+        if (h1) { const double2 t = sh.r[sh.perm[lane + 32]]; y1 = make_float2((float)(t.x * sc), (float)(t.y * sc)); }
+        for (int k = 0; k < n - 1; ++k) {          // unit-lower forward substitution
+          const float2 src = k < 32 ? y0 : y1;
+          const float2 yk = make_float2(__shfl_sync(0xffffffffu, src.x, k & 31), __shfl_sync(0xffffffffu, src.y, k & 31));
+          if (lane > k && h0) y0 = cfms(A[lane * ld + k], yk, y0);
+          if (lane + 32 > k && h1) y1 = cfms(A[(lane + 32) * ld + k], yk, y1);
+        }
+        for (int k = n - 1; k >= 0; --k) {         // upper back substitution
+          const float2 src = k < 32 ? y0 : y1;
+          const float2 yk = make_float2(__shfl_sync(0xffffffffu, src.x, k & 31), __shfl_sync(0xffffffffu, src.y, k & 31));
+          const float2 xk = cmul(yk, sh.invd[k]);
+          if (lane == k) y0 = xk;
+          if (lane + 32 == k) y1 = xk;
+          if (lane < k) y0 = cfms(A[lane * ld + k], xk, y0);
+          if (lane + 32 < k) y1 = cfms(A[(lane + 32) * ld + k], xk, y1);
+        }
+        double dn = 0.0, xn = 0.0;
+        if (h0) {
+          const double2 d = mk((double)y0.x * rm, (double)y0.y * rm);
+          const double2 xv = sh.x[lane] + d;
+          sh.x[lane] = xv;
+          sh.v[lane] = cmul(sh.xs[lane], xv);
+          dn = cabs1(d);
+          xn = cabs1(xv);
+        }
+        if (h1) {
+          const double2 d = mk((double)y1.x * rm, (double)y1.y * rm);
+          const double2 xv = sh.x[lane + 32] + d;
+          sh.x[lane + 32] = xv;
+          sh.v[lane + 32] = cmul(sh.xs[lane + 32], xv);
+          dn = fmax(dn, cabs1(d));
+          xn = fmax(xn, cabs1(xv));
+        }
+        // NaN compares false: a non-finite value hands the system back
+        dn = warp_max(isfinite(dn) ? dn : INFINITY);
+        xn = warp_max(isfinite(xn) ? xn : INFINITY);
+        int st = 0;
+        if (!(dn < INFINITY) || !(xn < INFINITY)) st = 2;
+        else if (dn <= tol * xn) st = 1;
+        else if (it > 0 && dn > 0.5 * dprev) st = 2;
+        else if (it > 0 && dn * dn <= 0.5 * tol * xn * dprev) st = 1;
+        else if (it + 1 >= max_steps) st = 2;
+        dprev = dn;
+        if (st == 1) {                              // out = chi0 + L . x
+          double2 s2 = mk(0.0, 0.0);
+          if (h0) s2 = cfma(sh.lv[lane], sh.x[lane], s2);
+          if (h1) s2 = cfma(sh.lv[lane + 32], sh.x[lane + 32], s2);
+          for (int o = 16; o > 0; o >>= 1) {
+            s2.x += __shfl_xor_sync(0xffffffffu, s2.x, o);
+            s2.y += __shfl_xor_sync(0xffffffffu, s2.y, o);
+          }
+          if (lane == 0) {
+            const double2 c0 = chi0[(size_t)a * N + q];
+            out[((size_t)c * nb + a) * N + q] = mk(c0.x + s2.x, c0.y + s2.y);
+          }
+        }
+        if (lane == 0) sh.state = st;
+      }
+      __syncthreads();
+      state = sh.state;
+      if (state != 0) break;
+      {   // r = gamma L - x + gamma (chi~ o x)
+        const double2 s = chi_ir_rowdot(G, sh.v, n, ri, rpart, tpr);
+        if (rpart == 0 && ri < n) sh.r[ri] = sh.b[ri] - sh.x[ri] + s;
+      }
+      __syncthreads();
+    }
+    if (tid == 0 && state == 2) {
+      const int slot = atomicAdd(redo, 1);
+      redo[1 + slot] = (int)sys;
+    }
+    __syncthreads();
   }
 }
 
@@ -729,9 +970,11 @@ cudaError_t launch_bse(df_ctx* c, int channel_mask) {
   return cudaSuccess;
 }
 
-// the ladder term of the susceptibilities for both channels (FP64); the
-// persistent grid and LU scratch of the FP64 ladder kernel
-cudaError_t launch_chi_ladder(df_ctx* c, const double2* Lb, const double2* chi0, double2* out) {
+// the ladder term of the susceptibilities for both channels: FP64 LU on the
+// persistent grid and LU scratch of the FP64 ladder kernel, or under
+// DF_FP32_IR the refinement kernel first and the FP64 LU only for the systems
+// it hands back (redo: 1 + 2 nb N ints)
+cudaError_t launch_chi_ladder(df_ctx* c, const double2* Lb, const double2* chi0, double2* out, int* redo) {
   const Dims& dm = c->dm;
   const int n = dm.n_w;
   const bool in_smem = bse_lu_in_smem(n);
@@ -740,13 +983,30 @@ cudaError_t launch_chi_ladder(df_ctx* c, const double2* Lb, const double2* chi0,
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const long systems = 2L * dm.nb * dm.N;
+  const int* list = nullptr;
+  if (c->opts.precision == DF_FP32_IR && n <= kChiIrMaxN) {
+    const size_t ism = sizeof(float2) * (size_t)n * (n + 1);
+    e = cudaFuncSetAttribute((const void*)chi_ladder_ir_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism);
+    if (e != cudaSuccess) return e;
+    int sms = 0, per_sm = 0;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device)) != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)chi_ladder_ir_kernel, kChiIrThreads, ism);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) per_sm = 1;
+    const long ig = (long)sms * per_sm;
+    if ((e = cudaMemsetAsync(redo, 0, sizeof(int), c->stream)) != cudaSuccess) return e;
+    chi_ladder_ir_kernel<<<(int)(systems < ig ? systems : ig), kChiIrThreads, ism, c->stream>>>(
+        dm, c->gam, c->chi, Lb, chi0, out, redo, c->opts.ir_max_steps, c->opts.ir_tol);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    list = redo;
+  }
   const int grid = (int)(systems < c->bse_grid ? systems : c->bse_grid);
   if (in_smem)
     chi_ladder_kernel<true><<<grid, kBseThreads, smem, c->stream>>>(dm, c->gam, c->chi, Lb, chi0, out, nullptr,
-                                                                    flag_ptr(c));
+                                                                    flag_ptr(c), list);
   else
     chi_ladder_kernel<false><<<grid, kBseThreads, smem, c->stream>>>(dm, c->gam, c->chi, Lb, chi0, out,
-                                                                     lu_ws_ptr(c), flag_ptr(c));
+                                                                     lu_ws_ptr(c), flag_ptr(c), list);
   return cudaGetLastError();
 }
 

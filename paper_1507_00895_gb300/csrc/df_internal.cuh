@@ -247,7 +247,7 @@ size_t mixed_workspace_bytes(const Dims& dm);
 cudaError_t launch_split_gamma(df_ctx* c, const double2* gg);
 cudaError_t launch_lattice(df_ctx* c, double2* s_out, double2* g_out);
 cudaError_t launch_obs_bubbles(df_ctx* c, double2* planes, double2* P, double2* L, double2* chi0);
-cudaError_t launch_chi_ladder(df_ctx* c, const double2* Lb, const double2* chi0, double2* out);
+cudaError_t launch_chi_ladder(df_ctx* c, const double2* Lb, const double2* chi0, double2* out, int* redo);
 const double2* gamma_gt_ptr(df_ctx* c);   // gamma o gamma^T, written by launch_gamma_gt
 cudaError_t launch_bse_mixed(df_ctx* c, int channel_mask, int* flags);
 }  // namespace df

@@ -71,6 +71,10 @@ def test_bad_sizes_are_rejected_before_any_device_call(lib):
     assert lib.df_init(C.byref(h), C.byref(lat), 1.0, 0.0, 1.0, p, p, p, p, C.byref(opts), None) == 1
     opts.precision, opts.radius_order = df.DF_FP64, 17
     assert lib.df_init(C.byref(h), C.byref(lat), 1.0, 0.0, 1.0, p, p, p, p, C.byref(opts), None) == 1
+    opts.radius_order, opts.ir_max_steps = 0, 0   # refinement steps in [1, 64] ...
+    assert lib.df_init(C.byref(h), C.byref(lat), 1.0, 0.0, 1.0, p, p, p, p, C.byref(opts), None) == 1
+    opts.ir_max_steps, opts.ir_tol = 8, 0.0       # ... and a tolerance in (0, 1)
+    assert lib.df_init(C.byref(h), C.byref(lat), 1.0, 0.0, 1.0, p, p, p, p, C.byref(opts), None) == 1
     assert lib.df_selftest_wait(0, 0) == df.DF_ERR_ARG   # the bounded-wait self-test needs a limit >= 1
 
 

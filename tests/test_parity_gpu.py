@@ -349,6 +349,34 @@ def test_susceptibility(df, name, kw):
         assert nrel(dev.cpu().numpy(), ref) < TOL64
 
 
+@pytest.mark.parametrize("name,kw", [("paper_u20", dict(nk=4, n_w=6, m_max=1)),
+                                     ("square32_tp", dict(nk=8, n_w=10, m_max=2)),
+                                     ("cubic16_crit", dict(nk=4, n_w=8, m_max=1)),
+                                     ("square32_tp", dict(nk=4, n_w=64, m_max=1))])
+def test_susceptibility_refined(df, name, kw):
+    # DF_FP32_IR: the ladder term by FP32 LU + FP64 refinement, the FP64 LU for
+    # the systems handed back; at the oracle's Sigma~ after two passes
+    w = I.workload(name, **kw)
+    st = O.run_workload(w, n_iter=2)
+    eps = O.dispersion(w.dim, w.nk, w.t, w.tp)
+    gd, gm = O.channel_vertices(w.gamma_uu, w.gamma_ud)
+    ref = O.susceptibilities(w.g, w.delta, eps, st.sigma, gd, gm, w.n_w, w.m_max, w.beta, w.dim, w.nk)
+    with df.DualFermion.from_workload(w, precision=df.DF_FP32_IR) as d:
+        d.set_sigma(st.sigma)
+        chi = d.susceptibility()
+    assert nrel(chi, ref) < TOL64
+    with df.DualFermion.from_workload(w) as d:
+        d.set_sigma(st.sigma)
+        chi64 = d.susceptibility()
+    # the refinement produced them (not bit-equal to the FP64 LU), to FP64 accuracy
+    assert 0 < np.max(np.abs(chi - chi64)) < 1e-11 * np.max(np.abs(chi64))
+    # one step cannot meet the tolerance: every system with a nonzero solution
+    # is handed back, and the FP64 LU's results come out bit for bit
+    with df.DualFermion.from_workload(w, precision=df.DF_FP32_IR, ir_max_steps=1) as d:
+        d.set_sigma(st.sigma)
+        assert np.array_equal(d.susceptibility(), chi64)
+
+
 @pytest.mark.parametrize("K", [1, 3])
 def test_radius_extension(df, K):
     # outside the ladder radius (|lambda| up to 25): flagged systems take the
