@@ -137,10 +137,12 @@ chi_ladder_kernel(Dims dm, const double2* __restrict__ gam, const double2* __res
 // contracting step); it is handed back to the FP64 LU kernel (appended to
 // `redo`, count in redo[0], output not written here) on an exactly zero FP32
 // pivot, a non-finite value, a correction that did not halve, or after
-// max_steps solves.  128 threads: warp 0 searches pivots and runs the FP32
-// triangular solves (two rows per lane in registers), all threads the
-// rank-1 updates (one column each, rows split in 128 / n groups) and the
-// FP64 row products (128 / n rounded down to a power of two lanes per row).
+// max_steps solves.  128 threads: all of them run the rank-1 updates (one
+// column each, rows split in 128 / n groups; the owners of the next column
+// leave per-group pivot candidates, so that a column step takes two
+// barriers) and the FP64 row products (128 / n rounded down to a power of
+// two lanes per row; those of gamma L interleaved with the column steps);
+// warp 0 runs the FP32 triangular solves (two rows per lane in registers).
 // ---------------------------------------------------------------------------
 constexpr int kChiIrThreads = 128;
 constexpr int kChiIrMaxN = 64;
@@ -149,8 +151,12 @@ struct ChiIrShared {
   int perm[kChiIrMaxN];
   double2 xs[kChiIrMaxN], lv[kChiIrMaxN], b[kChiIrMaxN], x[kChiIrMaxN], v[kChiIrMaxN], r[kChiIrMaxN];
   float2 invd[kChiIrMaxN];
-  float2 pv, oldkk;
-  int piv, bad, state;
+  // per row group: the largest |re| + |im| of the next pivot column among the
+  // group's rows, its row (n when the group has none) and its value
+  float pabs[kChiIrThreads];
+  int prow[kChiIrThreads];
+  float2 pval[kChiIrThreads];
+  int bad, state;
 };
 
 // sum_j gamma_ij v_j for row i by `tpr` adjacent lanes (lane part of them
@@ -176,12 +182,20 @@ __device__ __forceinline__ double2 chi_ir_rowdot(const double2* __restrict__ G, 
   return s0;
 }
 
+// 1/z in FP32 for the FP32 factorisation (a reciprocal of |z|^2: outside
+// ~1e-19 < |z| < 1e19 it gives 0 or non-finite values, and the system is
+// handed back by the refinement's checks)
+__device__ __forceinline__ float2 cinv_f32(float2 z) {
+  const float d = __frcp_rn(z.x * z.x + z.y * z.y);
+  return make_float2(z.x * d, -z.y * d);
+}
+
 __device__ __forceinline__ double warp_max(double v) {
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
 
-__global__ void __launch_bounds__(kChiIrThreads, 4)
+__global__ void __launch_bounds__(kChiIrThreads, 5)
 chi_ladder_ir_kernel(Dims dm, const double2* __restrict__ gam, const double2* __restrict__ chi,
                      const double2* __restrict__ Lb, const double2* __restrict__ chi0, double2* __restrict__ out,
                      int* __restrict__ redo, int max_steps, double tol) {
@@ -208,58 +222,56 @@ chi_ladder_ir_kernel(Dims dm, const double2* __restrict__ gam, const double2* __
     }
     if (tid == 0) sh.bad = 0;
     __syncthreads();
+    // D in FP32 from FP32-rounded gamma and chi~ (only the factorisation uses
+    // it; the residuals take D from FP64 gamma); the threads of column 0 leave
+    // their row group's pivot candidate
     if (i0 < rpp) {
+      const float2 xj = make_float2((float)sh.xs[j].x, (float)sh.xs[j].y);
+      float best = -1.f;
+      int brow = n;
+      float2 bval = make_float2(0.f, 0.f);
       for (int i = i0; i < n; i += rpp) {
-        const double2 t = cmul(__ldg(G + (size_t)i * n + j), sh.xs[j]);
-        A[i * ld + j] = make_float2((float)((i == j ? 1.0 : 0.0) - t.x), (float)(-t.y));
+        const double2 gd = __ldg(G + (size_t)i * n + j);
+        float2 t = cmul(make_float2((float)gd.x, (float)gd.y), xj);
+        t = make_float2((i == j ? 1.f : 0.f) - t.x, -t.y);
+        A[i * ld + j] = t;
+        if (j == 0 && cabs1(t) > best) { best = cabs1(t); brow = i; bval = t; }
       }
-    }
-    {   // b = gamma L, the first residual
-      const double2 s = chi_ir_rowdot(G, sh.lv, n, ri, rpart, tpr);
-      if (rpart == 0 && ri < n) {
-        sh.b[ri] = s;
-        sh.r[ri] = s;
-        sh.x[ri] = mk(0.0, 0.0);
-      }
+      if (j == 0) { sh.pabs[i0] = best; sh.prow[i0] = brow; sh.pval[i0] = bval; }
     }
     __syncthreads();
-    // ---- FP32 LU with partial pivoting ----
+    // ---- FP32 LU with partial pivoting, two barriers per column; the FP64
+    // row products b = gamma L run alongside, one term per column step, their
+    // loads issued a step ahead ----
+    double2 bacc = mk(0.0, 0.0), gnext = mk(0.0, 0.0);
+    if (ri < n && rpart < n) gnext = __ldg(G + (size_t)ri * n + rpart);
+    int npart = rpp < n ? rpp : n;         // row groups holding pivot candidates
     for (int k = 0; k < n; ++k) {
-      if (warp == 0) {
-        float best = -1.f;
-        int bi = k;
-        for (int r = k + lane; r < n; r += 32) {
-          const float v = cabs1(A[r * ld + k]);
-          if (v > best) { best = v; bi = r; }
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-          const float ov = __shfl_xor_sync(0xffffffffu, best, o);
-          const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-          if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
-        }
-        if (lane == 0) {
-          const float2 pv = A[bi * ld + k];
-          sh.piv = bi;
-          sh.pv = pv;
-          sh.oldkk = A[k * ld + k];
-          if (pv.x == 0.f && pv.y == 0.f) {
-            sh.bad = 1;
-            sh.invd[k] = make_float2(0.f, 0.f);
-          } else {
-            sh.invd[k] = cinv(pv);
-          }
-          if (bi != k) { const int t = sh.perm[k]; sh.perm[k] = sh.perm[bi]; sh.perm[bi] = t; }
-        }
+      // the pivot of column k from the row groups' candidates (every thread
+      // takes the same one: largest, then lowest row)
+      float best = -1.f;
+      int p = n;
+      float2 pv = make_float2(0.f, 0.f);
+      for (int g = 0; g < npart; ++g) {
+        const float v = sh.pabs[g];
+        const int rr = sh.prow[g];
+        if (v > best || (v == best && rr < p)) { best = v; p = rr; pv = sh.pval[g]; }
       }
-      __syncthreads();
-      const int p = sh.piv;
-      const float2 inv = sh.invd[k];
-      // rows k and p exchanged (column k: pivot on the diagonal, the old A_kk
-      // scaled into row p), the other multipliers of column k scaled
+      if (p >= n) { p = k; pv = make_float2(0.f, 0.f); }   // no candidate (NaN column): a zero pivot
+      const bool zero = (pv.x == 0.f && pv.y == 0.f);
+      const float2 inv = zero ? make_float2(0.f, 0.f) : cinv_f32(pv);
+      if (tid == 0) {
+        if (zero) sh.bad = 1;
+        sh.invd[k] = inv;
+        if (p != k) { const int t = sh.perm[k]; sh.perm[k] = sh.perm[p]; sh.perm[p] = t; }
+      }
+      // rows k and p exchanged (column k: the pivot on the diagonal, the old
+      // A_kk scaled into row p), the other multipliers of column k scaled
       if (p != k && tid < n) {
         if (tid == k) {
-          A[k * ld + k] = sh.pv;
-          A[p * ld + k] = cmul(sh.oldkk, inv);
+          const float2 okk = A[k * ld + k];
+          A[k * ld + k] = pv;
+          A[p * ld + k] = cmul(okk, inv);
         } else {
           const float2 t = A[k * ld + tid];
           A[k * ld + tid] = A[p * ld + tid];
@@ -268,12 +280,77 @@ chi_ladder_ir_kernel(Dims dm, const double2* __restrict__ gam, const double2* __
       }
       if (tid > k && tid < n && tid != p) A[tid * ld + k] = cmul(A[tid * ld + k], inv);
       __syncthreads();
-      if (i0 < rpp && j > k) {
-        const float2 u = A[k * ld + j];
-        for (int r = k + 1 + i0; r < n; r += rpp) A[r * ld + j] = cfms(A[r * ld + k], u, A[r * ld + j]);
+      // rank-1 update of the trailing m x m block, spread over all threads:
+      // thread = g m + jc takes column k + 1 + jc, rows k + 1 + g + ng t with
+      // ng = floor(128 / m) groups (the quotients in FP32: exact here, every
+      // true quotient is at least 0.5 / m from an integer); the threads of
+      // column k + 1 leave the next pivot candidates
+      const int m = n - k - 1;
+      if (m > 0) {
+        const float rcp = __frcp_rn((float)m);
+        const int ng = __float2int_rz(128.f * rcp + 0.5f * rcp);
+        const int g = __float2int_rz(((float)tid + 0.5f) * rcp);
+        npart = ng < m ? ng : m;
+        if (g < ng) {
+          const int jcol = k + 1 + (tid - g * m);
+          const bool cand = (jcol == k + 1);
+          const float2 u = A[k * ld + jcol];
+          float bb = -1.f;
+          int br = n;
+          float2 bv = make_float2(0.f, 0.f);
+          int r = k + 1 + g;
+          // rows in batches of four, all loads of a batch before its stores
+          // (the compiler cannot order them otherwise: columns k and jcol share A)
+          for (; r + 3 * ng < n; r += 4 * ng) {
+            float2 l[4], t[4];
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              l[e] = A[(r + e * ng) * ld + k];
+              t[e] = A[(r + e * ng) * ld + jcol];
+            }
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+              t[e] = cfms(l[e], u, t[e]);
+              A[(r + e * ng) * ld + jcol] = t[e];
+            }
+            if (cand) {
+#pragma unroll
+              for (int e = 0; e < 4; ++e)
+                if (cabs1(t[e]) > bb) { bb = cabs1(t[e]); br = r + e * ng; bv = t[e]; }
+            }
+          }
+          for (; r < n; r += ng) {
+            const float2 t = cfms(A[r * ld + k], u, A[r * ld + jcol]);
+            A[r * ld + jcol] = t;
+            if (cand && cabs1(t) > bb) { bb = cabs1(t); br = r; bv = t; }
+          }
+          if (cand && g < m) {
+            sh.pabs[g] = bb;
+            sh.prow[g] = br;
+            sh.pval[g] = bv;
+          }
+        }
+      }
+      {
+        const int jj = rpart + tpr * k;
+        if (ri < n && jj < n) {
+          const double2 gv = gnext;
+          if (jj + tpr < n) gnext = __ldg(G + (size_t)ri * n + jj + tpr);
+          bacc = cfma(gv, sh.lv[jj], bacc);
+        }
       }
       __syncthreads();
     }
+    for (int o = tpr >> 1; o > 0; o >>= 1) {
+      bacc.x += __shfl_xor_sync(0xffffffffu, bacc.x, o);
+      bacc.y += __shfl_xor_sync(0xffffffffu, bacc.y, o);
+    }
+    if (rpart == 0 && ri < n) {
+      sh.b[ri] = bacc;
+      sh.r[ri] = bacc;
+      sh.x[ri] = mk(0.0, 0.0);
+    }
+    __syncthreads();
     // ---- refinement: state 0 going on, 1 converged, 2 handed back; every
     // thread reads the state right after the barrier that follows its write,
     // and warp 0 writes it again only after the next barrier ----
@@ -987,6 +1064,9 @@ cudaError_t launch_chi_ladder(df_ctx* c, const double2* Lb, const double2* chi0,
   if (c->opts.precision == DF_FP32_IR && n <= kChiIrMaxN) {
     const size_t ism = sizeof(float2) * (size_t)n * (n + 1);
     e = cudaFuncSetAttribute((const void*)chi_ladder_ir_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute((const void*)chi_ladder_ir_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     int sms = 0, per_sm = 0;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device)) != cudaSuccess) return e;
