@@ -93,8 +93,11 @@ typedef struct df_opts {
   double mix;         /* Sigma~ <- mix * new + (1 - mix) * old, in (0, 1]; default 1 */
   int precision;      /* df_precision; default DF_FP64 */
   int eig_mode;       /* leading eigenvalue of gamma chi~: 0 off, 1 at W = 0 (default), 2 all W */
-  int ir_max_steps;   /* DF_FP32_IR: maximum refinement steps (default 8) */
-  double ir_tol;      /* DF_FP32_IR: relative correction size that stops refinement (default 1e-13) */
+  int ir_max_steps;   /* DF_FP32_IR, susceptibility ladders: most FP32 solves per system before it is
+                       * handed to the FP64 LU (default 8; 1..64) */
+  double ir_tol;      /* DF_FP32_IR, susceptibility ladders: the refinement stops when the predicted
+                       * error left, relative to max |re| + |im| of the solution, is below it
+                       * (default 1e-13; in (0, 1)) */
   int radius_order;   /* the convergence-radius extension (the remark after Eq. lin_alg_inv): 0 off
                        * (default: Eq. lin_alg_inv is solved regardless and |lambda| >= 1 raises
                        * DF_WARN_LADDER_RADIUS); K >= 1: every (q, W, channel) whose leading
@@ -189,7 +192,9 @@ df_status df_lattice_observables(df_ctx* c, double* sigma_lat, double* g_lat, in
  *   L_{W,w}(q) = -(T/N) sum_k frakG_{w,k} frakG_{w+W,k+q},
  *   frakG = G~ (G0~ + g) / G0~,
  * G from Eq. glat, Gamma = (1 - gamma chi~)^-1 gamma (Eq. lin_alg_inv, FP64
- * LU with partial pivoting) with chi~ the dual bubble of the current G~
+ * LU with partial pivoting; under DF_FP32_IR an FP32 LU refined in FP64
+ * until ir_tol, each system that does not get there within ir_max_steps
+ * solves taken again by the FP64 LU) with chi~ the dual bubble of the current G~
  * (recomputed here; df_get_chi returns it afterwards), w over the box.  The
  * printed k sums lack 1/N; both carry it here (per-site normalisation).
  * Synchronous.  Errors: DF_ERR_ARG (no handle or NULL out), DF_ERR_OOM (the

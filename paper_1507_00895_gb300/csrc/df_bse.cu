@@ -196,9 +196,10 @@ __device__ __forceinline__ double warp_max(double v) {
 }
 
 __global__ void __launch_bounds__(kChiIrThreads, 5)
-chi_ladder_ir_kernel(Dims dm, const double2* __restrict__ gam, const double2* __restrict__ chi,
-                     const double2* __restrict__ Lb, const double2* __restrict__ chi0, double2* __restrict__ out,
-                     int* __restrict__ redo, int max_steps, double tol) {
+chi_ladder_ir_kernel(Dims dm, const double2* __restrict__ gam, const float2* __restrict__ gam32,
+                     const double2* __restrict__ chi, const double2* __restrict__ Lb,
+                     const double2* __restrict__ chi0, double2* __restrict__ out, int* __restrict__ redo,
+                     int max_steps, double tol) {
   extern __shared__ float2 A[];        // [n][n + 1]
   __shared__ ChiIrShared sh;
   const int n = dm.n_w, N = dm.N, nb = dm.nb, ld = n + 1;
@@ -215,6 +216,7 @@ chi_ladder_ir_kernel(Dims dm, const double2* __restrict__ gam, const double2* __
     const int rem = (int)(sys - (long)c * nb * N);
     const int a = rem / N, q = rem - a * N;
     const double2* G = gam + ((size_t)c * nb + a) * n * n;
+    const float2* G32 = gam32 + ((size_t)c * nb + a) * n * n;
     for (int i = tid; i < n; i += kChiIrThreads) {
       sh.xs[i] = chi[((size_t)a * n + i) * N + q];
       sh.lv[i] = Lb[((size_t)a * n + i) * N + q];
@@ -222,17 +224,16 @@ chi_ladder_ir_kernel(Dims dm, const double2* __restrict__ gam, const double2* __
     }
     if (tid == 0) sh.bad = 0;
     __syncthreads();
-    // D in FP32 from FP32-rounded gamma and chi~ (only the factorisation uses
-    // it; the residuals take D from FP64 gamma); the threads of column 0 leave
-    // their row group's pivot candidate
+    // D in FP32 from gamma's leading FP32 words and FP32-rounded chi~ (only
+    // the factorisation uses it; the residuals take D from FP64 gamma); the
+    // threads of column 0 leave their row group's pivot candidate
     if (i0 < rpp) {
       const float2 xj = make_float2((float)sh.xs[j].x, (float)sh.xs[j].y);
       float best = -1.f;
       int brow = n;
       float2 bval = make_float2(0.f, 0.f);
       for (int i = i0; i < n; i += rpp) {
-        const double2 gd = __ldg(G + (size_t)i * n + j);
-        float2 t = cmul(make_float2((float)gd.x, (float)gd.y), xj);
+        float2 t = cmul(__ldg(G32 + (size_t)i * n + j), xj);
         t = make_float2((i == j ? 1.f : 0.f) - t.x, -t.y);
         A[i * ld + j] = t;
         if (j == 0 && cabs1(t) > best) { best = cabs1(t); brow = i; bval = t; }
@@ -1049,8 +1050,9 @@ cudaError_t launch_bse(df_ctx* c, int channel_mask) {
 
 // the ladder term of the susceptibilities for both channels: FP64 LU on the
 // persistent grid and LU scratch of the FP64 ladder kernel, or under
-// DF_FP32_IR the refinement kernel first and the FP64 LU only for the systems
-// it hands back (redo: 1 + 2 nb N ints)
+// DF_FP32_IR the refinement kernel first (D from gamma's FP32 leading words,
+// the first array of the mixed-precision workspace) and the FP64 LU only for
+// the systems it hands back (redo: 1 + 2 nb N ints)
 cudaError_t launch_chi_ladder(df_ctx* c, const double2* Lb, const double2* chi0, double2* out, int* redo) {
   const Dims& dm = c->dm;
   const int n = dm.n_w;
@@ -1061,7 +1063,7 @@ cudaError_t launch_chi_ladder(df_ctx* c, const double2* Lb, const double2* chi0,
   if (e != cudaSuccess) return e;
   const long systems = 2L * dm.nb * dm.N;
   const int* list = nullptr;
-  if (c->opts.precision == DF_FP32_IR && n <= kChiIrMaxN) {
+  if (c->opts.precision == DF_FP32_IR && n <= kChiIrMaxN && c->mixed_ws) {
     const size_t ism = sizeof(float2) * (size_t)n * (n + 1);
     e = cudaFuncSetAttribute((const void*)chi_ladder_ir_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ism);
     if (e != cudaSuccess) return e;
@@ -1076,7 +1078,7 @@ cudaError_t launch_chi_ladder(df_ctx* c, const double2* Lb, const double2* chi0,
     const long ig = (long)sms * per_sm;
     if ((e = cudaMemsetAsync(redo, 0, sizeof(int), c->stream)) != cudaSuccess) return e;
     chi_ladder_ir_kernel<<<(int)(systems < ig ? systems : ig), kChiIrThreads, ism, c->stream>>>(
-        dm, c->gam, c->chi, Lb, chi0, out, redo, c->opts.ir_max_steps, c->opts.ir_tol);
+        dm, c->gam, (const float2*)c->mixed_ws, c->chi, Lb, chi0, out, redo, c->opts.ir_max_steps, c->opts.ir_tol);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     list = redo;
   }
