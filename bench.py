@@ -379,6 +379,38 @@ def observables_bench(df, I, torch, reps: int = 20):
                                                "(chi_ladder_ir_kernel), FP64 LU for the systems handed back"}}
 
 
+def large_order_bench(df, I, passes: int = 2):
+    """The 3D critical workload (16^3, n_w = 96, N_W = 21: 172,032 ladders of order 96) one
+    pass at a time from Sigma~ = 0, FP64 and DF_FP32_IR (order > 64: the shared-memory
+    Gauss-Jordan kernel); ladder time from libdf's own events, and the normwise difference of
+    the two paths' Sigma~ after the first pass."""
+    import numpy as np
+    w = I.workload("cubic16_crit")
+    ladders = 2 * w.n_bos * w.N
+    fp64_eq = 8.0 * w.n_w ** 3 * ladders            # the FP64 kernel's flops for the same ladders
+    out = {"workload": "3D 16^3, n_w=96, N_W=21, the critical point's beta", "ladders": ladders}
+    zero = np.zeros((w.n_w, w.N), np.complex128)
+    sig = {}
+    for name, prec in (("fp64", df.DF_FP64), ("fp32ir", df.DF_FP32_IR)):
+        with df.DualFermion.from_workload(w, precision=prec) as d:
+            d.iterate(1)
+            sig[name] = d.get_sigma()
+            d.set_sigma(zero)
+            d.set_timing(True)
+            t0 = time.perf_counter()
+            d.iterate(passes)
+            d.synchronize()
+            wall = (time.perf_counter() - t0) / passes
+            t = d.get_timing()
+        bse_ms = t["bse"][0] / passes
+        out[name] = {"s_per_pass": wall, "ladder_ms_per_pass": bse_ms,
+                     "fp64_equivalent_TFLOP_per_s": fp64_eq / (bse_ms * 1e-3) / 1e12,
+                     "kernel": "bse_f64_kernel" if prec == df.DF_FP64 else "bse_gj_ir_kernel"}
+    out["err_fp32ir_vs_fp64_first_pass"] = float(np.max(np.abs(sig["fp32ir"] - sig["fp64"]))
+                                                 / np.max(np.abs(sig["fp64"])))
+    return out
+
+
 def radius_bench(df, I, torch, passes: int = 10):
     """The convergence-radius extension on the 16x16, n_w = 32 workload (outside the radius):
     ms per pass with eigenvalues at every W, plain inversion vs order-1 and order-3 evaluation
@@ -597,6 +629,9 @@ def run_ours(args):
     if rank == 0 and not args.no_observables:
         obs = observables_bench(df, I, torch)
         obs["radius_extension"] = radius_bench(df, I, torch)
+    large = None
+    if rank == 0 and not args.no_large:
+        large = large_order_bench(df, I)
     warm = None
     if rank == 0 and not args.no_warmstart:
         warm = warmstart_bench(df, I, torch)
@@ -623,7 +658,7 @@ def run_ours(args):
             "err_vs_fp64_first_pass": main.get("err_vs_fp64_first_pass"),
             "plain_fp64": plain if prec != df.DF_FP64 else None,
             "time_to_converged": ttc, "batch": batch, "warm_start": warm, "example_i": sweeps,
-            "observables": obs, "clocks": main["clocks"]}
+            "observables": obs, "large_order": large, "clocks": main["clocks"]}
     print(json.dumps(line))
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -643,6 +678,8 @@ def main():
     ap.add_argument("--batch-full", action="store_true", help="uneven batch at the recipe's full sizes")
     ap.add_argument("--no-warmstart", action="store_true", help="skip the learned warm-start measurement")
     ap.add_argument("--no-sweeps", action="store_true", help="skip the paper's Example I sweeps")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the 3D critical workload's passes (order 96, both precisions)")
     ap.add_argument("--no-observables", action="store_true",
                     help="skip the lattice-observable, susceptibility and radius-extension timings")
     args = ap.parse_args()

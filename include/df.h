@@ -74,8 +74,12 @@ typedef enum df_status {
 
 typedef enum df_precision {
   DF_FP64 = 0,       /* every step in FP64 (complex128) */
-  DF_FP32_IR = 1     /* ladder solves factorised in FP32 (complex64), refined to
-                        FP64 accuracy; bubble, Sigma~ and Dyson stay FP64 */
+  DF_FP32_IR = 1     /* ladder solves factorised in FP32 (complex64) and refined by
+                        one correction with an extended-precision residual (n_w <= 64:
+                        exact digit products on the tensor cores; 64 < n_w <= 128:
+                        double-float); Sigma~ within 1e-8 of the FP64 result.  Bubble,
+                        Sigma~, Dyson stay FP64.  The susceptibilities' ladders
+                        (n_w <= 64) refine to ir_tol */
 } df_precision;
 
 /* Hypercubic lattice eps_k = -2t sum_j cos k_j (the paper's dispersion),

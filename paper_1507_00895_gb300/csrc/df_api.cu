@@ -240,7 +240,7 @@ df_status df_init(df_ctx** out, const df_lattice* lat, double beta, double mu, d
     return DF_ERR_ARG;
   if (opts->radius_order > 0 && (opts->precision != DF_FP64 || opts->eig_mode != 2)) return DF_ERR_ARG;
   if (opts->precision == DF_FP32_IR && !mixed_supported(opts->n_w)) {
-    fprintf(stderr, "libdf: DF_FP32_IR supports n_w <= 64\n");
+    fprintf(stderr, "libdf: DF_FP32_IR supports n_w <= 128\n");
     return DF_ERR_ARG;
   }
 

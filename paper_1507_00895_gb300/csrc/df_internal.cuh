@@ -250,4 +250,7 @@ cudaError_t launch_obs_bubbles(df_ctx* c, double2* planes, double2* P, double2* 
 cudaError_t launch_chi_ladder(df_ctx* c, const double2* Lb, const double2* chi0, double2* out, int* redo);
 const double2* gamma_gt_ptr(df_ctx* c);   // gamma o gamma^T, written by launch_gamma_gt
 cudaError_t launch_bse_mixed(df_ctx* c, int channel_mask, int* flags);
+// orders 64 < n_w <= 128 (df_mixed_large.cu)
+cudaError_t launch_bse_mixed_large(df_ctx* c, int channel_mask, int* flags);
+cudaError_t launch_split_gamma_t(df_ctx* c);
 }  // namespace df

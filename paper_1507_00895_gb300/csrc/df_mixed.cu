@@ -120,10 +120,12 @@ cudaError_t launch_wait_selftest(int arrive, unsigned spins, int* flags, cudaStr
 
 static int mixed_np(int n) { return mixed_pad(n); }
 
-// the register-resident [D | RHS] tile limits this kernel to n_w <= 64
-bool mixed_supported(int n_w) { return mixed_np(n_w) <= 64; }
+// the register-resident [D | RHS] tile limits this kernel to n_w <= 64; orders
+// up to 128 take the shared-memory Gauss-Jordan kernel of df_mixed_large.cu
+bool mixed_supported(int n_w) { return mixed_np(n_w) <= 128; }
 
-// gamma hi, lo; gamma o gamma^T hi, lo; gamma's digits (tensor-core residual)
+// gamma hi, lo; gamma o gamma^T hi, lo (orders > 64: gamma^T hi, lo); gamma's
+// digits (tensor-core residual)
 size_t mixed_workspace_bytes(const Dims& dm) {
   const int np = mixed_np(dm.n_w);
   const size_t digits = use_tc_residual(np) ? (size_t)2 * dm.nb * gdig_bytes(np) : 0;
@@ -143,6 +145,7 @@ cudaError_t launch_split_gamma(df_ctx* c, const double2* gg) {
   split_gamma_kernel<<<256, 256, 0, c->stream>>>(count, c->gam, gg, hi, hi + count, hi + 2 * count, hi + 3 * count);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (mixed_np(dm.n_w) > 64) return launch_split_gamma_t(c);   // slots 2, 3: gamma^T's words
   if (unsigned char* gd = gdig_ptr(c)) {
     const int np = mixed_np(dm.n_w), rows = 2 * dm.nb * np;
     gamma_digits_kernel<<<(rows + 7) / 8, 256, 0, c->stream>>>(dm.n_w, np, 2 * dm.nb, c->gam, gd);
@@ -184,6 +187,7 @@ cudaError_t launch_bse_mixed(df_ctx* c, int channel_mask, int* flags) {
     case 16: return launch_bse_mixed_np<16>(c, channel_mask, flags);
     case 32: return launch_bse_mixed_np<32>(c, channel_mask, flags);
     case 64: return launch_bse_mixed_np<64>(c, channel_mask, flags);
+    case 128: return launch_bse_mixed_large(c, channel_mask, flags);   // df_mixed_large.cu
     default: return cudaErrorInvalidValue;
   }
 }

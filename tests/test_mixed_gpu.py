@@ -96,8 +96,34 @@ def test_mixed_matches_fp64_gpu_over_iterations(df):
         assert nrel(d32.get_sigma(), d64.get_sigma()) < TOL_SIGMA
 
 
-def test_mixed_rejects_large_ladders(df):
-    w = I.workload("cubic16_crit", nk=4, n_w=96, m_max=0)
-    with pytest.raises(df.DFError) as ei:
-        df.DualFermion.from_workload(w, precision=df.DF_FP32_IR)
-    assert ei.value.status == df.DF_ERR_ARG
+LARGE = [
+    ("cubic16_crit", dict(nk=4, n_w=96, m_max=1)),         # the 3D workload's order
+    ("square16_b5", dict(nk=4, n_w=66, m_max=1)),          # 2n threads not a warp multiple
+    ("paper_u20", dict(nk=4, n_w=128, m_max=0)),           # the largest order
+]
+
+
+@pytest.mark.parametrize("name,kw", LARGE)
+def test_mixed_large_orders_first_pass(df, name, kw):
+    # 64 < n_w <= 128: FP32 Gauss-Jordan inverse + one double-float-residual correction
+    w = I.workload(name, **kw)
+    st, kref = oracle_first_pass(w)
+    with df.DualFermion.from_workload(w, precision=df.DF_FP32_IR) as d:
+        d.bubble()
+        d.bse(3)
+        kern = d.get_kernel()
+        for c in range(2):
+            for a in range(w.n_bos):
+                assert nrel(kern[c, a], kref[c, a]) < TOL_KERNEL, (c, a)
+        d.sigma()
+        assert nrel(d.get_sigma(), st.sigma) < TOL_SIGMA
+
+
+def test_mixed_large_order_over_iterations(df):
+    # the 3D critical workload's order, three passes, against the GPU FP64 path
+    w = I.workload("cubic16_crit", nk=4, n_w=96, m_max=2)
+    with df.DualFermion.from_workload(w) as d64, \
+            df.DualFermion.from_workload(w, precision=df.DF_FP32_IR) as d32:
+        d64.iterate(3)
+        d32.iterate(3)
+        assert nrel(d32.get_sigma(), d64.get_sigma()) < TOL_SIGMA
