@@ -158,48 +158,56 @@ bse_gj_ir_kernel(Dims dm, int ch0, int nch, const float2* __restrict__ ghi, cons
         if (p != k) { const int t = sh.perm[k]; sh.perm[k] = sh.perm[p]; sh.perm[p] = t; }
       }
       // rows k and p exchanged, row k scaled by 1/pivot (its column-k entry
-      // becomes 1/pivot); column k's other entries saved as multipliers
+      // becomes 1/pivot); column k's other entries moved to the multipliers
+      // colk and zeroed (the update below then writes -colk_i / pivot there),
+      // row k's multiplier 0
       if (tid < n) {
         const float2 t1 = S[k * ld + tid], t2 = S[p * ld + tid];
-        if (p != k) S[p * ld + tid] = t1;
+        if (p != k) S[p * ld + tid] = (tid == k) ? make_float2(0.f, 0.f) : t1;
         S[k * ld + tid] = (tid == k) ? inv : cmul(t2, inv);
-        if (tid == k && p != k) colk[p] = t1;
-        if (tid != k && tid != p) colk[tid] = S[tid * ld + k];
+        if (tid == k) {
+          if (p != k) colk[p] = t1;
+          colk[k] = make_float2(0.f, 0.f);
+        }
+        if (tid != k && tid != p) {
+          colk[tid] = S[tid * ld + k];
+          S[tid * ld + k] = make_float2(0.f, 0.f);
+        }
       }
       __syncthreads();
-      // every row but k: S_ij -= colk_i S_kj (j != k), S_ik = -colk_i / pivot;
-      // rows in batches of four, loads before stores; the threads of column
-      // k + 1 leave its pivot candidates among rows > k
+      // every row: S_ij -= colk_i S_kj, the same code in every lane; rows in
+      // batches of four, loads before stores; the lanes of column k + 1 keep
+      // its pivot candidates among rows > k
       if (act) {
         const float2 u = S[k * ld + j];
         const bool cand = (j == k + 1);
         float bb = -1.f;
         int br = n;
         float2 bv = make_float2(0.f, 0.f);
-        if (j != k) {
-          for (int i0 = g; i0 < n; i0 += 8) {
-            float2 f[4], t[4];
+        float2* col = S + j;
+        int i = g;
+        for (; i + 6 < n; i += 8) {
+          float2 f[4], t[4];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const int ie = i0 + 2 * e;
-              if (ie < n && ie != k) { f[e] = colk[ie]; t[e] = S[ie * ld + j]; }
-            }
+          for (int e = 0; e < 4; ++e) {
+            f[e] = colk[i + 2 * e];
+            t[e] = col[(i + 2 * e) * ld];
+          }
 #pragma unroll
-            for (int e = 0; e < 4; ++e) {
-              const int ie = i0 + 2 * e;
-              if (ie < n && ie != k) {
-                t[e] = cfms(f[e], u, t[e]);
-                S[ie * ld + j] = t[e];
-                if (cand && ie > k && cabs1(t[e]) > bb) { bb = cabs1(t[e]); br = ie; bv = t[e]; }
-              }
-            }
+          for (int e = 0; e < 4; ++e) {
+            t[e] = cfms(f[e], u, t[e]);
+            col[(i + 2 * e) * ld] = t[e];
           }
-        } else {
-          for (int i = g; i < n; i += 2) {
-            if (i == k) continue;
-            const float2 t = cmul(colk[i], u);
-            S[i * ld + k] = make_float2(-t.x, -t.y);
+          if (cand) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e)
+              if (i + 2 * e > k && cabs1(t[e]) > bb) { bb = cabs1(t[e]); br = i + 2 * e; bv = t[e]; }
           }
+        }
+        for (; i < n; i += 2) {
+          const float2 t = cfms(colk[i], u, col[i * ld]);
+          col[i * ld] = t;
+          if (cand && i > k && cabs1(t) > bb) { bb = cabs1(t); br = i; bv = t; }
         }
         if (cand) { sh.pabs[g] = bb; sh.prow[g] = br; sh.pval[g] = bv; }
       }
@@ -244,9 +252,14 @@ bse_gj_ir_kernel(Dims dm, int ch0, int nch, const float2* __restrict__ ghi, cons
         for (int e = 0; e < 4; ++e) sr[e] = lr[e] = si[e] = li[e] = 0.f;
         for (int k = 0; k < n; ++k) {
           const float2 gh = __ldg(GTh + (size_t)k * n + j), gl = __ldg(GTl + (size_t)k * n + j);
-#pragma unroll
-          for (int e = 0; e < 4; ++e)
-            cdf_fma(sr[e], lr[e], si[e], li[e], gh, gl, Zh[k * kGjNc + 4 * g + e], Zl[k * kGjNc + 4 * g + e]);
+          const float4 h01 = *reinterpret_cast<const float4*>(Zh + k * kGjNc + 4 * g);
+          const float4 h23 = *reinterpret_cast<const float4*>(Zh + k * kGjNc + 4 * g + 2);
+          const float4 l01 = *reinterpret_cast<const float4*>(Zl + k * kGjNc + 4 * g);
+          const float4 l23 = *reinterpret_cast<const float4*>(Zl + k * kGjNc + 4 * g + 2);
+          cdf_fma(sr[0], lr[0], si[0], li[0], gh, gl, make_float2(h01.x, h01.y), make_float2(l01.x, l01.y));
+          cdf_fma(sr[1], lr[1], si[1], li[1], gh, gl, make_float2(h01.z, h01.w), make_float2(l01.z, l01.w));
+          cdf_fma(sr[2], lr[2], si[2], li[2], gh, gl, make_float2(h23.x, h23.y), make_float2(l23.x, l23.y));
+          cdf_fma(sr[3], lr[3], si[3], li[3], gh, gl, make_float2(h23.z, h23.w), make_float2(l23.z, l23.w));
         }
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
