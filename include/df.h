@@ -261,8 +261,9 @@ typedef struct df_point {
 
 typedef struct df_batch df_batch;
 
-/* precision: DF_FP64 for every point, or DF_FP32_IR (points with n_w <= 64
- * mixed, larger ones FP64).  tol > 0: a point stops once its residual
+/* precision: DF_FP64 for every point, or DF_FP32_IR for every point (n_w <= 64
+ * by the register-tile kernel, larger orders by the shared-memory Gauss-Jordan
+ * one).  tol > 0: a point stops once its residual
  * r <= tol.  stream may be NULL (the batch then creates its own). */
 df_status df_batch_init(df_batch** out, int npts, const df_point* pts, int precision, double mix, double tol,
                         void* stream);

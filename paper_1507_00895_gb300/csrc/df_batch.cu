@@ -20,6 +20,7 @@
 #include "df_bse_dev.cuh"
 #include "df_fft_dev.cuh"
 #include "df_mixed_dev.cuh"
+#include "df_mixed_large_dev.cuh"
 
 namespace df {
 
@@ -30,7 +31,7 @@ struct PointDev {
   int active;    // 1 until converged
   double mix, tol, resid;
   double2 *g, *delta, *gam, *gg, *g0, *gk, *gr, *chi, *kc, *prod, *sigma;
-  float2 *gam_hi, *gam_lo, *gg_hi, *gg_lo;   // mixed: FP32 (hi, lo) of gam and gg
+  float2 *gam_hi, *gam_lo, *gg_hi, *gg_lo;   // mixed: FP32 (hi, lo) of gam and gg (orders > 64: of gam^T)
   unsigned char* gdig;                         // mixed, n_pad 32 / 64: gamma's digits
   double* red;   // [2 n_w + 4]
   int* flags;    // [4]
@@ -123,9 +124,11 @@ __global__ void batch_setup_elem_kernel(const PointDev* __restrict__ pts, int p)
       float hx = (float)v.x, hy = (float)v.y;
       P.gam_hi[idx] = make_float2(hx, hy);
       P.gam_lo[idx] = make_float2((float)(v.x - (double)hx), (float)(v.y - (double)hy));
-      hx = (float)w.x; hy = (float)w.y;
+      // orders > 64 keep gamma^T's words in these slots (the large-order kernel's residual)
+      const double2 t = mixed_pad(n) > 64 ? G[j * n + i] : w;
+      hx = (float)t.x; hy = (float)t.y;
       P.gg_hi[idx] = make_float2(hx, hy);
-      P.gg_lo[idx] = make_float2((float)(w.x - (double)hx), (float)(w.y - (double)hy));
+      P.gg_lo[idx] = make_float2((float)(t.x - (double)hx), (float)(t.y - (double)hy));
     }
   }
   if (P.gdig)
@@ -224,6 +227,37 @@ batch_bse_mixed_kernel(const PointDev* __restrict__ pts, const int* __restrict__
     }
   }
   if constexpr (use_umma_residual(NP)) tc05_teardown(tc);
+}
+
+// mixed ladders of order 64 < n <= 128 (the shared-memory Gauss-Jordan body),
+// 256 threads, the same chunked queue over the class's cost-sorted points
+__global__ void __launch_bounds__(256, 1)
+batch_bse_gj_kernel(const PointDev* __restrict__ pts, const int* __restrict__ order, const long* __restrict__ start,
+                    int nseg, int chunk, unsigned long long* __restrict__ counter) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ GjShared sh;
+  __shared__ unsigned long long item_s;
+  const long total = start[nseg];
+  for (;;) {
+    if (threadIdx.x == 0) item_s = atomicAdd(counter, (unsigned long long)chunk);
+    __syncthreads();
+    const long item = (long)item_s;
+    __syncthreads();
+    if (item >= total) break;
+    const long end = min(item + (long)chunk, total);
+    for (long s = item; s < end; ++s) {
+      const int k = find_segment(start, nseg, s);
+      const PointDev& P = pts[order[k]];
+      if (!P.active) continue;
+      const Dims& dm = P.dm;
+      const long local = s - start[k];
+      const long per_ch = (long)dm.nb * dm.N;
+      const int c = (int)(local / per_ch);
+      const int rem = (int)(local - (long)c * per_ch);
+      const int a = rem / dm.N, q = rem - a * dm.N;
+      gj_ir_system(dm, c, a, q, P.gam_hi, P.gam_lo, P.gg_hi, P.gg_lo, P.gg, P.chi, P.kc, P.flags, smraw, sh);
+    }
+  }
 }
 
 }  // namespace df
@@ -334,6 +368,9 @@ df_status record_pass(df_batch* b) {
     if (!g.mixed) {
       batch_bse_f64_kernel<<<g.grid, kBseThreads, g.smem, s>>>(b->d_pts, g.d_order, g.d_start, g.nseg, b->chunk,
                                                                b->d_counters + g.counter_slot, b->ws, b->ws_stride);
+    } else if (g.np > 64) {
+      batch_bse_gj_kernel<<<g.grid, g.threads, g.smem, s>>>(b->d_pts, g.d_order, g.d_start, g.nseg, b->chunk,
+                                                            b->d_counters + g.counter_slot);
     } else {
       mixed_kernel_of(g.np)<<<g.grid, g.threads, g.smem, s>>>(b->d_pts, g.d_order, g.d_start, g.nseg, b->chunk,
                                                               b->d_counters + g.counter_slot);
@@ -377,7 +414,16 @@ df_status configure_groups(df_batch* b) {
   // mixed classes share one kernel, whose shared-memory limit is set once to
   // the largest class
   for (auto& g : b->groups) {
-    if (g.mixed) {
+    if (g.mixed && g.np > 64) {
+      g.threads = 256;
+      g.smem = (size_t)gj_layout(kGjMaxN).total;       // the largest order's layout serves every order
+      B_CUDA(b, cudaFuncSetAttribute((const void*)batch_bse_gj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)g.smem),
+             "large-order mixed smem attribute");
+      int per = 0;
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, batch_bse_gj_kernel, g.threads, g.smem);
+      g.grid = b->sms * std::max(1, per);
+    } else if (g.mixed) {
       g.threads = mixed_block_threads(g.np);
       g.smem = sizeof(float2) * (size_t)mixed_layout(g.np).total;
       B_CUDA(b, cudaFuncSetAttribute((const void*)mixed_kernel_of(g.np), cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -477,7 +523,7 @@ df_status df_batch_init(df_batch** out, int npts, const df_point* pts, int preci
     dm.mu = q.mu;
     dm.t = q.t;
     dm.tp = q.tp;
-    P.mixed = (precision == DF_FP32_IR && mixed_np_of(q.n_w) <= 64) ? 1 : 0;
+    P.mixed = (precision == DF_FP32_IR && mixed_np_of(q.n_w) <= kGjMaxN) ? 1 : 0;
     P.active = 1;
     P.mix = mix;
     P.tol = tol;
@@ -617,8 +663,8 @@ df_status df_batch_init(df_batch** out, int npts, const df_point* pts, int preci
       return b->host_pts[x].dm.n_w > b->host_pts[y].dm.n_w;   // largest ladders first
     });
     LadderGroup f64;
-    std::vector<LadderGroup> mixed_groups(5);
-    for (int k = 0; k < 5; ++k) {
+    std::vector<LadderGroup> mixed_groups(6);   // padded orders 4 .. 128
+    for (int k = 0; k < 6; ++k) {
       mixed_groups[k].mixed = true;
       mixed_groups[k].np = 4 << k;
     }
@@ -632,7 +678,7 @@ df_status df_batch_init(df_batch** out, int npts, const df_point* pts, int preci
       }
     }
     if (!f64.order.empty()) b->groups.push_back(f64);
-    for (int k = 4; k >= 0; --k)
+    for (int k = 5; k >= 0; --k)
       if (!mixed_groups[k].order.empty()) b->groups.push_back(mixed_groups[k]);
     for (size_t gi = 0; gi < b->groups.size(); ++gi) {
       LadderGroup& g = b->groups[gi];

@@ -495,9 +495,8 @@ def warmstart_sigma(d: "DualFermion", y, mean, sd, kmap):
 
 
 def mixed_supported(n_w: int) -> bool:
-    """DF_FP32_IR on a single handle: every ladder order the handle takes (n_w <= 64 with
-    [D | RHS] in registers, up to 128 by the shared-memory Gauss-Jordan kernel).  The
-    batch runs its points above n_w = 64 in FP64."""
+    """DF_FP32_IR covers every ladder order a handle or a batch takes: n_w <= 64 with
+    [D | RHS] in registers, up to 128 by the shared-memory Gauss-Jordan kernel."""
     return 2 <= n_w <= 128
 
 

@@ -75,6 +75,19 @@ def test_batch_mixed_matches_oracle(df):
             assert nrel(b.get_sigma(i), st.sigma) < 1e-8, (i, w.name)
 
 
+def test_batch_mixed_large_orders(df):
+    # DF_FP32_IR points above n_w = 64 (the Gauss-Jordan class) beside a register-tile one
+    ws = [I.workload("cubic16_crit", nk=4, n_w=96, m_max=1),
+          I.workload("square16_b5", nk=4, n_w=66, m_max=0),
+          I.workload("paper_u20", nk=4, n_w=128, m_max=0),
+          I.workload("paper_u20", nk=8, n_w=16, m_max=1)]
+    with df.DualFermionBatch(ws, precision=df.DF_FP32_IR) as b:
+        b.iterate(1)
+        for i, w in enumerate(ws):
+            st = O.run_workload(w, n_iter=1)
+            assert nrel(b.get_sigma(i), st.sigma) < 1e-8, (i, w.name)
+
+
 def test_batch_convergence_flags_freeze_points(df):
     # the paper's Example I inputs converge; the 32^2-like point does not
     conv = I.workload("paper_u20", nk=8, n_w=16, m_max=1)
