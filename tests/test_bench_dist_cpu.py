@@ -66,3 +66,17 @@ def test_reference_arm_is_rank_zero_only(monkeypatch, capsys):
     args = bench.argparse.Namespace(gpus=2, steps=1, warmup=3, impl="reference")
     assert bench.run_reference(args) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_oracle_baseline_over_all_host_cores():
+    # the oracle's pass with its bosonic planes in a spawned process pool runs
+    # (no GPU involved) and reports the workers it used
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_1507_00895_gb300 import inputs as I
+    w = I.workload("paper_u20", nk=4, n_w=8, m_max=2)
+    r = bench.cpu_baseline(w)
+    assert r["kind"] == "oracle" and r["value"] > 0
+    a = r["all_cores"]
+    assert "unavailable" not in a, a
+    assert a["value"] > 0 and 1 <= a["cores"] <= min(os.cpu_count() or 1, w.n_bos)
