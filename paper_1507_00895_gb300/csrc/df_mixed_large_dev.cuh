@@ -47,6 +47,49 @@ __device__ __forceinline__ float2 gj_cinv(float2 z) {   // 1/z in FP32 (|z|^2 in
   return make_float2(z.x * d, -z.y * d);
 }
 
+// Packed FP32 pairs (the sm_100+ f32x2 instructions, round to nearest like
+// their scalar forms): the real and imaginary halves of the double-float
+// residual take one instruction each step.
+__device__ __forceinline__ float2 x2_fma(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+      "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;}"
+      : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+__device__ __forceinline__ float2 x2_add(float2 a, float2 b) {
+  float2 d;
+  asm("{.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;}"
+      : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 x2_sub(float2 a, float2 b) {
+  float2 d;
+  asm("{.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "sub.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;}"
+      : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+__device__ __forceinline__ float2 x2_mul(float2 a, float2 b) {
+  float2 d;
+  asm("{.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;}"
+      : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return d;
+}
+// (S, L) += A o B exactly, elementwise: the product's rounding error by FMA
+// (nA = -A gives p - A B = -error), the sum's by TwoSum
+__device__ __forceinline__ void x2_acc(float2& S, float2& L, float2 A, float2 nA, float2 B) {
+  const float2 p = x2_mul(A, B);
+  const float2 ne = x2_fma(nA, B, p);
+  const float2 s = x2_add(S, p);
+  const float2 bb = x2_sub(s, S);
+  const float2 e = x2_add(x2_sub(S, x2_sub(s, bb)), x2_sub(p, bb));
+  S = s;
+  L = x2_sub(x2_add(L, e), ne);
+}
+
 // ghi, glo: gamma's (hi, lo) FP32 words [2][nb][n][n]; gth, gtl: gamma^T's;
 // gg: gamma o gamma^T (FP64); chi: chi~ [nb][n][N]; kc: the Eq. sd bracket
 // [2][nb][n][N]; flags bit 0: a zero FP32 pivot
@@ -210,31 +253,50 @@ __device__ __forceinline__ void gj_ir_system(const Dims& dm, int c, int a, int q
     }
     __syncthreads();
     if (act) {                                        // R = gamma - Y + gamma Z, double-float
-      float sr[4], lr[4], si[4], li[4];
+      // per column two packed accumulators: S (re, im) takes gamma_re * Z and
+      // the trailing-word terms with gamma_re; S2 (im, re), swapped, takes
+      // gamma_im * Z, so that Z's words are used in their stored order
+      float2 S1[4], L1[4], S2[4], L2[4];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) sr[e] = lr[e] = si[e] = li[e] = 0.f;
+      for (int e = 0; e < 4; ++e) S1[e] = L1[e] = S2[e] = L2[e] = make_float2(0.f, 0.f);
       for (int k = 0; k < n; ++k) {
         const float2 gh = __ldg(GTh + (size_t)k * n + j), gl = __ldg(GTl + (size_t)k * n + j);
+        const float2 A1 = make_float2(gh.x, gh.x), nA1 = make_float2(-gh.x, -gh.x);
+        const float2 A2 = make_float2(gh.y, -gh.y), nA2 = make_float2(-gh.y, gh.y);
+        const float2 AL1 = make_float2(gl.x, gl.x), AL2 = make_float2(gl.y, -gl.y);
         const float4 h01 = *reinterpret_cast<const float4*>(Zh + k * kGjNc + 4 * g);
         const float4 h23 = *reinterpret_cast<const float4*>(Zh + k * kGjNc + 4 * g + 2);
         const float4 l01 = *reinterpret_cast<const float4*>(Zl + k * kGjNc + 4 * g);
         const float4 l23 = *reinterpret_cast<const float4*>(Zl + k * kGjNc + 4 * g + 2);
-        cdf_fma(sr[0], lr[0], si[0], li[0], gh, gl, make_float2(h01.x, h01.y), make_float2(l01.x, l01.y));
-        cdf_fma(sr[1], lr[1], si[1], li[1], gh, gl, make_float2(h01.z, h01.w), make_float2(l01.z, l01.w));
-        cdf_fma(sr[2], lr[2], si[2], li[2], gh, gl, make_float2(h23.x, h23.y), make_float2(l23.x, l23.y));
-        cdf_fma(sr[3], lr[3], si[3], li[3], gh, gl, make_float2(h23.z, h23.w), make_float2(l23.z, l23.w));
+        const float2 Bh[4] = {make_float2(h01.x, h01.y), make_float2(h01.z, h01.w), make_float2(h23.x, h23.y),
+                              make_float2(h23.z, h23.w)};
+        const float2 Bl[4] = {make_float2(l01.x, l01.y), make_float2(l01.z, l01.w), make_float2(l23.x, l23.y),
+                              make_float2(l23.z, l23.w)};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          x2_acc(S1[e], L1[e], A1, nA1, Bh[e]);
+          x2_acc(S2[e], L2[e], A2, nA2, Bh[e]);
+          L1[e] = x2_fma(AL1, Bh[e], x2_fma(A1, Bl[e], L1[e]));
+          L2[e] = x2_fma(AL2, Bh[e], x2_fma(A2, Bl[e], L2[e]));
+        }
       }
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const int jj = 4 * g + e;
         if (jj < w) {
+          // re = S1.x + S2.y, im = S1.y + S2.x, each a double-float sum
+          float sr, lr, si, li;
+          two_sum(S1[e].x, S2[e].y, sr, lr);
+          lr += L1[e].x + L2[e].y;
+          two_sum(S1[e].y, S2[e].x, si, li);
+          li += L1[e].y + L2[e].x;
           const float2 gh = __ldg(GTh + (size_t)(j0 + jj) * n + j), gl = __ldg(GTl + (size_t)(j0 + jj) * n + j);
           const float2 y = Y[j * kGjNc + jj];
           float s, e1;
-          two_sum(sr[e], gh.x, s, e1);
-          const float rx = (s - y.x) + (e1 + lr[e] + gl.x);
-          two_sum(si[e], gh.y, s, e1);
-          const float ry = (s - y.y) + (e1 + li[e] + gl.y);
+          two_sum(sr, gh.x, s, e1);
+          const float rx = (s - y.x) + (e1 + lr + gl.x);
+          two_sum(si, gh.y, s, e1);
+          const float ry = (s - y.y) + (e1 + li + gl.y);
           B[j * kGjNc + jj] = make_float2(rx, ry);
         }
       }
