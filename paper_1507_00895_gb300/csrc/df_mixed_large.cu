@@ -13,7 +13,7 @@
 //      pivot candidates during column k's update.
 //   3. Right-hand sides in chunks of 8 columns j:
 //        Y = S (P gamma)                       FP32 product, n^2 per column
-//        R = gamma - Y + gamma (chi~ o Y)      double-float, n^2 per column
+//        R = gamma - Y + gamma (chi~ o Y)      double-float (packed f32x2), n^2 per column
 //        Gamma_jj = Y_jj + (S (P R))_jj        one row of S: n per column
 //      (D Y = Y - gamma diag(chi~) Y; D^-1 R = S (P R)).  One correction: the
 //      error left is ~(cond(D) 2^-24)^2 plus cond(D) times the double-float
