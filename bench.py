@@ -39,14 +39,23 @@ WORKLOAD = "square32_tp"
 WORKLOAD_DESC = ("2D 32x32 square lattice, t=1, t'=-0.2, U=4, beta=10, mu(atom n=0.9), "
                  "n_w=64, N_W=15 (W=-7..7), atomic vertex + symmetric Gaussian 0.05U (seed 2)")
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# FP64 CUDA-core peak of the GB300: 152 SMs x 2 FP64 FMA/clock/SM x 2 flop x 2.07 GHz
-FP64_PEAK_GFLOPS = 152 * 2 * 2 * 2.07
-# FP32 CUDA-core peak: 152 SMs x 128 FP32 FMA/clock/SM x 2 flop x 2.07 GHz
-FP32_PEAK_GFLOPS = 152 * 128 * 2 * 2.07
 FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) per launch of the ladder kernel from one ncu capture
 # of that kernel on this workload (None once the kernel changes)
-NCU_TRAFFIC = {"bse_f64_kernel": 33274112, "bse_mixed_kernel": 19808512}
+NCU_TRAFFIC = {"bse_f64_kernel": None, "bse_mixed_kernel": None}
+# tensor-pipe share of the mixed ladder kernel's cycles (ncu sm__pipe_tensor_cycles_active,
+# the committed profile of the same kernel; None once the kernel changes)
+NCU_TENSOR_PIPE = {"bse_mixed_kernel": None}
+
+
+def measured_alu_peaks(df):
+    """FP32 and FP64 peaks of this GPU, measured now by libdf's FMA-loop probe
+    (df_peak_probe): FP32 = the faster of scalar and packed f32x2 fma."""
+    p32 = max(df.peak_probe(0), df.peak_probe(1))
+    p64 = df.peak_probe(2)
+    return {"fp32_gflops": p32, "fp64_gflops": p64,
+            "source": "df_peak_probe in this run: FMA loop, 8 independent chains per thread, 8 x 256 "
+                      "threads per SM, best of 5 launches"}
 
 
 def dist_env():
@@ -562,6 +571,11 @@ def run_ours(args):
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     n = w.n_w
     systems_per_launch = w.n_bos * w.N               # one channel per launch
+    peaks = measured_alu_peaks(df)
+    # algorithmic work of one ladder for diag Gamma: LU n^3/3 + forward substitution with n
+    # right-hand sides n^3/2 + back substitution truncated at row j for column j n^3/6
+    # = n^3 complex multiply-adds = 8 n^3 real flops (full back substitutions: 10.67 n^3)
+    algo_flop = 8.0 * n ** 3
 
     def measure(prec):
         d = df.DualFermion.from_workload(w, precision=prec, eig_mode=1, stream=stream.cuda_stream)
@@ -601,28 +615,31 @@ def run_ours(args):
         ms = max_over_ranks(sum(step_ms) / len(step_ms), world)
         bse_ms, bse_launches = timing["bse"]
         bse_avg_s = bse_ms / max(1, bse_launches) * 1e-3
+        achieved = systems_per_launch * algo_flop / bse_avg_s / 1e9
+        flop_model = ("algorithmic: 8 n^3 real flops per ladder (diag Gamma by LU: n^3/3 + n^3/2 + n^3/6 "
+                      "complex multiply-adds); full back substitutions would count 10.67 n^3")
         if prec == df.DF_FP64:
-            flop = 8.0 * n ** 3       # LU n^3/3 + forward n^3/2 + truncated back n^3/6 complex MACs
-            achieved = systems_per_launch * flop / bse_avg_s / 1e9
-            roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_GFLOPS, "unit": "GFLOP/s",
-                    "frac": achieved / FP64_PEAK_GFLOPS, "traffic": NCU_TRAFFIC.get("bse_f64_kernel"),
-                    "kernel": "bse_f64_kernel",
-                    "peak_source": "FP64 CUDA cores: 152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz (nominal 1.25 TF/s; "
-                                   "1.20 TF/s measured by an FMA loop)",
-                    "flop_per_launch": systems_per_launch * flop, "launch_ms": bse_avg_s * 1e3}
+            pk = peaks["fp64_gflops"]
+            roof = {"bound": "alu", "achieved": achieved, "peak": pk, "unit": "GFLOP/s", "frac": achieved / pk,
+                    "traffic": NCU_TRAFFIC.get("bse_f64_kernel"), "kernel": "bse_f64_kernel",
+                    "peak_source": "FP64 pipe, " + peaks["source"], "flop_model": flop_model,
+                    "flop_per_launch": systems_per_launch * algo_flop,
+                    "issued_flop_per_launch": systems_per_launch * algo_flop, "launch_ms": bse_avg_s * 1e3}
         else:
-            # FP32 Gauss-Jordan sweep of [D | gamma] (2 n^3 complex MACs) plus the
-            # residual product gamma Y (n^3 complex MACs, on the tensor cores)
-            flop = 8.0 * 2.0 * n ** 3 + 8.0 * n ** 3
-            achieved = systems_per_launch * flop / bse_avg_s / 1e9
-            roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_GFLOPS, "unit": "GFLOP/s",
-                    "frac": achieved / FP32_PEAK_GFLOPS, "traffic": NCU_TRAFFIC.get("bse_mixed_kernel"),
-                    "kernel": "bse_mixed_kernel",
-                    "peak_source": "FP32 CUDA cores: 152 SM x 128 FMA/clk x 2 flop x 2.07 GHz "
-                                   "(75.2 TF/s measured by an FMA loop); the residual's n^3 complex MACs "
-                                   "count once each here but run as 36 bf16 digit-pair products on the "
-                                   "tensor cores (tcgen05, TMEM accumulators)",
-                    "flop_per_launch": systems_per_launch * flop, "launch_ms": bse_avg_s * 1e3}
+            pk = peaks["fp32_gflops"]
+            # issued: the FP32 Gauss-Jordan sweep of [D | gamma] (2 n^3 complex MACs) plus the
+            # residual product gamma Y (n^3 complex MACs, as exact bf16 digit products on tcgen05)
+            issued = 8.0 * 3.0 * n ** 3
+            roof = {"bound": "alu", "achieved": achieved, "peak": pk, "unit": "GFLOP/s", "frac": achieved / pk,
+                    "traffic": NCU_TRAFFIC.get("bse_mixed_kernel"), "kernel": "bse_mixed_kernel",
+                    "peak_source": "FP32 pipe, " + peaks["source"], "flop_model": flop_model,
+                    "flop_per_launch": systems_per_launch * algo_flop,
+                    "issued_flop_per_launch": systems_per_launch * issued, "launch_ms": bse_avg_s * 1e3,
+                    "tensor_pipe_frac": NCU_TENSOR_PIPE.get("bse_mixed_kernel")}
+        if prec != df.DF_FP64:
+            worst, back = d.ladder_stats()
+            roof["ladder_error_control"] = {"worst_rho2_last_step": worst, "handed_back_to_fp64": back,
+                                            "ladders": 2 * systems_per_launch}
         res = {"value": whole_job_rate(points, world, ms * 1e-3), "ms_per_step": ms, "roofline": roof,
                "gpu_launches": sum(v[1] for v in timing.values()),
                "kernel_ms_per_step": {k: v[0] / args.steps for k, v in timing.items()},
@@ -682,9 +699,10 @@ def run_ours(args):
     ttc = None
     if rank == 0 and not args.no_ttc:
         ttc = time_to_converged(df, I, torch)
-    batch = None
+    batch = batch_full = None
     if rank == 0 and not args.no_batch:
-        batch = batch_bench(df, I, torch, args.batch_full)
+        batch = batch_bench(df, I, torch, False)
+        batch_full = batch_bench(df, I, torch, True)
     sweeps = None
     if rank == 0 and not args.no_sweeps:
         sweeps = example_i_bench(df)
@@ -713,14 +731,16 @@ def run_ours(args):
             "config": {"workload": WORKLOAD_DESC, "points_per_step": points,
                        "ladders_per_step": 2 * points, "ladder_order": n,
                        "precision": "fp64" if prec == df.DF_FP64 else
-                                    "FP32 LU + one double-float-residual correction (DF_FP32_IR)",
+                                    "FP32 Gauss-Jordan + one exact-residual correction, per-ladder error "
+                                    "control with FP64 re-solve (DF_FP32_IR)",
                        "eigen_check": "W=0, both channels, FP64", "step_start": "Sigma~=0",
                        "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas{world}"},
             "roofline": main["roofline"], "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": main["gpu_launches"], "kernel_ms_per_step": main["kernel_ms_per_step"],
             "err_vs_fp64_first_pass": main.get("err_vs_fp64_first_pass"),
             "plain_fp64": plain if prec != df.DF_FP64 else None,
-            "time_to_converged": ttc, "batch": batch, "warm_start": warm, "example_i": sweeps,
+            "time_to_converged": ttc, "batch": batch, "batch_full": batch_full, "warm_start": warm,
+            "example_i": sweeps, "alu_peaks": peaks,
             "observables": obs, "large_order": large, "clocks": main["clocks"]}
     print(json.dumps(line))
     if world > 1:
@@ -738,7 +758,6 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttc", action="store_true", help="skip the time-to-converged comparison")
     ap.add_argument("--no-batch", action="store_true", help="skip the uneven-batch throughput")
-    ap.add_argument("--batch-full", action="store_true", help="uneven batch at the recipe's full sizes")
     ap.add_argument("--no-warmstart", action="store_true", help="skip the learned warm-start measurement")
     ap.add_argument("--no-sweeps", action="store_true", help="skip the paper's Example I sweeps")
     ap.add_argument("--no-large", action="store_true",

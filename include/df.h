@@ -77,7 +77,10 @@ typedef enum df_precision {
   DF_FP32_IR = 1     /* ladder solves factorised in FP32 (complex64) and refined by
                         one correction with an extended-precision residual (n_w <= 64:
                         exact digit products on the tensor cores; 64 < n_w <= 128:
-                        double-float); Sigma~ within 1e-8 of the FP64 result.  Bubble,
+                        double-float).  Per ladder, rho = max|correction| / max|diag Gamma|
+                        predicts the error left (~rho^2 of diag Gamma's largest entry);
+                        a ladder with rho^2 > ladder_tol is solved again by the FP64 LU
+                        (ladder_fallback = 1) or reported (DF_ERR_REFINE_STALL).  Bubble,
                         Sigma~, Dyson stay FP64.  The susceptibilities' ladders
                         (n_w <= 64) refine to ir_tol */
 } df_precision;
@@ -109,6 +112,17 @@ typedef struct df_opts {
                        * evaluation Gamma <- gamma + gamma chi~ Gamma, K times from Gamma = gamma
                        * (the Neumann series to order K), the others the inversion; decided anew
                        * every pass.  K in [0, 16]; K >= 1 needs DF_FP64 and eig_mode 2. */
+  double ladder_tol;  /* DF_FP32_IR: the per-ladder bound on the predicted error rho^2 (see
+                       * DF_FP32_IR); default 1e-9, a tenth of the stated 1e-8; in (0, 1) */
+  int ladder_fallback;/* DF_FP32_IR: 1 (default) a ladder above ladder_tol is solved again by
+                       * the FP64 LU in the same df_bse; 0 its mixed result is kept and the
+                       * next df_sigma / df_iterate returns DF_ERR_REFINE_STALL */
+  int w_lo, w_hi;     /* the Omega split (several GPUs, one problem): this handle owns the
+                       * bosonic planes a in [w_lo, w_hi) (index a = m + m_max); default 0, 0
+                       * = all.  df_bubble and df_bse then cover only those planes and the
+                       * pass ends with df_sigma_partial + (caller's sum over handles) +
+                       * df_sigma_finish; df_sigma, df_iterate and df_susceptibility need
+                       * the full range.  0 <= w_lo < w_hi <= N_W, or both 0. */
 } df_opts;
 
 /* Fill *o with the defaults above (n_w, m_max set to 0: the caller sets them). */
@@ -162,6 +176,32 @@ df_status df_bse(df_ctx* c, int channel_mask);
  * If resid != NULL, synchronises and stores
  *     r = max|Sigma~_new - Sigma~_old| / max|Sigma~_new|. */
 df_status df_sigma(df_ctx* c, double* resid);
+
+/* The Omega split of Eq. sd.  Eq. sd's sum over (W, q) is a sum of independent
+ * per-plane terms, so handles that own disjoint bosonic ranges (opts.w_lo,
+ * w_hi; same inputs and Sigma~) can each run df_bubble and df_bse on their
+ * planes and then:
+ *   df_sigma_partial: out [n_w][N] complex = T/(2N) sum over this handle's W
+ *                     and all q of [...] G~ (the bracket of Eq. sd), before
+ *                     mixing and Dyson;
+ *   (the caller sums the partials of all handles, e.g. an all-reduce)
+ *   df_sigma_finish:  from the sum `total` [n_w][N]: mixing with the handle's
+ *                     Sigma~, the residual, Eq. dyson and G~(r) for the next
+ *                     pass, as the second half of df_sigma (resid as there).
+ * Pointers are device memory when *_is_device != 0 (asynchronous on the
+ * handle's stream), else host memory (the call synchronises).  On a
+ * full-range handle df_sigma_partial + df_sigma_finish equals df_sigma up to
+ * the rounding of the host round trip (none when the buffers are device
+ * memory).  Errors: DF_ERR_ARG, DF_ERR_CUDA; df_sigma_finish with resid !=
+ * NULL reports the ladder flags like df_sigma. */
+df_status df_sigma_partial(df_ctx* c, double* out, int out_is_device);
+df_status df_sigma_finish(df_ctx* c, const double* total, int in_is_device, double* resid);
+
+/* Error control of the last df_bse under DF_FP32_IR: worst_rho2 = the
+ * largest predicted error rho^2 over its ladders, handed_back = how many
+ * were solved again by the FP64 LU (ladder_fallback = 1).  Synchronises.
+ * DF_ERR_ARG under DF_FP64 (no mixed-precision ladders). */
+df_status df_get_ladder_stats(df_ctx* c, double* worst_rho2, int* handed_back);
 
 /* The self-consistency loop (the paper: repeat until G~ converges):
  * df_bubble, df_bse(both), df_sigma, up to max_iter times or until
@@ -341,7 +381,10 @@ df_status df_warmstart_sigma(df_ctx* c, const float* y, const float* mean, const
  * the last call's contents stay in it: calls that overlap on the GPU (two
  * streams, or two host threads) race and must be serialised by the caller.
  * An exactly singular ladder matrix gives undefined values for that system
- * and is not reported (df_bse reports it). */
+ * and is not reported (df_bse reports it).  It always solves Eq. lin_alg_inv
+ * by the plain inverse: the convergence-radius extension (opts.radius_order
+ * of a handle) is not applied, so ladders with |lambda| >= 1 differ from a
+ * df_bse with radius_order > 0. */
 df_status df_bse_noalloc(const double* gamma, const double* chi, int n_w, int n_bos, int n_k_total,
                          double* kernel, void* stream);
 
@@ -354,6 +397,17 @@ df_status df_bse_noalloc(const double* gamma, const double* chi, int n_w, int n_
  * Synchronous.  Errors: DF_ERR_ARG (spins < 1; no CUDA call is made),
  * DF_ERR_CUDA. */
 df_status df_selftest_wait(int arrive, int spins);
+
+/* Measured arithmetic peak of the current device, the denominator of the
+ * ladder kernels' roofline fractions (the paper has no counterpart: this is
+ * measurement support).  kind 0: FP32 fma.rn.f32, 1: FP32 packed
+ * fma.rn.f32x2 (two multiply-adds per instruction), 2: FP64 fma.rn.f64.
+ * Runs an FMA loop with 8 independent chains per thread over 8 blocks of
+ * 256 threads per SM, best of 5 timed launches after one warm-up launch;
+ * *gflops = 2 x multiply-adds / second / 1e9.  Synchronous, on the legacy
+ * default stream.  Errors: DF_ERR_ARG (NULL gflops or kind out of range),
+ * DF_ERR_OOM, DF_ERR_CUDA. */
+df_status df_peak_probe(int kind, double* gflops);
 
 const char* df_last_error(const df_ctx* c);
 const char* df_status_string(df_status s);

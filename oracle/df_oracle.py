@@ -332,6 +332,17 @@ def leading_eigenvalue(gamma_W: np.ndarray, chi_Wq: np.ndarray) -> complex:
 # Eq. sd
 # ---------------------------------------------------------------------------
 
+def susceptibility_bare_term(g_lat, n_w, m_max, beta, dim, nk) -> np.ndarray:
+    """The bare term of chi^{ch/sp}: -(T/N) sum_{w,k} G_{w,k} G_{w+W,k+q}, [N_W][N]
+    (the dual bubble of the lattice G, summed over the box frequencies)."""
+    return dual_bubble_fft(g_lat, n_w, m_max, beta, dim, nk).sum(axis=1)
+
+
+def susceptibility_ladder_term(lv: np.ndarray, Gam: np.ndarray) -> complex:
+    """sum_{w,w'} L_{W,w}(q) Gamma_{W,w,w'}(q) L_{W,w'}(q) for one (q, W): L^T Gamma L."""
+    return lv @ Gam @ lv
+
+
 def susceptibilities(g_ext, delta_ext, eps, sigma_box, gamma_d, gamma_m, n_w, m_max,
                      beta, dim, nk) -> np.ndarray:
     """Charge and spin susceptibilities (section "Resulting observables"), [2][N_W][N]
@@ -344,11 +355,14 @@ def susceptibilities(g_ext, delta_ext, eps, sigma_box, gamma_d, gamma_m, n_w, m_
     G from Eq. glat, frakG = G~ (G0~ + g) / G0~, Gamma = (1 - gamma chi~)^-1 gamma
     (Eq. lin_alg_inv) with chi~ the dual bubble of the same G~, w over the box.
     Reading: the printed k sums lack 1/N; both carry it here (per-site normalisation,
-    pinned by the flat-band limit in tests/test_oracle_pins.py).
+    pinned by the flat-band limit in tests/test_oracle_pins.py).  The steps are the
+    module-level functions lattice_planes_ext, susceptibility_bare_term,
+    dual_bubble_fft, ladder_gamma_full and susceptibility_ladder_term, looked up at
+    call time (the pin tests plant mistakes in them one at a time).
     """
     g_lat, frak = lattice_planes_ext(g_ext, delta_ext, eps, sigma_box, n_w, m_max)
     gt = dual_g(bare_dual_g(g_ext, delta_ext, eps), sigma_box, n_w, m_max)
-    chi0 = dual_bubble_fft(g_lat, n_w, m_max, beta, dim, nk).sum(axis=1)     # [N_W][N]
+    chi0 = susceptibility_bare_term(g_lat, n_w, m_max, beta, dim, nk)       # [N_W][N]
     L = dual_bubble_fft(frak, n_w, m_max, beta, dim, nk)                     # [N_W][n_w][N]
     chi_t = dual_bubble_fft(gt, n_w, m_max, beta, dim, nk)
     nb, N = chi0.shape
@@ -357,8 +371,7 @@ def susceptibilities(g_ext, delta_ext, eps, sigma_box, gamma_d, gamma_m, n_w, m_
         for a in range(nb):
             for q in range(N):
                 Gam = ladder_gamma_full(gam[a], chi_t[a, :, q])
-                lv = L[a, :, q]
-                out[c, a, q] = chi0[a, q] + lv @ Gam @ lv
+                out[c, a, q] = chi0[a, q] + susceptibility_ladder_term(L[a, :, q], Gam)
     return out
 
 

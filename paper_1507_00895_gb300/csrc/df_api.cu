@@ -125,6 +125,9 @@ cudaError_t run_lambda(df_ctx* c, int mask) {
 cudaError_t run_ladders(df_ctx* c, int mask) {
   cudaError_t e = cudaMemsetAsync(bse_flags(c), 0, sizeof(int) * 4, c->stream);
   if (e != cudaSuccess) return e;
+  // the mixed path's error-control words: worst rho^2 and the hand-back count
+  if (c->mixed_ws && (e = cudaMemsetAsync(mixed_check_words(c), 0, sizeof(unsigned) * 4, c->stream)) != cudaSuccess)
+    return e;
   if (c->opts.radius_order > 0) {
     if ((e = run_lambda(c, mask)) != cudaSuccess) return e;
     return run_bse(c, mask);
@@ -162,6 +165,10 @@ df_status df_default_opts(df_opts* o) {
   o->ir_max_steps = 8;
   o->ir_tol = 1e-13;
   o->radius_order = 0;
+  o->ladder_tol = 1e-9;
+  o->ladder_fallback = 1;
+  o->w_lo = 0;
+  o->w_hi = 0;
   return DF_OK;
 }
 
@@ -239,6 +246,13 @@ df_status df_init(df_ctx** out, const df_lattice* lat, double beta, double mu, d
   if (opts->ir_max_steps < 1 || opts->ir_max_steps > 64 || !(opts->ir_tol > 0.0 && opts->ir_tol < 1.0))
     return DF_ERR_ARG;
   if (opts->radius_order > 0 && (opts->precision != DF_FP64 || opts->eig_mode != 2)) return DF_ERR_ARG;
+  if (!(opts->ladder_tol > 0.0 && opts->ladder_tol < 1.0) || (opts->ladder_fallback != 0 && opts->ladder_fallback != 1))
+    return DF_ERR_ARG;
+  {
+    const int nbos = 2 * opts->m_max + 1;
+    const bool full = opts->w_lo == 0 && opts->w_hi == 0;
+    if (!full && !(opts->w_lo >= 0 && opts->w_lo < opts->w_hi && opts->w_hi <= nbos)) return DF_ERR_ARG;
+  }
   if (opts->precision == DF_FP32_IR && !mixed_supported(opts->n_w)) {
     fprintf(stderr, "libdf: DF_FP32_IR supports n_w <= 128\n");
     return DF_ERR_ARG;
@@ -257,6 +271,8 @@ df_status df_init(df_ctx** out, const df_lattice* lat, double beta, double mu, d
   dm.n_w = opts->n_w;
   dm.m_max = opts->m_max;
   dm.nb = 2 * opts->m_max + 1;
+  dm.a0 = opts->w_lo;
+  dm.na = (opts->w_hi > 0 ? opts->w_hi : dm.nb) - opts->w_lo;
   dm.ne = opts->n_w + 2 * opts->m_max;
   dm.beta = beta;
   dm.T = 1.0 / beta;
@@ -315,7 +331,9 @@ df_status df_init(df_ctx** out, const df_lattice* lat, double beta, double mu, d
     if ((ea = cudaMemsetAsync(c->sigma, 0, sizeof(double2) * dm.n_w * dm.N, c->stream)) != cudaSuccess ||
         (ea = cudaMemsetAsync(c->lam, 0, sizeof(double2) * 2 * dm.nb * dm.N, c->stream)) != cudaSuccess ||
         (ea = cudaMemsetAsync(c->lam_ok, 0xff, sizeof(int) * 2 * dm.nb * dm.N, c->stream)) != cudaSuccess ||
-        (ea = cudaMemsetAsync(c->red, 0, sizeof(double) * (2 * dm.n_w + 4), c->stream)) != cudaSuccess) {
+        (ea = cudaMemsetAsync(c->red, 0, sizeof(double) * (2 * dm.n_w + 4), c->stream)) != cudaSuccess ||
+        (ea = cudaMemsetAsync(c->chi, 0, sizeof(double2) * nchi, c->stream)) != cudaSuccess ||
+        (ea = cudaMemsetAsync(c->kc, 0, sizeof(double2) * 2 * nchi, c->stream)) != cudaSuccess) {
       st = fail(c, DF_ERR_CUDA, "cudaMemsetAsync", ea);
       goto bad;
     }
@@ -360,6 +378,9 @@ df_status df_bse(df_ctx* c, int channel_mask) {
 // errors carried in the ladder kernels' flags word
 static df_status flag_error(df_ctx* c, int flags) {
   if (flags & kFlagSingular) return fail(c, DF_ERR_SINGULAR, "exactly zero pivot in a ladder solve");
+  if (flags & kFlagRefine)
+    return fail(c, DF_ERR_REFINE_STALL,
+                "a mixed-precision ladder's predicted error exceeded ladder_tol (ladder_fallback = 0)");
   if (flags & kFlagTcTimeout)
     return fail(c, DF_ERR_TIMEOUT, "a tensor-core completion wait in the mixed ladder kernel gave up");
   if (flags & kFlagTcLayout)
@@ -380,9 +401,10 @@ df_status df_selftest_wait(int arrive, int spins) {
   return (h & kFlagTcTimeout) ? DF_ERR_TIMEOUT : DF_OK;
 }
 
-df_status df_sigma(df_ctx* c, double* resid) {
-  if (!c) return DF_ERR_ARG;
-  DF_CUDA(c, run_sigma(c), "dual self-energy (Eq. sd) + Dyson");
+static bool full_range(const df_ctx* c) { return c->dm.a0 == 0 && c->dm.na == c->dm.nb; }
+
+// the end of a pass: the residual and the ladder flags of the pass, if asked for
+static df_status finish_pass(df_ctx* c, double* resid) {
   ++c->iter_done;
   if (resid) {
     int flags = 0;
@@ -395,9 +417,59 @@ df_status df_sigma(df_ctx* c, double* resid) {
   return DF_OK;
 }
 
+df_status df_sigma_partial(df_ctx* c, double* out, int is_device) {
+  if (!c) return DF_ERR_ARG;
+  if (!out) return fail(c, DF_ERR_ARG, "output pointer is NULL");
+  const size_t bytes = sizeof(double2) * c->dm.n_w * c->dm.N;
+  // host output: staged in the lattice-observables buffer
+  double2* dst = is_device ? (double2*)out : c->lat;
+  DF_CUDA(c, launch_sigma_partial(c, dst), "partial dual self-energy (Eq. sd over the handle's planes)");
+  if (!is_device) return copy_out(c, out, c->lat, bytes, 0, "df_sigma_partial");
+  return DF_OK;
+}
+
+df_status df_sigma_finish(df_ctx* c, const double* total, int is_device, double* resid) {
+  if (!c) return DF_ERR_ARG;
+  if (!total) return fail(c, DF_ERR_ARG, "input pointer is NULL");
+  const size_t bytes = sizeof(double2) * c->dm.n_w * c->dm.N;
+  const double2* src = (const double2*)total;
+  if (!is_device) {
+    DF_CUDA(c, cudaMemcpyAsync(c->lat, total, bytes, cudaMemcpyHostToDevice, c->stream), "df_sigma_finish");
+    src = c->lat;
+  }
+  {
+    Timed t(c, DF_T_SIGMA, 2);
+    DF_CUDA(c, launch_sigma_finish(c, src, c->opts.mix), "mixing + Dyson (Eq. dyson) of the summed Eq. sd");
+  }
+  df_status s = finish_pass(c, resid);
+  if (s == DF_OK && !is_device && !resid) DF_CUDA(c, cudaStreamSynchronize(c->stream), "df_sigma_finish");
+  return s;
+}
+
+df_status df_get_ladder_stats(df_ctx* c, double* worst_rho2, int* handed_back) {
+  if (!c) return DF_ERR_ARG;
+  if (!c->mixed_ws) return fail(c, DF_ERR_ARG, "df_get_ladder_stats: the handle is not DF_FP32_IR");
+  unsigned h[4] = {0, 0, 0, 0};
+  DF_CUDA(c, cudaMemcpyAsync(h, mixed_check_words(c), sizeof h, cudaMemcpyDeviceToHost, c->stream), "ladder stats");
+  DF_CUDA(c, cudaStreamSynchronize(c->stream), "ladder stats");
+  float w;
+  memcpy(&w, &h[0], sizeof w);
+  if (worst_rho2) *worst_rho2 = (double)w;
+  if (handed_back) *handed_back = c->opts.ladder_fallback ? (int)h[2] : 0;
+  return DF_OK;
+}
+
+df_status df_sigma(df_ctx* c, double* resid) {
+  if (!c) return DF_ERR_ARG;
+  if (!full_range(c)) return fail(c, DF_ERR_ARG, "df_sigma needs the full bosonic range (use df_sigma_partial)");
+  DF_CUDA(c, run_sigma(c), "dual self-energy (Eq. sd) + Dyson");
+  return finish_pass(c, resid);
+}
+
 df_status df_iterate(df_ctx* c, int max_iter, double tol, int* iters_done, double* resid) {
   if (!c) return DF_ERR_ARG;
   if (max_iter < 0) return fail(c, DF_ERR_ARG, "max_iter < 0");
+  if (!full_range(c)) return fail(c, DF_ERR_ARG, "df_iterate needs the full bosonic range");
   double r = -1.0;
   int it = 0, flags = 0;
   for (; it < max_iter; ++it) {
@@ -459,6 +531,7 @@ df_status df_lattice_observables(df_ctx* c, double* sigma_lat, double* g_lat, in
 df_status df_susceptibility(df_ctx* c, double* out, int is_device) {
   if (!c) return DF_ERR_ARG;
   if (!out) return fail(c, DF_ERR_ARG, "output pointer is NULL");
+  if (!full_range(c)) return fail(c, DF_ERR_ARG, "df_susceptibility needs the full bosonic range");
   const Dims& dm = c->dm;
   const size_t plane = (size_t)dm.ne * dm.N, pw = (size_t)dm.nb * dm.n_w * dm.N, pq = (size_t)dm.nb * dm.N;
   if (!c->sus) {

@@ -24,6 +24,11 @@
 
 namespace df {
 
+// the batched mixed ladders run without the per-ladder hand-back list (a point's
+// ladders all take the mixed path; the single-problem kernels have the check)
+__device__ __forceinline__ MixedCheck no_check() { return MixedCheck{nullptr, nullptr, __int_as_float(0x7f800000)}; }
+
+
 struct PointDev {
   Dims dm;
   int nc;        // FP64 ladder right-hand-side chunk
@@ -222,7 +227,8 @@ batch_bse_mixed_kernel(const PointDev* __restrict__ pts, const int* __restrict__
         mixed_producer(sp, &tc);                      // warp 8: the tensor-core MMAs
       else
         bse_mixed_system<NP>(dm, c, a, q, P.gam, P.gam_hi, P.gam_lo, P.gg_hi, P.gg_lo, P.chi, P.kc, P.flags, sp,
-                             P.gdig ? P.gdig + (size_t)(c * dm.nb + a) * gdig_bytes(NP) : nullptr, key != cur, &tc);
+                             P.gdig ? P.gdig + (size_t)(c * dm.nb + a) * gdig_bytes(NP) : nullptr, key != cur, &tc,
+                             no_check());
       cur = key;
     }
   }
@@ -255,7 +261,8 @@ batch_bse_gj_kernel(const PointDev* __restrict__ pts, const int* __restrict__ or
       const int c = (int)(local / per_ch);
       const int rem = (int)(local - (long)c * per_ch);
       const int a = rem / dm.N, q = rem - a * dm.N;
-      gj_ir_system(dm, c, a, q, P.gam_hi, P.gam_lo, P.gg_hi, P.gg_lo, P.gg, P.chi, P.kc, P.flags, smraw, sh);
+      gj_ir_system(dm, c, a, q, P.gam_hi, P.gam_lo, P.gg_hi, P.gg_lo, P.gg, P.chi, P.kc, P.flags, smraw, sh,
+                   no_check());
     }
   }
 }
@@ -517,6 +524,8 @@ df_status df_batch_init(df_batch** out, int npts, const df_point* pts, int preci
     dm.n_w = q.n_w;
     dm.m_max = q.m_max;
     dm.nb = 2 * q.m_max + 1;
+    dm.a0 = 0;
+    dm.na = dm.nb;
     dm.ne = q.n_w + 2 * q.m_max;
     dm.beta = q.beta;
     dm.T = 1.0 / q.beta;

@@ -36,17 +36,30 @@ __global__ void __launch_bounds__(kBseThreads)
 bse_f64_kernel(Dims dm, int ch0, int nch, int nc, const double2* __restrict__ gam,
                const double2* __restrict__ gg, const double2* __restrict__ chi,
                double2* __restrict__ kc, double2* __restrict__ ws, int* __restrict__ flags, int radius_K,
-               const double2* __restrict__ lam) {
+               const double2* __restrict__ lam, const int* __restrict__ list) {
   extern __shared__ double2 sm[];
   __shared__ BseF64Shared sh;
-  const int n = dm.n_w, N = dm.N, nb = dm.nb;
+  const int n = dm.n_w, N = dm.N, nb = dm.nb, na = dm.na;
   const BseSmem L = bse_layout(n, nc, LU_SMEM);
   double2* LU = LU_SMEM ? sm + L.lu : ws + (size_t)blockIdx.x * n * n;
-  const long systems = (long)nch * nb * N;
-  for (long sys = blockIdx.x; sys < systems; sys += gridDim.x) {
-    const int c = ch0 + (int)(sys / ((long)nb * N));
-    const int rem = (int)(sys - (long)(c - ch0) * nb * N);
-    const int a = rem / N, q = rem - a * N;
+  // the handle's planes of channels ch0 .. ch0 + nch - 1, or with `list` the
+  // list[0] systems (c N_W + a) N + q that follow it (ladders the mixed-precision
+  // kernels handed back)
+  const long systems = list ? (long)list[0] : (long)nch * na * N;
+  for (long s = blockIdx.x; s < systems; s += gridDim.x) {
+    int c, a, q;
+    if (list) {
+      const long sys = list[1 + s];
+      c = (int)(sys / ((long)nb * N));
+      const int rem = (int)(sys - (long)c * nb * N);
+      a = rem / N;
+      q = rem - a * N;
+    } else {
+      c = ch0 + (int)(s / ((long)na * N));
+      const int rem = (int)(s - (long)(c - ch0) * na * N);
+      a = dm.a0 + rem / N;
+      q = rem - (a - dm.a0) * N;
+    }
     bse_f64_system(dm, c, a, q, nc, gam, gg, chi, kc, LU, sm + L.y, sm + L.xs, sm + L.invu, sh, flags, radius_K,
                    lam);
   }
@@ -1034,18 +1047,40 @@ cudaError_t launch_bse(df_ctx* c, int channel_mask) {
   const double2* lam = K > 0 ? c->lam : nullptr;
   for (int ch = 0; ch < 2; ++ch) {
     if (!(channel_mask & (1 << ch))) continue;
-    const long systems = (long)dm.nb * dm.N;
+    const long systems = (long)dm.na * dm.N;
     const int grid = (int)(systems < c->bse_grid ? systems : c->bse_grid);
     if (bse_lu_in_smem(n)) {
       bse_f64_kernel<true><<<grid, kBseThreads, smem, c->stream>>>(dm, ch, 1, nc, c->gam, gg_ptr(c), c->chi,
-                                                                   c->kc, nullptr, flag_ptr(c), K, lam);
+                                                                   c->kc, nullptr, flag_ptr(c), K, lam, nullptr);
     } else {
       bse_f64_kernel<false><<<grid, kBseThreads, smem, c->stream>>>(dm, ch, 1, nc, c->gam, gg_ptr(c), c->chi,
-                                                                    c->kc, lu_ws_ptr(c), flag_ptr(c), K, lam);
+                                                                    c->kc, lu_ws_ptr(c), flag_ptr(c), K, lam,
+                                                                    nullptr);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+// the FP64 LU over the ladders the mixed-precision kernels handed back: list[0]
+// (read on the device) systems (c N_W + a) N + q, on the persistent grid
+cudaError_t launch_bse_f64_list(df_ctx* c, const int* list) {
+  const Dims& dm = c->dm;
+  const int n = dm.n_w;
+  const int nc = bse_chunk(n);
+  const size_t smem = bse_smem_bytes(n);
+  cudaError_t e = cudaFuncSetAttribute(bse_lu_in_smem(n) ? (const void*)bse_f64_kernel<true>
+                                                         : (const void*)bse_f64_kernel<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  if (bse_lu_in_smem(n))
+    bse_f64_kernel<true><<<c->bse_grid, kBseThreads, smem, c->stream>>>(dm, 0, 2, nc, c->gam, gg_ptr(c), c->chi,
+                                                                        c->kc, nullptr, flag_ptr(c), 0, nullptr, list);
+  else
+    bse_f64_kernel<false><<<c->bse_grid, kBseThreads, smem, c->stream>>>(dm, 0, 2, nc, c->gam, gg_ptr(c), c->chi,
+                                                                         c->kc, lu_ws_ptr(c), flag_ptr(c), 0, nullptr,
+                                                                         list);
+  return cudaGetLastError();
 }
 
 // the ladder term of the susceptibilities for both channels: FP64 LU on the
@@ -1095,8 +1130,10 @@ cudaError_t launch_chi_ladder(df_ctx* c, const double2* Lb, const double2* chi0,
 cudaError_t launch_lambda(df_ctx* c, int channel_mask) {
   const Dims& dm = c->dm;
   if (c->opts.eig_mode == 0) return cudaSuccess;
-  const int a0 = (c->opts.eig_mode == 1) ? dm.m_max : 0;
-  const int na = (c->opts.eig_mode == 1) ? 1 : dm.nb;
+  // W = 0 only (eig_mode 1) or every plane, within the handle's bosonic range
+  if (c->opts.eig_mode == 1 && (dm.m_max < dm.a0 || dm.m_max >= dm.a0 + dm.na)) return cudaSuccess;
+  const int a0 = (c->opts.eig_mode == 1) ? dm.m_max : dm.a0;
+  const int na = (c->opts.eig_mode == 1) ? 1 : dm.na;
   const int qtiles = (dm.N + kEigQ - 1) / kEigQ;
   const int ch0 = (channel_mask & 1) ? 0 : 1;
   const int nch = (channel_mask & 1) && (channel_mask & 2) ? 2 : 1;
@@ -1152,7 +1189,7 @@ cudaError_t launch_bse_both_raw(const Dims& dm, const double2* gam, const double
   const long systems = 2L * dm.nb * dm.N;
   const int grid = (int)(systems < grid_max ? systems : grid_max);
   bse_f64_kernel<true><<<grid, kBseThreads, smem, stream>>>(dm, 0, 2, nc, gam, gg, chi, kc, nullptr, flags, 0,
-                                                            nullptr);
+                                                            nullptr, nullptr);
   return cudaGetLastError();
 }
 

@@ -29,7 +29,7 @@ dyson_ifft_kernel(Dims dm, int first, const double2* __restrict__ g0, const doub
 __global__ void __launch_bounds__(kFftThreads)
 bubble_kernel(Dims dm, const double2* __restrict__ gr, double2* __restrict__ chi) {
   extern __shared__ double2 sm[];
-  const int a = blockIdx.x / dm.n_w, i = blockIdx.x - a * dm.n_w;
+  const int b = blockIdx.x / dm.n_w, i = blockIdx.x - b * dm.n_w, a = dm.a0 + b;
   bubble_plane(dm, a, i, gr, chi, sm, sm + dm.nk / 2);
 }
 
@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(kFftThreads)
 sigma_prod_kernel(Dims dm, const double2* __restrict__ kc, const double2* __restrict__ gr,
                   double2* __restrict__ prod) {
   extern __shared__ double2 sm[];
-  const int a = blockIdx.x / dm.n_w, i = blockIdx.x - a * dm.n_w;
+  const int b = blockIdx.x / dm.n_w, i = blockIdx.x - b * dm.n_w, a = dm.a0 + b;
   sigma_prod_plane(dm, a, i, kc, gr, prod, sm, sm + dm.nk / 2);
 }
 
@@ -49,6 +49,34 @@ sigma_dyson_kernel(Dims dm, double mix, const double2* __restrict__ prod, const 
   __shared__ double red_sm[32];
   sigma_dyson_plane(dm, blockIdx.x, mix, prod, g0, sigma, gk, gr, red, sm, sm + dm.nk / 2,
                     sm + dm.nk / 2 + dm.N, red_sm);
+}
+
+// The Omega split: this problem's share of Eq. sd, out[i][k] = (T/2) FFT[sum over
+// its bosonic planes of prod[W][i]](k), before mixing and Dyson
+__global__ void __launch_bounds__(kFftThreads)
+sigma_partial_kernel(Dims dm, const double2* __restrict__ prod, double2* __restrict__ out) {
+  extern __shared__ double2 sm[];
+  const int i = blockIdx.x;
+  double2* s = sm + dm.nk / 2;
+  sigma_sum_plane(dm, i, prod, sm, s);
+  const double pref = 0.5 * dm.T;
+  for (int k = threadIdx.x; k < dm.N; k += blockDim.x) out[(size_t)i * dm.N + k] = cscale(s[k], pref);
+}
+
+// ... and the rest of the pass from the sum of every share: mixing, residual
+// partials, Eq. dyson, G~(r)
+__global__ void __launch_bounds__(kFftThreads)
+sigma_finish_kernel(Dims dm, double mix, const double2* __restrict__ total, const double2* __restrict__ g0,
+                    double2* __restrict__ sigma, double2* __restrict__ gk, double2* __restrict__ gr,
+                    double* __restrict__ red) {
+  extern __shared__ double2 sm[];
+  __shared__ double red_sm[32];
+  const int i = blockIdx.x;
+  double2* s = sm + dm.nk / 2;
+  load_twiddles(sm, dm.nk);
+  for (int k = threadIdx.x; k < dm.N; k += blockDim.x) s[k] = total[(size_t)i * dm.N + k];
+  __syncthreads();
+  sigma_finish_plane(dm, i, mix, 1.0, s, g0, sigma, gk, gr, red, sm, s + dm.N, red_sm);
 }
 
 // Section "Resulting observables", per box element (w, k): Eq. sigma_lat
@@ -148,7 +176,7 @@ cudaError_t launch_bubble(df_ctx* c) {
   const size_t sm = fft_smem(dm, 1);
   cudaError_t e = set_smem((const void*)bubble_kernel, sm);
   if (e != cudaSuccess) return e;
-  bubble_kernel<<<dm.nb * dm.n_w, kFftThreads, sm, c->stream>>>(dm, c->gr, c->chi);
+  bubble_kernel<<<dm.na * dm.n_w, kFftThreads, sm, c->stream>>>(dm, c->gr, c->chi);
   return cudaGetLastError();
 }
 
@@ -186,12 +214,37 @@ cudaError_t launch_obs_bubbles(df_ctx* c, double2* planes, double2* P, double2* 
   return cudaGetLastError();
 }
 
+// the Omega split: this problem's planes of Eq. sd into out [n_w][N] (device)
+cudaError_t launch_sigma_partial(df_ctx* c, double2* out) {
+  const Dims& dm = c->dm;
+  size_t sm = fft_smem(dm, 1);
+  cudaError_t e = set_smem((const void*)sigma_prod_kernel, sm);
+  if (e != cudaSuccess) return e;
+  sigma_prod_kernel<<<dm.na * dm.n_w, kFftThreads, sm, c->stream>>>(dm, c->kc, c->gr, c->prod);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = set_smem((const void*)sigma_partial_kernel, sm)) != cudaSuccess) return e;
+  sigma_partial_kernel<<<dm.n_w, kFftThreads, sm, c->stream>>>(dm, c->prod, out);
+  return cudaGetLastError();
+}
+
+// ... and the rest of the pass from the summed shares total [n_w][N] (device)
+cudaError_t launch_sigma_finish(df_ctx* c, const double2* total, double mix) {
+  const Dims& dm = c->dm;
+  const size_t sm = fft_smem(dm, 2);
+  cudaError_t e = set_smem((const void*)sigma_finish_kernel, sm);
+  if (e != cudaSuccess) return e;
+  sigma_finish_kernel<<<dm.n_w, kFftThreads, sm, c->stream>>>(dm, mix, total, c->g0, c->sigma, c->gk, c->gr, c->red);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  residual_reduce_kernel<<<1, kFftThreads, 0, c->stream>>>(dm.n_w, c->red);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_sigma(df_ctx* c, double mix) {
   const Dims& dm = c->dm;
   size_t sm = fft_smem(dm, 1);
   cudaError_t e = set_smem((const void*)sigma_prod_kernel, sm);
   if (e != cudaSuccess) return e;
-  sigma_prod_kernel<<<dm.nb * dm.n_w, kFftThreads, sm, c->stream>>>(dm, c->kc, c->gr, c->prod);
+  sigma_prod_kernel<<<dm.na * dm.n_w, kFftThreads, sm, c->stream>>>(dm, c->kc, c->gr, c->prod);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   sm = fft_smem(dm, 2);
   if ((e = set_smem((const void*)sigma_dyson_kernel, sm)) != cudaSuccess) return e;

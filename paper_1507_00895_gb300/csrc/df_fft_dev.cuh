@@ -111,25 +111,31 @@ __device__ __forceinline__ double block_max(double v, double* red_sm) {
   return v;
 }
 
-// Eq. sd, stage 2, fused with mixing, the residual partials and Eq. dyson,
-// for box frequency i: acc(r) = sum_W prod[W][i](r); Sigma~_new(k) =
-// (T/2) FFT[acc](k); Sigma~ <- mix new + (1-mix) old; G~ = 1/(1/G0~ - Sigma~);
-// G~(r) = IFFT[G~(k)] / N.  red[i], red[n_w + i] = max|dSigma~|, max|Sigma~|.
-__device__ __forceinline__ void sigma_dyson_plane(const Dims& dm, int i, double mix, const double2* __restrict__ prod,
-                                                  const double2* __restrict__ g0, double2* __restrict__ sigma,
-                                                  double2* __restrict__ gk, double2* __restrict__ gr,
-                                                  double* __restrict__ red, double2* tw, double2* s, double2* s2,
-                                                  double* red_sm) {
-  const int e = i + dm.m_max;
+// Eq. sd, stage 2a, box frequency i: acc(r) = sum_W prod[W][i](r) over the
+// problem's bosonic planes, s = FFT[acc] (natural order; the T/2 is applied by
+// the caller).  Loads the twiddles into tw.
+__device__ __forceinline__ void sigma_sum_plane(const Dims& dm, int i, const double2* __restrict__ prod, double2* tw,
+                                                double2* s) {
   load_twiddles(tw, dm.nk);
   for (int r = threadIdx.x; r < dm.N; r += blockDim.x) {
     double2 acc = mk(0.0, 0.0);
-    for (int a = 0; a < dm.nb; ++a) acc = acc + prod[((size_t)a * dm.n_w + i) * dm.N + r];
+    for (int a = dm.a0; a < dm.a0 + dm.na; ++a) acc = acc + prod[((size_t)a * dm.n_w + i) * dm.N + r];
     s[bitrev_axes(r, dm.D, dm.p)] = acc;
   }
   __syncthreads();
   fft_dit_smem(s, dm.D, dm.p, tw, false);
-  const double pref = 0.5 * dm.T;
+}
+
+// Eq. sd, stage 2b, fused with mixing, the residual partials and Eq. dyson,
+// for box frequency i: Sigma~_new(k) = pref s(k); Sigma~ <- mix new +
+// (1-mix) old; G~ = 1/(1/G0~ - Sigma~); G~(r) = IFFT[G~(k)] / N.
+// red[i], red[n_w + i] = max|dSigma~|, max|Sigma~|.  Needs the twiddles in tw.
+__device__ __forceinline__ void sigma_finish_plane(const Dims& dm, int i, double mix, double pref, const double2* s,
+                                                   const double2* __restrict__ g0, double2* __restrict__ sigma,
+                                                   double2* __restrict__ gk, double2* __restrict__ gr,
+                                                   double* __restrict__ red, const double2* tw, double2* s2,
+                                                   double* red_sm) {
+  const int e = i + dm.m_max;
   double dmax = 0.0, smax = 0.0;
   for (int k = threadIdx.x; k < dm.N; k += blockDim.x) {
     const size_t idx = (size_t)i * dm.N + k;
@@ -154,6 +160,16 @@ __device__ __forceinline__ void sigma_dyson_plane(const Dims& dm, int i, double 
   const double invN = 1.0 / (double)dm.N;
   for (int r = threadIdx.x; r < dm.N; r += blockDim.x) gr[(size_t)e * dm.N + r] = cscale(s2[r], invN);
   __syncthreads();
+}
+
+// Eq. sd (stages 2a and 2b) for box frequency i: Sigma~_new = (T/2) FFT[sum_W prod]
+__device__ __forceinline__ void sigma_dyson_plane(const Dims& dm, int i, double mix, const double2* __restrict__ prod,
+                                                  const double2* __restrict__ g0, double2* __restrict__ sigma,
+                                                  double2* __restrict__ gk, double2* __restrict__ gr,
+                                                  double* __restrict__ red, double2* tw, double2* s, double2* s2,
+                                                  double* red_sm) {
+  sigma_sum_plane(dm, i, prod, tw, s);
+  sigma_finish_plane(dm, i, mix, 0.5 * dm.T, s, g0, sigma, gk, gr, red, tw, s2, red_sm);
 }
 
 // max over red[0..n) and red[n..2n) into red[2n], red[2n+1] (one block)

@@ -18,6 +18,39 @@ constexpr int kFlagSingular = 1;    // an exactly zero pivot
 constexpr int kFlagRadius = 2;      // a ladder outside the radius of convergence
 constexpr int kFlagTcTimeout = 4;   // a bounded tensor-core completion wait gave up
 constexpr int kFlagTcLayout = 8;    // tensor-core operands not 1024-byte aligned (no MMA issued)
+constexpr int kFlagRefine = 16;     // a mixed-precision ladder missed its error bound and was not re-solved
+
+// Per-ladder error control of the mixed-precision ladder solves.  After the
+// one correction E of X0 ~ D^-1 gamma, rho = max_j |E_jj| / max_j |Gamma_jj|
+// (|re| + |im|) is the relative size of the correction; with a fixed FP32
+// factorisation each correction shrinks the error by about the same factor,
+// so the error left in diag Gamma is about rho^2 of its largest entry.  A
+// ladder with rho^2 above rho2_max (or a non-finite value) is appended to
+// the hand-back list (redo[0] = count, redo[1 + i] = (c N_W + a) N + q) for
+// the FP64 LU, or, without a list, flagged kFlagRefine.  worst receives the
+// call's largest rho^2 (float bits; non-negative floats order as integers).
+struct MixedCheck {
+  int* redo;
+  unsigned* worst;
+  float rho2_max;
+};
+
+__device__ __forceinline__ void mixed_check_ladder(const MixedCheck& mc, float emax, float gmax, bool finite,
+                                                   long sys, int* flags) {
+  float rho2;
+  if (!finite) rho2 = __int_as_float(0x7f800000);
+  else if (gmax > 0.f) rho2 = (emax / gmax) * (emax / gmax);
+  else rho2 = emax > 0.f ? __int_as_float(0x7f800000) : 0.f;
+  if (mc.worst) atomicMax(mc.worst, __float_as_uint(rho2));
+  if (!(rho2 <= mc.rho2_max)) {
+    if (mc.redo) {
+      const int i = atomicAdd(mc.redo, 1);
+      mc.redo[1 + i] = (int)sys;
+    } else {
+      atomicOr(flags, kFlagRefine);
+    }
+  }
+}
 
 // ---------------------------------------------------------------------------
 // complex arithmetic on double2 / float2 (x = real, y = imag)
@@ -153,6 +186,7 @@ __device__ void fft_dit_smem(C* s, int D, int p, const C* tw, bool inverse) {
 struct Dims {
   int D, nk, p, N;       // lattice
   int n_w, m_max, nb, ne;
+  int a0, na;            // the bosonic planes a0 .. a0 + na - 1 this problem owns (the Omega split)
   double beta, T, mu, t, tp;
 };
 
@@ -266,6 +300,8 @@ cudaError_t launch_wait_selftest(int arrive, unsigned spins, int* flags, cudaStr
 cudaError_t launch_dyson_ifft(df_ctx* c, int first_plane, int n_planes);
 cudaError_t launch_bubble(df_ctx* c);
 cudaError_t launch_sigma(df_ctx* c, double mix);
+cudaError_t launch_sigma_partial(df_ctx* c, double2* out);
+cudaError_t launch_sigma_finish(df_ctx* c, const double2* total, double mix);
 cudaError_t launch_gamma_gt(df_ctx* c);
 cudaError_t launch_bse(df_ctx* c, int channel_mask);
 cudaError_t launch_lambda(df_ctx* c, int channel_mask);
@@ -283,5 +319,8 @@ const double2* gamma_gt_ptr(df_ctx* c);   // gamma o gamma^T, written by launch_
 cudaError_t launch_bse_mixed(df_ctx* c, int channel_mask, int* flags);
 // orders 64 < n_w <= 128 (df_mixed_large.cu)
 cudaError_t launch_bse_mixed_large(df_ctx* c, int channel_mask, int* flags);
+MixedCheck mixed_check(df_ctx* c);
+unsigned* mixed_check_words(df_ctx* c);   // [0] worst rho^2, [2] hand-back count, [3 ..] list
+cudaError_t launch_bse_f64_list(df_ctx* c, const int* list);
 cudaError_t launch_split_gamma_t(df_ctx* c);
 }  // namespace df

@@ -57,7 +57,7 @@ bse_mixed_kernel(Dims dm, int ch0, int nch, const double2* __restrict__ gam,
                  const float2* __restrict__ gam_hi, const float2* __restrict__ gam_lo,
                  const float2* __restrict__ gg_hi, const float2* __restrict__ gg_lo,
                  const double2* __restrict__ chi, double2* __restrict__ kc,
-                 const unsigned char* __restrict__ gdig, int* __restrict__ flags) {
+                 const unsigned char* __restrict__ gdig, int* __restrict__ flags, MixedCheck mc) {
   extern __shared__ __align__(1024) float2 smf[];
   __shared__ int piv_s[128];
   __shared__ uint64_t mbar_s;
@@ -72,21 +72,21 @@ bse_mixed_kernel(Dims dm, int ch0, int nch, const double2* __restrict__ gam,
     }
     tc05_setup(tc, &mbar_s, &tslot_s);
   }
-  const int N = dm.N, nb = dm.nb;
-  const long systems = (long)nch * nb * N;
+  const int N = dm.N, nb = dm.nb, na = dm.na;
+  const long systems = (long)nch * na * N;
   const long per = (systems + gridDim.x - 1) / gridDim.x;
   const long s0 = (long)blockIdx.x * per, s1 = s0 + per < systems ? s0 + per : systems;
   int cur = -1;
   for (long sys = s0; sys < s1; ++sys) {
-    const int c = ch0 + (int)(sys / ((long)nb * N));
-    const int rem = (int)(sys - (long)(c - ch0) * nb * N);
-    const int a = rem / N, q = rem - a * N;
+    const int c = ch0 + (int)(sys / ((long)na * N));
+    const int rem = (int)(sys - (long)(c - ch0) * na * N);
+    const int a = dm.a0 + rem / N, q = rem - (a - dm.a0) * N;
     const int key = c * nb + a;
     if (use_umma_residual(NP) && (threadIdx.x >> 5) == mixed_compute_threads(NP) / 32)
       mixed_producer(sp, &tc);                        // warp 8: the tensor-core MMAs
     else
       bse_mixed_system<NP>(dm, c, a, q, gam, gam_hi, gam_lo, gg_hi, gg_lo, chi, kc, flags, sp,
-                           gdig ? gdig + (size_t)key * gdig_bytes(NP) : nullptr, key != cur, &tc);
+                           gdig ? gdig + (size_t)key * gdig_bytes(NP) : nullptr, key != cur, &tc, mc);
     cur = key;
   }
   if constexpr (use_umma_residual(NP)) tc05_teardown(tc);
@@ -125,11 +125,26 @@ static int mixed_np(int n) { return mixed_pad(n); }
 bool mixed_supported(int n_w) { return mixed_np(n_w) <= 128; }
 
 // gamma hi, lo; gamma o gamma^T hi, lo (orders > 64: gamma^T hi, lo); gamma's
-// digits (tensor-core residual)
-size_t mixed_workspace_bytes(const Dims& dm) {
+// digits (tensor-core residual); then the error control's words: the call's
+// largest rho^2 and the hand-back list (count + 2 N_W N system indices)
+static size_t mixed_check_offset(const Dims& dm) {
   const int np = mixed_np(dm.n_w);
   const size_t digits = use_tc_residual(np) ? (size_t)2 * dm.nb * gdig_bytes(np) : 0;
-  return (size_t)4 * 2 * dm.nb * dm.n_w * dm.n_w * sizeof(float2) + digits;
+  return ((size_t)4 * 2 * dm.nb * dm.n_w * dm.n_w * sizeof(float2) + digits + 15) & ~(size_t)15;
+}
+size_t mixed_workspace_bytes(const Dims& dm) {
+  return mixed_check_offset(dm) + sizeof(int) * (4 + (size_t)2 * dm.nb * dm.N);
+}
+// [0] worst rho^2 (float bits), [1] unused, [2] hand-back count, [3 ..] list
+unsigned* mixed_check_words(df_ctx* c) { return (unsigned*)((char*)c->mixed_ws + mixed_check_offset(c->dm)); }
+
+MixedCheck mixed_check(df_ctx* c) {
+  unsigned* w = mixed_check_words(c);
+  MixedCheck mc;
+  mc.worst = w;
+  mc.redo = c->opts.ladder_fallback ? (int*)(w + 2) : nullptr;
+  mc.rho2_max = (float)c->opts.ladder_tol;
+  return mc;
 }
 
 static unsigned char* gdig_ptr(df_ctx* c) {
@@ -170,26 +185,33 @@ static cudaError_t launch_bse_mixed_np(df_ctx* c, int channel_mask, int* flags) 
   }
   const size_t count = (size_t)2 * dm.nb * dm.n_w * dm.n_w;
   const float2* hi = (const float2*)c->mixed_ws;
+  const MixedCheck mc = mixed_check(c);
   for (int ch = 0; ch < 2; ++ch) {
     if (!(channel_mask & (1 << ch))) continue;
-    const long systems = (long)dm.nb * dm.N;
+    const long systems = (long)dm.na * dm.N;
     const int grid = (int)(systems < c->mixed_grid ? systems : c->mixed_grid);
     bse_mixed_kernel<NP><<<grid, threads, smem, c->stream>>>(dm, ch, 1, c->gam, hi, hi + count, hi + 2 * count,
-                                                             hi + 3 * count, c->chi, c->kc, gdig_ptr(c), flags);
+                                                             hi + 3 * count, c->chi, c->kc, gdig_ptr(c), flags, mc);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
+// the mixed-precision ladder solves of one df_bse call, then the FP64 LU over
+// the ladders whose predicted error exceeded the bound (none: its blocks exit
+// at once).  The caller zeroes the check words before (run_ladders).
 cudaError_t launch_bse_mixed(df_ctx* c, int channel_mask, int* flags) {
+  cudaError_t e;
   switch (mixed_np(c->dm.n_w)) {
-    case 8: return launch_bse_mixed_np<8>(c, channel_mask, flags);
-    case 16: return launch_bse_mixed_np<16>(c, channel_mask, flags);
-    case 32: return launch_bse_mixed_np<32>(c, channel_mask, flags);
-    case 64: return launch_bse_mixed_np<64>(c, channel_mask, flags);
-    case 128: return launch_bse_mixed_large(c, channel_mask, flags);   // df_mixed_large.cu
+    case 8: e = launch_bse_mixed_np<8>(c, channel_mask, flags); break;
+    case 16: e = launch_bse_mixed_np<16>(c, channel_mask, flags); break;
+    case 32: e = launch_bse_mixed_np<32>(c, channel_mask, flags); break;
+    case 64: e = launch_bse_mixed_np<64>(c, channel_mask, flags); break;
+    case 128: e = launch_bse_mixed_large(c, channel_mask, flags); break;   // df_mixed_large.cu
     default: return cudaErrorInvalidValue;
   }
+  if (e != cudaSuccess || !c->opts.ladder_fallback) return e;
+  return launch_bse_f64_list(c, (const int*)(mixed_check_words(c) + 2));
 }
 
 }  // namespace df

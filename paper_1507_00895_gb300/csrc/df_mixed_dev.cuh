@@ -658,7 +658,7 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
                                                  const double2* __restrict__ chi, double2* __restrict__ kc,
                                                  int* __restrict__ flags, const MixedPtrs& sp,
                                                  const unsigned char* __restrict__ gdig, bool reload,
-                                                 Tc05* umma) {
+                                                 Tc05* umma, const MixedCheck& mc) {
   const int n = dm.n_w, N = dm.N, nb = dm.nb;
   constexpr int np = NP, P = NP / kTile;
   constexpr int kThr = mixed_compute_threads(NP);       // threads taking part (the producer warp does not)
@@ -1294,6 +1294,19 @@ __device__ __forceinline__ void bse_mixed_system(const Dims& dm, int c, int a, i
       kc[(((size_t)c * nb + a) * n + j) * N + q] =
           mk(wgt * (gdiag.x - 0.5 * g2.x), wgt * (gdiag.y - 0.5 * g2.y));
     }
+  }
+  // per-ladder error control: the size of the correction against diag Gamma
+  if (t == 0) {
+    float emax = 0.f, gmax = 0.f;
+    bool fin = true;
+    for (int j = 0; j < n; ++j) {
+      const float2 x0 = x0d[j], e = ediag[j];
+      const float ea = fabsf(e.x) + fabsf(e.y), ga = fabsf(x0.x + e.x) + fabsf(x0.y + e.y);
+      fin = fin && isfinite(ea) && isfinite(ga);
+      emax = fmaxf(emax, ea);
+      gmax = fmaxf(gmax, ga);
+    }
+    mixed_check_ladder(mc, emax, gmax, fin, ((long)c * nb + a) * N + q, flags);
   }
   block_sync<NP>();
 }

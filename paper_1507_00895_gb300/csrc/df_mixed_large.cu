@@ -45,15 +45,16 @@ __global__ void split_gamma_t_kernel(int n, size_t mats, const double2* __restri
 __global__ void __launch_bounds__(256, 1)
 bse_gj_ir_kernel(Dims dm, int ch0, int nch, const float2* __restrict__ ghi, const float2* __restrict__ glo,
                  const float2* __restrict__ gth, const float2* __restrict__ gtl, const double2* __restrict__ gg,
-                 const double2* __restrict__ chi, double2* __restrict__ kc, int* __restrict__ flags) {
+                 const double2* __restrict__ chi, double2* __restrict__ kc, int* __restrict__ flags,
+                 MixedCheck mc) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ GjShared sh;
-  const long systems = (long)nch * dm.nb * dm.N;
+  const long systems = (long)nch * dm.na * dm.N;
   for (long sys = blockIdx.x; sys < systems; sys += gridDim.x) {
-    const int c = ch0 + (int)(sys / ((long)dm.nb * dm.N));
-    const int rem = (int)(sys - (long)(c - ch0) * dm.nb * dm.N);
-    const int a = rem / dm.N, q = rem - a * dm.N;
-    gj_ir_system(dm, c, a, q, ghi, glo, gth, gtl, gg, chi, kc, flags, smraw, sh);
+    const int c = ch0 + (int)(sys / ((long)dm.na * dm.N));
+    const int rem = (int)(sys - (long)(c - ch0) * dm.na * dm.N);
+    const int a = dm.a0 + rem / dm.N, q = rem - (a - dm.a0) * dm.N;
+    gj_ir_system(dm, c, a, q, ghi, glo, gth, gtl, gg, chi, kc, flags, smraw, sh, mc);
   }
 }
 
@@ -91,12 +92,13 @@ cudaError_t launch_bse_mixed_large(df_ctx* c, int channel_mask, int* flags) {
   if (per_sm < 1) per_sm = 1;
   const size_t count = (size_t)2 * dm.nb * n * n;
   const float2* ws = (const float2*)c->mixed_ws;
+  const MixedCheck mc = mixed_check(c);
   for (int ch = 0; ch < 2; ++ch) {
     if (!(channel_mask & (1 << ch))) continue;
-    const long systems = (long)dm.nb * dm.N;
+    const long systems = (long)dm.na * dm.N;
     const long grid = (long)sms * per_sm;
     bse_gj_ir_kernel<<<(int)(systems < grid ? systems : grid), threads, smem, c->stream>>>(
-        dm, ch, 1, ws, ws + count, ws + 2 * count, ws + 3 * count, gamma_gt_ptr(c), c->chi, c->kc, flags);
+        dm, ch, 1, ws, ws + count, ws + 2 * count, ws + 3 * count, gamma_gt_ptr(c), c->chi, c->kc, flags, mc);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;

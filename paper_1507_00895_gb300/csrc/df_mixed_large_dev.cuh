@@ -40,6 +40,9 @@ struct GjShared {
   float pabs[2];
   int prow[2];
   float2 pval[2];
+  // per-ladder error control: max |correction|, max |Gamma_jj| (float bits), non-finite seen
+  unsigned emax, gmax;
+  int bad;
 };
 
 __device__ __forceinline__ float2 gj_cinv(float2 z) {   // 1/z in FP32 (|z|^2 in range here)
@@ -66,7 +69,8 @@ __device__ __forceinline__ void gj_ir_system(const Dims& dm, int c, int a, int q
                                              const float2* __restrict__ glo, const float2* __restrict__ gth,
                                              const float2* __restrict__ gtl, const double2* __restrict__ gg,
                                              const double2* __restrict__ chi, double2* __restrict__ kc,
-                                             int* __restrict__ flags, unsigned char* smraw, GjShared& sh) {
+                                             int* __restrict__ flags, unsigned char* smraw, GjShared& sh,
+                                             const MixedCheck& mc) {
   const int n = dm.n_w, N = dm.N, nb = dm.nb, ld = n + 1;
   const GjLayout L = gj_layout(n);
   float2* S = (float2*)(smraw + L.S);      // [n][n + 1]: D, then (P D)^-1
@@ -96,6 +100,11 @@ __device__ __forceinline__ void gj_ir_system(const Dims& dm, int c, int a, int q
     xh[i] = make_float2(hx, hy);
     xl[i] = make_float2((float)(v.x - (double)hx), (float)(v.y - (double)hy));
     sh.perm[i] = i;
+  }
+  if (tid == 0) {
+    sh.emax = 0u;
+    sh.gmax = 0u;
+    sh.bad = 0;
   }
   __syncthreads();
   // 1. D in double-float, rounded once; column 0's pivot candidates
@@ -287,12 +296,23 @@ __device__ __forceinline__ void gj_ir_system(const Dims& dm, int c, int a, int q
       if (lane == 0) {
         const float2 y = Y[jc * kGjNc + jj];
         const double gx = (double)y.x + (double)d.x, gy = (double)y.y + (double)d.y;
+        const float ea = fabsf(d.x) + fabsf(d.y), ga = (float)(fabs(gx) + fabs(gy));
+        if (isfinite(ea) && isfinite(ga)) {
+          atomicMax(&sh.emax, __float_as_uint(ea));
+          atomicMax(&sh.gmax, __float_as_uint(ga));
+        } else {
+          sh.bad = 1;
+        }
         const double wgt = (c == 0) ? 1.0 : 3.0;
         kc[(((size_t)c * nb + a) * n + jc) * N + q] = mk(wgt * (gx - 0.5 * g2.x), wgt * (gy - 0.5 * g2.y));
       }
     }
     __syncthreads();
   }
+  // per-ladder error control (the next system's reset is by this thread too)
+  if (tid == 0)
+    mixed_check_ladder(mc, __uint_as_float(sh.emax), __uint_as_float(sh.gmax), sh.bad == 0,
+                       ((long)c * nb + a) * N + q, flags);
 }
 
 }  // namespace df

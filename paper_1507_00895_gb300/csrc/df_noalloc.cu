@@ -79,6 +79,8 @@ extern "C" df_status df_bse_noalloc(const double* gamma, const double* chi, int 
   dm.N = n_k_total;
   dm.n_w = n_w;
   dm.nb = n_bos;
+  dm.a0 = 0;
+  dm.na = n_bos;
   dm.m_max = (n_bos - 1) / 2;
   dm.ne = n_w + 2 * dm.m_max;
   // the flags must start at zero; gamma o gamma^T is fully rewritten below

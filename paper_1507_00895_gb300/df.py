@@ -36,13 +36,13 @@ DF_FP32_IR = 1
 # every symbol include/df.h declares (checked by the CPU tests)
 EXPORTS = (
     "df_default_opts", "df_init", "df_set_inputs", "df_vertex_from_spin", "df_bubble", "df_bse",
-    "df_sigma", "df_iterate", "df_get_sigma", "df_set_sigma", "df_get_gtilde", "df_lattice_observables", "df_susceptibility", "df_get_chi",
+    "df_sigma", "df_sigma_partial", "df_sigma_finish", "df_get_ladder_stats", "df_iterate", "df_get_sigma", "df_set_sigma", "df_get_gtilde", "df_lattice_observables", "df_susceptibility", "df_get_chi",
     "df_get_kernel", "df_get_lambda", "df_get_sizes", "df_set_timing", "df_get_timing",
     "df_synchronize", "df_bse_noalloc", "df_batch_init", "df_batch_iterate", "df_batch_get_sigma",
     "df_batch_reset", "df_batch_autotune", "df_batch_last_error", "df_batch_destroy", "df_mlp_create",
     "df_mlp_param_count", "df_mlp_forward", "df_mlp_gradients", "df_mlp_adam_step", "df_mlp_train_step",
     "df_mlp_params", "df_mlp_grads", "df_mlp_last_error", "df_mlp_destroy", "df_warmstart_sigma", "df_last_error",
-    "df_status_string", "df_destroy", "df_selftest_wait",
+    "df_status_string", "df_destroy", "df_selftest_wait", "df_peak_probe",
 )
 
 
@@ -65,7 +65,8 @@ class df_point(C.Structure):
 class df_opts(C.Structure):
     _fields_ = [("n_w", C.c_int), ("m_max", C.c_int), ("mix", C.c_double), ("precision", C.c_int),
                 ("eig_mode", C.c_int), ("ir_max_steps", C.c_int), ("ir_tol", C.c_double),
-                ("radius_order", C.c_int)]
+                ("radius_order", C.c_int), ("ladder_tol", C.c_double), ("ladder_fallback", C.c_int),
+                ("w_lo", C.c_int), ("w_hi", C.c_int)]
 
 
 _lib = None
@@ -92,6 +93,9 @@ def load(path: str = LIB_PATH):
         "df_bubble": [P],
         "df_bse": [P, C.c_int],
         "df_sigma": [P, D],
+        "df_sigma_partial": [P, P, C.c_int],
+        "df_sigma_finish": [P, P, C.c_int, D],
+        "df_get_ladder_stats": [P, D, I],
         "df_iterate": [P, C.c_int, C.c_double, I, D],
         "df_get_sigma": [P, P, C.c_int],
         "df_set_sigma": [P, P, C.c_int],
@@ -107,6 +111,7 @@ def load(path: str = LIB_PATH):
         "df_synchronize": [P],
         "df_bse_noalloc": [P, P, C.c_int, C.c_int, C.c_int, P, P],
         "df_selftest_wait": [C.c_int, C.c_int],
+        "df_peak_probe": [C.c_int, D],
         "df_batch_init": [C.POINTER(P), C.c_int, C.c_void_p, C.c_int, C.c_double, C.c_double, P],
         "df_batch_iterate": [P, C.c_int, I, D, I],
         "df_batch_get_sigma": [P, C.c_int, P, C.c_int],
@@ -183,7 +188,8 @@ class DualFermion:
     def __init__(self, *, dim: int, nk: int, t: float, tp: float, beta: float, mu: float,
                  n_w: int, m_max: int, g, delta, gamma_d, gamma_m, mix: float = 1.0,
                  precision: int = DF_FP64, eig_mode: int = 1, ir_max_steps: int = 8,
-                 ir_tol: float = 1e-13, radius_order: int = 0, stream: Optional[int] = None):
+                 ir_tol: float = 1e-13, radius_order: int = 0, ladder_tol: float = 1e-9,
+                 ladder_fallback: int = 1, w_range: Optional[tuple] = None, stream: Optional[int] = None):
         self.lib = load()
         self.dim, self.nk, self.n_w, self.m_max = dim, nk, n_w, m_max
         self.N = nk ** dim
@@ -195,6 +201,10 @@ class DualFermion:
         opts.n_w, opts.m_max, opts.mix, opts.precision = n_w, m_max, mix, precision
         opts.eig_mode, opts.ir_max_steps, opts.ir_tol = eig_mode, ir_max_steps, ir_tol
         opts.radius_order = radius_order
+        opts.ladder_tol, opts.ladder_fallback = ladder_tol, ladder_fallback
+        if w_range is not None:
+            opts.w_lo, opts.w_hi = int(w_range[0]), int(w_range[1])
+        self.w_range = (opts.w_lo, opts.w_hi if opts.w_hi > 0 else self.nb)
         g, delta = _c128(g), _c128(delta)
         gd, gm = _c128(gamma_d), _c128(gamma_m)
         if g.shape != (self.ne,) or delta.shape != (self.ne,):
@@ -255,6 +265,27 @@ class DualFermion:
         s = self.lib.df_sigma(self.h, C.byref(r) if want_residual else None)
         self._check(s, (DF_OK, DF_WARN_LADDER_RADIUS))
         return r.value if want_residual else None
+
+    def sigma_partial(self, out=None):
+        """This handle's share of Eq. sd (its bosonic planes), [n_w][N], before mixing and Dyson."""
+        return self._get(self.lib.df_sigma_partial, (self.n_w, self.N), out)
+
+    def sigma_finish(self, total, want_residual: bool = True):
+        """Mixing, residual and Dyson from the sum of every handle's sigma_partial."""
+        if isinstance(total, np.ndarray):
+            total = _c128(total)
+        p, dev = _ptr(total)
+        r = C.c_double(-1.0)
+        s = self.lib.df_sigma_finish(self.h, p, dev, C.byref(r) if want_residual else None)
+        self._check(s, (DF_OK, DF_WARN_LADDER_RADIUS))
+        return r.value if want_residual else None
+
+    def ladder_stats(self):
+        """(largest predicted error rho^2, ladders handed back to FP64) of the last bse() under DF_FP32_IR."""
+        w = C.c_double(0.0)
+        n = C.c_int(0)
+        self._check(self.lib.df_get_ladder_stats(self.h, C.byref(w), C.byref(n)))
+        return w.value, n.value
 
     def iterate(self, max_iter: int, tol: float = 0.0):
         """Returns (iterations done, residual, status)."""
@@ -510,3 +541,14 @@ def vertex_from_spin(gamma_uu, gamma_ud):
     if s != DF_OK:
         raise DFError(s, "df_vertex_from_spin")
     return d, m
+
+
+def peak_probe(kind: int) -> float:
+    """Measured GFLOP/s of the current device by an FMA loop (df_peak_probe):
+    kind 0 FP32 fma, 1 FP32 packed f32x2 fma, 2 FP64 fma."""
+    lib = load()
+    v = C.c_double(0.0)
+    s = lib.df_peak_probe(kind, C.byref(v))
+    if s != DF_OK:
+        raise DFError(s, "df_peak_probe")
+    return v.value

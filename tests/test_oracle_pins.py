@@ -483,19 +483,108 @@ def _sus(w, eps, sigma, gd, gm):
     return O.susceptibilities(w.g, w.delta, eps, sigma, gd, gm, w.n_w, w.m_max, w.beta, w.dim, w.nk)
 
 
-@pytest.mark.parametrize("nk", [2, 4])
-def test_susceptibility_flat_band_closed_form(nk):
-    # t = 0: G_lat = 1/(1/g + Delta) for every k, so the bare term is the atom's
-    # -T sum_w G_w G_{w+W}, independent of q and of N (an extensive sum would not be)
+# Each pin of the susceptibilities is a function returning its error measure, so
+# that the planted-mistake tests below can show which pin a mistake breaks.
+
+def pin_flat_band(nk=4):
+    """t = 0: G_lat = 1/(1/g + Delta) for every k, so the bare term is the atom's
+    -T sum_w G_w G_{w+W}, independent of q and of N (an extensive sum would not be).
+    Returns max over W of max |chi - ref| / |ref| (vertex = 0)."""
     w = I.workload("paper_u20", nk=nk, n_w=8, m_max=2)
     eps = np.zeros(w.N)
     zero_g = np.zeros_like(O.channel_vertices(w.gamma_uu, w.gamma_ud)[0])
     chi = _sus(w, eps, np.zeros((w.n_w, w.N), complex), zero_g, zero_g)
     gl = 1.0 / (1.0 / w.g + w.delta)
     T = 1.0 / w.beta
+    err = 0.0
     for a in range(w.n_bos):
         ref = -T * sum(gl[i + w.m_max] * gl[i + a] for i in range(w.n_w))
-        assert np.max(np.abs(chi[:, a, :] - ref)) < 1e-11 * abs(ref)
+        err = max(err, float(np.max(np.abs(chi[:, a, :] - ref)) / abs(ref)))
+    return err
+
+
+def pin_frak_closed_form(seed=21):
+    """frakG at Sigma~ != 0 against a closed form that follows from Eqs. gd0, dyson
+    and glat: with A = (Delta - eps)^-1, G0~ + g = (1/g + Delta - eps)^-1 gives
+    (G0~ + g)/G0~ = -A/g, so frakG = -A g^-1 G~ = g (1 - (Delta - eps) G), G from
+    Eq. glat.  Non-symmetric random inputs; returns max |frakG - ref| / max |ref|."""
+    w = I.random_nonsymmetric(6, 1, 2, 4, seed=seed)
+    eps = O.dispersion(2, 4, 1.0, 0.0)
+    rng = np.random.default_rng(seed + 1)
+    sig = 0.3 * (rng.normal(size=(6, 16)) + 1j * rng.normal(size=(6, 16)))
+    g_lat, frak = O.lattice_planes_ext(w.g, w.delta, eps, sig, 6, 1)
+    # G (Eq. glat) written out with G~ from Eq. gd0 and Eq. dyson, independently of the oracle
+    g = w.g[:, None]
+    a = 1.0 / (w.delta[:, None] - eps[None, :])
+    g0 = 1.0 / (1.0 / g + w.delta[:, None] - eps[None, :]) - g
+    gt = g0.copy()
+    gt[1:7] = 1.0 / (1.0 / g0[1:7] - sig)
+    g_ref = a + a * gt * a / (g * g)
+    ref = g * (1.0 - (w.delta[:, None] - eps[None, :]) * g_ref)
+    return max(float(np.max(np.abs(frak - ref)) / np.max(np.abs(ref))),
+               float(np.max(np.abs(g_lat - g_ref)) / np.max(np.abs(g_ref))))
+
+
+def pin_brute_force():
+    """Non-symmetric inputs, tiny grid: L and the bare term by explicit k sums of
+    G (Eq. glat) and frakG from their closed forms, Gamma by an explicit inverse,
+    L Gamma L by a double loop.  Returns the largest relative deviation."""
+    w = I.random_nonsymmetric(4, 1, 2, 2, seed=23, scale=0.2)
+    eps = O.dispersion(2, 2, 1.0, 0.0)
+    rng = np.random.default_rng(9)
+    sig = 0.2 * (rng.normal(size=(4, 4)) + 1j * rng.normal(size=(4, 4)))
+    gd, gm = O.channel_vertices(w.gamma_uu, w.gamma_ud)
+    chi = _sus(w, eps, sig, gd, gm)
+    g = w.g[:, None]
+    a = 1.0 / (w.delta[:, None] - eps[None, :])
+    g0 = 1.0 / (1.0 / g + w.delta[:, None] - eps[None, :]) - g
+    gt = g0.copy()
+    gt[1:5] = 1.0 / (1.0 / g0[1:5] - sig)
+    g_lat = a + a * gt * a / (g * g)
+    frak = -a * gt / g
+    chi0 = O.dual_bubble_direct(g_lat, 4, 1, w.beta, 2, 2).sum(axis=1)
+    L = O.dual_bubble_direct(frak, 4, 1, w.beta, 2, 2)
+    ct = O.dual_bubble_direct(gt, 4, 1, w.beta, 2, 2)
+    err = 0.0
+    for c, gam in enumerate((gd, gm)):
+        for aa in range(3):
+            for q in range(4):
+                Gam = np.linalg.inv(np.eye(4) - gam[aa] * ct[aa, :, q][None, :]) @ gam[aa]
+                s = sum(L[aa, i, q] * Gam[i, j] * L[aa, j, q] for i in range(4) for j in range(4))
+                err = max(err, abs(chi[c, aa, q] - (chi0[aa, q] + s)) / max(1.0, abs(chi[c, aa, q])))
+    zero = np.zeros_like(gd)
+    chi_z = _sus(w, eps, sig, zero, zero)
+    err = max(err, float(np.max(np.abs(chi_z - chi0[None]))))
+    return err
+
+
+def pin_first_order():
+    """chi(e gamma) = chi0 + e L^T gamma L + O(e^2): the ladder enters as gamma at
+    first order; L from the closed form of frakG.  Returns the relative deviation
+    of the Richardson-extrapolated first-order coefficient."""
+    w = I.workload("paper_u20", nk=4, n_w=4, m_max=1)
+    eps = O.dispersion(2, 4, 1.0, 0.0)
+    sig = np.zeros((4, 16), complex)
+    gd, gm = O.channel_vertices(w.gamma_uu, w.gamma_ud)
+    base = _sus(w, eps, sig, 0 * gd, 0 * gm)
+    e1, e2 = 1e-4, 2e-4
+    d1 = (_sus(w, eps, sig, e1 * gd, e1 * gm) - base) / e1
+    d2 = (_sus(w, eps, sig, e2 * gd, e2 * gm) - base) / e2
+    first = 2 * d1 - d2                                   # Richardson: O(e^2) removed
+    g = w.g[:, None]
+    gt = 1.0 / (1.0 / g + w.delta[:, None] - eps[None, :]) - g     # Sigma~ = 0: G~ = G0~
+    frak = -gt / (g * (w.delta[:, None] - eps[None, :]))
+    L = O.dual_bubble_direct(frak, 4, 1, w.beta, 2, 4)
+    err = 0.0
+    for c, gam in enumerate((gd, gm)):
+        ref = np.einsum("aiq,aij,ajq->aq", L, gam, L)
+        err = max(err, float(np.max(np.abs(first[c] - ref)) / np.max(np.abs(ref))))
+    return err
+
+
+@pytest.mark.parametrize("nk", [2, 4])
+def test_susceptibility_flat_band_closed_form(nk):
+    assert pin_flat_band(nk) < 1e-11
 
 
 def test_frak_g_is_lattice_g_at_zero_dual_self_energy():
@@ -507,47 +596,69 @@ def test_frak_g_is_lattice_g_at_zero_dual_self_energy():
     assert np.max(np.abs(g_lat - g_dmft)) < 1e-12 * np.max(np.abs(g_dmft))
 
 
+def test_frak_g_closed_form_at_nonzero_dual_self_energy():
+    assert pin_frak_closed_form() < 1e-13
+
+
 def test_susceptibility_brute_force_and_zero_vertex():
-    # non-symmetric inputs, tiny grid: L and the bare term by explicit k sums,
-    # Gamma by an explicit inverse, L Gamma L by a double loop
-    w = I.random_nonsymmetric(4, 1, 2, 2, seed=23, scale=0.2)
-    eps = O.dispersion(2, 2, 1.0, 0.0)
-    rng = np.random.default_rng(9)
-    sig = 0.2 * (rng.normal(size=(4, 4)) + 1j * rng.normal(size=(4, 4)))
-    gd, gm = O.channel_vertices(w.gamma_uu, w.gamma_ud)
-    chi = _sus(w, eps, sig, gd, gm)
-    g_lat, frak = O.lattice_planes_ext(w.g, w.delta, eps, sig, 4, 1)
-    gt = O.dual_g(O.bare_dual_g(w.g, w.delta, eps), sig, 4, 1)
-    chi0 = O.dual_bubble_direct(g_lat, 4, 1, w.beta, 2, 2).sum(axis=1)
-    L = O.dual_bubble_direct(frak, 4, 1, w.beta, 2, 2)
-    ct = O.dual_bubble_direct(gt, 4, 1, w.beta, 2, 2)
-    for c, gam in enumerate((gd, gm)):
-        for a in range(3):
-            for q in range(4):
-                Gam = np.linalg.inv(np.eye(4) - gam[a] * ct[a, :, q][None, :]) @ gam[a]
-                s = sum(L[a, i, q] * Gam[i, j] * L[a, j, q] for i in range(4) for j in range(4))
-                assert abs(chi[c, a, q] - (chi0[a, q] + s)) < 1e-12 * max(1.0, abs(chi[c, a, q]))
-    zero = np.zeros_like(gd)
-    chi_z = _sus(w, eps, sig, zero, zero)
-    assert np.max(np.abs(chi_z[0] - chi0)) < 1e-13 and np.max(np.abs(chi_z[1] - chi0)) < 1e-13
+    assert pin_brute_force() < 1e-12
 
 
 def test_susceptibility_first_order_in_the_vertex():
-    # chi(e gamma) = chi0 + e L^T gamma L + O(e^2): the ladder enters as gamma at first order
-    w = I.workload("paper_u20", nk=4, n_w=4, m_max=1)
-    eps = O.dispersion(2, 4, 1.0, 0.0)
-    sig = np.zeros((4, 16), complex)
-    gd, gm = O.channel_vertices(w.gamma_uu, w.gamma_ud)
-    base = _sus(w, eps, sig, 0 * gd, 0 * gm)
-    e1, e2 = 1e-4, 2e-4
-    d1 = (_sus(w, eps, sig, e1 * gd, e1 * gm) - base) / e1
-    d2 = (_sus(w, eps, sig, e2 * gd, e2 * gm) - base) / e2
-    first = 2 * d1 - d2                                   # Richardson: O(e^2) removed
-    _, frak = O.lattice_planes_ext(w.g, w.delta, eps, sig, 4, 1)
-    L = O.dual_bubble_direct(frak, 4, 1, w.beta, 2, 4)
-    for c, gam in enumerate((gd, gm)):
-        ref = np.einsum("aiq,aij,ajq->aq", L, gam, L)
-        assert np.max(np.abs(first[c] - ref)) < 1e-6 * np.max(np.abs(ref))
+    assert pin_first_order() < 1e-6
+
+
+# planted mistakes (in the oracle, on the CPU): each breaks the pin named
+
+def test_planted_frak_without_its_factor_fails(monkeypatch):
+    orig = O.lattice_planes_ext
+
+    def planted(g_ext, delta_ext, eps, sigma_box, n_w, m_max):
+        g_lat, _ = orig(g_ext, delta_ext, eps, sigma_box, n_w, m_max)
+        gt = O.dual_g(O.bare_dual_g(g_ext, delta_ext, eps), sigma_box, n_w, m_max)
+        return g_lat, gt                                   # frakG = G~, factor dropped
+
+    monkeypatch.setattr(O, "lattice_planes_ext", planted)
+    assert pin_frak_closed_form() > 1e-3
+    assert pin_brute_force() > 1e-3
+    assert pin_first_order() > 1e-3
+
+
+def test_planted_frak_as_gtilde_plus_g_fails(monkeypatch):
+    orig = O.lattice_planes_ext
+
+    def planted(g_ext, delta_ext, eps, sigma_box, n_w, m_max):
+        g_lat, _ = orig(g_ext, delta_ext, eps, sigma_box, n_w, m_max)
+        gt = O.dual_g(O.bare_dual_g(g_ext, delta_ext, eps), sigma_box, n_w, m_max)
+        return g_lat, gt + g_ext[:, None]                  # equal to frakG only at Sigma~ = 0
+
+    monkeypatch.setattr(O, "lattice_planes_ext", planted)
+    assert pin_frak_closed_form() > 1e-3
+    assert pin_brute_force() > 1e-3
+
+
+def test_planted_conjugated_l_fails(monkeypatch):
+    monkeypatch.setattr(O, "susceptibility_ladder_term", lambda lv, Gam: np.conj(lv) @ Gam @ np.conj(lv))
+    assert pin_brute_force() > 1e-3
+
+
+def test_planted_no_ladder_fails(monkeypatch):
+    monkeypatch.setattr(O, "ladder_gamma_full", lambda gamma_W, chi_Wq: np.array(gamma_W))
+    # the vertex is scaled down in this pin, so Gamma - gamma is second order: 3e-4
+    assert pin_brute_force() > 1e-6
+
+
+def test_planted_bare_term_from_gtilde_fails(monkeypatch):
+    orig = O.lattice_planes_ext
+
+    def planted(g_ext, delta_ext, eps, sigma_box, n_w, m_max):
+        _, frak = orig(g_ext, delta_ext, eps, sigma_box, n_w, m_max)
+        gt = O.dual_g(O.bare_dual_g(g_ext, delta_ext, eps), sigma_box, n_w, m_max)
+        return gt, frak                                    # bare term summed over G~, not G
+
+    monkeypatch.setattr(O, "lattice_planes_ext", planted)
+    assert pin_flat_band() > 1e-3
+    assert pin_brute_force() > 1e-3
 
 
 def test_susceptibility_conjugation_symmetry():
@@ -558,6 +669,38 @@ def test_susceptibility_conjugation_symmetry():
     st = O.run_workload(w, n_iter=3)
     chi = _sus(w, eps, st.sigma, gd, gm)
     assert np.max(np.abs(chi[:, ::-1, :] - np.conj(chi))) < 1e-11 * np.max(np.abs(chi))
+
+
+# ---------------------------------------------------------------------------
+# mixing (the loop's closing step: Sigma~ <- mix new + (1 - mix) old)
+# ---------------------------------------------------------------------------
+
+def test_mixing_first_pass_scales_the_new_self_energy():
+    # from Sigma~ = 0 one pass with mix = a gives a * (the unmixed pass): a swapped
+    # a <-> 1 - a, or mixing in the wrong order, gives 0.7 instead of 0.3 of it
+    w = I.workload("paper_u20", nk=4, n_w=6, m_max=1)
+    one = O.run_workload(w, n_iter=1)
+    mixed = O.run_workload(w, n_iter=1, mix=0.3)
+    assert np.max(np.abs(mixed.sigma - 0.3 * one.sigma)) <= 1e-15 * np.max(np.abs(one.sigma))
+
+
+def test_mixing_keeps_the_fixed_point():
+    # a fixed point of the unmixed map is one of the mixed map: both loops reach the
+    # same converged Sigma~, the mixed one more slowly (its contraction is weaker)
+    w = I.workload("paper_u20", nk=4, n_w=6, m_max=1)
+    a = O.run_workload(w, n_iter=60, tol=1e-14)
+    b = O.run_workload(w, n_iter=200, mix=0.3, tol=1e-14)
+    assert a.residuals[-1] <= 1e-14 and b.residuals[-1] <= 1e-14
+    assert len(b.residuals) > len(a.residuals)
+    assert np.max(np.abs(a.sigma - b.sigma)) < 1e-12 * np.max(np.abs(a.sigma))
+    # mixed residual: r_k = a max|F(S) - S| / max|S_k|, so a step of the mixed loop
+    # moves Sigma~ by exactly 0.3 of the unmixed step from the same state
+    st = O.LoopState(g0_ext=O.bare_dual_g(w.g, w.delta, O.dispersion(2, 4, w.t, w.tp)), sigma=b.sigmas[2].copy())
+    gd, gm = O.channel_vertices(w.gamma_uu, w.gamma_ud)
+    full, _ = O.one_iteration(O.LoopState(g0_ext=st.g0_ext, sigma=b.sigmas[2].copy()), gd, gm, 6, 1, w.beta, 2, 4)
+    part, _ = O.one_iteration(st, gd, gm, 6, 1, w.beta, 2, 4, mix=0.3)
+    step_full = full - b.sigmas[2]
+    assert np.max(np.abs((part - b.sigmas[2]) - 0.3 * step_full)) < 1e-14 * np.max(np.abs(step_full)) + 1e-17
 
 
 # ---------------------------------------------------------------------------

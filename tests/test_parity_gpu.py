@@ -1,10 +1,11 @@
 """Parity of the CUDA path (through the C ABI) against the CPU oracle.
 
 FP64 path: every result within 1e-10 of the oracle, measured normwise
-(max |gpu - oracle| / max |oracle| over the compared array).  Where the
-ladder matrices are ill-conditioned the bound is widened to the oracle's
-own spread (LAPACK vs a second FP64 factorisation, the oracle-vs-oracle
-difference), stated at each use.
+(max |gpu - oracle| / max |oracle| over the compared array), and Sigma~
+also elementwise (|gpu - oracle| / |oracle| for every element above 1e-6 of
+the largest, so that small high-frequency entries are held to the bound too).
+Where the loop itself is chaotic the comparison is teacher-forced, stated at
+each use.
 """
 import numpy as np
 import pytest
@@ -30,6 +31,13 @@ def df():
 
 def nrel(a, b):
     return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def erel(a, b, floor=1e-6):
+    """Largest elementwise relative difference over the elements of b above
+    floor * max |b| (the rest are rounding-level relative to the array)."""
+    m = np.abs(b) > floor * np.max(np.abs(b))
+    return float(np.max(np.abs(a - b)[m] / np.abs(b)[m]))
 
 
 def oracle_first_pass(w):
@@ -71,6 +79,7 @@ def test_first_pass_all_stages(df, name, kw):
         assert nrel(d.get_kernel(), kernel_channels(st, gd, gm)) < TOL64
         r = d.sigma()
         assert nrel(d.get_sigma(), st.sigma) < TOL64
+        assert erel(d.get_sigma(), st.sigma) < TOL64
         assert abs(r - st.residuals[0]) < 1e-12
         # Dyson of the new Sigma~ (Eq. dyson)
         gt_next = O.dual_g(st.g0_ext, st.sigma, w.n_w, w.m_max)
@@ -125,7 +134,9 @@ def test_paper_workload_converges_on_gpu(df):
 
 
 def test_square32_tp_full_size_first_pass(df):
-    # full 2D 32^2, n_w=64, 15 bosonic frequencies: every (q, W) ladder of both channels
+    # full 2D 32^2, n_w=64, 15 bosonic frequencies: every (q, W) ladder of both
+    # channels (condition numbers up to ~1e6), normwise per (channel, W) plane
+    # (measured worst 2.5e-13), and Sigma~ normwise and elementwise
     w = I.workload("square32_tp")
     st, gd, gm = oracle_first_pass(w)
     with df.DualFermion.from_workload(w) as d:
@@ -134,12 +145,12 @@ def test_square32_tp_full_size_first_pass(df):
         d.bse(3)
         kern = d.get_kernel()
         ref = kernel_channels(st, gd, gm)
-        # normwise per (channel, W) plane; condition numbers reach ~1e6 here
         for c in range(2):
             for a in range(w.n_bos):
-                assert nrel(kern[c, a], ref[c, a]) < 1e-9, (c, a)
+                assert nrel(kern[c, a], ref[c, a]) < TOL64, (c, a)
         d.sigma()
-        assert nrel(d.get_sigma(), st.sigma) < 1e-9
+        assert nrel(d.get_sigma(), st.sigma) < TOL64
+        assert erel(d.get_sigma(), st.sigma) < TOL64
 
 
 def test_cubic16_sampled_ladders_and_lambda(df):
@@ -394,3 +405,89 @@ def test_radius_extension(df, K):
     # the plain inversion differs: the extension is active
     plain = O.run_workload(w, n_iter=1)
     assert nrel(st.sigmas[0], plain.sigmas[0]) > 1e-3
+
+
+def test_mixing_three_passes(df):
+    # Sigma~ <- 0.3 new + 0.7 old (the loop's closing step with mix != 1), three
+    # free-running passes of the convergent paper workload against the oracle
+    w = I.workload("paper_u20", nk=8, n_w=6, m_max=1)
+    st = O.run_workload(w, n_iter=3, mix=0.3)
+    with df.DualFermion.from_workload(w, mix=0.3) as d:
+        for p in range(3):
+            d.bubble()
+            d.bse(3)
+            r = d.sigma()
+            assert nrel(d.get_sigma(), st.sigmas[p]) < TOL64, p
+            assert abs(r - st.residuals[p]) < 1e-10 * max(1.0, st.residuals[p])
+
+
+def singular_inputs(df, precision):
+    """A ladder with an exactly zero pivot: 1D, N_k = 2, t = 0, g = Delta = 1
+    give G0~ = -1/2 on every k and frequency (all operations exact in binary
+    floating point), beta = 4 then chi~ = -(T/N) sum_k G0~ G0~ = -1/16 exactly,
+    and gamma_00 = -16, gamma_10 = 0 make the first column of D = 1 - gamma chi~
+    exactly zero."""
+    g = np.ones(2, complex)
+    gam = np.array([[[-16.0, 0.5], [0.0, 1.0]]], complex)
+    return df.DualFermion(dim=1, nk=2, t=0.0, tp=0.0, beta=4.0, mu=0.0, n_w=2, m_max=0, g=g, delta=g,
+                          gamma_d=gam, gamma_m=gam, precision=precision)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_exactly_singular_ladder_is_reported(df, prec):
+    with singular_inputs(df, df.DF_FP64 if prec == "fp64" else df.DF_FP32_IR) as d:
+        d.bubble()
+        assert np.array_equal(d.get_chi(), np.full((1, 2, 2), -1.0 / 16.0, complex))
+        with pytest.raises(df.DFError) as e:
+            d.iterate(1)
+        assert e.value.status == df.DF_ERR_SINGULAR
+
+
+def test_radius_warning_is_raised_outside_the_radius(df):
+    # the 16^2, U = 2, beta = 5 workload: |lambda| of gamma chi~ at W = 0 reaches ~25
+    w = I.workload("square16_b5")
+    with df.DualFermion.from_workload(w) as d:
+        it, r, s = d.iterate(1)
+        assert s == df.DF_WARN_LADDER_RADIUS
+        lam, ok = d.get_lambda()
+        assert np.max(np.abs(lam[:, w.m_max])) > 1.0
+    w = I.workload("paper_u20", nk=8, n_w=8, m_max=1)      # inside the radius: no warning
+    with df.DualFermion.from_workload(w) as d:
+        assert d.iterate(1)[2] == df.DF_OK
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_omega_split_two_handles(df, prec):
+    # the Omega split of Eq. sd: two handles own disjoint bosonic ranges, each runs
+    # the bubble and the ladders of its planes, their partial Sigma~ are summed (the
+    # all-reduce of a multi-GPU run) and each finishes the pass from the sum
+    w = I.workload("square32_tp", nk=8, n_w=10, m_max=3)
+    st = O.run_workload(w, n_iter=2)
+    p = df.DF_FP64 if prec == "fp64" else df.DF_FP32_IR
+    tol = TOL64 if prec == "fp64" else 1e-8
+    cut = 3
+    with df.DualFermion.from_workload(w, precision=p, w_range=(0, cut)) as d0, \
+            df.DualFermion.from_workload(w, precision=p, w_range=(cut, w.n_bos)) as d1:
+        for it in range(2):
+            parts = []
+            for d in (d0, d1):
+                d.bubble()
+                d.bse(3)
+                parts.append(d.sigma_partial())
+            total = parts[0] + parts[1]
+            r0 = d0.sigma_finish(total)
+            r1 = d1.sigma_finish(total)
+            assert r0 == r1
+            assert abs(r0 - st.residuals[it]) < 1e-10 * max(1.0, st.residuals[it])
+            assert nrel(d0.get_sigma(), st.sigmas[it]) < tol, it
+            assert np.array_equal(d0.get_sigma(), d1.get_sigma())
+        # a range handle refuses the full-range calls
+        with pytest.raises(df.DFError):
+            d0.sigma()
+    # one full-range handle: partial + finish is the fused df_sigma
+    with df.DualFermion.from_workload(w, precision=p) as d, df.DualFermion.from_workload(w, precision=p) as e:
+        d.bubble(); d.bse(3)
+        e.bubble(); e.bse(3)
+        d.sigma()
+        e.sigma_finish(e.sigma_partial())
+        assert nrel(e.get_sigma(), d.get_sigma()) < 1e-14
