@@ -117,6 +117,9 @@ typedef struct df_opts {
   int ladder_fallback;/* DF_FP32_IR: 1 (default) a ladder above ladder_tol is solved again by
                        * the FP64 LU in the same df_bse; 0 its mixed result is kept and the
                        * next df_sigma / df_iterate returns DF_ERR_REFINE_STALL */
+  int mixed_sweep;    /* DF_FP32_IR, orders 64 < n_w <= 128: the FP32 Gauss-Jordan inversion on the
+                       * tensor cores (0, default: tcgen05 panel updates with three-piece BF16
+                       * operands, FP32 accumulation in tensor memory) or on the CUDA cores (1) */
   int w_lo, w_hi;     /* the Omega split (several GPUs, one problem): this handle owns the
                        * bosonic planes a in [w_lo, w_hi) (index a = m + m_max); default 0, 0
                        * = all.  df_bubble and df_bse then cover only those planes and the

@@ -167,6 +167,7 @@ df_status df_default_opts(df_opts* o) {
   o->radius_order = 0;
   o->ladder_tol = 1e-9;
   o->ladder_fallback = 1;
+  o->mixed_sweep = 0;
   o->w_lo = 0;
   o->w_hi = 0;
   return DF_OK;
@@ -248,6 +249,7 @@ df_status df_init(df_ctx** out, const df_lattice* lat, double beta, double mu, d
   if (opts->radius_order > 0 && (opts->precision != DF_FP64 || opts->eig_mode != 2)) return DF_ERR_ARG;
   if (!(opts->ladder_tol > 0.0 && opts->ladder_tol < 1.0) || (opts->ladder_fallback != 0 && opts->ladder_fallback != 1))
     return DF_ERR_ARG;
+  if (opts->mixed_sweep != 0 && opts->mixed_sweep != 1) return DF_ERR_ARG;
   {
     const int nbos = 2 * opts->m_max + 1;
     const bool full = opts->w_lo == 0 && opts->w_hi == 0;

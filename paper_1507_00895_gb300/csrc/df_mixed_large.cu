@@ -58,6 +58,51 @@ bse_gj_ir_kernel(Dims dm, int ch0, int nch, const float2* __restrict__ ghi, cons
   }
 }
 
+// The same ladders with the Gauss-Jordan inversion on the tensor cores
+// (df_tcgj_dev.cuh): 256 threads, 256 TMEM columns per block, two blocks per
+// SM (the launch asks for enough shared memory that no third fits), systems
+// strided over the persistent grid.  A completion wait that gives up stops
+// the block: it sets kFlagTcTimeout, waits (bounded) for its last MMAs and
+// frees its tensor memory.
+constexpr int kTcTmemCols = 256;
+
+__global__ void __launch_bounds__(kTcThreads, 2)
+bse_tc_ir_kernel(Dims dm, int ch0, int nch, const float2* __restrict__ ghi, const float2* __restrict__ glo,
+                 const float2* __restrict__ gth, const float2* __restrict__ gtl, const double2* __restrict__ gg,
+                 const double2* __restrict__ chi, double2* __restrict__ kc, int* __restrict__ flags,
+                 MixedCheck mc) {
+  extern __shared__ __align__(1024) unsigned char smtc[];
+  __shared__ GjShared sh;
+  __shared__ uint64_t mbar_s;
+  __shared__ unsigned tslot_s;
+  if (smem_u32(smtc) & 1023u) {                  // the swizzled operand tiles need 1024-byte alignment
+    if (threadIdx.x == 0) atomicOr(flags, kFlagTcLayout);
+    return;
+  }
+  if ((threadIdx.x >> 5) == 0) tmem_alloc_cols<kTcTmemCols>(&tslot_s);
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar_s)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc05_fence_before();
+  __syncthreads();
+  tc05_fence_after();
+  GjTc tc{tslot_s, &mbar_s, 0u};
+  bool ok = true;
+  const long systems = (long)nch * dm.na * dm.N;
+  for (long sys = blockIdx.x; sys < systems && ok; sys += gridDim.x) {
+    const int c = ch0 + (int)(sys / ((long)dm.na * dm.N));
+    const int rem = (int)(sys - (long)(c - ch0) * dm.na * dm.N);
+    const int a = dm.a0 + rem / dm.N, q = rem - (a - dm.a0) * dm.N;
+    ok = gj_ir_system<true>(dm, c, a, q, ghi, glo, gth, gtl, gg, chi, kc, flags, smtc, sh, mc, &tc);
+  }
+  if (!ok && threadIdx.x == 0) mbar_wait(&mbar_s, tc.phase ^ 1u);   // the abandoned commit, bounded
+  tc05_fence_before();
+  __syncthreads();
+  tc05_fence_after();
+  if ((threadIdx.x >> 5) == 0) tmem_dealloc_cols<kTcTmemCols>(tc.tmem);
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
@@ -73,10 +118,48 @@ cudaError_t launch_split_gamma_t(df_ctx* c) {
   return cudaGetLastError();
 }
 
+// the tensor-core variant: at most two blocks per SM (256 TMEM columns each)
+static cudaError_t launch_bse_tc_large(df_ctx* c, int channel_mask, int* flags) {
+  const Dims& dm = c->dm;
+  const int n = dm.n_w;
+  size_t smem = (size_t)gj_layout(n, true).total;
+  if (smem < 80 * 1024) smem = 80 * 1024;         // no third block per SM (its TMEM allocation would wait)
+  cudaError_t e = cudaFuncSetAttribute((const void*)bse_tc_ir_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute((const void*)bse_tc_ir_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           (int)cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess) return e;
+  // blocks per SM from shared memory alone (the register cap of the launch bounds
+  // allows two; the occupancy calculator reports one for any kernel that
+  // allocates tensor memory, while two 256-column allocations fit the SM's 512)
+  int sms = 0, sm_smem = 0;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sm_smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, c->device)) != cudaSuccess)
+    return e;
+  cudaFuncAttributes fa;
+  if ((e = cudaFuncGetAttributes(&fa, (const void*)bse_tc_ir_kernel)) != cudaSuccess) return e;
+  int per_sm = (int)((size_t)sm_smem / (smem + fa.sharedSizeBytes + 1024));
+  per_sm = per_sm < 1 ? 1 : (per_sm > 2 ? 2 : per_sm);
+  const size_t count = (size_t)2 * dm.nb * n * n;
+  const float2* ws = (const float2*)c->mixed_ws;
+  const MixedCheck mc = mixed_check(c);
+  for (int ch = 0; ch < 2; ++ch) {
+    if (!(channel_mask & (1 << ch))) continue;
+    const long systems = (long)dm.na * dm.N;
+    const long grid = (long)sms * per_sm;
+    bse_tc_ir_kernel<<<(int)(systems < grid ? systems : grid), kTcThreads, smem, c->stream>>>(
+        dm, ch, 1, ws, ws + count, ws + 2 * count, ws + 3 * count, gamma_gt_ptr(c), c->chi, c->kc, flags, mc);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t launch_bse_mixed_large(df_ctx* c, int channel_mask, int* flags) {
   const Dims& dm = c->dm;
   const int n = dm.n_w;
   if (n > kGjMaxN) return cudaErrorInvalidValue;
+  if (c->opts.mixed_sweep == 0) return launch_bse_tc_large(c, channel_mask, flags);
   const size_t smem = gj_smem_bytes(n);
   const int threads = gj_threads(n);
   cudaError_t e = cudaFuncSetAttribute((const void*)bse_gj_ir_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -5,6 +5,7 @@
 // gj_layout(n).total bytes of dynamic shared memory at smraw.
 #pragma once
 #include "df_internal.cuh"
+#include "df_tcgj_dev.cuh"
 
 namespace df {
 
@@ -16,11 +17,13 @@ struct GjLayout {
   int S, B, Y, Zh, Zl, colk, xh, xl, xs, total;
 };
 
-__host__ __device__ inline GjLayout gj_layout(int n) {
+// tc: the tensor-core sweep's operand tiles share the S region (used before S is written)
+__host__ __device__ inline GjLayout gj_layout(int n, bool tc = false) {
   GjLayout L;
   int off = 0;
   auto take = [&](int bytes) { const int o = off; off += (bytes + 15) & ~15; return o; };
-  L.S = take(8 * n * (n + 1));
+  const int s_bytes = 8 * n * (n + 1);
+  L.S = take(tc && tc_smem_bytes(n) > s_bytes ? tc_smem_bytes(n) : s_bytes);
   L.B = take(8 * n * kGjNc);
   L.Y = take(8 * n * kGjNc);
   L.Zh = take(8 * n * kGjNc);
@@ -37,6 +40,7 @@ __host__ __device__ inline int gj_threads(int n) { return (2 * n + 31) / 32 * 32
 
 struct GjShared {
   int perm[kGjMaxN];
+  int ipiv[kGjMaxN];      // tensor-core sweep: the position of each row in the pivot order
   float pabs[2];
   int prow[2];
   float2 pval[2];
@@ -62,17 +66,29 @@ __device__ __forceinline__ void x2_acc(float2& S, float2& L, float2 A, float2 nA
   L = x2_sub(x2_add(L, e), ne);
 }
 
+// Tensor-core state of a block running the TC variant (TC = true): TMEM base of
+// its 256 columns, the MMA completion barrier and its parity.
+struct GjTc {
+  unsigned tmem;
+  uint64_t* mbar;
+  unsigned phase;
+};
+
 // ghi, glo: gamma's (hi, lo) FP32 words [2][nb][n][n]; gth, gtl: gamma^T's;
 // gg: gamma o gamma^T (FP64); chi: chi~ [nb][n][N]; kc: the Eq. sd bracket
-// [2][nb][n][N]; flags bit 0: a zero FP32 pivot
-__device__ __forceinline__ void gj_ir_system(const Dims& dm, int c, int a, int q, const float2* __restrict__ ghi,
+// [2][nb][n][N]; flags bit 0: a zero FP32 pivot.  TC: the Gauss-Jordan
+// inversion on the tensor cores (df_tcgj_dev.cuh; kTcThreads threads, tc
+// set up), else on the CUDA cores.  Returns false when a tensor-core wait
+// gave up (the block must stop; the same value in every thread).
+template <bool TC = false>
+__device__ __forceinline__ bool gj_ir_system(const Dims& dm, int c, int a, int q, const float2* __restrict__ ghi,
                                              const float2* __restrict__ glo, const float2* __restrict__ gth,
                                              const float2* __restrict__ gtl, const double2* __restrict__ gg,
                                              const double2* __restrict__ chi, double2* __restrict__ kc,
                                              int* __restrict__ flags, unsigned char* smraw, GjShared& sh,
-                                             const MixedCheck& mc) {
+                                             const MixedCheck& mc, GjTc* tc = nullptr) {
   const int n = dm.n_w, N = dm.N, nb = dm.nb, ld = n + 1;
-  const GjLayout L = gj_layout(n);
+  const GjLayout L = gj_layout(n, TC);
   float2* S = (float2*)(smraw + L.S);      // [n][n + 1]: D, then (P D)^-1
   float2* B = (float2*)(smraw + L.B);      // [n][8]: P gamma, then R
   float2* Y = (float2*)(smraw + L.Y);      // [n][8]
@@ -107,6 +123,52 @@ __device__ __forceinline__ void gj_ir_system(const Dims& dm, int c, int a, int q
     sh.bad = 0;
   }
   __syncthreads();
+  if constexpr (TC) {
+    // 1-2. D into tensor memory (lane j = column j, TMEM column 2i + c = row i), in
+    // double-float rounded once, then the Gauss-Jordan sweep on the tensor cores
+    const int np = tc_pad(n);
+    const int qd = warp & 3, jl = 32 * qd + lane;
+    const unsigned tq = tc->tmem + ((32u * qd) << 16);
+    tc05_fence_after();
+    {
+      const float2 ah = jl < n ? xh[jl] : make_float2(0.f, 0.f), al = jl < n ? xl[jl] : make_float2(0.f, 0.f);
+      for (int r = 8 * (warp >> 2); r < np; r += 16) {
+        float v[16];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int i = r + e;
+          float2 d = make_float2(0.f, 0.f);
+          if (i < n && jl < n) {
+            float sr = 0.f, lr = 0.f, si = 0.f, li = 0.f;
+            cdf_fma(sr, lr, si, li, __ldg(Gh + (size_t)i * n + jl), __ldg(Gl + (size_t)i * n + jl), ah, al);
+            d = make_float2(((i == jl ? 1.f : 0.f) - sr) - lr, -si - li);
+          }
+          v[2 * e] = d.x;
+          v[2 * e + 1] = d.y;
+        }
+        tmem_st16(tq + 2 * r, v);
+      }
+      tmem_wait_st();
+    }
+    tc05_fence_before();
+    __syncthreads();
+    tc05_fence_after();
+    if (!tcgj_sweep(tc->tmem, n, n, tc_smem(smraw + L.S, n), sh.perm, tc->mbar, tc->phase, flags)) return false;
+    for (int k = tid; k < n; k += T) sh.ipiv[sh.perm[k]] = k;
+    __syncthreads();
+    // S = (P D)^-1, S[k][l] = D^-1[k][p_l] = A[p_k][l]: row r of the swept A is row ipiv[r] of S
+    for (int r = 8 * (warp >> 2); r < np; r += 16) {
+      float v[16];
+      tmem_ld16(tq + 2 * r, v);
+      if (jl < n) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+          if (r + e < n) S[sh.ipiv[r + e] * ld + jl] = make_float2(v[2 * e], v[2 * e + 1]);
+      }
+    }
+    tc05_fence_before();
+    __syncthreads();
+  } else {
   // 1. D in double-float, rounded once; column 0's pivot candidates
   if (act) {
     const float2 ah = xh[j], al = xl[j];
@@ -197,6 +259,7 @@ __device__ __forceinline__ void gj_ir_system(const Dims& dm, int c, int a, int q
     }
     __syncthreads();
   }
+  }   // CUDA-core sweep
   // 3. right-hand sides in chunks of kGjNc columns
   for (int j0 = 0; j0 < n; j0 += kGjNc) {
     const int w = min(kGjNc, n - j0);
@@ -313,6 +376,7 @@ __device__ __forceinline__ void gj_ir_system(const Dims& dm, int c, int a, int q
   if (tid == 0)
     mixed_check_ladder(mc, __uint_as_float(sh.emax), __uint_as_float(sh.gmax), sh.bad == 0,
                        ((long)c * nb + a) * N + q, flags);
+  return true;
 }
 
 }  // namespace df

@@ -66,7 +66,7 @@ class df_opts(C.Structure):
     _fields_ = [("n_w", C.c_int), ("m_max", C.c_int), ("mix", C.c_double), ("precision", C.c_int),
                 ("eig_mode", C.c_int), ("ir_max_steps", C.c_int), ("ir_tol", C.c_double),
                 ("radius_order", C.c_int), ("ladder_tol", C.c_double), ("ladder_fallback", C.c_int),
-                ("w_lo", C.c_int), ("w_hi", C.c_int)]
+                ("mixed_sweep", C.c_int), ("w_lo", C.c_int), ("w_hi", C.c_int)]
 
 
 _lib = None
@@ -189,7 +189,8 @@ class DualFermion:
                  n_w: int, m_max: int, g, delta, gamma_d, gamma_m, mix: float = 1.0,
                  precision: int = DF_FP64, eig_mode: int = 1, ir_max_steps: int = 8,
                  ir_tol: float = 1e-13, radius_order: int = 0, ladder_tol: float = 1e-9,
-                 ladder_fallback: int = 1, w_range: Optional[tuple] = None, stream: Optional[int] = None):
+                 ladder_fallback: int = 1, mixed_sweep: int = 0, w_range: Optional[tuple] = None,
+                 stream: Optional[int] = None):
         self.lib = load()
         self.dim, self.nk, self.n_w, self.m_max = dim, nk, n_w, m_max
         self.N = nk ** dim
@@ -201,7 +202,7 @@ class DualFermion:
         opts.n_w, opts.m_max, opts.mix, opts.precision = n_w, m_max, mix, precision
         opts.eig_mode, opts.ir_max_steps, opts.ir_tol = eig_mode, ir_max_steps, ir_tol
         opts.radius_order = radius_order
-        opts.ladder_tol, opts.ladder_fallback = ladder_tol, ladder_fallback
+        opts.ladder_tol, opts.ladder_fallback, opts.mixed_sweep = ladder_tol, ladder_fallback, mixed_sweep
         if w_range is not None:
             opts.w_lo, opts.w_hi = int(w_range[0]), int(w_range[1])
         self.w_range = (opts.w_lo, opts.w_hi if opts.w_hi > 0 else self.nb)

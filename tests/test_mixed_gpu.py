@@ -113,12 +113,14 @@ LARGE = [
 ]
 
 
+@pytest.mark.parametrize("sweep", [0, 1])
 @pytest.mark.parametrize("name,kw", LARGE)
-def test_mixed_large_orders_first_pass(df, name, kw):
-    # 64 < n_w <= 128: FP32 Gauss-Jordan inverse + one double-float-residual correction
+def test_mixed_large_orders_first_pass(df, name, kw, sweep):
+    # 64 < n_w <= 128: FP32 Gauss-Jordan inverse (on the tensor cores, sweep 0, or the
+    # CUDA cores, sweep 1) + one double-float-residual correction
     w = I.workload(name, **kw)
     st, kref = oracle_first_pass(w)
-    with df.DualFermion.from_workload(w, precision=df.DF_FP32_IR) as d:
+    with df.DualFermion.from_workload(w, precision=df.DF_FP32_IR, mixed_sweep=sweep) as d:
         d.bubble()
         d.bse(3)
         kern = d.get_kernel()
@@ -234,3 +236,24 @@ def test_mixed_cubic16_full_size_against_the_oracle(df):
           f"{erel(sig, sig_ref):.2e}), handed back {back}, worst rho^2 {worst_rho2:.1e}")
     assert worst < TOL_KERNEL
     assert err < TOL_SIGMA and erel(sig, sig_ref) < TOL_SIGMA
+
+
+def test_tensor_core_sweep_matches_the_cuda_core_sweep(df):
+    # the two FP32 Gauss-Jordan inversions of the large-order kernel (tcgen05 panel
+    # updates with three-piece BF16 operands vs FP32 FMAs) give the same corrected
+    # ladders within the mixed bound, and both within it of the FP64 path
+    w = I.workload("cubic16_crit", nk=4, n_w=96, m_max=2)
+    out = {}
+    for sweep in (0, 1):
+        with df.DualFermion.from_workload(w, precision=df.DF_FP32_IR, mixed_sweep=sweep) as d:
+            d.bubble()
+            d.bse(3)
+            out[sweep] = d.get_kernel()
+    with df.DualFermion.from_workload(w) as d:
+        d.bubble()
+        d.bse(3)
+        k64 = d.get_kernel()
+    for c in range(2):
+        for a in range(w.n_bos):
+            assert nrel(out[0][c, a], out[1][c, a]) < TOL_KERNEL
+            assert nrel(out[0][c, a], k64[c, a]) < TOL_KERNEL
