@@ -127,8 +127,8 @@ __device__ __forceinline__ void panel_bar() { asm volatile("bar.sync %0, 128;" :
 // completion barrier and its parity (updated).  Zero pivots set
 // kFlagSingular.  Returns false when a bounded completion wait gave up (then
 // the block must stop issuing MMAs; the flag kFlagTcTimeout is set).
-static __device__ __noinline__ bool tcgj_sweep(unsigned tmem, int nr, int nc, const TcGjSmem& sm, int* piv, uint64_t* mbar,
-                                        unsigned& phase, int* __restrict__ flags) {
+__device__ __forceinline__ bool tcgj_sweep(unsigned tmem, int nr, int nc, const TcGjSmem sm, int* piv, uint64_t* mbar,
+                                           unsigned& phase, int* __restrict__ flags) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, q = warp & 3;
   const int np = tc_pad(nr);
   const int j = 32 * q + lane;                  // the TMEM lane this thread reaches
