@@ -320,6 +320,8 @@ cudaError_t launch_bse_mixed(df_ctx* c, int channel_mask, int* flags);
 // orders 64 < n_w <= 128 (df_mixed_large.cu)
 cudaError_t launch_bse_mixed_large(df_ctx* c, int channel_mask, int* flags);
 MixedCheck mixed_check(df_ctx* c);
+size_t mixed_tcr_offset(const Dims& dm);      // byte offset of the tensor-core residual's gamma digits
+size_t tcr_workspace_bytes(const Dims& dm);
 unsigned* mixed_check_words(df_ctx* c);   // [0] worst rho^2, [2] hand-back count, [3 ..] list
 cudaError_t launch_bse_f64_list(df_ctx* c, const int* list);
 cudaError_t launch_split_gamma_t(df_ctx* c);

@@ -132,9 +132,10 @@ static size_t mixed_check_offset(const Dims& dm) {
   const size_t digits = use_tc_residual(np) ? (size_t)2 * dm.nb * gdig_bytes(np) : 0;
   return ((size_t)4 * 2 * dm.nb * dm.n_w * dm.n_w * sizeof(float2) + digits + 15) & ~(size_t)15;
 }
-size_t mixed_workspace_bytes(const Dims& dm) {
-  return mixed_check_offset(dm) + sizeof(int) * (4 + (size_t)2 * dm.nb * dm.N);
+size_t mixed_tcr_offset(const Dims& dm) {
+  return (mixed_check_offset(dm) + sizeof(int) * (4 + (size_t)2 * dm.nb * dm.N) + 1023) & ~(size_t)1023;
 }
+size_t mixed_workspace_bytes(const Dims& dm) { return mixed_tcr_offset(dm) + tcr_workspace_bytes(dm); }
 // [0] worst rho^2 (float bits), [1] unused, [2] hand-back count, [3 ..] list
 unsigned* mixed_check_words(df_ctx* c) { return (unsigned*)((char*)c->mixed_ws + mixed_check_offset(c->dm)); }
 

@@ -24,6 +24,7 @@
 // trailing words (slots 2 and 3), so that a warp's 32 rows read one
 // contiguous 256-byte line per k in the residual product.
 #include "df_mixed_large_dev.cuh"
+#include "df_tcr_dev.cuh"
 
 namespace df {
 
@@ -103,19 +104,117 @@ bse_tc_ir_kernel(Dims dm, int ch0, int nch, const float2* __restrict__ ghi, cons
   if ((threadIdx.x >> 5) == 0) tmem_dealloc_cols<kTcTmemCols>(tc.tmem);
 }
 
+// Orders 64 < n <= 96 with the residual on the tensor cores too
+// (df_tcr_dev.cuh): 256 threads, all 512 TMEM columns, one block per SM.
+__global__ void tcr_gamma_digits_kernel(int n, int count, const double2* __restrict__ gam,
+                                        unsigned char* __restrict__ out, int* __restrict__ rowe) {
+  tcr_gamma_digits_rows(n, count, gam, out, rowe, (blockIdx.x * blockDim.x + threadIdx.x) >> 5,
+                        (gridDim.x * blockDim.x) >> 5, threadIdx.x & 31);
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+bse_tcr_kernel(Dims dm, int ch0, int nch, const float2* __restrict__ ghi, const float2* __restrict__ glo,
+               const double2* __restrict__ gg, const unsigned char* __restrict__ gdig, const int* __restrict__ growe,
+               const double2* __restrict__ chi, double2* __restrict__ kc, int* __restrict__ flags, MixedCheck mc) {
+  extern __shared__ __align__(1024) unsigned char smtcr[];
+  __shared__ int piv_s[128], ipiv_s[128];
+  __shared__ uint64_t bars_s[1 + 2 * kTcrBufs];   // sweep / fold, full[kTcrBufs], empty[kTcrBufs]
+  __shared__ unsigned tslot_s;
+  if (smem_u32(smtcr) & 1023u) {
+    if (threadIdx.x == 0) atomicOr(flags, kFlagTcLayout);
+    return;
+  }
+  {                                    // Y digits: K beyond n stays zero for the whole launch
+    const TcrLayout L = tcr_layout(dm.n_w);
+    uint4* y = reinterpret_cast<uint4*>(smtcr + L.ystk);
+    for (int i = threadIdx.x; i < 128 * 2 * 128 / 16; i += blockDim.x) y[i] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  if ((threadIdx.x >> 5) == 0) tmem_alloc_cols<512>(&tslot_s);
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < 1 + 2 * kTcrBufs; ++b)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars_s[b])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc05_fence_before();
+  __syncthreads();
+  tc05_fence_after();
+  TcrState st;
+  st.tmem = tslot_s;
+  st.mbar = &bars_s[0];
+  st.full = &bars_s[1];
+  st.empty = &bars_s[1 + kTcrBufs];
+  st.phase = 0u;
+  for (int b = 0; b < kTcrBufs; ++b) st.fphase[b] = st.ephase[b] = 0u;
+  bool ok = true;
+  const long systems = (long)nch * dm.na * dm.N;
+  for (long sys = blockIdx.x; sys < systems && ok; sys += gridDim.x) {
+    const int c = ch0 + (int)(sys / ((long)dm.na * dm.N));
+    const int rem = (int)(sys - (long)(c - ch0) * dm.na * dm.N);
+    const int a = dm.a0 + rem / dm.N, q = rem - (a - dm.a0) * dm.N;
+    ok = tcr_system(dm, c, a, q, ghi, glo, gg, gdig, growe, chi, kc, flags, smtcr, piv_s, ipiv_s, st, mc);
+  }
+  if (!ok && threadIdx.x == 0) {       // bounded waits for what may still be in flight
+    mbar_wait(st.mbar, st.phase ^ 1u);
+    for (int b = 0; b < kTcrBufs; ++b) mbar_wait(&st.full[b], st.fphase[b]);
+  }
+  tc05_fence_before();
+  __syncthreads();
+  tc05_fence_after();
+  if ((threadIdx.x >> 5) == 0) tmem_dealloc_cols<512>(st.tmem);
+}
+
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 
 size_t gj_smem_bytes(int n_w) { return (size_t)gj_layout(n_w).total; }
 
-// gamma^T's (hi, lo) words into workspace slots 2 and 3 (orders > 64)
+// gamma's digit chunks of the tensor-core residual (orders 64 < n <= 96),
+// after the mixed workspace's other parts
+size_t tcr_workspace_bytes(const Dims& dm) {
+  if (!tcr_supported(dm.n_w)) return 0;
+  return (size_t)2 * dm.nb * (tcr_gdig_bytes() + 2 * 128 * sizeof(int));
+}
+static unsigned char* tcr_gdig_ptr(df_ctx* c) { return (unsigned char*)c->mixed_ws + mixed_tcr_offset(c->dm); }
+static int* tcr_rowe_ptr(df_ctx* c) {
+  return (int*)(tcr_gdig_ptr(c) + (size_t)2 * c->dm.nb * tcr_gdig_bytes());
+}
+
+// gamma^T's (hi, lo) words into workspace slots 2 and 3 (orders > 64); the
+// tensor-core residual's digit chunks where that kernel takes the order
 cudaError_t launch_split_gamma_t(df_ctx* c) {
   const Dims& dm = c->dm;
   const size_t count = (size_t)2 * dm.nb * dm.n_w * dm.n_w;
   float2* ws = (float2*)c->mixed_ws;
   split_gamma_t_kernel<<<256, 256, 0, c->stream>>>(dm.n_w, (size_t)2 * dm.nb, c->gam, ws + 2 * count, ws + 3 * count);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !tcr_supported(dm.n_w)) return e;
+  const int warps = 2 * dm.nb * 128;
+  tcr_gamma_digits_kernel<<<(warps + 7) / 8, 256, 0, c->stream>>>(dm.n_w, 2 * dm.nb, c->gam, tcr_gdig_ptr(c),
+                                                                  tcr_rowe_ptr(c));
   return cudaGetLastError();
+}
+
+// orders 64 < n <= 96: sweep and residual on the tensor cores, one block per SM
+static cudaError_t launch_bse_tcr(df_ctx* c, int channel_mask, int* flags) {
+  const Dims& dm = c->dm;
+  const size_t smem = (size_t)tcr_layout(dm.n_w).total;
+  cudaError_t e = cudaFuncSetAttribute((const void*)bse_tcr_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  int sms = 0;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device)) != cudaSuccess) return e;
+  const size_t count = (size_t)2 * dm.nb * dm.n_w * dm.n_w;
+  const float2* ws = (const float2*)c->mixed_ws;
+  const MixedCheck mc = mixed_check(c);
+  for (int ch = 0; ch < 2; ++ch) {
+    if (!(channel_mask & (1 << ch))) continue;
+    const long systems = (long)dm.na * dm.N;
+    bse_tcr_kernel<<<(int)(systems < sms ? systems : sms), kTcThreads, smem, c->stream>>>(
+        dm, ch, 1, ws, ws + count, gamma_gt_ptr(c), tcr_gdig_ptr(c), tcr_rowe_ptr(c), c->chi, c->kc, flags, mc);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 // the tensor-core variant: at most two blocks per SM (256 TMEM columns each)
@@ -159,7 +258,8 @@ cudaError_t launch_bse_mixed_large(df_ctx* c, int channel_mask, int* flags) {
   const Dims& dm = c->dm;
   const int n = dm.n_w;
   if (n > kGjMaxN) return cudaErrorInvalidValue;
-  if (c->opts.mixed_sweep == 0) return launch_bse_tc_large(c, channel_mask, flags);
+  if (c->opts.mixed_sweep == 0)
+    return tcr_supported(n) ? launch_bse_tcr(c, channel_mask, flags) : launch_bse_tc_large(c, channel_mask, flags);
   const size_t smem = gj_smem_bytes(n);
   const int threads = gj_threads(n);
   cudaError_t e = cudaFuncSetAttribute((const void*)bse_gj_ir_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

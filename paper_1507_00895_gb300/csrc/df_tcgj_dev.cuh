@@ -123,12 +123,17 @@ __device__ __forceinline__ void panel_bar() { asm volatile("bar.sync %0, 128;" :
 // The sweep over the nr pivot columns of the TMEM-resident matrix (see above).
 // All kTcThreads threads call it.  tmem: TMEM base of the matrix (lane 0);
 // nc <= 128 columns (lanes), nr <= nc rows; TMEM columns 0 .. 2 tc_pad(nr) - 1.
+// With ng > 0 a second matrix of ng <= 128 columns at TMEM base tmem_g (the
+// right-hand sides, same row layout) takes the same row operations: its
+// columns are never pivot columns, so it ends as the rows of D^-1 times the
+// original columns, row p_k holding row k (A operand tile atile_g).
 // piv[k] receives the pivot row of column k.  mbar / phase: the MMA
 // completion barrier and its parity (updated).  Zero pivots set
 // kFlagSingular.  Returns false when a bounded completion wait gave up (then
 // the block must stop issuing MMAs; the flag kFlagTcTimeout is set).
 __device__ __forceinline__ bool tcgj_sweep(unsigned tmem, int nr, int nc, const TcGjSmem sm, int* piv, uint64_t* mbar,
-                                           unsigned& phase, int* __restrict__ flags) {
+                                           unsigned& phase, int* __restrict__ flags, unsigned tmem_g = 0u,
+                                           int ng = 0, __nv_bfloat16* atile_g = nullptr) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, q = warp & 3;
   const int np = tc_pad(nr);
   const int j = 32 * q + lane;                  // the TMEM lane this thread reaches
@@ -238,6 +243,25 @@ __device__ __forceinline__ bool tcgj_sweep(unsigned tmem, int nr, int nc, const 
         put_split_row(sm.btile, 2 * tid, wr);
         put_split_row(sm.btile, 2 * tid + 1, wi);
       }
+      if (ng > 0) {                             // A operand of the right-hand sides: row j = G[p_s][j]
+        const unsigned tg = tmem_g + ((32u * q) << 16);
+        float a[16];
+#pragma unroll
+        for (int s = 0; s < kTcPanel; ++s) {
+          if (s < nb) {
+            tmem_ld_x2(tg + 2 * pivs[s], a[2 * s], a[2 * s + 1]);
+          } else {
+            a[2 * s] = 0.f;
+            a[2 * s + 1] = 0.f;
+          }
+        }
+        tmem_wait_ld();
+        if (j >= ng) {
+#pragma unroll
+          for (int t = 0; t < 16; ++t) a[t] = 0.f;
+        }
+        put_split_row(atile_g, j, a);
+      }
     }
     __syncthreads();                            // the panel's pivots in piv[]
     // 3b. A operand (warps 4-7): row j = A[p_s][j] (+1 at the panel's own column's slot)
@@ -270,6 +294,12 @@ __device__ __forceinline__ bool tcgj_sweep(unsigned tmem, int nr, int nc, const 
 #pragma unroll
       for (int t = 0; t < 6; ++t)
         umma_bf16(tmem, umma_desc_sw128(abase + 32 * ap[t]), umma_desc_sw128(bbase + 32 * bp[t]), idesc, 1u);
+      if (ng > 0) {
+        const unsigned gbase = smem_u32(atile_g);
+#pragma unroll
+        for (int t = 0; t < 6; ++t)
+          umma_bf16(tmem_g, umma_desc_sw128(gbase + 32 * ap[t]), umma_desc_sw128(bbase + 32 * bp[t]), idesc, 1u);
+      }
       umma_commit(mbar);
     }
     const bool done = mbar_wait(mbar, phase);
