@@ -453,9 +453,10 @@ def observables_bench(df, I, torch, reps: int = 20):
 
 def large_order_bench(df, I, passes: int = 2):
     """The 3D critical workload (16^3, n_w = 96, N_W = 21: 172,032 ladders of order 96) one
-    pass at a time from Sigma~ = 0, FP64 and DF_FP32_IR (order > 64: the shared-memory
-    Gauss-Jordan kernel); ladder time from libdf's own events, and the normwise difference of
-    the two paths' Sigma~ after the first pass."""
+    pass at a time from Sigma~ = 0, FP64 and DF_FP32_IR (orders 64 < n_w <= 96: the Gauss-Jordan
+    inversion and the residual on the tensor cores); ladder time from libdf's own events, the
+    CUDA-core sweep's time beside it (mixed_sweep = 1), and the normwise difference of the two
+    paths' Sigma~ after the first pass."""
     import numpy as np
     w = I.workload("cubic16_crit")
     ladders = 2 * w.n_bos * w.N
@@ -477,9 +478,17 @@ def large_order_bench(df, I, passes: int = 2):
         bse_ms = t["bse"][0] / passes
         out[name] = {"s_per_pass": wall, "ladder_ms_per_pass": bse_ms,
                      "fp64_equivalent_TFLOP_per_s": fp64_eq / (bse_ms * 1e-3) / 1e12,
-                     "kernel": "bse_f64_kernel" if prec == df.DF_FP64 else "bse_gj_ir_kernel"}
+                     "kernel": "bse_f64_kernel" if prec == df.DF_FP64 else
+                               "bse_tcr_kernel (tcgen05 Gauss-Jordan sweep and digit residual)"}
     out["err_fp32ir_vs_fp64_first_pass"] = float(np.max(np.abs(sig["fp32ir"] - sig["fp64"]))
                                                  / np.max(np.abs(sig["fp64"])))
+    with df.DualFermion.from_workload(w, precision=df.DF_FP32_IR, mixed_sweep=1) as d:
+        d.iterate(1)
+        d.set_sigma(zero)
+        d.set_timing(True)
+        d.iterate(passes)
+        t = d.get_timing()
+    out["fp32ir_cuda_core_sweep"] = {"ladder_ms_per_pass": t["bse"][0] / passes, "kernel": "bse_gj_ir_kernel"}
     return out
 
 

@@ -306,8 +306,10 @@ typedef struct df_batch df_batch;
 
 /* precision: DF_FP64 for every point, or DF_FP32_IR for every point (n_w <= 64
  * by the register-tile kernel, larger orders by the shared-memory Gauss-Jordan
- * one).  tol > 0: a point stops once its residual
- * r <= tol.  stream may be NULL (the batch then creates its own). */
+ * one), with the per-ladder error control of DF_FP32_IR at ladder_tol = 1e-9:
+ * ladders above it are solved again by the FP64 LU in the same pass.
+ * npts in [1, 4096] (DF_FP32_IR: [1, 127]).  tol > 0: a point stops once its
+ * residual r <= tol.  stream may be NULL (the batch then creates its own). */
 df_status df_batch_init(df_batch** out, int npts, const df_point* pts, int precision, double mix, double tol,
                         void* stream);
 /* Up to max_iter passes (graph replays); stops early when every point has

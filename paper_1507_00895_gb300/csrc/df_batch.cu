@@ -24,9 +24,14 @@
 
 namespace df {
 
-// the batched mixed ladders run without the per-ladder hand-back list (a point's
-// ladders all take the mixed path; the single-problem kernels have the check)
-__device__ __forceinline__ MixedCheck no_check() { return MixedCheck{nullptr, nullptr, __int_as_float(0x7f800000)}; }
+// Per-ladder error control of the batch's mixed ladders: a ladder whose
+// predicted error rho^2 exceeds kBatchLadderTol goes to one batch-wide list,
+// entries (point << 24) | ((c N_W + a) N + q), solved again by the FP64 LU
+// (batch_bse_f64_list_kernel) in the same pass.
+constexpr float kBatchLadderTol = 1e-9f;
+__device__ __forceinline__ MixedCheck batch_check(int* redo, int point) {
+  return MixedCheck{redo, nullptr, kBatchLadderTol, point << 24};
+}
 
 
 struct PointDev {
@@ -41,6 +46,9 @@ struct PointDev {
   double* red;   // [2 n_w + 4]
   int* flags;    // [4]
 };
+
+// the FP64 right-hand-side chunk of an order (as default_nc on the host)
+__device__ __forceinline__ int default_nc_dev(int n) { return n <= 32 ? n : (n <= 64 ? 32 : 16); }
 
 __device__ __forceinline__ int find_segment(const long* start, int nseg, long x) {
   // largest k with start[k] <= x (start[0] = 0, start[nseg] = total)
@@ -184,10 +192,32 @@ batch_bse_f64_kernel(const PointDev* __restrict__ pts, const int* __restrict__ o
   }
 }
 
+// the FP64 LU over the mixed ladders handed back this pass (redo[0] entries)
+__global__ void __launch_bounds__(kBseThreads)
+batch_bse_f64_list_kernel(const PointDev* __restrict__ pts, const int* __restrict__ redo, double2* __restrict__ ws,
+                          size_t ws_stride) {
+  extern __shared__ double2 sm[];
+  __shared__ BseF64Shared sh;
+  const int count = redo[0];
+  for (int s = blockIdx.x; s < count; s += gridDim.x) {
+    const int code = redo[1 + s];
+    const PointDev& P = pts[code >> 24];
+    const Dims& dm = P.dm;
+    const int sys = code & 0xFFFFFF;
+    const int c = sys / (dm.nb * dm.N), rem = sys - c * dm.nb * dm.N;
+    const int a = rem / dm.N, q = rem - a * dm.N;
+    const int nc = default_nc_dev(dm.n_w);
+    const bool lu_smem = dm.n_w <= kLuSmemOrder;
+    const BseSmem L = bse_layout(dm.n_w, nc, lu_smem);
+    double2* LU = lu_smem ? sm + L.lu : ws + blockIdx.x * ws_stride;
+    bse_f64_system(dm, c, a, q, nc, P.gam, P.gg, P.chi, P.kc, LU, sm + L.y, sm + L.xs, sm + L.invu, sh, P.flags);
+  }
+}
+
 template <int NP>
 __global__ void __launch_bounds__(mixed_block_threads(NP), use_umma_residual(NP) ? 1 : 0)
 batch_bse_mixed_kernel(const PointDev* __restrict__ pts, const int* __restrict__ order, const long* __restrict__ start,
-                       int nseg, int chunk, unsigned long long* __restrict__ counter) {
+                       int nseg, int chunk, unsigned long long* __restrict__ counter, int* __restrict__ redo) {
   extern __shared__ __align__(1024) float2 smf[];
   __shared__ int piv_s[128];
   __shared__ unsigned long long item_s;
@@ -228,7 +258,7 @@ batch_bse_mixed_kernel(const PointDev* __restrict__ pts, const int* __restrict__
       else
         bse_mixed_system<NP>(dm, c, a, q, P.gam, P.gam_hi, P.gam_lo, P.gg_hi, P.gg_lo, P.chi, P.kc, P.flags, sp,
                              P.gdig ? P.gdig + (size_t)(c * dm.nb + a) * gdig_bytes(NP) : nullptr, key != cur, &tc,
-                             no_check());
+                             batch_check(redo, order[k]));
       cur = key;
     }
   }
@@ -239,7 +269,7 @@ batch_bse_mixed_kernel(const PointDev* __restrict__ pts, const int* __restrict__
 // 256 threads, the same chunked queue over the class's cost-sorted points
 __global__ void __launch_bounds__(256, 1)
 batch_bse_gj_kernel(const PointDev* __restrict__ pts, const int* __restrict__ order, const long* __restrict__ start,
-                    int nseg, int chunk, unsigned long long* __restrict__ counter) {
+                    int nseg, int chunk, unsigned long long* __restrict__ counter, int* __restrict__ redo) {
   extern __shared__ __align__(16) unsigned char smraw[];
   __shared__ GjShared sh;
   __shared__ unsigned long long item_s;
@@ -262,7 +292,7 @@ batch_bse_gj_kernel(const PointDev* __restrict__ pts, const int* __restrict__ or
       const int rem = (int)(local - (long)c * per_ch);
       const int a = rem / dm.N, q = rem - a * dm.N;
       gj_ir_system(dm, c, a, q, P.gam_hi, P.gam_lo, P.gg_hi, P.gg_lo, P.gg, P.chi, P.kc, P.flags, smraw, sh,
-                   no_check());
+                   batch_check(redo, order[k]));
     }
   }
 }
@@ -279,7 +309,7 @@ namespace {
 
 int mixed_np_of(int n) { return mixed_pad(n); }
 
-using MixedKernel = void (*)(const PointDev*, const int*, const long*, int, int, unsigned long long*);
+using MixedKernel = void (*)(const PointDev*, const int*, const long*, int, int, unsigned long long*, int*);
 
 // the ladder kernel instance of a padded order (8, 16, 32 or 64)
 MixedKernel mixed_kernel_of(int np) {
@@ -326,6 +356,9 @@ struct df_batch {
   unsigned long long* d_counters = nullptr;   // one per ladder group
   double2* ws = nullptr;                       // global LU scratch (FP64, n > 96)
   size_t ws_stride = 0;
+  int* d_redo = nullptr;                       // mixed ladders handed back to the FP64 LU: count, list
+  int redo_grid = 0;
+  size_t redo_smem = 0;
   double* d_out = nullptr;                     // [3 npts] residual, active, flags
   double* h_out = nullptr;
   int chunk = 1;                               // scheduler chunk (autotuned)
@@ -368,6 +401,7 @@ df_status record_pass(df_batch* b) {
   cudaStream_t s = b->stream;
   const int ng = (int)b->groups.size();
   B_CUDA(b, cudaMemsetAsync(b->d_counters, 0, sizeof(unsigned long long) * (ng ? ng : 1), s), "counter reset");
+  if (b->d_redo) B_CUDA(b, cudaMemsetAsync(b->d_redo, 0, sizeof(int), s), "hand-back count reset");
   batch_bubble_kernel<<<(unsigned)b->total_planes, kFftThreads, b->fft_smem1, s>>>(b->d_pts, b->d_plane_start, b->npts);
   B_CUDA(b, cudaGetLastError(), "batch bubble");
   for (auto& g : b->groups) {
@@ -377,12 +411,17 @@ df_status record_pass(df_batch* b) {
                                                                b->d_counters + g.counter_slot, b->ws, b->ws_stride);
     } else if (g.np > 64) {
       batch_bse_gj_kernel<<<g.grid, g.threads, g.smem, s>>>(b->d_pts, g.d_order, g.d_start, g.nseg, b->chunk,
-                                                            b->d_counters + g.counter_slot);
+                                                            b->d_counters + g.counter_slot, b->d_redo);
     } else {
       mixed_kernel_of(g.np)<<<g.grid, g.threads, g.smem, s>>>(b->d_pts, g.d_order, g.d_start, g.nseg, b->chunk,
-                                                              b->d_counters + g.counter_slot);
+                                                              b->d_counters + g.counter_slot, b->d_redo);
     }
     B_CUDA(b, cudaGetLastError(), "batch ladder");
+  }
+  if (b->d_redo) {
+    batch_bse_f64_list_kernel<<<b->redo_grid, kBseThreads, b->redo_smem, s>>>(b->d_pts, b->d_redo, b->ws,
+                                                                              b->ws_stride);
+    B_CUDA(b, cudaGetLastError(), "batch hand-back ladders");
   }
   batch_sigma_prod_kernel<<<(unsigned)b->total_planes, kFftThreads, b->fft_smem1, s>>>(b->d_pts, b->d_plane_start,
                                                                                       b->npts);
@@ -469,6 +508,7 @@ extern "C" {
 df_status df_batch_init(df_batch** out, int npts, const df_point* pts, int precision, double mix, double tol,
                         void* stream) {
   if (!out || !pts || npts < 1 || npts > 4096) return DF_ERR_ARG;
+  if (precision == DF_FP32_IR && npts > 127) return DF_ERR_ARG;   // the hand-back list's point field
   if (precision != DF_FP64 && precision != DF_FP32_IR) return DF_ERR_ARG;
   if (!(mix > 0.0 && mix <= 1.0)) return DF_ERR_ARG;
   *out = nullptr;
@@ -706,14 +746,33 @@ df_status df_batch_init(df_batch** out, int npts, const df_point* pts, int preci
     }
     BALLOC(b->d_counters, sizeof(unsigned long long) * std::max<size_t>(1, b->groups.size()), "counters");
     // global LU scratch for FP64 ladders of order > kLuSmemOrder
+    // (mixed points: their hand-back ladders use the same scratch, one slice per block)
     int big = 0;
+    long mixed_ladders = 0;
     for (auto& g : b->groups)
-      if (!g.mixed)
-        for (int p : g.order)
-          big = std::max(big, b->host_pts[p].dm.n_w > kLuSmemOrder ? b->host_pts[p].dm.n_w : 0);
+      for (int p : g.order) {
+        const Dims& dm = b->host_pts[p].dm;
+        big = std::max(big, dm.n_w > kLuSmemOrder ? dm.n_w : 0);
+        if (g.mixed) mixed_ladders += 2L * dm.nb * dm.N;
+      }
     if (big) {
       b->ws_stride = (size_t)big * big;
       BALLOC(b->ws, sizeof(double2) * b->ws_stride * (size_t)b->sms * kLuScratchPerSm, "LU scratch");
+    }
+    if (mixed_ladders > 0) {
+      BALLOC(b->d_redo, sizeof(int) * (1 + (size_t)mixed_ladders), "hand-back list");
+      size_t sm_max = 0;
+      for (auto& g : b->groups)
+        if (g.mixed)
+          for (int p : g.order) {
+            const int n = b->host_pts[p].dm.n_w;
+            sm_max = std::max(sm_max, sizeof(double2) * (size_t)bse_layout(n, default_nc(n), n <= kLuSmemOrder).total);
+          }
+      b->redo_smem = sm_max;
+      b->redo_grid = b->sms * kLuScratchPerSm;   // blocks beyond the list's count exit at once
+      e = cudaFuncSetAttribute((const void*)batch_bse_f64_list_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)sm_max);
+      if (e != cudaSuccess) { st = bfail(b, DF_ERR_CUDA, "hand-back kernel", e); goto bad; }
     }
   }
 #undef BALLOC
@@ -743,6 +802,7 @@ void df_batch_destroy(df_batch* b) {
   cudaFree(b->d_box_start);
   cudaFree(b->d_counters);
   cudaFree(b->ws);
+  cudaFree(b->d_redo);
   if (b->h_out) cudaFreeHost(b->h_out);
   if (b->own_stream) cudaStreamDestroy(b->stream);
   delete b;

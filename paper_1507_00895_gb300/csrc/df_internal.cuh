@@ -33,6 +33,7 @@ struct MixedCheck {
   int* redo;
   unsigned* worst;
   float rho2_max;
+  int base;       // added to the system index in the list (the batch: point << 24)
 };
 
 __device__ __forceinline__ void mixed_check_ladder(const MixedCheck& mc, float emax, float gmax, bool finite,
@@ -45,7 +46,7 @@ __device__ __forceinline__ void mixed_check_ladder(const MixedCheck& mc, float e
   if (!(rho2 <= mc.rho2_max)) {
     if (mc.redo) {
       const int i = atomicAdd(mc.redo, 1);
-      mc.redo[1 + i] = (int)sys;
+      mc.redo[1 + i] = mc.base + (int)sys;
     } else {
       atomicOr(flags, kFlagRefine);
     }

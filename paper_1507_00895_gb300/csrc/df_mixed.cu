@@ -145,6 +145,7 @@ MixedCheck mixed_check(df_ctx* c) {
   mc.worst = w;
   mc.redo = c->opts.ladder_fallback ? (int*)(w + 2) : nullptr;
   mc.rho2_max = (float)c->opts.ladder_tol;
+  mc.base = 0;
   return mc;
 }
 
