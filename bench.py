@@ -15,7 +15,9 @@ L2 is flushed (256 MiB write) between steps, outside the timed region.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 N > 1 runs N independent replicas (one parameter point per GPU, no
-collective), launched by torch.distributed.run.
+collective), launched by torch.distributed.run; with --omega-split the N
+GPUs share one problem instead (bosonic planes split, one all-reduce of
+Sigma~ per pass).
 """
 from __future__ import annotations
 
@@ -556,6 +558,60 @@ def read_peaks():
         return {}
 
 
+def run_omega_split(args):
+    """One problem over N GPUs (the Omega split): every rank owns a contiguous range of the
+    bosonic planes (split.omega_partition), runs the bubble and the ladders of its planes, its
+    share of Eq. sd is summed by one NCCL all-reduce per pass and every rank applies mixing,
+    the residual and Eq. dyson (split.split_pass).  Strong scaling: the same 15,360 (q, W)
+    points per pass at every N."""
+    import torch
+    import torch.distributed as dist
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1507_00895_gb300 import build, df, inputs as I, split
+    if rank == 0:
+        build.build_lib()
+    if world > 1:
+        dist.barrier()
+    build.build_lib()
+    w = I.workload(WORKLOAD)
+    lo, hi = split.omega_partition(w.n_bos, world, rank)
+    zeros = torch.zeros((w.n_w, w.N), dtype=torch.complex128, device="cuda")
+    stream = torch.cuda.current_stream()
+    with df.DualFermion.from_workload(w, precision=df.DF_FP32_IR, eig_mode=1, w_range=(lo, hi),
+                                      stream=stream.cuda_stream) as d:
+        for _ in range(args.warmup):
+            d.set_sigma(zeros)
+            split.split_pass(d)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            d.set_sigma(zeros)
+            split.split_pass(d)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
+    points = w.n_bos * w.N
+    if rank == 0:
+        print(json.dumps({"metric": METRIC, "value": points / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                          "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+                          "dtype": "f32+f64-refinement", "data": "synthetic",
+                          "config": {"workload": WORKLOAD_DESC, "points_per_step": points,
+                                     "parallelism": f"omega-split{world}",
+                                     "l2": "inputs resident; no flush between steps"}}))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -773,10 +829,15 @@ def main():
                     help="skip the 3D critical workload's passes (order 96, both precisions)")
     ap.add_argument("--no-observables", action="store_true",
                     help="skip the lattice-observable, susceptibility and radius-extension timings")
+    ap.add_argument("--omega-split", action="store_true",
+                    help="one problem over the N GPUs (bosonic planes split, one all-reduce per pass) "
+                         "instead of N replicas")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)       # at least 3 untimed warm-up steps
     if args.impl == "reference":
         return run_reference(args)
+    if args.omega_split:
+        return run_omega_split(args)
     return run_ours(args)
 
 

@@ -31,12 +31,14 @@ def allreduce_sum(x, group=None):
     """Sum a complex128 array over the ranks of `group`, in place.
 
     x is a torch tensor (complex128, contiguous; a CUDA tensor under NCCL, a
-    CPU tensor under gloo); the sum runs on its float64 view."""
+    CPU tensor under gloo); the sum runs on its float64 view.  Without an
+    initialised process group (one rank) x is already the sum."""
     import torch
     import torch.distributed as dist
     if not x.is_contiguous():
         raise ValueError("allreduce_sum needs a contiguous tensor")
-    dist.all_reduce(torch.view_as_real(x), op=dist.ReduceOp.SUM, group=group)
+    if dist.is_available() and dist.is_initialized():
+        dist.all_reduce(torch.view_as_real(x), op=dist.ReduceOp.SUM, group=group)
     return x
 
 
