@@ -558,6 +558,48 @@ def read_peaks():
         return {}
 
 
+def run_config5_probe(args, npts: int = 8, passes: int = 12):
+    """The learned warm start's workload at its stated size (2D 64^2, n_w = 128, N_W = 31,
+    U in [2, 6], beta in [5, 25], t' in [-0.3, 0]): for `npts` of its points, up to `passes`
+    mixed-precision passes from Sigma~ = 0, the residual of every pass, the device time of a
+    pass and the largest |lambda| at W = 0 (the ladder's convergence radius): whether the
+    plain loop converges there at all, which decides whether its 2000 converged runs can be
+    generated."""
+    import numpy as np
+    import torch
+    from paper_1507_00895_gb300 import build, df, inputs as I
+    build.build_lib()
+    rows = []
+    for w in I.config5_points(npts):
+        with df.DualFermion.from_workload(w, precision=df.DF_FP32_IR, eig_mode=1) as d:
+            d.set_timing(True)
+            res = []
+            t0 = time.perf_counter()
+            for _ in range(passes):
+                d.bubble()
+                d.bse(3)
+                try:
+                    r = d.sigma()
+                except df.DFError as e:
+                    res.append(f"{e}")
+                    break
+                res.append(r)
+                if not np.isfinite(r) or r > 1e6 or r < 1e-8:
+                    break
+            d.synchronize()
+            wall = time.perf_counter() - t0
+            t = d.get_timing()
+            lam, ok = d.get_lambda()
+        rows.append({"U": w.U, "beta": w.beta, "tp": w.tp, "mu": w.mu, "passes": len(res), "residuals": res,
+                     "s_per_pass": wall / max(1, len(res)),
+                     "ladder_ms_per_pass": t["bse"][0] / max(1, len(res)),
+                     "max_abs_lambda_W0": float(np.max(np.abs(lam[:, w.m_max]))),
+                     "converged": bool(res and isinstance(res[-1], float) and res[-1] < 1e-8)})
+    print(json.dumps({"probe": "learned-warm-start workload at its stated size", "points": rows,
+                      "converged": sum(r["converged"] for r in rows), "of": len(rows)}))
+    return 0
+
+
 def run_omega_split(args):
     """One problem over N GPUs (the Omega split): every rank owns a contiguous range of the
     bosonic planes (split.omega_partition), runs the bubble and the ladders of its planes, its
@@ -829,6 +871,8 @@ def main():
                     help="skip the 3D critical workload's passes (order 96, both precisions)")
     ap.add_argument("--no-observables", action="store_true",
                     help="skip the lattice-observable, susceptibility and radius-extension timings")
+    ap.add_argument("--config5-probe", action="store_true",
+                    help="only: convergence and pass time of the warm-start workload at its stated size")
     ap.add_argument("--omega-split", action="store_true",
                     help="one problem over the N GPUs (bosonic planes split, one all-reduce per pass) "
                          "instead of N replicas")
@@ -838,6 +882,8 @@ def main():
         return run_reference(args)
     if args.omega_split:
         return run_omega_split(args)
+    if args.config5_probe:
+        return run_config5_probe(args)
     return run_ours(args)
 
 

@@ -1,9 +1,9 @@
 // Learned warm start of the dual self-energy: a dense network (4 layers,
 // n_in -> W -> W -> W -> n_out, tanh between, linear output) evaluated and
 // trained with this file's kernels.  Operands of every matrix product are
-// rounded to BF16 and multiplied on the tensor cores (mma.sync m16n8k16,
-// FP32 accumulate); master weights, biases, Adam moments and activations
-// are FP32.  The network's output is Sigma~ on the irreducible wedge of the
+// rounded to BF16 and multiplied on the tensor cores (tcgen05, FP32
+// accumulate in tensor memory); master weights, biases, Adam moments and
+// activations are FP32.  The network's output is Sigma~ on the irreducible wedge of the
 // square lattice's point group at positive Matsubara frequencies;
 // df_warmstart_sigma expands it to the whole grid (D4 images and
 // Sigma~(k, -w) = conj Sigma~(k, w)) and sets it as the loop's Sigma~.
@@ -17,102 +17,122 @@
 
 #include <cuda_bf16.h>
 
-#include "df_internal.cuh"
+#include "df_tcgj_dev.cuh"
 
 namespace df {
 
-constexpr int kTm = 64, kTn = 64, kTk = 32;   // block tile
-constexpr int kGemmThreads = 128;             // 4 warps, 32 x 32 each
-constexpr int kPad = 8;                       // bf16 padding of the k rows
-
-__device__ __forceinline__ unsigned pack_bf16(float lo, float hi) {
-  const __nv_bfloat16 a = __float2bfloat16_rn(lo), b = __float2bfloat16_rn(hi);
-  return (unsigned)__bfloat16_as_ushort(a) | ((unsigned)__bfloat16_as_ushort(b) << 16);
-}
+constexpr int kGm = 128, kGn = 128, kGk = 64;  // block tile: M x N outputs, K per stage
+constexpr int kGemmThreads = 256;               // 8 warps: staging, epilogue; thread 0 issues the MMAs
+constexpr int kGemmTmemCols = 128;              // the FP32 accumulator tile (N = 128 columns)
+constexpr int kGemmStage = kGm * kGk * 2;       // bytes of one operand tile (128 rows x 64 bf16)
+constexpr int kGemmSmem = 4 * kGemmStage + 1024;   // two stages of (A, B) + alignment slack
 
 // C[m][n] = act(sum_k bf16(A(m,k)) bf16(B(k,n)) + bias[n]) (+ C[m][n] if accumulate)
 // A(m,k) = A[m sam + k sak], B(k,n) = B[k sbk + n sbn], C row-major with ldc.
-// act: 0 identity, 1 tanh.
+// act: 0 identity, 1 tanh.  One 128 x 128 output tile per block on the tensor
+// cores (tcgen05, M = 128, N = 128, K = 16 per MMA, FP32 accumulator in tensor
+// memory): per stage of 64 k the block rounds its A and B tiles to BF16 into
+// shared memory (K-major, 128-byte swizzle), thread 0 issues 4 MMAs and commits
+// them to the stage buffer's barrier, and the next stage is staged into the
+// other buffer meanwhile.  The epilogue reads the accumulator from tensor
+// memory (warp w: lanes 32 (w % 4) .., columns 64 (w / 4) ..).  Waits are
+// bounded; one that gives up sets *err.
 __global__ void __launch_bounds__(kGemmThreads)
-gemm_bf16_kernel(int M, int N, int K, const float* __restrict__ A, long sam, long sak, const float* __restrict__ B,
-                 long sbk, long sbn, float* __restrict__ C, long ldc, const float* __restrict__ bias, int act,
-                 int accumulate) {
-  __shared__ __align__(16) __nv_bfloat16 As[kTm][kTk + kPad];
-  __shared__ __align__(16) __nv_bfloat16 Bs[kTn][kTk + kPad];   // [n][k]
-  const int m0 = blockIdx.y * kTm, n0 = blockIdx.x * kTn;
+gemm_tc_kernel(int M, int N, int K, const float* __restrict__ A, long sam, long sak, const float* __restrict__ B,
+               long sbk, long sbn, float* __restrict__ C, long ldc, const float* __restrict__ bias, int act,
+               int accumulate, int* __restrict__ err) {
+  extern __shared__ unsigned char gsm_raw[];
+  __shared__ uint64_t bar_s[2];
+  __shared__ unsigned tslot_s;
+  unsigned char* gsm = reinterpret_cast<unsigned char*>(((uintptr_t)gsm_raw + 1023) & ~(uintptr_t)1023);
+  const int m0 = blockIdx.y * kGm, n0 = blockIdx.x * kGn;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
-  const int g = lane >> 2, t4 = lane & 3;
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
-
-  for (int k0 = 0; k0 < K; k0 += kTk) {
-    for (int idx = tid; idx < kTm * kTk; idx += kGemmThreads) {
-      const int r = idx / kTk, k = idx % kTk;
+  if (warp == 0) tmem_alloc_cols<kGemmTmemCols>(&tslot_s);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_s[0])) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bar_s[1])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc05_fence_before();
+  __syncthreads();
+  tc05_fence_after();
+  const unsigned tmem = tslot_s;
+  const unsigned idesc = umma_idesc_bf16(kGm, kGn);
+  unsigned ph = 0u;                                  // bit b: the phase of buffer b's barrier
+  bool ok = true;
+  const int nst = (K + kGk - 1) / kGk;
+  for (int st = 0; st < nst; ++st) {
+    const int b = st & 1, k0 = st * kGk;
+    if (st >= 2) {                                   // the MMAs that read this buffer are done
+      ok = ok && mbar_wait(&bar_s[b], (ph >> b) & 1u);
+      ph ^= 1u << b;
+    }
+    if (__syncthreads_or(!ok)) break;
+    __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(gsm + b * 2 * kGemmStage);
+    __nv_bfloat16* Bs = reinterpret_cast<__nv_bfloat16*>(gsm + b * 2 * kGemmStage + kGemmStage);
+    // A tile [m][k]: k fastest when A's rows are contiguous, m fastest otherwise
+    for (int idx = tid; idx < kGm * kGk; idx += kGemmThreads) {
+      const int r = sak == 1 ? idx / kGk : idx % kGm, k = sak == 1 ? idx % kGk : idx / kGm;
       const int gm = m0 + r, gk = k0 + k;
       const float v = (gm < M && gk < K) ? A[gm * sam + gk * sak] : 0.f;
-      As[r][k] = __float2bfloat16_rn(v);
+      As[swz(r, k)] = __float2bfloat16_rn(v);
     }
-    for (int idx = tid; idx < kTn * kTk; idx += kGemmThreads) {
-      const int nn = idx / kTk, k = idx % kTk;
+    // B tile [n][k]: n fastest when B's rows (over n) are contiguous, k fastest otherwise
+    for (int idx = tid; idx < kGn * kGk; idx += kGemmThreads) {
+      const int nn = sbn == 1 ? idx % kGn : idx / kGk, k = sbn == 1 ? idx / kGn : idx % kGk;
       const int gn = n0 + nn, gk = k0 + k;
       const float v = (gn < N && gk < K) ? B[gk * sbk + gn * sbn] : 0.f;
-      Bs[nn][k] = __float2bfloat16_rn(v);
+      Bs[swz(nn, k)] = __float2bfloat16_rn(v);
     }
+    fence_async_smem();
+    tc05_fence_before();
     __syncthreads();
+    if (tid == 0) {
+      tc05_fence_after();
+      const unsigned a = smem_u32(As), bb = smem_u32(Bs);
 #pragma unroll
-    for (int kk = 0; kk < kTk; kk += 16) {
-      unsigned af[2][4], bfr[4][2];
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt) {
-        const int r = wm + mt * 16 + g;
-        af[mt][0] = *reinterpret_cast<const unsigned*>(&As[r][kk + 2 * t4]);
-        af[mt][1] = *reinterpret_cast<const unsigned*>(&As[r + 8][kk + 2 * t4]);
-        af[mt][2] = *reinterpret_cast<const unsigned*>(&As[r][kk + 2 * t4 + 8]);
-        af[mt][3] = *reinterpret_cast<const unsigned*>(&As[r + 8][kk + 2 * t4 + 8]);
-      }
-#pragma unroll
-      for (int nt = 0; nt < 4; ++nt) {
-        const int cn = wn + nt * 8 + g;
-        bfr[nt][0] = *reinterpret_cast<const unsigned*>(&Bs[cn][kk + 2 * t4]);
-        bfr[nt][1] = *reinterpret_cast<const unsigned*>(&Bs[cn][kk + 2 * t4 + 8]);
-      }
-#pragma unroll
-      for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-        for (int nt = 0; nt < 4; ++nt) {
-          float* d = acc[mt][nt];
-          asm volatile(
-              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 "
-              "{%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
-              : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-              : "r"(af[mt][0]), "r"(af[mt][1]), "r"(af[mt][2]), "r"(af[mt][3]), "r"(bfr[nt][0]),
-                "r"(bfr[nt][1]));
-        }
+      for (int ks = 0; ks < kGk / 16; ++ks)
+        umma_bf16(tmem, umma_desc_sw128(a + 32 * ks), umma_desc_sw128(bb + 32 * ks), idesc,
+                  (st > 0 || ks > 0) ? 1u : 0u);
+      umma_commit(&bar_s[b]);
     }
-    __syncthreads();
   }
+  // the last one or two commits: every MMA done before the epilogue
+  for (int st = nst - 2 < 0 ? 0 : nst - 2; ok && st < nst; ++st) {
+    const int b = st & 1;
+    ok = mbar_wait(&bar_s[b], (ph >> b) & 1u);
+    ph ^= 1u << b;
+  }
+  tc05_fence_after();
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) atomicOr(err, 1);
+  } else {
+    const int q = warp & 3, half = warp >> 2;
+    const int r = m0 + 32 * q + lane;
+    const unsigned tl = tmem + ((32u * q) << 16) + (unsigned)(64 * half);
 #pragma unroll
-  for (int mt = 0; mt < 2; ++mt)
+    for (int c16 = 0; c16 < 4; ++c16) {
+      float v[16];
+      tmem_ld16(tl + 16 * c16, v);
+      if (r < M) {
 #pragma unroll
-    for (int nt = 0; nt < 4; ++nt)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int r = m0 + wm + mt * 16 + g + (e >= 2 ? 8 : 0);
-        const int cn = n0 + wn + nt * 8 + 2 * t4 + (e & 1);
-        if (r < M && cn < N) {
-          float v = acc[mt][nt][e];
-          if (bias) v += bias[cn];
-          if (act == 1) v = tanhf(v);
-          float* dst = C + r * ldc + cn;
-          *dst = accumulate ? *dst + v : v;
+        for (int e = 0; e < 16; ++e) {
+          const int cn = n0 + 64 * half + 16 * c16 + e;
+          if (cn < N) {
+            float x = v[e];
+            if (bias) x += bias[cn];
+            if (act == 1) x = tanhf(x);
+            float* dst = C + (long)r * ldc + cn;
+            *dst = accumulate ? *dst + x : x;
+          }
         }
       }
+    }
+  }
+  tc05_fence_before();
+  __syncthreads();
+  tc05_fence_after();
+  if (warp == 0) tmem_dealloc_cols<kGemmTmemCols>(tmem);
 }
 
 // dY = 2 (Y - T) / (B n_out); per-block partial sums of (Y - T)^2
@@ -200,6 +220,7 @@ struct df_mlp {
   float* dact = nullptr;     // scratch for dA / dZ (max width)
   float* dact2 = nullptr;
   float* partial = nullptr;
+  int* d_timeout = nullptr;  // set by a tensor-core GEMM whose bounded wait gave up
   float* h_loss = nullptr;
   long step = 0;
 };
@@ -222,10 +243,19 @@ df_status mfail(df_mlp* m, df_status s, const char* what, cudaError_t e = cudaSu
       return mfail((m), e__ == cudaErrorMemoryAllocation ? DF_ERR_OOM : DF_ERR_CUDA, (what), e__); \
   } while (0)
 
-cudaError_t gemm(cudaStream_t s, int M, int N, int K, const float* A, long sam, long sak, const float* B, long sbk,
-                 long sbn, float* C, long ldc, const float* bias, int act, int accumulate) {
-  dim3 grid((N + kTn - 1) / kTn, (M + kTm - 1) / kTm);
-  gemm_bf16_kernel<<<grid, kGemmThreads, 0, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, bias, act, accumulate);
+// err: the handle's device flag a GEMM sets when a bounded tensor-core wait gave up
+cudaError_t gemm(cudaStream_t s, int* err, int M, int N, int K, const float* A, long sam, long sak, const float* B,
+                 long sbk, long sbn, float* C, long ldc, const float* bias, int act, int accumulate) {
+  static bool attr = false;
+  if (!attr) {
+    const cudaError_t e = cudaFuncSetAttribute((const void*)gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               kGemmSmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  dim3 grid((N + kGn - 1) / kGn, (M + kGm - 1) / kGm);
+  gemm_tc_kernel<<<grid, kGemmThreads, kGemmSmem, s>>>(M, N, K, A, sam, sak, B, sbk, sbn, C, ldc, bias, act, accumulate,
+                                                       err);
   return cudaGetLastError();
 }
 
@@ -236,7 +266,7 @@ df_status forward(df_mlp* m, const float* x, int B) {
          "copy input");
   for (int l = 0; l < 4; ++l) {
     const int in = m->dims[l], out = m->dims[l + 1];
-    M_CUDA(m, gemm(m->stream, B, out, in, m->act[l], in, 1, m->params + m->off_w[l], out, 1, m->act[l + 1], out,
+    M_CUDA(m, gemm(m->stream, m->d_timeout, B, out, in, m->act[l], in, 1, m->params + m->off_w[l], out, 1, m->act[l + 1], out,
                    m->params + m->off_b[l], l < 3 ? 1 : 0, 0),
            "forward GEMM");
   }
@@ -254,13 +284,13 @@ df_status backward(df_mlp* m, const float* target, int B, float* loss_host) {
   for (int l = 3; l >= 0; --l) {
     const int in = m->dims[l], out = m->dims[l + 1];
     // dW_l[in][out] = A_{l}^T dZ   (M = in, N = out, K = B)
-    M_CUDA(m, gemm(m->stream, in, out, B, m->act[l], 1, in, dz, out, 1, m->grads + m->off_w[l], out, nullptr, 0, 0),
+    M_CUDA(m, gemm(m->stream, m->d_timeout, in, out, B, m->act[l], 1, in, dz, out, 1, m->grads + m->off_w[l], out, nullptr, 0, 0),
            "weight gradient");
     colsum_kernel<<<(out + 255) / 256, 256, 0, m->stream>>>(B, out, dz, m->grads + m->off_b[l]);
     M_CUDA(m, cudaGetLastError(), "bias gradient");
     if (l == 0) break;
     // dA_{l} [B][in] = dZ W_l^T   (M = B, N = in, K = out; B(k, n) = W[n][k])
-    M_CUDA(m, gemm(m->stream, B, in, out, dz, out, 1, m->params + m->off_w[l], 1, out, da, in, nullptr, 0, 0),
+    M_CUDA(m, gemm(m->stream, m->d_timeout, B, in, out, dz, out, 1, m->params + m->off_w[l], 1, out, da, in, nullptr, 0, 0),
            "activation gradient");
     tanh_back_kernel<<<blocks_for((long)B * in), 256, 0, m->stream>>>((long)B * in, m->act[l], da);
     M_CUDA(m, cudaGetLastError(), "tanh backward");
@@ -272,7 +302,10 @@ df_status backward(df_mlp* m, const float* target, int B, float* loss_host) {
     std::vector<float> part(nb);
     M_CUDA(m, cudaMemcpyAsync(part.data(), m->partial, sizeof(float) * nb, cudaMemcpyDeviceToHost, m->stream),
            "loss copy");
+    int timeout = 0;
+    M_CUDA(m, cudaMemcpyAsync(&timeout, m->d_timeout, sizeof(int), cudaMemcpyDeviceToHost, m->stream), "flag copy");
     M_CUDA(m, cudaStreamSynchronize(m->stream), "loss");
+    if (timeout) return mfail(m, DF_ERR_TIMEOUT, "a tensor-core GEMM's completion wait gave up");
     double s = 0.0;
     for (float v : part) s += v;
     *loss_host = (float)(s / (double)count);
@@ -319,7 +352,9 @@ df_status df_mlp_create(df_mlp** out, int n_in, int width, int n_out, int max_ba
       (e = cudaMalloc(&m->m2, sizeof(float) * o)) != cudaSuccess ||
       (e = cudaMalloc(&m->dact, sizeof(float) * (long)max_batch * maxw)) != cudaSuccess ||
       (e = cudaMalloc(&m->dact2, sizeof(float) * (long)max_batch * maxw)) != cudaSuccess ||
-      (e = cudaMalloc(&m->partial, sizeof(float) * 1024)) != cudaSuccess) {
+      (e = cudaMalloc(&m->partial, sizeof(float) * 1024)) != cudaSuccess ||
+      (e = cudaMalloc(&m->d_timeout, sizeof(int))) != cudaSuccess ||
+      (e = cudaMemset(m->d_timeout, 0, sizeof(int))) != cudaSuccess) {
     st = mfail(m, DF_ERR_OOM, "cudaMalloc", e);
   }
   for (int l = 0; l < 5 && st == DF_OK; ++l)
@@ -349,6 +384,7 @@ void df_mlp_destroy(df_mlp* m) {
   cudaFree(m->dact);
   cudaFree(m->dact2);
   cudaFree(m->partial);
+  cudaFree(m->d_timeout);
   for (auto* a : m->act) cudaFree(a);
   delete m;
 }

@@ -301,6 +301,26 @@ def uneven_batch(npts: int = 64, seed: int = 4, max_n_w: int = 128, max_m: int =
     return out
 
 
+def config5_points(npts: int, seed0: int = 5000, nk: int = 64, n_w: int = 128, m_max: int = 15):
+    """Parameter points of the learned-warm-start workload at its stated size:
+    2D 64^2, n_w = 128, N_W = 31, U ~ U[2, 6], beta ~ U[5, 25], t' ~ U[-0.3, 0],
+    mu = U/2 + U[-0.5, 0.5]; point i from numpy's default_rng(seed0 + i); g of
+    the atom at mu, the half-filled closed-form vertex, Delta = <eps^2> g."""
+    out = []
+    for i in range(npts):
+        rng = np.random.default_rng(seed0 + i)
+        u = float(rng.uniform(2.0, 6.0))
+        b = float(rng.uniform(5.0, 25.0))
+        t2 = float(rng.uniform(-0.3, 0.0))
+        mu = u / 2.0 + float(rng.uniform(-0.5, 0.5))
+        g = atom_g(u, b, mu, n_w, m_max)
+        delta = second_moment(2, 1.0, t2) * g
+        guu, gud = atom_vertices(u, b, n_w, m_max)
+        out.append(Workload(f"c5_{seed0 + i}", 2, nk, 1.0, t2, u, b, mu, n_w, m_max, g, delta,
+                            guu.astype(np.complex128), gud.astype(np.complex128)))
+    return out
+
+
 def warmstart_family(npts: int, seed: int, nk: int = 16, n_w: int = 16, m_max: int = 1,
                      U=(12.0, 28.0), beta=(0.6, 1.4), tp=(-0.3, 0.0), dmu=(-1.0, 1.0)):
     """Parameter points of the learned warm start: Hubbard-atom inputs around
