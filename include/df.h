@@ -126,6 +126,18 @@ typedef struct df_opts {
                        * pass ends with df_sigma_partial + (caller's sum over handles) +
                        * df_sigma_finish; df_sigma, df_iterate and df_susceptibility need
                        * the full range.  0 <= w_lo < w_hi <= N_W, or both 0. */
+  int symmetry;       /* point-group reduction of the ladders: 0 (default) every (q, W, channel)
+                       * is solved; 1 only one momentum per orbit of the lattice's point group
+                       * (axis permutations and sign flips k_j -> -k_j: D4 on the square
+                       * lattice, O_h on the cubic one; df_wedge lists the orbits) is solved
+                       * and its diag Gamma, Eq. sd bracket and leading eigenvalue are copied
+                       * to the orbit's other momenta.  Exact when G~(k) is invariant under
+                       * the group, which holds for the input contract (local g, Delta and
+                       * gamma; eps_k of df_lattice is invariant) whenever Sigma~ is:
+                       * Sigma~ = 0 at df_init, and Eq. sd keeps it invariant.  With 1,
+                       * df_set_sigma checks the invariance of what it is given (relative
+                       * 1e-12 of max |Sigma~|), and rejects with DF_ERR_ARG and Sigma~ = 0
+                       * otherwise.  The susceptibilities' ladders are not reduced. */
 } df_opts;
 
 /* Fill *o with the defaults above (n_w, m_max set to 0: the caller sets them). */
@@ -413,6 +425,18 @@ df_status df_selftest_wait(int arrive, int spins);
  * default stream.  Errors: DF_ERR_ARG (NULL gflops or kind out of range),
  * DF_ERR_OOM, DF_ERR_CUDA. */
 df_status df_peak_probe(int kind, double* gflops);
+
+/* The momentum orbits of the point group used by df_opts.symmetry (host only,
+ * no device work).  For the grid nk^dim (flat index, last axis fastest;
+ * dim, nk as in df_lattice) two momenta share an orbit when one maps to the
+ * other by permuting axes and flipping signs k_j -> -k_j (mod nk): the
+ * canonical form folds every coordinate to min(j, nk - j) and sorts them.
+ * qmap [nk^dim] (caller-owned, may be NULL) receives each momentum's orbit
+ * index; qrep [*n_orbits] (may be NULL; room for nk^dim entries) the
+ * smallest flat index in each orbit; orbits are numbered in the order of
+ * their qrep.  *n_orbits = C(nk/2 + dim, dim).  DF_ERR_ARG for sizes
+ * df_lattice does not allow. */
+df_status df_wedge(int dim, int nk, int* qmap, int* qrep, int* n_orbits);
 
 const char* df_last_error(const df_ctx* c);
 const char* df_status_string(df_status s);

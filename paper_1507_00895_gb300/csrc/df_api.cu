@@ -122,18 +122,54 @@ cudaError_t run_lambda(df_ctx* c, int mask) {
 }
 // both ladder stages of a pass: the solves and the leading eigenvalue; with the
 // radius extension the eigenvalue goes first (the solves read it)
-cudaError_t run_ladders(df_ctx* c, int mask) {
-  cudaError_t e = cudaMemsetAsync(bse_flags(c), 0, sizeof(int) * 4, c->stream);
-  if (e != cudaSuccess) return e;
-  // the mixed path's error-control words: worst rho^2 and the hand-back count
-  if (c->mixed_ws && (e = cudaMemsetAsync(mixed_check_words(c), 0, sizeof(unsigned) * 4, c->stream)) != cudaSuccess)
-    return e;
+cudaError_t run_ladders_on(df_ctx* c, int mask) {
+  cudaError_t e;
   if (c->opts.radius_order > 0) {
     if ((e = run_lambda(c, mask)) != cudaSuccess) return e;
     return run_bse(c, mask);
   }
   if ((e = run_bse(c, mask)) != cudaSuccess) return e;
   return run_lambda(c, mask);
+}
+// With the point-group reduction the ladder kernels run on the compact
+// arrays of the orbit representatives, seen as a grid of n_orb momenta.
+struct WedgeView {
+  df_ctx* c;
+  int N;
+  double2 *chi, *kc, *lam;
+  int* ok;
+  explicit WedgeView(df_ctx* cc) : c(cc), N(cc->dm.N), chi(cc->chi), kc(cc->kc), lam(cc->lam), ok(cc->lam_ok) {
+    c->dm.N = c->n_orb;
+    c->chi = c->chi_w;
+    c->kc = c->kc_w;
+    c->lam = c->lam_w;
+    c->lam_ok = c->lam_ok_w;
+  }
+  ~WedgeView() {
+    c->dm.N = N;
+    c->chi = chi;
+    c->kc = kc;
+    c->lam = lam;
+    c->lam_ok = ok;
+  }
+};
+cudaError_t run_ladders(df_ctx* c, int mask) {
+  cudaError_t e = cudaMemsetAsync(bse_flags(c), 0, sizeof(int) * 4, c->stream);
+  if (e != cudaSuccess) return e;
+  // the mixed path's error-control words: worst rho^2 and the hand-back count
+  if (c->mixed_ws && (e = cudaMemsetAsync(mixed_check_words(c), 0, sizeof(unsigned) * 4, c->stream)) != cudaSuccess)
+    return e;
+  if (!c->opts.symmetry) return run_ladders_on(c, mask);
+  {
+    Timed t(c, DF_T_BSE, 1);
+    if ((e = launch_wedge_gather(c)) != cudaSuccess) return e;
+  }
+  {
+    WedgeView view(c);
+    if ((e = run_ladders_on(c, mask)) != cudaSuccess) return e;
+  }
+  Timed t(c, DF_T_BSE, 1);
+  return launch_wedge_scatter(c, c->opts.eig_mode != 0);
 }
 cudaError_t run_sigma(df_ctx* c) {
   Timed t(c, DF_T_SIGMA, 3);
@@ -170,6 +206,7 @@ df_status df_default_opts(df_opts* o) {
   o->mixed_sweep = 0;
   o->w_lo = 0;
   o->w_hi = 0;
+  o->symmetry = 0;
   return DF_OK;
 }
 
@@ -219,6 +256,13 @@ void df_destroy(df_ctx* c) {
   cudaFree(c->red);
   cudaFree(c->bse_ws);
   cudaFree(c->mixed_ws);
+  cudaFree(c->qmap);
+  cudaFree(c->qrep);
+  cudaFree(c->chi_w);
+  cudaFree(c->kc_w);
+  cudaFree(c->lam_w);
+  cudaFree(c->lam_ok_w);
+  cudaFree(c->sym_chk);
   if (c->h_red) cudaFreeHost(c->h_red);
   for (auto& m : c->marks) {
     cudaEventDestroy(m.a);
@@ -250,6 +294,7 @@ df_status df_init(df_ctx** out, const df_lattice* lat, double beta, double mu, d
   if (!(opts->ladder_tol > 0.0 && opts->ladder_tol < 1.0) || (opts->ladder_fallback != 0 && opts->ladder_fallback != 1))
     return DF_ERR_ARG;
   if (opts->mixed_sweep != 0 && opts->mixed_sweep != 1) return DF_ERR_ARG;
+  if (opts->symmetry != 0 && opts->symmetry != 1) return DF_ERR_ARG;
   {
     const int nbos = 2 * opts->m_max + 1;
     const bool full = opts->w_lo == 0 && opts->w_hi == 0;
@@ -315,12 +360,35 @@ df_status df_init(df_ctx** out, const df_lattice* lat, double beta, double mu, d
   ALLOC(c->lam, (size_t)2 * dm.nb * dm.N);
   ALLOC(c->lam_ok, (size_t)2 * dm.nb * dm.N);
   ALLOC(c->red, (size_t)2 * dm.n_w + 4);
+  if (opts->symmetry) {
+    std::vector<int> qmap, qrep;
+    c->n_orb = build_wedge(dm.D, dm.nk, qmap, qrep);
+    const size_t nw = (size_t)c->n_orb;
+    ALLOC(c->qmap, (size_t)dm.N);
+    ALLOC(c->qrep, nw);
+    ALLOC(c->chi_w, (size_t)dm.nb * dm.n_w * nw);
+    ALLOC(c->kc_w, (size_t)2 * dm.nb * dm.n_w * nw);
+    ALLOC(c->lam_w, (size_t)2 * dm.nb * nw);
+    ALLOC(c->lam_ok_w, (size_t)2 * dm.nb * nw);
+    ALLOC(c->sym_chk, 2);
+    cudaError_t ea;
+    if ((ea = cudaMemcpy(c->qmap, qmap.data(), sizeof(int) * dm.N, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (ea = cudaMemcpy(c->qrep, qrep.data(), sizeof(int) * nw, cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (ea = cudaMemsetAsync(c->chi_w, 0, sizeof(double2) * dm.nb * dm.n_w * nw, c->stream)) != cudaSuccess ||
+        (ea = cudaMemsetAsync(c->kc_w, 0, sizeof(double2) * 2 * dm.nb * dm.n_w * nw, c->stream)) != cudaSuccess ||
+        (ea = cudaMemsetAsync(c->lam_w, 0, sizeof(double2) * 2 * dm.nb * nw, c->stream)) != cudaSuccess ||
+        (ea = cudaMemsetAsync(c->lam_ok_w, 0xff, sizeof(int) * 2 * dm.nb * nw, c->stream)) != cudaSuccess) {
+      st = fail(c, DF_ERR_CUDA, "point-group tables", ea);
+      goto bad;
+    }
+  }
   c->bse_grid = bse_default_grid(dm, c->device);
   c->bse_ws_bytes = bse_workspace_bytes(dm, c->bse_grid);
   {
     cudaError_t ea = cudaMalloc(&c->bse_ws, c->bse_ws_bytes);
     if (ea != cudaSuccess) { st = fail(c, DF_ERR_OOM, "cudaMalloc bse workspace", ea); goto bad; }
     if (opts->precision == DF_FP32_IR) {
+      c->tcr_off = mixed_tcr_offset(dm);
       ea = cudaMalloc(&c->mixed_ws, mixed_workspace_bytes(dm));
       if (ea != cudaSuccess) { st = fail(c, DF_ERR_OOM, "cudaMalloc mixed workspace", ea); goto bad; }
     }
@@ -510,6 +578,22 @@ df_status df_set_sigma(df_ctx* c, const double* in, int is_device) {
   if (!in) return fail(c, DF_ERR_ARG, "input pointer is NULL");
   DF_CUDA(c, cudaMemcpyAsync(c->sigma, in, sizeof(double2) * c->dm.n_w * c->dm.N, kind_to_dev(is_device), c->stream),
           "df_set_sigma");
+  if (c->opts.symmetry) {
+    // the reduction needs an invariant Sigma~: max deviation from the orbit representative
+    unsigned long long h[2];
+    DF_CUDA(c, launch_sigma_invariance(c, c->sym_chk), "point-group invariance of Sigma~");
+    DF_CUDA(c, cudaMemcpyAsync(h, c->sym_chk, sizeof h, cudaMemcpyDeviceToHost, c->stream), "invariance check");
+    DF_CUDA(c, cudaStreamSynchronize(c->stream), "invariance check");
+    double dev, mag;
+    memcpy(&dev, &h[0], sizeof dev);
+    memcpy(&mag, &h[1], sizeof mag);
+    if (!(dev <= 1e-12 * mag)) {
+      DF_CUDA(c, cudaMemsetAsync(c->sigma, 0, sizeof(double2) * c->dm.n_w * c->dm.N, c->stream), "reset Sigma~");
+      DF_CUDA(c, launch_dyson_ifft(c, c->dm.m_max, c->dm.n_w), "Dyson + FFT to real space");
+      DF_CUDA(c, cudaStreamSynchronize(c->stream), "df_set_sigma");
+      return fail(c, DF_ERR_ARG, "Sigma~ is not invariant under the lattice's point group (df_opts.symmetry = 1)");
+    }
+  }
   DF_CUDA(c, launch_dyson_ifft(c, c->dm.m_max, c->dm.n_w), "Dyson + FFT to real space");
   if (!is_device) DF_CUDA(c, cudaStreamSynchronize(c->stream), "df_set_sigma");
   return DF_OK;

@@ -278,6 +278,8 @@ struct df_ctx {
   double* h_red = nullptr;     // pinned host mirror of the final residual
   void* bse_ws = nullptr;      // global scratch of the BSE kernel (large n)
   void* mixed_ws = nullptr;    // DF_FP32_IR: gamma as FP32 (hi, lo) pairs
+  size_t tcr_off = 0;          // byte offset of the tensor-core residual's digits in mixed_ws (fixed at
+                               // df_init: the hand-back list before it is sized for the full grid)
   int mixed_grid = 0;
   size_t bse_ws_bytes = 0;
   int bse_grid = 0;
@@ -285,6 +287,15 @@ struct df_ctx {
   int sigma_valid = 0;         // gk/gr reflect sigma
   double last_resid = -1.0;
   int radius_flag = 0;         // |lambda| >= 1 seen on the last df_bse
+  // point-group reduction (opts.symmetry): orbit map, representatives and the compact arrays
+  int n_orb = 0;
+  int* qmap = nullptr;         // [N] orbit of each momentum
+  int* qrep = nullptr;         // [n_orb] smallest momentum of each orbit
+  double2* chi_w = nullptr;    // [nb][n_w][n_orb]
+  double2* kc_w = nullptr;     // [2][nb][n_w][n_orb]
+  double2* lam_w = nullptr;    // [2][nb][n_orb]
+  int* lam_ok_w = nullptr;     // [2][nb][n_orb]
+  unsigned long long* sym_chk = nullptr;   // [2] invariance check of df_set_sigma
   // per-kernel-group timing (df_set_timing)
   int timing = 0;
   struct Mark { int slot; int launches; cudaEvent_t a, b; };
@@ -326,4 +337,9 @@ size_t tcr_workspace_bytes(const Dims& dm);
 unsigned* mixed_check_words(df_ctx* c);   // [0] worst rho^2, [2] hand-back count, [3 ..] list
 cudaError_t launch_bse_f64_list(df_ctx* c, const int* list);
 cudaError_t launch_split_gamma_t(df_ctx* c);
+// point-group reduction (df_sym.cu)
+int build_wedge(int dim, int nk, std::vector<int>& qmap, std::vector<int>& qrep);
+cudaError_t launch_wedge_gather(df_ctx* c);
+cudaError_t launch_wedge_scatter(df_ctx* c, bool with_lambda);
+cudaError_t launch_sigma_invariance(df_ctx* c, unsigned long long* out);
 }  // namespace df

@@ -175,7 +175,7 @@ size_t tcr_workspace_bytes(const Dims& dm) {
   if (!tcr_supported(dm.n_w)) return 0;
   return (size_t)2 * dm.nb * (tcr_gdig_bytes() + 2 * 128 * sizeof(int));
 }
-static unsigned char* tcr_gdig_ptr(df_ctx* c) { return (unsigned char*)c->mixed_ws + mixed_tcr_offset(c->dm); }
+static unsigned char* tcr_gdig_ptr(df_ctx* c) { return (unsigned char*)c->mixed_ws + c->tcr_off; }
 static int* tcr_rowe_ptr(df_ctx* c) {
   return (int*)(tcr_gdig_ptr(c) + (size_t)2 * c->dm.nb * tcr_gdig_bytes());
 }

@@ -42,7 +42,7 @@ EXPORTS = (
     "df_batch_reset", "df_batch_autotune", "df_batch_last_error", "df_batch_destroy", "df_mlp_create",
     "df_mlp_param_count", "df_mlp_forward", "df_mlp_gradients", "df_mlp_adam_step", "df_mlp_train_step",
     "df_mlp_params", "df_mlp_grads", "df_mlp_last_error", "df_mlp_destroy", "df_warmstart_sigma", "df_last_error",
-    "df_status_string", "df_destroy", "df_selftest_wait", "df_peak_probe",
+    "df_status_string", "df_destroy", "df_selftest_wait", "df_peak_probe", "df_wedge",
 )
 
 
@@ -66,7 +66,7 @@ class df_opts(C.Structure):
     _fields_ = [("n_w", C.c_int), ("m_max", C.c_int), ("mix", C.c_double), ("precision", C.c_int),
                 ("eig_mode", C.c_int), ("ir_max_steps", C.c_int), ("ir_tol", C.c_double),
                 ("radius_order", C.c_int), ("ladder_tol", C.c_double), ("ladder_fallback", C.c_int),
-                ("mixed_sweep", C.c_int), ("w_lo", C.c_int), ("w_hi", C.c_int)]
+                ("mixed_sweep", C.c_int), ("w_lo", C.c_int), ("w_hi", C.c_int), ("symmetry", C.c_int)]
 
 
 _lib = None
@@ -112,6 +112,7 @@ def load(path: str = LIB_PATH):
         "df_bse_noalloc": [P, P, C.c_int, C.c_int, C.c_int, P, P],
         "df_selftest_wait": [C.c_int, C.c_int],
         "df_peak_probe": [C.c_int, D],
+        "df_wedge": [C.c_int, C.c_int, P, P, I],
         "df_batch_init": [C.POINTER(P), C.c_int, C.c_void_p, C.c_int, C.c_double, C.c_double, P],
         "df_batch_iterate": [P, C.c_int, I, D, I],
         "df_batch_get_sigma": [P, C.c_int, P, C.c_int],
@@ -190,7 +191,7 @@ class DualFermion:
                  precision: int = DF_FP64, eig_mode: int = 1, ir_max_steps: int = 8,
                  ir_tol: float = 1e-13, radius_order: int = 0, ladder_tol: float = 1e-9,
                  ladder_fallback: int = 1, mixed_sweep: int = 0, w_range: Optional[tuple] = None,
-                 stream: Optional[int] = None):
+                 symmetry: bool = False, stream: Optional[int] = None):
         self.lib = load()
         self.dim, self.nk, self.n_w, self.m_max = dim, nk, n_w, m_max
         self.N = nk ** dim
@@ -206,6 +207,7 @@ class DualFermion:
         if w_range is not None:
             opts.w_lo, opts.w_hi = int(w_range[0]), int(w_range[1])
         self.w_range = (opts.w_lo, opts.w_hi if opts.w_hi > 0 else self.nb)
+        opts.symmetry = 1 if symmetry else 0
         g, delta = _c128(g), _c128(delta)
         gd, gm = _c128(gamma_d), _c128(gamma_m)
         if g.shape != (self.ne,) or delta.shape != (self.ne,):
@@ -542,6 +544,21 @@ def vertex_from_spin(gamma_uu, gamma_ud):
     if s != DF_OK:
         raise DFError(s, "df_vertex_from_spin")
     return d, m
+
+
+def wedge(dim: int, nk: int):
+    """(qmap [nk^dim] int32: orbit index of every momentum, qrep [n_orb] int32:
+    smallest momentum of each orbit) for the point group of the hypercubic grid
+    (df_wedge: axis permutations and sign flips)."""
+    lib = load()
+    n = C.c_int(0)
+    N = nk ** dim
+    qmap = np.empty(N, np.int32)
+    qrep = np.empty(N, np.int32)
+    s = lib.df_wedge(dim, nk, qmap.ctypes.data, qrep.ctypes.data, C.byref(n))
+    if s != DF_OK:
+        raise DFError(s, "df_wedge")
+    return qmap, qrep[:n.value].copy()
 
 
 def peak_probe(kind: int) -> float:

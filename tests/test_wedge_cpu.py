@@ -1,0 +1,116 @@
+"""The momentum orbits of df_wedge (host only) against a brute-force action
+of the hypercubic point group, and the invariance that makes the ladder
+reduction of df_opts.symmetry exact, shown on the oracle: eps_k, the bubble
+chi~ (Eq. dual_bubble) and the Eq. sd kernel are constant on every orbit
+when Sigma~ is, and stop being so for a Sigma~ that is not."""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from oracle import df_oracle as O
+from paper_1507_00895_gb300 import inputs as I
+
+
+@pytest.fixture(scope="module")
+def df():
+    from paper_1507_00895_gb300 import build, df as dfm
+    build.build_lib()
+    return dfm
+
+
+def brute_orbits(dim, nk):
+    """Orbit label of every flat momentum under all 2^dim dim! signed axis
+    permutations, applied to the coordinate tuples."""
+    N = nk ** dim
+    coords = np.array(list(itertools.product(range(nk), repeat=dim)))   # C order = flat index
+    label = -np.ones(N, int)
+    ops = [(perm, signs) for perm in itertools.permutations(range(dim))
+           for signs in itertools.product((1, -1), repeat=dim)]
+    nxt = 0
+    for q in range(N):
+        if label[q] >= 0:
+            continue
+        for perm, signs in ops:
+            img = [(signs[d] * coords[q][perm[d]]) % nk for d in range(dim)]
+            flat = 0
+            for x in img:
+                flat = flat * nk + x
+            label[flat] = nxt
+        nxt += 1
+    return label, nxt
+
+
+@pytest.mark.parametrize("dim,nk", [(1, 8), (2, 4), (2, 16), (3, 8), (4, 4)])
+def test_orbits_match_the_group_action(df, dim, nk):
+    qmap, qrep = df.wedge(dim, nk)
+    label, n = brute_orbits(dim, nk)
+    assert len(qrep) == n == math.comb(nk // 2 + dim, dim)
+    # same partition: the maps are one relabelling of each other
+    pairs = set(zip(label.tolist(), qmap.tolist()))
+    assert len(pairs) == n
+    # representatives: the smallest member, orbits numbered in their order
+    for o, r in enumerate(qrep):
+        assert r == np.flatnonzero(qmap == o).min()
+    assert np.all(np.diff(qrep) > 0)
+
+
+def test_wedge_rejects_sizes_the_lattice_does_not_allow(df):
+    import ctypes as C
+    lib = df.load()
+    n = C.c_int(0)
+    assert lib.df_wedge(2, 6, None, None, C.byref(n)) == df.DF_ERR_ARG      # not a power of two
+    assert lib.df_wedge(3, 32, None, None, C.byref(n)) == df.DF_ERR_ARG     # 32^3 > 4096
+    assert lib.df_wedge(5, 2, None, None, C.byref(n)) == df.DF_ERR_ARG
+    assert lib.df_wedge(2, 8, None, None, C.byref(n)) == df.DF_OK and n.value == 15
+
+
+def spread(x, qmap):
+    """max over orbits of the spread of x[..., q] within the orbit, relative to max |x|."""
+    worst = 0.0
+    for o in range(qmap.max() + 1):
+        cols = x[..., qmap == o]
+        worst = max(worst, float(np.max(np.abs(cols - cols[..., :1]))))
+    return worst / max(float(np.max(np.abs(x))), 1e-300)
+
+
+@pytest.mark.parametrize("dim,nk,tp", [(2, 8, -0.2), (3, 4, 0.0)])
+def test_eps_is_invariant(df, dim, nk, tp):
+    qmap, _ = df.wedge(dim, nk)
+    eps = O.dispersion(dim, nk, 1.0, tp)
+    assert spread(eps[None, :], qmap) < 1e-14
+
+
+def one_pass_pieces(w, sigma):
+    eps = O.dispersion(w.dim, w.nk, w.t, w.tp)
+    g0 = O.bare_dual_g(w.g, w.delta, eps)
+    gt = O.dual_g(g0, sigma, w.n_w, w.m_max)
+    chi = O.dual_bubble_fft(gt, w.n_w, w.m_max, w.beta, w.dim, w.nk)
+    gd, gm = O.channel_vertices(w.gamma_uu, w.gamma_ud)
+    kern = O.sd_kernel(O.ladder_gamma_diag(gd, chi), O.second_order_diag(gd, chi),
+                       O.ladder_gamma_diag(gm, chi), O.second_order_diag(gm, chi))
+    return chi, kern
+
+
+def test_bubble_and_kernel_are_invariant_for_an_invariant_sigma(df):
+    w = I.workload("square32_tp", nk=8, n_w=8, m_max=1)
+    qmap, _ = df.wedge(w.dim, w.nk)
+    # an invariant Sigma~: the oracle's after three passes from zero
+    st = O.run_workload(w, n_iter=3)
+    assert spread(st.sigma, qmap) < 1e-12
+    chi, kern = one_pass_pieces(w, st.sigma)
+    assert spread(chi, qmap) < 1e-12
+    assert spread(kern, qmap) < 1e-10
+
+
+def test_a_sigma_that_breaks_the_symmetry_breaks_the_reduction(df):
+    # planted on the oracle side: Sigma~ with a k_x-only ripple is not D4-invariant,
+    # and the bubble then differs within orbits, so the reduction would not be exact
+    w = I.workload("square32_tp", nk=8, n_w=8, m_max=1)
+    qmap, _ = df.wedge(w.dim, w.nk)
+    kx = 2 * np.pi * np.repeat(np.arange(w.nk), w.nk) / w.nk
+    sigma = 0.05 * np.cos(kx)[None, :] * np.ones((w.n_w, 1))
+    assert spread(sigma, qmap) > 0.1
+    chi, _ = one_pass_pieces(w, sigma.astype(np.complex128))
+    assert spread(chi, qmap) > 1e-6
