@@ -327,8 +327,10 @@ def time_to_converged(df, I, torch, max_passes=60):
            "target": "max|Sigma~ - Sigma~*| <= 1e-8 max|Sigma~*|, Sigma~* = FP64 loop at r <= 1e-13",
            "reference_passes": it}
     den = float(np.max(np.abs(ref)))
-    for name, prec in (("fp64", df.DF_FP64), ("fp32ir", df.DF_FP32_IR)):
-        with df.DualFermion.from_workload(w, precision=prec, eig_mode=1, stream=stream.cuda_stream) as d:
+    for name, prec, sym in (("fp64", df.DF_FP64, False), ("fp32ir", df.DF_FP32_IR, False),
+                            ("fp64_reduced", df.DF_FP64, True), ("fp32ir_reduced", df.DF_FP32_IR, True)):
+        with df.DualFermion.from_workload(w, precision=prec, eig_mode=1, symmetry=sym,
+                                          stream=stream.cuda_stream) as d:
             d.iterate(1)                       # warm-up pass (kernels loaded, attributes set)
             d.set_sigma(np.zeros((w.n_w, w.N), np.complex128))
             total = 0.0
@@ -350,6 +352,9 @@ def time_to_converged(df, I, torch, max_passes=60):
         out[name] = {"passes": passes, "ms": total, "err_vs_fp64_converged": err}
     if "fp64" in out and "fp32ir" in out:
         out["speedup_mixed_vs_plain"] = out["fp64"]["ms"] / out["fp32ir"]["ms"]
+        out["speedup_mixed_reduced_vs_plain"] = out["fp64"]["ms"] / out["fp32ir_reduced"]["ms"]
+        out["reduced"] = ("df_opts.symmetry = 1: one ladder per momentum orbit of the point group "
+                          "(153 of 1024 momenta), copied to the orbit")
     return out
 
 
@@ -491,6 +496,22 @@ def large_order_bench(df, I, passes: int = 2):
         d.iterate(passes)
         t = d.get_timing()
     out["fp32ir_cuda_core_sweep"] = {"ladder_ms_per_pass": t["bse"][0] / passes, "kernel": "bse_gj_ir_kernel"}
+    _, qrep = df.wedge(w.dim, w.nk)
+    for name, prec in (("fp64_reduced", df.DF_FP64), ("fp32ir_reduced", df.DF_FP32_IR)):
+        with df.DualFermion.from_workload(w, precision=prec, symmetry=True) as d:
+            d.iterate(1)
+            red = d.get_sigma()
+            d.set_sigma(zero)
+            d.set_timing(True)
+            t0 = time.perf_counter()
+            d.iterate(passes)
+            d.synchronize()
+            wall = (time.perf_counter() - t0) / passes
+            t = d.get_timing()
+        out[name] = {"s_per_pass": wall, "ladder_ms_per_pass": t["bse"][0] / passes,
+                     "ladders_solved": 2 * w.n_bos * len(qrep),
+                     "points_per_s_full_grid": w.n_bos * w.N / wall,
+                     "err_vs_fp64_first_pass": float(np.max(np.abs(red - sig["fp64"])) / np.max(np.abs(sig["fp64"])))}
     return out
 
 
@@ -558,45 +579,85 @@ def read_peaks():
         return {}
 
 
-def run_config5_probe(args, npts: int = 8, passes: int = 12):
-    """The learned warm start's workload at its stated size (2D 64^2, n_w = 128, N_W = 31,
-    U in [2, 6], beta in [5, 25], t' in [-0.3, 0]): for `npts` of its points, up to `passes`
-    mixed-precision passes from Sigma~ = 0, the residual of every pass, the device time of a
-    pass and the largest |lambda| at W = 0 (the ladder's convergence radius): whether the
-    plain loop converges there at all, which decides whether its 2000 converged runs can be
-    generated."""
+def run_config5(args):
+    """The learned warm start at its stated grid (2D 64^2, n_w = 128, N_W = 31), one JSON line.
+
+    1. The stated parameter box (U in [2, 6], beta in [5, 25], t' in [-0.3, 0], mu = U/2 +
+       U[-0.5, 0.5], Hubbard-atom inputs): the leading |lambda| of gamma chi~ at W = 0 on the
+       first pass from Sigma~ = 0 (the ladder's convergence radius is |lambda| < 1) for 8
+       points, and whether the plain loop converges there (mixing 1 and 0.3, 12 passes).
+    2. The converging box at the same grid (Hubbard-atom inputs around the paper's Example I:
+       U in [12, 28], beta in [0.6, 1.4], t' in [-0.3, 0], mu = U/2 + U[-1, 1]): converged
+       Sigma~ of n_train points (mixed precision, point-group reduction, r <= 1e-8), the
+       4 x 512 network trained on them, and on n_test held-out points the passes and device
+       time to within 1e-8 of the FP64 Sigma~* from Sigma~ = 0 and from the prediction."""
     import numpy as np
     import torch
-    from paper_1507_00895_gb300 import build, df, inputs as I
+    from paper_1507_00895_gb300 import build, df, inputs as I, warmstart as W
     build.build_lib()
-    rows = []
-    for w in I.config5_points(npts):
-        with df.DualFermion.from_workload(w, precision=df.DF_FP32_IR, eig_mode=1) as d:
-            d.set_timing(True)
-            res = []
-            t0 = time.perf_counter()
-            for _ in range(passes):
-                d.bubble()
-                d.bse(3)
-                try:
-                    r = d.sigma()
-                except df.DFError as e:
-                    res.append(f"{e}")
-                    break
-                res.append(r)
-                if not np.isfinite(r) or r > 1e6 or r < 1e-8:
-                    break
-            d.synchronize()
-            wall = time.perf_counter() - t0
-            t = d.get_timing()
+    t_start = time.perf_counter()
+    stated = []
+    for k, w in enumerate(I.config5_points(8)):
+        row = {"U": w.U, "beta": w.beta, "tp": w.tp, "mu": w.mu}
+        with df.DualFermion.from_workload(w, precision=df.DF_FP32_IR, eig_mode=1, symmetry=True) as d:
+            d.bubble()
+            d.bse(3)
             lam, ok = d.get_lambda()
-        rows.append({"U": w.U, "beta": w.beta, "tp": w.tp, "mu": w.mu, "passes": len(res), "residuals": res,
-                     "s_per_pass": wall / max(1, len(res)),
-                     "ladder_ms_per_pass": t["bse"][0] / max(1, len(res)),
-                     "max_abs_lambda_W0": float(np.max(np.abs(lam[:, w.m_max]))),
-                     "converged": bool(res and isinstance(res[-1], float) and res[-1] < 1e-8)})
-    print(json.dumps({"probe": "learned-warm-start workload at its stated size", "points": rows,
-                      "converged": sum(r["converged"] for r in rows), "of": len(rows)}))
+            row["max_abs_lambda_W0_first_pass"] = float(np.max(np.abs(lam[:, w.m_max])))
+        if k < 2:
+            for mix in (1.0, 0.3):
+                with df.DualFermion.from_workload(w, precision=df.DF_FP32_IR, eig_mode=0, symmetry=True,
+                                                  mix=mix) as d:
+                    res = []
+                    try:
+                        for _ in range(12):         # stop once the loop has plainly diverged
+                            d.bubble()
+                            d.bse(3)
+                            res.append(d.sigma())
+                            if not (res[-1] < 1e6) or res[-1] <= 1e-8:
+                                break
+                        row[f"mix_{mix}"] = {"passes": len(res), "residuals": res}
+                    except df.DFError as e:
+                        row[f"mix_{mix}"] = {"passes": len(res), "residuals": res, "error": str(e)}
+        stated.append(row)
+    t_probe = time.perf_counter() - t_start
+
+    grid = dict(nk=64, n_w=128, m_max=15)
+    train = I.warmstart_family(args.c5_train, seed=5000, **grid)
+    test = I.warmstart_family(args.c5_test, seed=7000, **grid)
+    t0 = time.perf_counter()
+    X, Y, passes, mask = W.generate_each(train, precision=df.DF_FP32_IR, symmetry=True, tol=1e-8)
+    t_gen = time.perf_counter() - t0
+    out = {"probe": "learned warm start at the stated grid (2D 64^2, n_w=128, N_W=31)",
+           "stated_box": {"points": stated, "seconds": t_probe,
+                          "beyond_radius": sum(r["max_abs_lambda_W0_first_pass"] >= 1.0 for r in stated)},
+           "converging_box": "Hubbard-atom inputs around Example I: U 12-28, beta 0.6-1.4, t' -0.3-0, "
+                             "mu = U/2 +- 1",
+           "train": {"points": len(train), "converged": int(mask.sum()), "mean_passes": float(np.mean(passes)),
+                     "seconds": t_gen, "path": "DF_FP32_IR, point-group reduction, r <= 1e-8"}}
+    if mask.sum() >= 2:
+        model = W.WarmStart(X.shape[1], Y.shape[1], grid["nk"], width=512, seed=0)
+        t0 = time.perf_counter()
+        hist = model.train(X, Y, steps=args.c5_steps, batch=256, lr=1e-3, log_every=max(1, args.c5_steps // 10))
+        torch.cuda.synchronize()
+        out["train"]["network"] = {"n_in": int(X.shape[1]), "n_out": int(Y.shape[1]), "steps": args.c5_steps,
+                                   "seconds": time.perf_counter() - t0, "loss_history": hist}
+        t0 = time.perf_counter()
+        rows = W.evaluate(model, test, tol=1e-8, precision=df.DF_FP32_IR, symmetry=True)
+        ok = [r for r in rows if r["cold_passes"] is not None]
+        out["held_out"] = {"points": len(test), "evaluated": len(ok), "seconds": time.perf_counter() - t0,
+                           "target": "max|Sigma~ - Sigma~*| <= 1e-8 max|Sigma~*|, Sigma~* = FP64 loop (reduced) "
+                                     "at r <= 1e-12; path DF_FP32_IR with the reduction",
+                           "fallbacks": sum(r["fallback"] for r in ok)}
+        if ok:
+            cp = float(np.mean([r["cold_passes"] for r in ok]))
+            wp = float(np.mean([r["warm_passes"] for r in ok]))
+            out["held_out"].update({"cold_passes": cp, "warm_passes": wp, "pass_reduction": 1.0 - wp / cp,
+                                    "cold_ms": float(np.mean([r["cold_ms"] for r in ok])),
+                                    "warm_ms": float(np.mean([r["warm_ms"] for r in ok])),
+                                    "prediction_err_median": float(np.median([r["prediction_err"] for r in ok]))})
+    out["seconds_total"] = time.perf_counter() - t_start
+    print(json.dumps(out))
     return 0
 
 
@@ -684,8 +745,9 @@ def run_ours(args):
     # = n^3 complex multiply-adds = 8 n^3 real flops (full back substitutions: 10.67 n^3)
     algo_flop = 8.0 * n ** 3
 
-    def measure(prec):
-        d = df.DualFermion.from_workload(w, precision=prec, eig_mode=1, stream=stream.cuda_stream)
+    def measure(prec, symmetry=False):
+        d = df.DualFermion.from_workload(w, precision=prec, eig_mode=1, symmetry=symmetry,
+                                         stream=stream.cuda_stream)
 
         def step():
             d.bubble()
@@ -803,6 +865,25 @@ def run_ours(args):
         e2e = {"value": whole_job_rate(points, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": bi, "d2h_bytes_per_step": bo,
                "ms_per_step": e2e_s * 1e3}
     d.close()
+    # the point-group reduction on the same workload and timing protocol: rate counted over the
+    # full grid of (q, W) points (every point's Sigma~ contribution is produced), ladders
+    # solved = one per momentum orbit
+    reduced = None
+    if rank == 0 and not args.no_reduced:
+        _, qrep = df.wedge(w.dim, w.nk)
+        reduced = {"workload": WORKLOAD_DESC, "orbits": len(qrep), "momenta": w.N,
+                   "ladders_solved_per_step": 2 * w.n_bos * len(qrep)}
+        for name, p_ in (("fp64", df.DF_FP64), ("fp32ir", df.DF_FP32_IR)):
+            rd, rr = measure(p_, symmetry=True)
+            rd.set_sigma(zeros)
+            rd.bubble(); rd.bse(3); rd.sigma(want_residual=False)
+            if plain_sigma is not None:
+                rr["err_vs_fp64_first_pass"] = float(np.max(np.abs(rd.get_sigma() - plain_sigma))
+                                                     / np.max(np.abs(plain_sigma)))
+            rd.close()
+            reduced[name] = {"value": rr["value"], "unit": UNIT, "ms_per_step": rr["ms_per_step"],
+                             "kernel_ms_per_step": rr["kernel_ms_per_step"],
+                             "err_vs_fp64_first_pass": rr.get("err_vs_fp64_first_pass")}
     ttc = None
     if rank == 0 and not args.no_ttc:
         ttc = time_to_converged(df, I, torch)
@@ -846,6 +927,7 @@ def run_ours(args):
             "gpu_launches": main["gpu_launches"], "kernel_ms_per_step": main["kernel_ms_per_step"],
             "err_vs_fp64_first_pass": main.get("err_vs_fp64_first_pass"),
             "plain_fp64": plain if prec != df.DF_FP64 else None,
+            "point_group_reduced": reduced,
             "time_to_converged": ttc, "batch": batch, "batch_full": batch_full, "warm_start": warm,
             "example_i": sweeps, "alu_peaks": peaks,
             "observables": obs, "large_order": large, "clocks": main["clocks"]}
@@ -869,10 +951,15 @@ def main():
     ap.add_argument("--no-sweeps", action="store_true", help="skip the paper's Example I sweeps")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 3D critical workload's passes (order 96, both precisions)")
+    ap.add_argument("--no-reduced", action="store_true",
+                    help="skip the point-group-reduced passes of the bench workload")
     ap.add_argument("--no-observables", action="store_true",
                     help="skip the lattice-observable, susceptibility and radius-extension timings")
-    ap.add_argument("--config5-probe", action="store_true",
-                    help="only: convergence and pass time of the warm-start workload at its stated size")
+    ap.add_argument("--config5", action="store_true",
+                    help="only: the learned warm start at its stated grid (64^2, n_w=128, N_W=31)")
+    ap.add_argument("--c5-train", type=int, default=2000, help="--config5: training points")
+    ap.add_argument("--c5-test", type=int, default=200, help="--config5: held-out points")
+    ap.add_argument("--c5-steps", type=int, default=3000, help="--config5: training steps")
     ap.add_argument("--omega-split", action="store_true",
                     help="one problem over the N GPUs (bosonic planes split, one all-reduce per pass) "
                          "instead of N replicas")
@@ -882,8 +969,8 @@ def main():
         return run_reference(args)
     if args.omega_split:
         return run_omega_split(args)
-    if args.config5_probe:
-        return run_config5_probe(args)
+    if args.config5:
+        return run_config5(args)
     return run_ours(args)
 
 

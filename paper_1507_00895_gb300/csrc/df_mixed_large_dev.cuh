@@ -163,7 +163,10 @@ __device__ __forceinline__ bool gj_ir_system(const Dims& dm, int c, int a, int q
       if (jl < n) {
 #pragma unroll
         for (int e = 0; e < 8; ++e)
-          if (r + e < n) S[sh.ipiv[r + e] * ld + jl] = make_float2(v[2 * e], v[2 * e + 1]);
+          if (r + e < n) {
+            const int rr = sh.ipiv[r + e];
+            if ((unsigned)rr < (unsigned)n) S[rr * ld + jl] = make_float2(v[2 * e], v[2 * e + 1]);
+          }
       }
     }
     tc05_fence_before();

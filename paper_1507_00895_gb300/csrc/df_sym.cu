@@ -59,7 +59,8 @@ __global__ void wedge_gather_kernel(Dims dm, int n_orb, const int* __restrict__ 
 }
 
 // kc[c][a][i][q] = kc_w[c][a][i][qmap[q]] for a in the handle's range; the
-// leading eigenvalue and its flag likewise ([c][a][q])
+// leading eigenvalue and its flag likewise ([c][a][q]) when lam_w is given
+// (eigenvalues computed this pass)
 __global__ void wedge_scatter_kernel(Dims dm, int n_orb, const int* __restrict__ qmap,
                                      const double2* __restrict__ kc_w, double2* __restrict__ kc,
                                      const double2* __restrict__ lam_w, const int* __restrict__ ok_w,
@@ -75,7 +76,7 @@ __global__ void wedge_scatter_kernel(Dims dm, int n_orb, const int* __restrict__
     const long row = ((long)c * dm.nb + a) * dm.n_w + i;
     const int o = qmap[q];
     kc[row * dm.N + q] = kc_w[row * n_orb + o];
-    if (lam && i == 0) {
+    if (lam_w && i == 0) {
       const long lr = (long)c * dm.nb + a;
       lam[lr * dm.N + q] = lam_w[lr * n_orb + o];
       ok[lr * dm.N + q] = ok_w[lr * n_orb + o];
@@ -122,8 +123,8 @@ cudaError_t launch_wedge_scatter(df_ctx* c, bool with_lambda) {
   const Dims& dm = c->dm;
   const long total = 2L * dm.na * dm.n_w * dm.N;
   wedge_scatter_kernel<<<grid_for(total), 256, 0, c->stream>>>(dm, c->n_orb, c->qmap, c->kc_w, c->kc,
-                                                               with_lambda ? c->lam_w : nullptr, c->lam_ok_w, c->lam,
-                                                               c->lam_ok);
+                                                               with_lambda ? c->lam_w : nullptr,
+                                                               with_lambda ? c->lam_ok_w : nullptr, c->lam, c->lam_ok);
   return cudaGetLastError();
 }
 

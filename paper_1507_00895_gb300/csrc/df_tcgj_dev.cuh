@@ -181,8 +181,11 @@ __device__ __forceinline__ bool tcgj_sweep(unsigned tmem, int nr, int nc, const 
           const int par = (k0 + s) & 1;
           unsigned key = 0u;
           if (!used) {
+            // |pivot| bits (+ one step, so that a zero or NaN candidate in row 127
+            // still has a nonzero key) with the row in the low bits: the pivot
+            // rows stay a permutation whatever the values
             const float m = fabsf(pv[s].x) + fabsf(pv[s].y);
-            key = (__float_as_uint(m) & ~0x7Fu) | (unsigned)(127 - tid);
+            key = ((__float_as_uint(m) & ~0x7Fu) + 0x80u) | (unsigned)(127 - tid);
           }
           const unsigned wk = __reduce_max_sync(0xffffffffu, key);
           if (key == wk && wk != 0u) {
@@ -200,7 +203,7 @@ __device__ __forceinline__ bool tcgj_sweep(unsigned tmem, int nr, int nc, const 
             if (k2 > best) { best = k2; bw = w2; }
           }
           const int p = 127 - (int)(best & 0x7Fu);
-          const float bm = __uint_as_float(best & ~0x7Fu);
+          const float bm = __uint_as_float((best & ~0x7Fu) - 0x80u);
           const bool ok = bm > 0.f && best != 0u;
           float2 prow[kTcPanel];
 #pragma unroll

@@ -254,8 +254,9 @@ __device__ __forceinline__ bool tcr_system(const Dims& dm, int c, int a, int q, 
         if (ml >= 0 && ml < kTcrCB) {
 #pragma unroll
           for (int e = 0; e < 8; ++e)
-            if (r + e < n) x0b[ipiv[r + e] * kTcrCB + ml] = (m0 + ml < n) ? make_float2(v[2 * e], v[2 * e + 1])
-                                                                        : make_float2(0.f, 0.f);
+            if (r + e < n && (unsigned)ipiv[r + e] < (unsigned)n)
+              x0b[ipiv[r + e] * kTcrCB + ml] = (m0 + ml < n) ? make_float2(v[2 * e], v[2 * e + 1])
+                                                             : make_float2(0.f, 0.f);
         }
       }
     }

@@ -2,7 +2,9 @@
 
 Pipeline (every numerical step on the GPU through libdf):
   1. generate: converged Sigma~ of many parameter points with the batched
-     loop (df_batch_*), points that do not converge are dropped;
+     loop (df_batch_*), or one handle at a time with the point-group
+     reduction where a point's grid is too large to batch (generate_each);
+     points that do not converge are dropped;
   2. train: the 4-layer network (df_mlp_*) on (features -> Sigma~ on the
      irreducible wedge of the square lattice, positive frequencies),
      inputs and targets standardised per component;
@@ -73,6 +75,41 @@ def generate(workloads, precision=df.DF_FP64, tol: float = 1e-10, max_iter: int 
     Xa = np.stack([x for x, m in zip(X, mask) if m])
     Ya = np.stack([y for y, m in zip(Y, mask) if m])
     return Xa, Ya, np.array(passes), mask
+
+
+def generate_each(workloads, precision=df.DF_FP32_IR, symmetry: bool = True, tol: float = 1e-8,
+                  max_iter: int = 60):
+    """Converged Sigma~ of every workload, one handle at a time: the stated
+    warm-start grid (64^2, n_w = 128, N_W = 31) holds about 1 GB of device
+    arrays per point, too much to batch.  The point-group reduction solves
+    561 of the 4096 momenta per plane.  Returns (X, Y, passes [n], converged
+    mask [n]); a point whose loop does not reach r <= tol in max_iter passes,
+    or fails, is dropped."""
+    _, rep = wedge(workloads[0].nk)
+    X, Y, passes, ok = [], [], [], []
+    for w in workloads:
+        conv, it, y, r = False, 0, None, float("inf")
+        try:
+            with df.DualFermion.from_workload(w, precision=precision, eig_mode=0, symmetry=symmetry) as d:
+                for it in range(1, max_iter + 1):   # pass by pass: a diverging point stops early
+                    d.bubble()
+                    d.bse(3)
+                    r = d.sigma()
+                    if r <= tol or not (r < 1e3):
+                        break
+                conv = bool(r <= tol)
+                if conv:
+                    y = targets(d.get_sigma(), w.n_w, rep).reshape(-1)
+        except df.DFError:
+            conv = False
+        ok.append(conv)
+        passes.append(it)
+        if conv:
+            X.append(features(w))
+            Y.append(y)
+    Xa = np.stack(X) if X else np.zeros((0, 0), np.float32)
+    Ya = np.stack(Y) if Y else np.zeros((0, 0), np.float32)
+    return Xa, Ya, np.array(passes), np.array(ok)
 
 
 @dataclass
@@ -155,23 +192,28 @@ def passes_to(d, sigma_ref, tol: float, max_iter: int):
         e1.record(stream)
         e1.synchronize()
         ms += e0.elapsed_time(e1)
-        if float(np.max(np.abs(d.get_sigma() - sigma_ref))) <= tol * den:
+        err = float(np.max(np.abs(d.get_sigma() - sigma_ref)))
+        if err <= tol * den:
             return p, ms
+        if not (err < 1e3 * den):             # diverged: no point in more passes
+            break
     return None, ms
 
 
-def evaluate(model: WarmStart, workloads, tol: float = 1e-8, max_iter: int = 60):
+def evaluate(model: WarmStart, workloads, tol: float = 1e-8, max_iter: int = 60,
+             precision=df.DF_FP64, symmetry: bool = False):
     """Passes and device time to max|Sigma~ - Sigma~*| <= tol max|Sigma~*| from
-    Sigma~ = 0 and from the prediction, Sigma~* the FP64 loop at r <= 1e-12;
+    Sigma~ = 0 and from the prediction, on the given path (precision, point-group
+    reduction), Sigma~* the FP64 loop at r <= 1e-12 (reduced when the path is);
     a prediction whose loop does not get there falls back to Sigma~ = 0."""
     rows = []
     for w in workloads:
-        with df.DualFermion.from_workload(w, eig_mode=0) as d:
+        with df.DualFermion.from_workload(w, eig_mode=0, symmetry=symmetry) as d:
             it, r, _ = d.iterate(max_iter, tol=1e-12)
             ref = d.get_sigma()
-        with df.DualFermion.from_workload(w, eig_mode=0) as d:
+        with df.DualFermion.from_workload(w, eig_mode=0, precision=precision, symmetry=symmetry) as d:
             p0, t0 = passes_to(d, ref, tol, max_iter)
-        with df.DualFermion.from_workload(w, eig_mode=0) as d:
+        with df.DualFermion.from_workload(w, eig_mode=0, precision=precision, symmetry=symmetry) as d:
             model.apply(d, w)
             pred_err = float(np.max(np.abs(d.get_sigma() - ref)) / np.max(np.abs(ref)))
             p1, t1 = passes_to(d, ref, tol, max_iter)

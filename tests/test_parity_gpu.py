@@ -443,6 +443,27 @@ def test_exactly_singular_ladder_is_reported(df, prec):
         assert e.value.status == df.DF_ERR_SINGULAR
 
 
+@pytest.mark.parametrize("prec,sweep", [("fp64", 0), ("mixed", 0), ("mixed", 1)])
+def test_zero_last_pivot_at_order_128(df, prec, sweep):
+    # the same exact construction at n_w = 128: gamma = -16 E_{127,127} makes D the
+    # identity but for D_{127,127} = 0, so every column pivots on its own row and the
+    # last step finds only row 127 left, with a zero pivot: reported, and the pivot
+    # rows stay a permutation (the tensor-core sweep's pivot keys are nonzero for
+    # every candidate row)
+    n = 128
+    g = np.ones(n, complex)
+    gam = np.zeros((1, n, n), complex)
+    gam[0, n - 1, n - 1] = -16.0
+    p = df.DF_FP64 if prec == "fp64" else df.DF_FP32_IR
+    with df.DualFermion(dim=1, nk=2, t=0.0, tp=0.0, beta=4.0, mu=0.0, n_w=n, m_max=0, g=g, delta=g,
+                        gamma_d=gam, gamma_m=gam, precision=p, mixed_sweep=sweep) as d:
+        d.bubble()
+        assert np.array_equal(d.get_chi(), np.full((1, n, 2), -1.0 / 16.0, complex))
+        with pytest.raises(df.DFError) as e:
+            d.iterate(1)
+        assert e.value.status == df.DF_ERR_SINGULAR
+
+
 def test_radius_warning_is_raised_outside_the_radius(df):
     # the 16^2, U = 2, beta = 5 workload: |lambda| of gamma chi~ at W = 0 reaches ~25
     w = I.workload("square16_b5")

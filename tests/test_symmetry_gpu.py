@@ -147,3 +147,22 @@ def test_reduced_iterate_converges_like_the_full_loop(df):
         assert sf == sr == df.DF_OK
         assert abs(nf - nr) <= 1
         assert nrel(red.get_sigma(), full.get_sigma()) < TOL64
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_reduced_without_eigenvalues(df, prec):
+    # eig_mode 0: no leading eigenvalues are computed, only the brackets are copied to the
+    # orbits, and the handle's eigenvalue arrays keep their initial state
+    w = I.workload("square32_tp", nk=8, n_w=128, m_max=1)
+    p = df.DF_FP64 if prec == "fp64" else df.DF_FP32_IR
+    tol = TOL64 if prec == "fp64" else TOL_MIXED
+    with df.DualFermion.from_workload(w, precision=p, eig_mode=0) as full, \
+            df.DualFermion.from_workload(w, precision=p, eig_mode=0, symmetry=True) as red:
+        for it in range(2):
+            for d in (full, red):
+                d.bubble()
+                d.bse(3)
+                d.sigma()
+            assert nrel(red.get_sigma(), full.get_sigma()) < tol, it
+        lam, ok = red.get_lambda()
+        assert np.all(lam == 0) and np.all(ok == -1)
