@@ -625,15 +625,36 @@ def run_config5(args):
     grid = dict(nk=64, n_w=128, m_max=15)
     train = I.warmstart_family(args.c5_train, seed=5000, **grid)
     test = I.warmstart_family(args.c5_test, seed=7000, **grid)
+    budget = args.c5_budget_s if args.c5_budget_s else float("inf")
+
+    def progress(stage, **kw):
+        if args.c5_progress:
+            with open(args.c5_progress, "w") as f:
+                json.dump({"stage": stage, "elapsed_s": time.perf_counter() - t_start, **kw}, f)
+
     t0 = time.perf_counter()
-    X, Y, passes, mask = W.generate_each(train, precision=df.DF_FP32_IR, symmetry=True, tol=1e-8)
+    Xs, Ys, P, M = [], [], [], []
+    for i0 in range(0, len(train), 50):           # in chunks, within the time budget
+        if time.perf_counter() - t_start > 0.6 * budget:
+            break
+        X_, Y_, p_, m_ = W.generate_each(train[i0:i0 + 50], precision=df.DF_FP32_IR, symmetry=True, tol=1e-8)
+        if len(X_):
+            Xs.append(X_)
+            Ys.append(Y_)
+        P.extend(p_.tolist())
+        M.extend(m_.tolist())
+        progress("generate", attempted=len(M), converged=int(sum(M)))
+    X = np.concatenate(Xs) if Xs else np.zeros((0, 0), np.float32)
+    Y = np.concatenate(Ys) if Ys else np.zeros((0, 0), np.float32)
+    passes, mask = np.array(P), np.array(M, bool)
     t_gen = time.perf_counter() - t0
     out = {"probe": "learned warm start at the stated grid (2D 64^2, n_w=128, N_W=31)",
            "stated_box": {"points": stated, "seconds": t_probe,
                           "beyond_radius": sum(r["max_abs_lambda_W0_first_pass"] >= 1.0 for r in stated)},
            "converging_box": "Hubbard-atom inputs around Example I: U 12-28, beta 0.6-1.4, t' -0.3-0, "
                              "mu = U/2 +- 1",
-           "train": {"points": len(train), "converged": int(mask.sum()), "mean_passes": float(np.mean(passes)),
+           "train": {"points": len(train), "attempted": int(len(mask)), "converged": int(mask.sum()),
+                     "mean_passes": float(np.mean(passes[mask])) if mask.any() else None,
                      "seconds": t_gen, "path": "DF_FP32_IR, point-group reduction, r <= 1e-8"}}
     if mask.sum() >= 2:
         model = W.WarmStart(X.shape[1], Y.shape[1], grid["nk"], width=512, seed=0)
@@ -642,10 +663,18 @@ def run_config5(args):
         torch.cuda.synchronize()
         out["train"]["network"] = {"n_in": int(X.shape[1]), "n_out": int(Y.shape[1]), "steps": args.c5_steps,
                                    "seconds": time.perf_counter() - t0, "loss_history": hist}
+        del X, Y
+        progress("trained")
         t0 = time.perf_counter()
-        rows = W.evaluate(model, test, tol=1e-8, precision=df.DF_FP32_IR, symmetry=True)
+        rows = []
+        for w in test:
+            if time.perf_counter() - t_start > budget:
+                break
+            rows.extend(W.evaluate(model, [w], tol=1e-8, precision=df.DF_FP32_IR, symmetry=True))
+            progress("evaluate", evaluated=len(rows))
         ok = [r for r in rows if r["cold_passes"] is not None]
-        out["held_out"] = {"points": len(test), "evaluated": len(ok), "seconds": time.perf_counter() - t0,
+        out["held_out"] = {"points": len(test), "attempted": len(rows), "evaluated": len(ok),
+                           "seconds": time.perf_counter() - t0,
                            "target": "max|Sigma~ - Sigma~*| <= 1e-8 max|Sigma~*|, Sigma~* = FP64 loop (reduced) "
                                      "at r <= 1e-12; path DF_FP32_IR with the reduction",
                            "fallbacks": sum(r["fallback"] for r in ok)}
@@ -960,6 +989,9 @@ def main():
     ap.add_argument("--c5-train", type=int, default=2000, help="--config5: training points")
     ap.add_argument("--c5-test", type=int, default=200, help="--config5: held-out points")
     ap.add_argument("--c5-steps", type=int, default=3000, help="--config5: training steps")
+    ap.add_argument("--c5-budget-s", type=float, default=0.0,
+                    help="--config5: wall-clock budget; generation stops at 60%% of it, evaluation at 100%%")
+    ap.add_argument("--c5-progress", default="", help="--config5: file rewritten with the progress")
     ap.add_argument("--omega-split", action="store_true",
                     help="one problem over the N GPUs (bosonic planes split, one all-reduce per pass) "
                          "instead of N replicas")
