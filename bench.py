@@ -372,12 +372,19 @@ def batch_bench(df, I, torch, full: bool, passes: int = 3):
         ws = I.uneven_batch(64, seed=4, max_n_w=64, max_m=7, grids=((2, 8), (2, 16), (2, 32), (4, 4)))
         desc = "64 uneven points, capped recipe (n_w 16-64, N_W 1-15, 8^2/16^2/32^2 and 4^4)"
     pts = sum(w.n_bos * w.N for w in ws)
-    out = {"workload": desc, "points_per_pass": pts, "ladders_per_pass": 2 * pts}
+    orbits = {}
+    for w in ws:
+        if (w.dim, w.nk) not in orbits:
+            orbits[(w.dim, w.nk)] = len(df.wedge(w.dim, w.nk)[1])
+    out = {"workload": desc, "points_per_pass": pts, "ladders_per_pass": 2 * pts,
+           "reduced_ladders_per_pass": 2 * sum(w.n_bos * orbits[(w.dim, w.nk)] for w in ws),
+           "reduced": "df_point.symmetry = 1: one ladder per momentum orbit, rate over the full grid"}
     cache = os.path.join(tempfile.gettempdir(), "df_batch_tune.txt")
     if full:
         passes = 1         # ~20 TFLOP of ladders per pass: one warm and one timed pass, default tiles
-    for name, prec in (("fp64", df.DF_FP64), ("fp32ir", df.DF_FP32_IR)):
-        with df.DualFermionBatch(ws, precision=prec) as b:
+    for name, prec, sym in (("fp64", df.DF_FP64, False), ("fp32ir", df.DF_FP32_IR, False),
+                            ("fp64_reduced", df.DF_FP64, True), ("fp32ir_reduced", df.DF_FP32_IR, True)):
+        with df.DualFermionBatch(ws, precision=prec, symmetry=sym) as b:
             nc, ch, cached = b.autotune(cache) if not full else (None, None, None)
             b.iterate(1)
             b.reset()

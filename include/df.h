@@ -312,6 +312,9 @@ typedef struct df_point {
   const double* delta;    /* [n_w + 2 m_max] */
   const double* gamma_d;  /* [2 m_max + 1][n_w][n_w] */
   const double* gamma_m;
+  int symmetry;           /* 1: the point-group reduction of df_opts.symmetry for this
+                           * point (exact here: a batch always starts from Sigma~ = 0);
+                           * 0: every ladder solved */
 } df_point;
 
 typedef struct df_batch df_batch;

@@ -36,6 +36,12 @@ __device__ __forceinline__ MixedCheck batch_check(int* redo, int point) {
 
 struct PointDev {
   Dims dm;
+  // the ladder stage's view: dm, chi and kc, or with the point-group reduction
+  // (sym) the compact grid of one momentum per orbit (ldm.N = n_orb) and its arrays
+  Dims ldm;
+  double2 *lchi, *lkc;
+  int sym, n_orb;
+  int *qmap, *qrep;
   int nc;        // FP64 ladder right-hand-side chunk
   int mixed;     // ladders of this point run in DF_FP32_IR
   int active;    // 1 until converged
@@ -177,7 +183,7 @@ batch_bse_f64_kernel(const PointDev* __restrict__ pts, const int* __restrict__ o
       const int k = find_segment(start, nseg, s);
       const PointDev& P = pts[order[k]];
       if (!P.active) continue;
-      const Dims& dm = P.dm;
+      const Dims& dm = P.ldm;
       const long local = s - start[k];
       const long per_ch = (long)dm.nb * dm.N;
       const int c = (int)(local / per_ch);
@@ -186,7 +192,7 @@ batch_bse_f64_kernel(const PointDev* __restrict__ pts, const int* __restrict__ o
       const bool lu_smem = dm.n_w <= kLuSmemOrder;
       const BseSmem L = bse_layout(dm.n_w, P.nc, lu_smem);
       double2* LU = lu_smem ? sm + L.lu : ws + blockIdx.x * ws_stride;
-      bse_f64_system(dm, c, a, q, P.nc, P.gam, P.gg, P.chi, P.kc, LU, sm + L.y, sm + L.xs, sm + L.invu, sh,
+      bse_f64_system(dm, c, a, q, P.nc, P.gam, P.gg, P.lchi, P.lkc, LU, sm + L.y, sm + L.xs, sm + L.invu, sh,
                      P.flags);
     }
   }
@@ -202,7 +208,7 @@ batch_bse_f64_list_kernel(const PointDev* __restrict__ pts, const int* __restric
   for (int s = blockIdx.x; s < count; s += gridDim.x) {
     const int code = redo[1 + s];
     const PointDev& P = pts[code >> 24];
-    const Dims& dm = P.dm;
+    const Dims& dm = P.ldm;
     const int sys = code & 0xFFFFFF;
     const int c = sys / (dm.nb * dm.N), rem = sys - c * dm.nb * dm.N;
     const int a = rem / dm.N, q = rem - a * dm.N;
@@ -210,7 +216,34 @@ batch_bse_f64_list_kernel(const PointDev* __restrict__ pts, const int* __restric
     const bool lu_smem = dm.n_w <= kLuSmemOrder;
     const BseSmem L = bse_layout(dm.n_w, nc, lu_smem);
     double2* LU = lu_smem ? sm + L.lu : ws + blockIdx.x * ws_stride;
-    bse_f64_system(dm, c, a, q, nc, P.gam, P.gg, P.chi, P.kc, LU, sm + L.y, sm + L.xs, sm + L.invu, sh, P.flags);
+    bse_f64_system(dm, c, a, q, nc, P.gam, P.gg, P.lchi, P.lkc, LU, sm + L.y, sm + L.xs, sm + L.invu, sh, P.flags);
+  }
+}
+
+// the point-group reduction (df_point.symmetry): per reduced point (blockIdx.y),
+// chi~'s orbit representatives into the compact array before the ladders, the
+// compact brackets back to every momentum after them
+__global__ void batch_wedge_gather_kernel(const PointDev* __restrict__ pts) {
+  const PointDev& P = pts[blockIdx.y];
+  if (!P.sym || !P.active) return;
+  const Dims& dm = P.dm;
+  const long total = (long)dm.nb * dm.n_w * P.n_orb;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int o = (int)(idx % P.n_orb);
+    const long row = idx / P.n_orb;
+    P.lchi[idx] = P.chi[row * dm.N + P.qrep[o]];
+  }
+}
+
+__global__ void batch_wedge_scatter_kernel(const PointDev* __restrict__ pts) {
+  const PointDev& P = pts[blockIdx.y];
+  if (!P.sym || !P.active) return;
+  const Dims& dm = P.dm;
+  const long total = 2L * dm.nb * dm.n_w * dm.N;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int q = (int)(idx % dm.N);
+    const long row = idx / dm.N;
+    P.kc[idx] = P.lkc[row * P.n_orb + P.qmap[q]];
   }
 }
 
@@ -246,7 +279,7 @@ batch_bse_mixed_kernel(const PointDev* __restrict__ pts, const int* __restrict__
       const int k = find_segment(start, nseg, s);
       const PointDev& P = pts[order[k]];
       if (!P.active) continue;
-      const Dims& dm = P.dm;
+      const Dims& dm = P.ldm;
       const long local = s - start[k];
       const long per_ch = (long)dm.nb * dm.N;
       const int c = (int)(local / per_ch);
@@ -256,7 +289,7 @@ batch_bse_mixed_kernel(const PointDev* __restrict__ pts, const int* __restrict__
       if (use_umma_residual(NP) && (threadIdx.x >> 5) == mixed_compute_threads(NP) / 32)
         mixed_producer(sp, &tc);                      // warp 8: the tensor-core MMAs
       else
-        bse_mixed_system<NP>(dm, c, a, q, P.gam, P.gam_hi, P.gam_lo, P.gg_hi, P.gg_lo, P.chi, P.kc, P.flags, sp,
+        bse_mixed_system<NP>(dm, c, a, q, P.gam, P.gam_hi, P.gam_lo, P.gg_hi, P.gg_lo, P.lchi, P.lkc, P.flags, sp,
                              P.gdig ? P.gdig + (size_t)(c * dm.nb + a) * gdig_bytes(NP) : nullptr, key != cur, &tc,
                              batch_check(redo, order[k]));
       cur = key;
@@ -285,13 +318,13 @@ batch_bse_gj_kernel(const PointDev* __restrict__ pts, const int* __restrict__ or
       const int k = find_segment(start, nseg, s);
       const PointDev& P = pts[order[k]];
       if (!P.active) continue;
-      const Dims& dm = P.dm;
+      const Dims& dm = P.ldm;
       const long local = s - start[k];
       const long per_ch = (long)dm.nb * dm.N;
       const int c = (int)(local / per_ch);
       const int rem = (int)(local - (long)c * per_ch);
       const int a = rem / dm.N, q = rem - a * dm.N;
-      gj_ir_system(dm, c, a, q, P.gam_hi, P.gam_lo, P.gg_hi, P.gg_lo, P.gg, P.chi, P.kc, P.flags, smraw, sh,
+      gj_ir_system(dm, c, a, q, P.gam_hi, P.gam_lo, P.gg_hi, P.gg_lo, P.gg, P.lchi, P.lkc, P.flags, smraw, sh,
                    batch_check(redo, order[k]));
     }
   }
@@ -360,6 +393,7 @@ struct df_batch {
   int redo_grid = 0;
   size_t redo_smem = 0;
   double* d_out = nullptr;                     // [3 npts] residual, active, flags
+  bool any_sym = false;                        // some point uses the point-group reduction
   double* h_out = nullptr;
   int chunk = 1;                               // scheduler chunk (autotuned)
   int nc_override = 0;                         // FP64 RHS chunk (autotuned; 0 = per-point default)
@@ -395,6 +429,7 @@ int default_nc(int n) { return n <= 32 ? n : (n <= 64 ? 32 : 16); }
 size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
 constexpr int kLuScratchPerSm = 4;   // global LU slices per SM (FP64 ladders of order > kLuSmemOrder)
+constexpr int kWedgeBlocks = 32;     // blocks per point of the orbit gather and scatter
 
 // the pass: all stages, captured into b->graph
 df_status record_pass(df_batch* b) {
@@ -404,6 +439,10 @@ df_status record_pass(df_batch* b) {
   if (b->d_redo) B_CUDA(b, cudaMemsetAsync(b->d_redo, 0, sizeof(int), s), "hand-back count reset");
   batch_bubble_kernel<<<(unsigned)b->total_planes, kFftThreads, b->fft_smem1, s>>>(b->d_pts, b->d_plane_start, b->npts);
   B_CUDA(b, cudaGetLastError(), "batch bubble");
+  if (b->any_sym) {
+    batch_wedge_gather_kernel<<<dim3(kWedgeBlocks, b->npts), 256, 0, s>>>(b->d_pts);
+    B_CUDA(b, cudaGetLastError(), "batch orbit gather");
+  }
   for (auto& g : b->groups) {
     if (g.total == 0) continue;
     if (!g.mixed) {
@@ -422,6 +461,10 @@ df_status record_pass(df_batch* b) {
     batch_bse_f64_list_kernel<<<b->redo_grid, kBseThreads, b->redo_smem, s>>>(b->d_pts, b->d_redo, b->ws,
                                                                               b->ws_stride);
     B_CUDA(b, cudaGetLastError(), "batch hand-back ladders");
+  }
+  if (b->any_sym) {
+    batch_wedge_scatter_kernel<<<dim3(kWedgeBlocks, b->npts), 256, 0, s>>>(b->d_pts);
+    B_CUDA(b, cudaGetLastError(), "batch orbit scatter");
   }
   batch_sigma_prod_kernel<<<(unsigned)b->total_planes, kFftThreads, b->fft_smem1, s>>>(b->d_pts, b->d_plane_start,
                                                                                       b->npts);
@@ -548,6 +591,7 @@ df_status df_batch_init(df_batch** out, int npts, const df_point* pts, int preci
   // ---- sizes and the arena ----
   b->host_pts.resize(npts);
   std::vector<size_t> off(npts);
+  std::vector<std::vector<int>> qmaps(npts), qreps(npts);
   size_t total = 0;
   int nmax = 0;
   for (int i = 0; i < npts; ++i) {
@@ -573,6 +617,11 @@ df_status df_batch_init(df_batch** out, int npts, const df_point* pts, int preci
     dm.t = q.t;
     dm.tp = q.tp;
     P.mixed = (precision == DF_FP32_IR && mixed_np_of(q.n_w) <= kGjMaxN) ? 1 : 0;
+    P.sym = q.symmetry ? 1 : 0;
+    P.n_orb = P.sym ? build_wedge(q.dim, q.nk, qmaps[i], qreps[i]) : dm.N;
+    P.ldm = dm;
+    P.ldm.N = P.n_orb;
+    b->any_sym = b->any_sym || P.sym;
     P.active = 1;
     P.mix = mix;
     P.tol = tol;
@@ -592,6 +641,11 @@ df_status df_batch_init(df_batch** out, int npts, const df_point* pts, int preci
     if (P.mixed) total += align_up(sizeof(float2) * nv) * 4;      // gam hi, lo; gg hi, lo
     if (P.mixed && use_tc_residual(mixed_pad(dm.n_w)))
       total += align_up((size_t)2 * dm.nb * gdig_bytes(mixed_pad(dm.n_w)));   // gamma's digits
+    if (P.sym) {
+      const size_t nw = (size_t)dm.nb * dm.n_w * P.n_orb;
+      total += align_up(sizeof(double2) * nw) * 3;                // compact chi, kc (2)
+      total += align_up(sizeof(int) * dm.N) + align_up(sizeof(int) * P.n_orb);   // orbit map, representatives
+    }
   }
   b->arena_bytes = total;
   df_status st = DF_OK;
@@ -631,6 +685,16 @@ df_status df_batch_init(df_batch** out, int npts, const df_point* pts, int preci
       if (use_tc_residual(mixed_pad(dm.n_w)))
         P.gdig = (unsigned char*)take((size_t)2 * dm.nb * gdig_bytes(mixed_pad(dm.n_w)));
     }
+    if (P.sym) {
+      const size_t nw = (size_t)dm.nb * dm.n_w * P.n_orb;
+      P.lchi = (double2*)take(sizeof(double2) * nw);
+      P.lkc = (double2*)take(sizeof(double2) * 2 * nw);
+      P.qmap = (int*)take(sizeof(int) * dm.N);
+      P.qrep = (int*)take(sizeof(int) * P.n_orb);
+    } else {
+      P.lchi = P.chi;
+      P.lkc = P.kc;
+    }
     const char* limit = b->arena + (i + 1 < npts ? off[i + 1] : total);
     if (cur > limit) {
       st = bfail(b, DF_ERR_ARG, "internal: point buffers exceed their arena slice");
@@ -661,6 +725,13 @@ df_status df_batch_init(df_batch** out, int npts, const df_point* pts, int preci
         (e = cudaMemsetAsync(P.red, 0, sizeof(double) * (2 * dm.n_w + 4), s)) != cudaSuccess ||
         (e = cudaMemsetAsync(P.flags, 0, sizeof(int) * 4, s)) != cudaSuccess) {
       st = bfail(b, DF_ERR_CUDA, "batch inputs", e);
+      goto bad;
+    }
+    if (P.sym && ((e = cudaMemcpyAsync(P.qmap, qmaps[i].data(), sizeof(int) * dm.N, cudaMemcpyHostToDevice, s)) !=
+                      cudaSuccess ||
+                  (e = cudaMemcpyAsync(P.qrep, qreps[i].data(), sizeof(int) * P.n_orb, cudaMemcpyHostToDevice, s)) !=
+                      cudaSuccess)) {
+      st = bfail(b, DF_ERR_CUDA, "batch orbit tables", e);
       goto bad;
     }
   }
@@ -735,7 +806,7 @@ df_status df_batch_init(df_batch** out, int npts, const df_point* pts, int preci
       g.nseg = (int)g.order.size();
       std::vector<long> st_(g.nseg + 1, 0);
       for (int k = 0; k < g.nseg; ++k) {
-        const Dims& dm = b->host_pts[g.order[k]].dm;
+        const Dims& dm = b->host_pts[g.order[k]].ldm;
         st_[k + 1] = st_[k] + 2L * dm.nb * dm.N;
       }
       g.total = st_[g.nseg];
@@ -751,7 +822,7 @@ df_status df_batch_init(df_batch** out, int npts, const df_point* pts, int preci
     long mixed_ladders = 0;
     for (auto& g : b->groups)
       for (int p : g.order) {
-        const Dims& dm = b->host_pts[p].dm;
+        const Dims& dm = b->host_pts[p].ldm;
         big = std::max(big, dm.n_w > kLuSmemOrder ? dm.n_w : 0);
         if (g.mixed) mixed_ladders += 2L * dm.nb * dm.N;
       }
@@ -866,11 +937,11 @@ df_status df_batch_reset(df_batch* b) {
 
 df_status df_batch_autotune(df_batch* b, const char* cache_path, int* chosen) {
   if (!b) return DF_ERR_ARG;
-  // signature of the batch: every point's (D, N_k, n_w, N_W) and the precision
+  // signature of the batch: every point's (D, N_k, n_w, N_W, reduced) and the precision
   std::string sig = "v1 p" + std::to_string(b->precision);
   for (auto& P : b->host_pts)
     sig += " " + std::to_string(P.dm.D) + "," + std::to_string(P.dm.nk) + "," + std::to_string(P.dm.n_w) + "," +
-           std::to_string(P.dm.nb);
+           std::to_string(P.dm.nb) + (P.sym ? "s" : "");
   const int nc_c[] = {0, 8, 16, 32};
   const int ch_c[] = {1, 4};
   int best_nc = 0, best_ch = 1;

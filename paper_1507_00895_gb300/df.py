@@ -59,7 +59,8 @@ class df_lattice(C.Structure):
 class df_point(C.Structure):
     _fields_ = [("dim", C.c_int), ("nk", C.c_int), ("tp", C.c_double), ("t", C.c_double),
                 ("beta", C.c_double), ("mu", C.c_double), ("n_w", C.c_int), ("m_max", C.c_int),
-                ("g", C.c_void_p), ("delta", C.c_void_p), ("gamma_d", C.c_void_p), ("gamma_m", C.c_void_p)]
+                ("g", C.c_void_p), ("delta", C.c_void_p), ("gamma_d", C.c_void_p), ("gamma_m", C.c_void_p),
+                ("symmetry", C.c_int)]
 
 
 class df_opts(C.Structure):
@@ -378,7 +379,7 @@ class DualFermionBatch:
     one launch per stage over all points, one CUDA graph per pass."""
 
     def __init__(self, workloads, precision: int = DF_FP64, mix: float = 1.0, tol: float = 0.0,
-                 stream: Optional[int] = None):
+                 symmetry: bool = False, stream: Optional[int] = None):
         self.lib = load()
         self.workloads = list(workloads)
         n = len(self.workloads)
@@ -389,7 +390,8 @@ class DualFermionBatch:
             g, dl = _c128(w.g), _c128(w.delta)
             self._keep += [g, dl, gd, gm]
             arr[i] = df_point(w.dim, w.nk, w.tp, w.t, w.beta, w.mu, w.n_w, w.m_max,
-                              g.ctypes.data, dl.ctypes.data, gd.ctypes.data, gm.ctypes.data)
+                              g.ctypes.data, dl.ctypes.data, gd.ctypes.data, gm.ctypes.data,
+                              1 if symmetry else 0)
         if stream is None:
             stream = current_stream_handle()
         h = C.c_void_p()

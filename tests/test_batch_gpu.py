@@ -127,3 +127,18 @@ def test_uneven_batch_recipe_first_pass_sampled(df):
         for i in (0, 7, 21, 42, 63):
             st = O.run_workload(ws[i], n_iter=1)
             assert nrel(b.get_sigma(i), st.sigma) < 1e-8, i
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_point_group_reduction_equals_full(df, prec):
+    # the reduction per point (df_point.symmetry): one ladder per momentum orbit on
+    # 2D, 3D and 4D grids with orders across the mixed classes (16 .. 128), two passes,
+    # every point's Sigma~ within 1e-10 (FP64) / 1e-8 (mixed) of the full batch's
+    ws = I.uneven_batch(npts=10, seed=11, max_n_w=128, max_m=2, grids=((2, 8), (2, 16), (3, 4), (4, 4)))
+    p = df.DF_FP64 if prec == "fp64" else df.DF_FP32_IR
+    tol = 1e-10 if prec == "fp64" else 1e-8
+    with df.DualFermionBatch(ws, precision=p) as full, df.DualFermionBatch(ws, precision=p, symmetry=True) as red:
+        full.iterate(2)
+        red.iterate(2)
+        for i in range(len(ws)):
+            assert nrel(red.get_sigma(i), full.get_sigma(i)) < tol, (i, ws[i].dim, ws[i].nk, ws[i].n_w)
