@@ -126,18 +126,29 @@ typedef struct df_opts {
                        * pass ends with df_sigma_partial + (caller's sum over handles) +
                        * df_sigma_finish; df_sigma, df_iterate and df_susceptibility need
                        * the full range.  0 <= w_lo < w_hi <= N_W, or both 0. */
-  int symmetry;       /* point-group reduction of the ladders: 0 (default) every (q, W, channel)
-                       * is solved; 1 only one momentum per orbit of the lattice's point group
-                       * (axis permutations and sign flips k_j -> -k_j: D4 on the square
-                       * lattice, O_h on the cubic one; df_wedge lists the orbits) is solved
-                       * and its diag Gamma, Eq. sd bracket and leading eigenvalue are copied
-                       * to the orbit's other momenta.  Exact when G~(k) is invariant under
-                       * the group, which holds for the input contract (local g, Delta and
-                       * gamma; eps_k of df_lattice is invariant) whenever Sigma~ is:
-                       * Sigma~ = 0 at df_init, and Eq. sd keeps it invariant.  With 1,
-                       * df_set_sigma checks the invariance of what it is given (relative
-                       * 1e-12 of max |Sigma~|), and rejects with DF_ERR_ARG and Sigma~ = 0
-                       * otherwise.  The susceptibilities' ladders are not reduced. */
+  int symmetry;       /* reductions of the ladder stage, exact for inputs with the stated
+                       * symmetries.  0 (default): every (q, W, channel) is solved.
+                       * 1: the point group -- one momentum per orbit of the lattice's
+                       * point group (axis permutations and sign flips k_j -> -k_j: D4 on
+                       * the square lattice, O_h on the cubic one; df_wedge lists the
+                       * orbits) is solved and its diag Gamma, Eq. sd bracket and leading
+                       * eigenvalue are copied to the orbit's other momenta.  Exact when
+                       * G~(k) is invariant under the group, which holds for the input
+                       * contract (local g, Delta and gamma; eps_k of df_lattice is
+                       * invariant) whenever Sigma~ is: Sigma~ = 0 at df_init, and Eq. sd
+                       * keeps it invariant.
+                       * 2: the point group and the frequency reflection -- only the planes
+                       * W >= 0 are solved; those of -W are their frequency-reversed complex
+                       * conjugates (bracket_{-W}(w) = bracket_W(-w)*, lambda_{-W} =
+                       * lambda_W*).  Needs g(-w) = g(w)*, Delta(-w) = Delta(w)* and
+                       * gamma(-W; w, w') = gamma(W; -w, -w')* (checked by df_init and
+                       * df_set_inputs to 1e-12 of each array's largest entry: DF_ERR_ARG
+                       * and nothing changed otherwise), Sigma~(-w) = Sigma~(w)* (kept by
+                       * Eq. sd), and the full bosonic range (w_lo = w_hi = 0).
+                       * With 1 or 2 df_set_sigma checks what it is given against the same
+                       * symmetries (relative 1e-12 of max |Sigma~|) and rejects it with
+                       * DF_ERR_ARG, Sigma~ reset to 0, otherwise.  The susceptibilities'
+                       * ladders are not reduced. */
 } df_opts;
 
 /* Fill *o with the defaults above (n_w, m_max set to 0: the caller sets them). */
@@ -312,9 +323,9 @@ typedef struct df_point {
   const double* delta;    /* [n_w + 2 m_max] */
   const double* gamma_d;  /* [2 m_max + 1][n_w][n_w] */
   const double* gamma_m;
-  int symmetry;           /* 1: the point-group reduction of df_opts.symmetry for this
+  int symmetry;           /* 1: the point-group reduction of df_opts.symmetry = 1 for this
                            * point (exact here: a batch always starts from Sigma~ = 0);
-                           * 0: every ladder solved */
+                           * 0: every ladder solved; other values: DF_ERR_ARG */
 } df_point;
 
 typedef struct df_batch df_batch;

@@ -1,5 +1,7 @@
 // C ABI of libdf (include/df.h): handle, validation, buffers and the
 // sequence of launches of one pass of the ladder dual-fermion loop.
+#include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -53,6 +55,55 @@ df_status copy_out(df_ctx* c, void* dst, const void* src, size_t bytes, int is_d
   if (!dst) return fail(c, DF_ERR_ARG, "output pointer is NULL");
   DF_CUDA(c, cudaMemcpyAsync(dst, src, bytes, kind_from_dev(is_device), c->stream), what);
   if (!is_device) DF_CUDA(c, cudaStreamSynchronize(c->stream), what);
+  return DF_OK;
+}
+
+// The conditions of the frequency reflection (df_opts.symmetry = 2) on the
+// inputs: g(-w) = g(w)*, Delta(-w) = Delta(w)* on the extended grid (index
+// e -> n_e - 1 - e) and gamma(-W; w, w') = gamma(W; -w, -w')* for both
+// channels, each within 1e-12 of its array's largest |re| + |im|.
+df_status check_reflection(df_ctx* c, const double* g, const double* delta, const double* gd, const double* gm,
+                           int is_device) {
+  const Dims& dm = c->dm;
+  const size_t nv = (size_t)dm.nb * dm.n_w * dm.n_w;
+  auto host = [&](const double* p, size_t count, std::vector<double2>& v) -> cudaError_t {
+    v.resize(count);
+    if (!is_device) {
+      memcpy(v.data(), p, sizeof(double2) * count);
+      return cudaSuccess;
+    }
+    cudaError_t e = cudaMemcpyAsync(v.data(), p, sizeof(double2) * count, cudaMemcpyDeviceToHost, c->stream);
+    return e == cudaSuccess ? cudaStreamSynchronize(c->stream) : e;
+  };
+  auto mag = [](double2 z) { return fabs(z.x) + fabs(z.y); };
+  auto dconj = [](double2 a, double2 b) { return fabs(a.x - b.x) + fabs(a.y + b.y); };   // |a - b*|
+  std::vector<double2> v;
+  const double* vec[2] = {g, delta};
+  for (const double* p : vec) {
+    DF_CUDA(c, host(p, dm.ne, v), "read inputs for the reflection check");
+    double top = 0.0, dev = 0.0;
+    for (int e = 0; e < dm.ne; ++e) {
+      top = std::max(top, mag(v[e]));
+      dev = std::max(dev, dconj(v[e], v[dm.ne - 1 - e]));
+    }
+    if (!(dev <= 1e-12 * top)) return fail(c, DF_ERR_ARG, "g or Delta breaks g(-w) = g(w)* (df_opts.symmetry = 2)");
+  }
+  const double* mats[2] = {gd, gm};
+  const int n = dm.n_w;
+  for (const double* p : mats) {
+    DF_CUDA(c, host(p, nv, v), "read gamma for the reflection check");
+    double top = 0.0, dev = 0.0;
+    for (int a = 0; a < dm.nb; ++a)
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+          const double2 x = v[((size_t)a * n + i) * n + j];
+          const double2 y = v[((size_t)(dm.nb - 1 - a) * n + (n - 1 - i)) * n + (n - 1 - j)];
+          top = std::max(top, mag(x));
+          dev = std::max(dev, dconj(x, y));
+        }
+    if (!(dev <= 1e-12 * top))
+      return fail(c, DF_ERR_ARG, "gamma breaks gamma(-W;w,w') = gamma(W;-w,-w')* (df_opts.symmetry = 2)");
+  }
   return DF_OK;
 }
 
@@ -133,20 +184,31 @@ cudaError_t run_ladders_on(df_ctx* c, int mask) {
 }
 // With the point-group reduction the ladder kernels run on the compact
 // arrays of the orbit representatives, seen as a grid of n_orb momenta.
+// With the frequency reflection only the planes W >= 0 (a >= m_max) are in
+// the view.
+Dims wedge_dims(const df_ctx* c) {
+  Dims d = c->dm;
+  d.N = c->n_orb;
+  if (c->opts.symmetry == 2) {
+    d.a0 = d.m_max;
+    d.na = d.m_max + 1;
+  }
+  return d;
+}
 struct WedgeView {
   df_ctx* c;
-  int N;
+  Dims dm;
   double2 *chi, *kc, *lam;
   int* ok;
-  explicit WedgeView(df_ctx* cc) : c(cc), N(cc->dm.N), chi(cc->chi), kc(cc->kc), lam(cc->lam), ok(cc->lam_ok) {
-    c->dm.N = c->n_orb;
+  explicit WedgeView(df_ctx* cc) : c(cc), dm(cc->dm), chi(cc->chi), kc(cc->kc), lam(cc->lam), ok(cc->lam_ok) {
+    c->dm = wedge_dims(c);
     c->chi = c->chi_w;
     c->kc = c->kc_w;
     c->lam = c->lam_w;
     c->lam_ok = c->lam_ok_w;
   }
   ~WedgeView() {
-    c->dm.N = N;
+    c->dm = dm;
     c->chi = chi;
     c->kc = kc;
     c->lam = lam;
@@ -162,7 +224,7 @@ cudaError_t run_ladders(df_ctx* c, int mask) {
   if (!c->opts.symmetry) return run_ladders_on(c, mask);
   {
     Timed t(c, DF_T_BSE, 1);
-    if ((e = launch_wedge_gather(c)) != cudaSuccess) return e;
+    if ((e = launch_wedge_gather(c, wedge_dims(c))) != cudaSuccess) return e;
   }
   {
     WedgeView view(c);
@@ -294,7 +356,8 @@ df_status df_init(df_ctx** out, const df_lattice* lat, double beta, double mu, d
   if (!(opts->ladder_tol > 0.0 && opts->ladder_tol < 1.0) || (opts->ladder_fallback != 0 && opts->ladder_fallback != 1))
     return DF_ERR_ARG;
   if (opts->mixed_sweep != 0 && opts->mixed_sweep != 1) return DF_ERR_ARG;
-  if (opts->symmetry != 0 && opts->symmetry != 1) return DF_ERR_ARG;
+  if (opts->symmetry < 0 || opts->symmetry > 2) return DF_ERR_ARG;
+  if (opts->symmetry == 2 && (opts->w_lo != 0 || opts->w_hi != 0)) return DF_ERR_ARG;   // needs both +-W
   {
     const int nbos = 2 * opts->m_max + 1;
     const bool full = opts->w_lo == 0 && opts->w_hi == 0;
@@ -408,6 +471,7 @@ df_status df_init(df_ctx** out, const df_lattice* lat, double beta, double mu, d
       goto bad;
     }
   }
+  if (opts->symmetry == 2 && (st = check_reflection(c, g, delta, gamma_d, gamma_m, 0)) != DF_OK) goto bad;
   st = upload_inputs(c, g, delta, gamma_d, gamma_m, 0);
   if (st != DF_OK) goto bad;
   {
@@ -426,7 +490,9 @@ df_status df_set_inputs(df_ctx* c, const double* g, const double* delta, const d
                         int is_device) {
   if (!c) return DF_ERR_ARG;
   if (!g || !delta || !gd || !gm) return fail(c, DF_ERR_ARG, "NULL input");
-  df_status s = upload_inputs(c, g, delta, gd, gm, is_device);
+  df_status s;
+  if (c->opts.symmetry == 2 && (s = check_reflection(c, g, delta, gd, gm, is_device)) != DF_OK) return s;
+  s = upload_inputs(c, g, delta, gd, gm, is_device);
   if (s != DF_OK) return s;
   if (!is_device) DF_CUDA(c, cudaStreamSynchronize(c->stream), "df_set_inputs");
   return DF_OK;
@@ -591,7 +657,9 @@ df_status df_set_sigma(df_ctx* c, const double* in, int is_device) {
       DF_CUDA(c, cudaMemsetAsync(c->sigma, 0, sizeof(double2) * c->dm.n_w * c->dm.N, c->stream), "reset Sigma~");
       DF_CUDA(c, launch_dyson_ifft(c, c->dm.m_max, c->dm.n_w), "Dyson + FFT to real space");
       DF_CUDA(c, cudaStreamSynchronize(c->stream), "df_set_sigma");
-      return fail(c, DF_ERR_ARG, "Sigma~ is not invariant under the lattice's point group (df_opts.symmetry = 1)");
+      return fail(c, DF_ERR_ARG,
+                  c->opts.symmetry == 2 ? "Sigma~ breaks the point group or Sigma~(-w) = Sigma~(w)* (df_opts.symmetry = 2)"
+                                        : "Sigma~ is not invariant under the lattice's point group (df_opts.symmetry = 1)");
     }
   }
   DF_CUDA(c, launch_dyson_ifft(c, c->dm.m_max, c->dm.n_w), "Dyson + FFT to real space");

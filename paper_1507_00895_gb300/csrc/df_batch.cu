@@ -563,6 +563,7 @@ df_status df_batch_init(df_batch** out, int npts, const df_point* pts, int preci
     if (N > 4096 || (q.tp != 0.0 && q.dim != 2)) return DF_ERR_ARG;
     if (q.n_w < 2 || q.n_w > 128 || (q.n_w & 1) || q.m_max < 0 || q.m_max > 31 || !(q.beta > 0.0)) return DF_ERR_ARG;
     if (!q.g || !q.delta || !q.gamma_d || !q.gamma_m) return DF_ERR_ARG;
+    if (q.symmetry != 0 && q.symmetry != 1) return DF_ERR_ARG;   // the point group only
   }
   df_batch* b = new (std::nothrow) df_batch();
   if (!b) return DF_ERR_OOM;

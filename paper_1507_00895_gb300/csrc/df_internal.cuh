@@ -339,7 +339,7 @@ cudaError_t launch_bse_f64_list(df_ctx* c, const int* list);
 cudaError_t launch_split_gamma_t(df_ctx* c);
 // point-group reduction (df_sym.cu)
 int build_wedge(int dim, int nk, std::vector<int>& qmap, std::vector<int>& qrep);
-cudaError_t launch_wedge_gather(df_ctx* c);
+cudaError_t launch_wedge_gather(df_ctx* c, const Dims& ladder_dims);
 cudaError_t launch_wedge_scatter(df_ctx* c, bool with_lambda);
 cudaError_t launch_sigma_invariance(df_ctx* c, unsigned long long* out);
 }  // namespace df

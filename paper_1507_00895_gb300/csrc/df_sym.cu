@@ -10,6 +10,15 @@
 // representative per orbit: chi~ is gathered into a compact [nb][n_w][n_orb]
 // array, the unchanged ladder kernels run on it as on a grid of n_orb
 // momenta, and the results are copied back to every momentum of the orbit.
+//
+// The frequency reflection (df_opts.symmetry = 2) halves the bosonic planes
+// too.  With g(-w) = g(w)*, Delta(-w) = Delta(w)* and a real eps_k, G~(k,-w)
+// = G~(k,w)* (Eqs. gd0 and dyson, given the same of Sigma~), so Eq.
+// dual_bubble gives chi~(q,-W;w) = chi~(q,W;-w)*; with gamma(-W;w,w') =
+// gamma(W;-w,-w')* the ladder matrix of -W is the frequency-reversed complex
+// conjugate of that of W, and so are its solution, Gamma^(2), the bracket and
+// the eigenvalues.  Only the planes W >= 0 are solved; index-wise W -> -W is
+// a -> N_W - 1 - a and w -> -w is i -> n_w - 1 - i.
 #include <algorithm>
 #include <vector>
 
@@ -47,7 +56,8 @@ int build_wedge(int dim, int nk, std::vector<int>& qmap, std::vector<int>& qrep)
 
 namespace {
 
-// chi_w[a][i][o] = chi[a][i][qrep[o]] for the handle's planes a in [a0, a0 + na)
+// chi_w[a][i][o] = chi[a][i][qrep[o]] for the planes a in [a0, a0 + na) of dm
+// (the ladder stage's planes)
 __global__ void wedge_gather_kernel(Dims dm, int n_orb, const int* __restrict__ qrep, const double2* __restrict__ chi,
                                     double2* __restrict__ chi_w) {
   const long total = (long)dm.na * dm.n_w * n_orb;
@@ -60,8 +70,9 @@ __global__ void wedge_gather_kernel(Dims dm, int n_orb, const int* __restrict__ 
 
 // kc[c][a][i][q] = kc_w[c][a][i][qmap[q]] for a in the handle's range; the
 // leading eigenvalue and its flag likewise ([c][a][q]) when lam_w is given
-// (eigenvalues computed this pass)
-__global__ void wedge_scatter_kernel(Dims dm, int n_orb, const int* __restrict__ qmap,
+// (eigenvalues computed this pass).  With refl, the planes a < m_max are the
+// reflections of a' = 2 m_max - a: kc_w[c][a'][n_w - 1 - i][o]*, lam_w[c][a'][o]*.
+__global__ void wedge_scatter_kernel(Dims dm, int n_orb, int refl, const int* __restrict__ qmap,
                                      const double2* __restrict__ kc_w, double2* __restrict__ kc,
                                      const double2* __restrict__ lam_w, const int* __restrict__ ok_w,
                                      double2* __restrict__ lam, int* __restrict__ ok) {
@@ -73,20 +84,26 @@ __global__ void wedge_scatter_kernel(Dims dm, int n_orb, const int* __restrict__
     const int i = (int)(r % dm.n_w);
     const long ca = r / dm.n_w;
     const int c = (int)(ca / dm.na), a = dm.a0 + (int)(ca % dm.na);
+    const bool mirror = refl && a < dm.m_max;
+    const int as = mirror ? 2 * dm.m_max - a : a, is = mirror ? dm.n_w - 1 - i : i;
     const long row = ((long)c * dm.nb + a) * dm.n_w + i;
+    const long srow = ((long)c * dm.nb + as) * dm.n_w + is;
     const int o = qmap[q];
-    kc[row * dm.N + q] = kc_w[row * n_orb + o];
+    const double2 v = kc_w[srow * n_orb + o];
+    kc[row * dm.N + q] = mirror ? make_double2(v.x, -v.y) : v;
     if (lam_w && i == 0) {
-      const long lr = (long)c * dm.nb + a;
-      lam[lr * dm.N + q] = lam_w[lr * n_orb + o];
-      ok[lr * dm.N + q] = ok_w[lr * n_orb + o];
+      const long lr = (long)c * dm.nb + a, ls = (long)c * dm.nb + as;
+      const double2 l = lam_w[ls * n_orb + o];
+      lam[lr * dm.N + q] = mirror ? make_double2(l.x, -l.y) : l;
+      ok[lr * dm.N + q] = ok_w[ls * n_orb + o];
     }
   }
 }
 
-// out[0] = max |sigma(k) - sigma(qrep[qmap[k]])|, out[1] = max |sigma| (|re| + |im|;
+// out[0] = max |sigma(k) - sigma(qrep[qmap[k]])| (with refl also
+// max |sigma(w, k) - sigma(-w, k)*|), out[1] = max |sigma| (|re| + |im|;
 // non-negative doubles order as their bit patterns)
-__global__ void sigma_invariance_kernel(Dims dm, const int* __restrict__ qmap, const int* __restrict__ qrep,
+__global__ void sigma_invariance_kernel(Dims dm, int refl, const int* __restrict__ qmap, const int* __restrict__ qrep,
                                         const double2* __restrict__ sigma, unsigned long long* __restrict__ out) {
   double dev = 0.0, mag = 0.0;
   const long total = (long)dm.n_w * dm.N;
@@ -94,8 +111,17 @@ __global__ void sigma_invariance_kernel(Dims dm, const int* __restrict__ qmap, c
     const int q = (int)(idx % dm.N);
     const long row = idx / dm.N;
     const double2 s = sigma[idx], r = sigma[row * dm.N + qrep[qmap[q]]];
-    const double d = fabs(s.x - r.x) + fabs(s.y - r.y), m = fabs(s.x) + fabs(s.y);
-    if (!(d <= dev)) dev = (d == d) ? d : __longlong_as_double(0x7ff0000000000000LL);   // NaN -> inf
+    double d = fabs(s.x - r.x) + fabs(s.y - r.y);
+    bool bad = !(d == d);                      // a NaN counts as an infinite deviation
+    const double m = fabs(s.x) + fabs(s.y);
+    if (refl) {
+      const double2 t = sigma[(dm.n_w - 1 - row) * dm.N + q];
+      const double d2 = fabs(s.x - t.x) + fabs(s.y + t.y);
+      bad = bad || !(d2 == d2);
+      d = fmax(d, d2);
+    }
+    if (bad) d = __longlong_as_double(0x7ff0000000000000LL);
+    dev = fmax(dev, d);
     mag = fmax(mag, m);
   }
   for (int o = 16; o > 0; o >>= 1) {
@@ -112,8 +138,7 @@ int grid_for(long total) { return (int)std::min<long>(4096, (total + 255) / 256)
 
 }  // namespace
 
-cudaError_t launch_wedge_gather(df_ctx* c) {
-  const Dims& dm = c->dm;
+cudaError_t launch_wedge_gather(df_ctx* c, const Dims& dm) {
   const long total = (long)dm.na * dm.n_w * c->n_orb;
   wedge_gather_kernel<<<grid_for(total), 256, 0, c->stream>>>(dm, c->n_orb, c->qrep, c->chi, c->chi_w);
   return cudaGetLastError();
@@ -122,7 +147,8 @@ cudaError_t launch_wedge_gather(df_ctx* c) {
 cudaError_t launch_wedge_scatter(df_ctx* c, bool with_lambda) {
   const Dims& dm = c->dm;
   const long total = 2L * dm.na * dm.n_w * dm.N;
-  wedge_scatter_kernel<<<grid_for(total), 256, 0, c->stream>>>(dm, c->n_orb, c->qmap, c->kc_w, c->kc,
+  wedge_scatter_kernel<<<grid_for(total), 256, 0, c->stream>>>(dm, c->n_orb, c->opts.symmetry == 2, c->qmap,
+                                                               c->kc_w, c->kc,
                                                                with_lambda ? c->lam_w : nullptr,
                                                                with_lambda ? c->lam_ok_w : nullptr, c->lam, c->lam_ok);
   return cudaGetLastError();
@@ -132,7 +158,8 @@ cudaError_t launch_sigma_invariance(df_ctx* c, unsigned long long* out) {
   const Dims& dm = c->dm;
   cudaError_t e = cudaMemsetAsync(out, 0, 2 * sizeof(unsigned long long), c->stream);
   if (e != cudaSuccess) return e;
-  sigma_invariance_kernel<<<grid_for((long)dm.n_w * dm.N), 256, 0, c->stream>>>(dm, c->qmap, c->qrep, c->sigma, out);
+  sigma_invariance_kernel<<<grid_for((long)dm.n_w * dm.N), 256, 0, c->stream>>>(dm, c->opts.symmetry == 2, c->qmap,
+                                                                                c->qrep, c->sigma, out);
   return cudaGetLastError();
 }
 

@@ -192,7 +192,7 @@ class DualFermion:
                  precision: int = DF_FP64, eig_mode: int = 1, ir_max_steps: int = 8,
                  ir_tol: float = 1e-13, radius_order: int = 0, ladder_tol: float = 1e-9,
                  ladder_fallback: int = 1, mixed_sweep: int = 0, w_range: Optional[tuple] = None,
-                 symmetry: bool = False, stream: Optional[int] = None):
+                 symmetry: int = 0, stream: Optional[int] = None):
         self.lib = load()
         self.dim, self.nk, self.n_w, self.m_max = dim, nk, n_w, m_max
         self.N = nk ** dim
@@ -208,7 +208,7 @@ class DualFermion:
         if w_range is not None:
             opts.w_lo, opts.w_hi = int(w_range[0]), int(w_range[1])
         self.w_range = (opts.w_lo, opts.w_hi if opts.w_hi > 0 else self.nb)
-        opts.symmetry = 1 if symmetry else 0
+        opts.symmetry = int(symmetry)          # 0 off, 1 point group, 2 + frequency reflection
         g, delta = _c128(g), _c128(delta)
         gd, gm = _c128(gamma_d), _c128(gamma_m)
         if g.shape != (self.ne,) or delta.shape != (self.ne,):

@@ -5,6 +5,8 @@
 Cases (inputs from paper_1507_00895_gb300.inputs; every stage runs in libdf):
   mixed64  2D 16x16, n_w = 64, N_W = 15, DF_FP32_IR: bubble + both ladder
            channels (7,680 ladders of order 64, bse_mixed_kernel)
+  bench64  the benchmark's workload itself (2D 32x32, n_w = 64, N_W = 15),
+           DF_FP32_IR: bubble + both ladder channels (30,720 ladders)
   tc96     3D 8^3, n_w = 96, N_W = 5, DF_FP32_IR: bubble + both ladder channels
            (5,120 ladders of order 96, the tensor-core Gauss-Jordan kernel)
   simt96   the same with the CUDA-core Gauss-Jordan (mixed_sweep = 1)
@@ -26,6 +28,8 @@ def main(argv=None) -> int:
     build.build_lib()
     if case == "mixed64":
         w, kw, stages = I.workload("square32_tp", nk=16), dict(precision=df.DF_FP32_IR), ("bubble", "bse")
+    elif case == "bench64":
+        w, kw, stages = I.workload("square32_tp"), dict(precision=df.DF_FP32_IR), ("bubble", "bse")
     elif case in ("tc96", "simt96"):
         w = I.workload("cubic16_crit", nk=8, m_max=2)
         kw = dict(precision=df.DF_FP32_IR, mixed_sweep=0 if case == "tc96" else 1)

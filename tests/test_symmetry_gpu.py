@@ -166,3 +166,72 @@ def test_reduced_without_eigenvalues(df, prec):
             assert nrel(red.get_sigma(), full.get_sigma()) < tol, it
         lam, ok = red.get_lambda()
         assert np.all(lam == 0) and np.all(ok == -1)
+
+
+@pytest.mark.parametrize("name,kw", [("square32_tp", dict(nk=16, n_w=32, m_max=3)),
+                                     ("cubic16_crit", dict(nk=4, n_w=96, m_max=2)),
+                                     ("square32_tp", dict(nk=8, n_w=128, m_max=2)),
+                                     ("paper_u20", dict(nk=8, n_w=12, m_max=0))])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_reflection_equals_full(df, name, kw, prec):
+    # symmetry = 2: the planes W >= 0 solved on the orbit representatives, W < 0 by
+    # the frequency reflection; brackets, eigenvalues (all W) and Sigma~ against the
+    # full solve over two passes
+    w = I.workload(name, **kw)
+    p = df.DF_FP64 if prec == "fp64" else df.DF_FP32_IR
+    tol = TOL64 if prec == "fp64" else TOL_MIXED
+    with df.DualFermion.from_workload(w, precision=p, eig_mode=2) as full, \
+            df.DualFermion.from_workload(w, precision=p, eig_mode=2, symmetry=2) as red:
+        for it in range(2):
+            for d in (full, red):
+                d.bubble()
+                d.bse(3)
+            assert nrel(red.get_kernel(), full.get_kernel()) < tol, it
+            lf, okf = full.get_lambda()
+            lr, okr = red.get_lambda()
+            scale = max(1.0, float(np.max(np.abs(lf))))
+            for flag, bound in ((1, 1e-5), (2, 1e-4)):
+                m = (okf == flag) & (okr == flag)
+                if np.any(m):
+                    assert np.max(np.abs(lr[m] - lf[m])) < bound * scale, flag
+            full.sigma()
+            red.sigma()
+            assert nrel(red.get_sigma(), full.get_sigma()) < tol, it
+
+
+def test_reflection_matches_the_oracle(df):
+    w = I.workload("square32_tp", nk=8, n_w=10, m_max=3)
+    st = O.run_workload(w, n_iter=3)
+    with df.DualFermion.from_workload(w, symmetry=2) as d:
+        for it in range(3):
+            d.bubble()
+            d.bse(3)
+            d.sigma()
+            assert nrel(d.get_sigma(), st.sigmas[it]) < TOL64, it
+
+
+def test_reflection_refuses_inputs_and_sigma_without_it(df):
+    # inputs without the reflection: refused at df_init and by df_set_inputs (the
+    # handle keeps its inputs); a Sigma~ without it: refused, Sigma~ reset to 0
+    bad = I.random_nonsymmetric(8, 1, 2, 4, seed=5)
+    with pytest.raises(df.DFError) as e:
+        df.DualFermion.from_workload(bad, symmetry=2)
+    assert e.value.status == df.DF_ERR_ARG
+    w = I.workload("square32_tp", nk=8, n_w=8, m_max=1)
+    st = O.run_workload(w, n_iter=1)
+    with df.DualFermion.from_workload(w, symmetry=2) as d:
+        gd, gm = df.vertex_from_spin(bad.gamma_uu, bad.gamma_ud)
+        with pytest.raises(df.DFError) as e:
+            d.set_inputs(bad.g, bad.delta, gd, gm)
+        assert e.value.status == df.DF_ERR_ARG
+        d.set_sigma(st.sigmas[0])                              # has the reflection
+        sig = st.sigmas[0] + 0.01j * np.arange(w.n_w)[:, None]   # an imaginary ramp in w: breaks it
+        with pytest.raises(df.DFError):
+            d.set_sigma(sig)
+        assert np.all(d.get_sigma() == 0)
+        d.bubble()
+        d.bse(3)
+        d.sigma()
+        assert nrel(d.get_sigma(), st.sigmas[0]) < TOL64      # the handle's inputs are unchanged
+    with pytest.raises(df.DFError):                            # needs the full bosonic range
+        df.DualFermion.from_workload(w, symmetry=2, w_range=(0, 2))

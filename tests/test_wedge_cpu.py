@@ -114,3 +114,42 @@ def test_a_sigma_that_breaks_the_symmetry_breaks_the_reduction(df):
     assert spread(sigma, qmap) > 0.1
     chi, _ = one_pass_pieces(w, sigma.astype(np.complex128))
     assert spread(chi, qmap) > 1e-6
+
+
+def reflect(x, axis_w, axis_a=None):
+    """x with the fermionic axis reversed (w -> -w) and, if given, the bosonic
+    axis reversed (W -> -W), complex-conjugated."""
+    y = np.flip(x, axis=axis_w)
+    if axis_a is not None:
+        y = np.flip(y, axis=axis_a)
+    return np.conj(y)
+
+
+def test_frequency_reflection_of_the_inputs_bubble_and_kernel():
+    # df_opts.symmetry = 2: with g(-w) = g(w)*, Delta likewise and gamma(-W;w,w') =
+    # gamma(W;-w,-w')*, the oracle's chi~ and Eq. sd bracket of -W are the
+    # frequency-reversed conjugates of those of W, at Sigma~ = 0 and after passes
+    w = I.workload("square32_tp", nk=8, n_w=8, m_max=2)
+    gd, gm = O.channel_vertices(w.gamma_uu, w.gamma_ud)
+    for x in (w.g, w.delta):
+        assert np.max(np.abs(x - reflect(x, 0))) < 1e-14 * np.max(np.abs(x))
+    for gx in (gd, gm):
+        assert np.max(np.abs(gx - np.flip(reflect(gx, 1, 0), axis=2))) < 1e-13 * np.max(np.abs(gx))
+    for sigma in (np.zeros((w.n_w, w.N), complex), O.run_workload(w, n_iter=2).sigma):
+        assert np.max(np.abs(sigma - reflect(sigma, 0))) <= 1e-13 * max(np.max(np.abs(sigma)), 1e-300)
+        chi, kern = one_pass_pieces(w, sigma)
+        assert np.max(np.abs(chi - reflect(chi, 1, 0))) < 1e-13 * np.max(np.abs(chi))
+        assert np.max(np.abs(kern - reflect(kern, 1, 0)) / np.abs(kern)) < 1e-11      # elementwise
+
+
+def test_a_vertex_without_the_reflection_breaks_it():
+    # planted on the oracle side: a complex perturbation of gamma that does not map
+    # onto its reflection leaves chi~ symmetric (it does not depend on gamma) but
+    # breaks the bracket's reflection, so df_init must refuse such a vertex
+    w = I.workload("square32_tp", nk=8, n_w=8, m_max=2)
+    rng = np.random.default_rng(3)
+    w.gamma_ud = w.gamma_ud + 0.5j * rng.normal(size=w.gamma_ud.shape)
+    chi, kern = one_pass_pieces(w, np.zeros((w.n_w, w.N), complex))
+    assert np.max(np.abs(chi - reflect(chi, 1, 0))) < 1e-13 * np.max(np.abs(chi))
+    # (relative to the typical entry: this workload has a few near-singular ladders)
+    assert np.max(np.abs(kern - reflect(kern, 1, 0))) > 1e-2 * np.median(np.abs(kern))
