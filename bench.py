@@ -327,8 +327,9 @@ def time_to_converged(df, I, torch, max_passes=60):
            "target": "max|Sigma~ - Sigma~*| <= 1e-8 max|Sigma~*|, Sigma~* = FP64 loop at r <= 1e-13",
            "reference_passes": it}
     den = float(np.max(np.abs(ref)))
-    for name, prec, sym in (("fp64", df.DF_FP64, False), ("fp32ir", df.DF_FP32_IR, False),
-                            ("fp64_reduced", df.DF_FP64, True), ("fp32ir_reduced", df.DF_FP32_IR, True)):
+    for name, prec, sym in (("fp64", df.DF_FP64, 0), ("fp32ir", df.DF_FP32_IR, 0),
+                            ("fp64_reduced", df.DF_FP64, 1), ("fp32ir_reduced", df.DF_FP32_IR, 1),
+                            ("fp64_reduced_reflected", df.DF_FP64, 2), ("fp32ir_reduced_reflected", df.DF_FP32_IR, 2)):
         with df.DualFermion.from_workload(w, precision=prec, eig_mode=1, symmetry=sym,
                                           stream=stream.cuda_stream) as d:
             d.iterate(1)                       # warm-up pass (kernels loaded, attributes set)
@@ -353,8 +354,10 @@ def time_to_converged(df, I, torch, max_passes=60):
     if "fp64" in out and "fp32ir" in out:
         out["speedup_mixed_vs_plain"] = out["fp64"]["ms"] / out["fp32ir"]["ms"]
         out["speedup_mixed_reduced_vs_plain"] = out["fp64"]["ms"] / out["fp32ir_reduced"]["ms"]
+        out["speedup_mixed_reduced_reflected_vs_plain"] = out["fp64"]["ms"] / out["fp32ir_reduced_reflected"]["ms"]
         out["reduced"] = ("df_opts.symmetry = 1: one ladder per momentum orbit of the point group "
-                          "(153 of 1024 momenta), copied to the orbit")
+                          "(153 of 1024 momenta), copied to the orbit; 2: also only W >= 0 (8 of 15 planes), "
+                          "W < 0 by the frequency reflection")
     return out
 
 
@@ -504,8 +507,9 @@ def large_order_bench(df, I, passes: int = 2):
         t = d.get_timing()
     out["fp32ir_cuda_core_sweep"] = {"ladder_ms_per_pass": t["bse"][0] / passes, "kernel": "bse_gj_ir_kernel"}
     _, qrep = df.wedge(w.dim, w.nk)
-    for name, prec in (("fp64_reduced", df.DF_FP64), ("fp32ir_reduced", df.DF_FP32_IR)):
-        with df.DualFermion.from_workload(w, precision=prec, symmetry=True) as d:
+    for name, prec, sym in (("fp64_reduced", df.DF_FP64, 1), ("fp32ir_reduced", df.DF_FP32_IR, 1),
+                            ("fp32ir_reduced_reflected", df.DF_FP32_IR, 2)):
+        with df.DualFermion.from_workload(w, precision=prec, symmetry=sym) as d:
             d.iterate(1)
             red = d.get_sigma()
             d.set_sigma(zero)
@@ -515,8 +519,9 @@ def large_order_bench(df, I, passes: int = 2):
             d.synchronize()
             wall = (time.perf_counter() - t0) / passes
             t = d.get_timing()
+        planes = w.n_bos if sym == 1 else w.m_max + 1
         out[name] = {"s_per_pass": wall, "ladder_ms_per_pass": t["bse"][0] / passes,
-                     "ladders_solved": 2 * w.n_bos * len(qrep),
+                     "ladders_solved": 2 * planes * len(qrep),
                      "points_per_s_full_grid": w.n_bos * w.N / wall,
                      "err_vs_fp64_first_pass": float(np.max(np.abs(red - sig["fp64"])) / np.max(np.abs(sig["fp64"])))}
     return out
@@ -781,7 +786,7 @@ def run_ours(args):
     # = n^3 complex multiply-adds = 8 n^3 real flops (full back substitutions: 10.67 n^3)
     algo_flop = 8.0 * n ** 3
 
-    def measure(prec, symmetry=False):
+    def measure(prec, symmetry=0):
         d = df.DualFermion.from_workload(w, precision=prec, eig_mode=1, symmetry=symmetry,
                                          stream=stream.cuda_stream)
 
@@ -908,9 +913,11 @@ def run_ours(args):
     if rank == 0 and not args.no_reduced:
         _, qrep = df.wedge(w.dim, w.nk)
         reduced = {"workload": WORKLOAD_DESC, "orbits": len(qrep), "momenta": w.N,
-                   "ladders_solved_per_step": 2 * w.n_bos * len(qrep)}
-        for name, p_ in (("fp64", df.DF_FP64), ("fp32ir", df.DF_FP32_IR)):
-            rd, rr = measure(p_, symmetry=True)
+                   "ladders_solved_per_step": 2 * w.n_bos * len(qrep),
+                   "ladders_solved_per_step_reflected": 2 * (w.m_max + 1) * len(qrep)}
+        for name, p_, sym in (("fp64", df.DF_FP64, 1), ("fp32ir", df.DF_FP32_IR, 1),
+                              ("fp64_reflected", df.DF_FP64, 2), ("fp32ir_reflected", df.DF_FP32_IR, 2)):
+            rd, rr = measure(p_, symmetry=sym)
             rd.set_sigma(zeros)
             rd.bubble(); rd.bse(3); rd.sigma(want_residual=False)
             if plain_sigma is not None:
