@@ -611,14 +611,14 @@ def run_config5(args):
     stated = []
     for k, w in enumerate(I.config5_points(8)):
         row = {"U": w.U, "beta": w.beta, "tp": w.tp, "mu": w.mu}
-        with df.DualFermion.from_workload(w, precision=df.DF_FP32_IR, eig_mode=1, symmetry=True) as d:
+        with df.DualFermion.from_workload(w, precision=df.DF_FP32_IR, eig_mode=1, symmetry=2) as d:
             d.bubble()
             d.bse(3)
             lam, ok = d.get_lambda()
             row["max_abs_lambda_W0_first_pass"] = float(np.max(np.abs(lam[:, w.m_max])))
         if k < 2:
             for mix in (1.0, 0.3):
-                with df.DualFermion.from_workload(w, precision=df.DF_FP32_IR, eig_mode=0, symmetry=True,
+                with df.DualFermion.from_workload(w, precision=df.DF_FP32_IR, eig_mode=0, symmetry=2,
                                                   mix=mix) as d:
                     res = []
                     try:
@@ -647,9 +647,9 @@ def run_config5(args):
     t0 = time.perf_counter()
     Xs, Ys, P, M = [], [], [], []
     for i0 in range(0, len(train), 50):           # in chunks, within the time budget
-        if time.perf_counter() - t_start > 0.6 * budget:
+        if time.perf_counter() - t_start > args.c5_gen_frac * budget:
             break
-        X_, Y_, p_, m_ = W.generate_each(train[i0:i0 + 50], precision=df.DF_FP32_IR, symmetry=True, tol=1e-8)
+        X_, Y_, p_, m_ = W.generate_each(train[i0:i0 + 50], precision=df.DF_FP32_IR, symmetry=2, tol=1e-8)
         if len(X_):
             Xs.append(X_)
             Ys.append(Y_)
@@ -667,7 +667,8 @@ def run_config5(args):
                              "mu = U/2 +- 1",
            "train": {"points": len(train), "attempted": int(len(mask)), "converged": int(mask.sum()),
                      "mean_passes": float(np.mean(passes[mask])) if mask.any() else None,
-                     "seconds": t_gen, "path": "DF_FP32_IR, point-group reduction, r <= 1e-8"}}
+                     "seconds": t_gen,
+                     "path": "DF_FP32_IR, point-group reduction and frequency reflection, r <= 1e-8"}}
     if mask.sum() >= 2:
         model = W.WarmStart(X.shape[1], Y.shape[1], grid["nk"], width=512, seed=0)
         t0 = time.perf_counter()
@@ -682,13 +683,13 @@ def run_config5(args):
         for w in test:
             if time.perf_counter() - t_start > budget:
                 break
-            rows.extend(W.evaluate(model, [w], tol=1e-8, precision=df.DF_FP32_IR, symmetry=True))
+            rows.extend(W.evaluate(model, [w], tol=1e-8, precision=df.DF_FP32_IR, symmetry=2))
             progress("evaluate", evaluated=len(rows))
         ok = [r for r in rows if r["cold_passes"] is not None]
         out["held_out"] = {"points": len(test), "attempted": len(rows), "evaluated": len(ok),
                            "seconds": time.perf_counter() - t0,
                            "target": "max|Sigma~ - Sigma~*| <= 1e-8 max|Sigma~*|, Sigma~* = FP64 loop (reduced) "
-                                     "at r <= 1e-12; path DF_FP32_IR with the reduction",
+                                     "at r <= 1e-12; path DF_FP32_IR with the reductions (symmetry = 2)",
                            "fallbacks": sum(r["fallback"] for r in ok)}
         if ok:
             cp = float(np.mean([r["cold_passes"] for r in ok]))
@@ -1004,8 +1005,10 @@ def main():
     ap.add_argument("--c5-test", type=int, default=200, help="--config5: held-out points")
     ap.add_argument("--c5-steps", type=int, default=3000, help="--config5: training steps")
     ap.add_argument("--c5-budget-s", type=float, default=0.0,
-                    help="--config5: wall-clock budget; generation stops at 60%% of it, evaluation at 100%%")
+                    help="--config5: wall-clock budget; generation stops at --c5-gen-frac of it, evaluation at all of it")
     ap.add_argument("--c5-progress", default="", help="--config5: file rewritten with the progress")
+    ap.add_argument("--c5-gen-frac", type=float, default=0.6,
+                    help="--config5: share of the budget after which generation stops")
     ap.add_argument("--omega-split", action="store_true",
                     help="one problem over the N GPUs (bosonic planes split, one all-reduce per pass) "
                          "instead of N replicas")

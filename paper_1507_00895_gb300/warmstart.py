@@ -77,12 +77,13 @@ def generate(workloads, precision=df.DF_FP64, tol: float = 1e-10, max_iter: int 
     return Xa, Ya, np.array(passes), mask
 
 
-def generate_each(workloads, precision=df.DF_FP32_IR, symmetry: bool = True, tol: float = 1e-8,
+def generate_each(workloads, precision=df.DF_FP32_IR, symmetry: int = 2, tol: float = 1e-8,
                   max_iter: int = 60):
     """Converged Sigma~ of every workload, one handle at a time: the stated
     warm-start grid (64^2, n_w = 128, N_W = 31) holds about 1 GB of device
-    arrays per point, too much to batch.  The point-group reduction solves
-    561 of the 4096 momenta per plane.  Returns (X, Y, passes [n], converged
+    arrays per point, too much to batch.  With symmetry = 2 the reductions
+    solve 561 of the 4096 momenta on 16 of the 31 planes.  Returns (X, Y,
+    passes [n], converged
     mask [n]); a point whose loop does not reach r <= tol in max_iter passes,
     or fails, is dropped."""
     _, rep = wedge(workloads[0].nk)
@@ -201,7 +202,7 @@ def passes_to(d, sigma_ref, tol: float, max_iter: int):
 
 
 def evaluate(model: WarmStart, workloads, tol: float = 1e-8, max_iter: int = 60,
-             precision=df.DF_FP64, symmetry: bool = False):
+             precision=df.DF_FP64, symmetry: int = 0):
     """Passes and device time to max|Sigma~ - Sigma~*| <= tol max|Sigma~*| from
     Sigma~ = 0 and from the prediction, on the given path (precision, point-group
     reduction), Sigma~* the FP64 loop at r <= 1e-12 (reduced when the path is);
