@@ -380,13 +380,14 @@ def batch_bench(df, I, torch, full: bool, passes: int = 3):
         if (w.dim, w.nk) not in orbits:
             orbits[(w.dim, w.nk)] = len(df.wedge(w.dim, w.nk)[1])
     out = {"workload": desc, "points_per_pass": pts, "ladders_per_pass": 2 * pts,
-           "reduced_ladders_per_pass": 2 * sum(w.n_bos * orbits[(w.dim, w.nk)] for w in ws),
-           "reduced": "df_point.symmetry = 1: one ladder per momentum orbit, rate over the full grid"}
+           "reduced_ladders_per_pass": 2 * sum((w.m_max + 1) * orbits[(w.dim, w.nk)] for w in ws),
+           "reduced": "df_point.symmetry = 2: one ladder per momentum orbit on the planes W >= 0, "
+                      "rate over the full grid"}
     cache = os.path.join(tempfile.gettempdir(), "df_batch_tune.txt")
     if full:
         passes = 1         # ~20 TFLOP of ladders per pass: one warm and one timed pass, default tiles
-    for name, prec, sym in (("fp64", df.DF_FP64, False), ("fp32ir", df.DF_FP32_IR, False),
-                            ("fp64_reduced", df.DF_FP64, True), ("fp32ir_reduced", df.DF_FP32_IR, True)):
+    for name, prec, sym in (("fp64", df.DF_FP64, 0), ("fp32ir", df.DF_FP32_IR, 0),
+                            ("fp64_reduced", df.DF_FP64, 2), ("fp32ir_reduced", df.DF_FP32_IR, 2)):
         with df.DualFermionBatch(ws, precision=prec, symmetry=sym) as b:
             nc, ch, cached = b.autotune(cache) if not full else (None, None, None)
             b.iterate(1)

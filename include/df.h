@@ -323,9 +323,10 @@ typedef struct df_point {
   const double* delta;    /* [n_w + 2 m_max] */
   const double* gamma_d;  /* [2 m_max + 1][n_w][n_w] */
   const double* gamma_m;
-  int symmetry;           /* 1: the point-group reduction of df_opts.symmetry = 1 for this
-                           * point (exact here: a batch always starts from Sigma~ = 0);
-                           * 0: every ladder solved; other values: DF_ERR_ARG */
+  int symmetry;           /* the reductions of df_opts.symmetry for this point (exact here:
+                           * a batch always starts from Sigma~ = 0): 0 every ladder solved,
+                           * 1 the point group, 2 also the frequency reflection (inputs
+                           * checked as by df_init: DF_ERR_ARG if they lack it) */
 } df_point;
 
 typedef struct df_batch df_batch;

@@ -37,10 +37,12 @@ __device__ __forceinline__ MixedCheck batch_check(int* redo, int point) {
 struct PointDev {
   Dims dm;
   // the ladder stage's view: dm, chi and kc, or with the point-group reduction
-  // (sym) the compact grid of one momentum per orbit (ldm.N = n_orb) and its arrays
+  // (sym) the compact grid of one momentum per orbit (ldm.N = n_orb) and its
+  // arrays; with the frequency reflection (refl) only the planes W >= 0
+  // (ldm.a0 = m_max, ldm.na = m_max + 1)
   Dims ldm;
   double2 *lchi, *lkc;
-  int sym, n_orb;
+  int sym, refl, n_orb;
   int *qmap, *qrep;
   int nc;        // FP64 ladder right-hand-side chunk
   int mixed;     // ladders of this point run in DF_FP32_IR
@@ -185,10 +187,10 @@ batch_bse_f64_kernel(const PointDev* __restrict__ pts, const int* __restrict__ o
       if (!P.active) continue;
       const Dims& dm = P.ldm;
       const long local = s - start[k];
-      const long per_ch = (long)dm.nb * dm.N;
+      const long per_ch = (long)dm.na * dm.N;      // the view's planes a0 .. a0 + na - 1
       const int c = (int)(local / per_ch);
       const int rem = (int)(local - (long)c * per_ch);
-      const int a = rem / dm.N, q = rem - a * dm.N;
+      const int a = dm.a0 + rem / dm.N, q = rem - (a - dm.a0) * dm.N;
       const bool lu_smem = dm.n_w <= kLuSmemOrder;
       const BseSmem L = bse_layout(dm.n_w, P.nc, lu_smem);
       double2* LU = lu_smem ? sm + L.lu : ws + blockIdx.x * ws_stride;
@@ -227,11 +229,11 @@ __global__ void batch_wedge_gather_kernel(const PointDev* __restrict__ pts) {
   const PointDev& P = pts[blockIdx.y];
   if (!P.sym || !P.active) return;
   const Dims& dm = P.dm;
-  const long total = (long)dm.nb * dm.n_w * P.n_orb;
+  const long total = (long)P.ldm.na * dm.n_w * P.n_orb;
   for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
     const int o = (int)(idx % P.n_orb);
-    const long row = idx / P.n_orb;
-    P.lchi[idx] = P.chi[row * dm.N + P.qrep[o]];
+    const long row = (long)P.ldm.a0 * dm.n_w + idx / P.n_orb;   // a * n_w + i
+    P.lchi[row * P.n_orb + o] = P.chi[row * dm.N + P.qrep[o]];
   }
 }
 
@@ -242,8 +244,17 @@ __global__ void batch_wedge_scatter_kernel(const PointDev* __restrict__ pts) {
   const long total = 2L * dm.nb * dm.n_w * dm.N;
   for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
     const int q = (int)(idx % dm.N);
-    const long row = idx / dm.N;
-    P.kc[idx] = P.lkc[row * P.n_orb + P.qmap[q]];
+    const long row = idx / dm.N;                   // (c nb + a) n_w + i
+    const int i = (int)(row % dm.n_w);
+    const long ca = row / dm.n_w;
+    const int a = (int)(ca % dm.nb);
+    if (P.refl && a < dm.m_max) {                  // W < 0: the reflection of 2 m_max - a
+      const long src = (ca + 2 * (dm.m_max - a)) * dm.n_w + (dm.n_w - 1 - i);
+      const double2 v = P.lkc[src * P.n_orb + P.qmap[q]];
+      P.kc[idx] = make_double2(v.x, -v.y);
+    } else {
+      P.kc[idx] = P.lkc[row * P.n_orb + P.qmap[q]];
+    }
   }
 }
 
@@ -281,10 +292,10 @@ batch_bse_mixed_kernel(const PointDev* __restrict__ pts, const int* __restrict__
       if (!P.active) continue;
       const Dims& dm = P.ldm;
       const long local = s - start[k];
-      const long per_ch = (long)dm.nb * dm.N;
+      const long per_ch = (long)dm.na * dm.N;      // the view's planes a0 .. a0 + na - 1
       const int c = (int)(local / per_ch);
       const int rem = (int)(local - (long)c * per_ch);
-      const int a = rem / dm.N, q = rem - a * dm.N;
+      const int a = dm.a0 + rem / dm.N, q = rem - (a - dm.a0) * dm.N;
       const long key = (long)k * 256 + c * dm.nb + a;
       if (use_umma_residual(NP) && (threadIdx.x >> 5) == mixed_compute_threads(NP) / 32)
         mixed_producer(sp, &tc);                      // warp 8: the tensor-core MMAs
@@ -320,10 +331,10 @@ batch_bse_gj_kernel(const PointDev* __restrict__ pts, const int* __restrict__ or
       if (!P.active) continue;
       const Dims& dm = P.ldm;
       const long local = s - start[k];
-      const long per_ch = (long)dm.nb * dm.N;
+      const long per_ch = (long)dm.na * dm.N;      // the view's planes a0 .. a0 + na - 1
       const int c = (int)(local / per_ch);
       const int rem = (int)(local - (long)c * per_ch);
-      const int a = rem / dm.N, q = rem - a * dm.N;
+      const int a = dm.a0 + rem / dm.N, q = rem - (a - dm.a0) * dm.N;
       gj_ir_system(dm, c, a, q, P.gam_hi, P.gam_lo, P.gg_hi, P.gg_lo, P.gg, P.lchi, P.lkc, P.flags, smraw, sh,
                    batch_check(redo, order[k]));
     }
@@ -548,6 +559,38 @@ df_status configure_groups(df_batch* b) {
 
 extern "C" {
 
+// df_point.symmetry = 2: g(-w) = g(w)*, Delta(-w) = Delta(w)* and gamma(-W; w, w')
+// = gamma(W; -w, -w')* for both channels, within 1e-12 of each array's largest entry
+static bool reflection_holds(const df_point& q) {
+  const int ne = q.n_w + 2 * q.m_max, nb = 2 * q.m_max + 1, n = q.n_w;
+  auto dev = [](const double* x, size_t i, size_t j) {   // |x_i - conj(x_j)|, x interleaved (re, im)
+    return fabs(x[2 * i] - x[2 * j]) + fabs(x[2 * i + 1] + x[2 * j + 1]);
+  };
+  auto mag = [](const double* x, size_t i) { return fabs(x[2 * i]) + fabs(x[2 * i + 1]); };
+  const double* vec[2] = {q.g, q.delta};
+  for (const double* x : vec) {
+    double top = 0.0, d = 0.0;
+    for (int e = 0; e < ne; ++e) {
+      top = std::max(top, mag(x, e));
+      d = std::max(d, dev(x, e, ne - 1 - e));
+    }
+    if (!(d <= 1e-12 * top)) return false;
+  }
+  const double* mats[2] = {q.gamma_d, q.gamma_m};
+  for (const double* x : mats) {
+    double top = 0.0, d = 0.0;
+    for (int a = 0; a < nb; ++a)
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+          const size_t u = ((size_t)a * n + i) * n + j, v = ((size_t)(nb - 1 - a) * n + (n - 1 - i)) * n + (n - 1 - j);
+          top = std::max(top, mag(x, u));
+          d = std::max(d, dev(x, u, v));
+        }
+    if (!(d <= 1e-12 * top)) return false;
+  }
+  return true;
+}
+
 df_status df_batch_init(df_batch** out, int npts, const df_point* pts, int precision, double mix, double tol,
                         void* stream) {
   if (!out || !pts || npts < 1 || npts > 4096) return DF_ERR_ARG;
@@ -563,7 +606,8 @@ df_status df_batch_init(df_batch** out, int npts, const df_point* pts, int preci
     if (N > 4096 || (q.tp != 0.0 && q.dim != 2)) return DF_ERR_ARG;
     if (q.n_w < 2 || q.n_w > 128 || (q.n_w & 1) || q.m_max < 0 || q.m_max > 31 || !(q.beta > 0.0)) return DF_ERR_ARG;
     if (!q.g || !q.delta || !q.gamma_d || !q.gamma_m) return DF_ERR_ARG;
-    if (q.symmetry != 0 && q.symmetry != 1) return DF_ERR_ARG;   // the point group only
+    if (q.symmetry < 0 || q.symmetry > 2) return DF_ERR_ARG;
+    if (q.symmetry == 2 && !reflection_holds(q)) return DF_ERR_ARG;
   }
   df_batch* b = new (std::nothrow) df_batch();
   if (!b) return DF_ERR_OOM;
@@ -619,9 +663,14 @@ df_status df_batch_init(df_batch** out, int npts, const df_point* pts, int preci
     dm.tp = q.tp;
     P.mixed = (precision == DF_FP32_IR && mixed_np_of(q.n_w) <= kGjMaxN) ? 1 : 0;
     P.sym = q.symmetry ? 1 : 0;
+    P.refl = q.symmetry == 2 ? 1 : 0;
     P.n_orb = P.sym ? build_wedge(q.dim, q.nk, qmaps[i], qreps[i]) : dm.N;
     P.ldm = dm;
     P.ldm.N = P.n_orb;
+    if (P.refl) {
+      P.ldm.a0 = dm.m_max;
+      P.ldm.na = dm.m_max + 1;
+    }
     b->any_sym = b->any_sym || P.sym;
     P.active = 1;
     P.mix = mix;
@@ -808,7 +857,7 @@ df_status df_batch_init(df_batch** out, int npts, const df_point* pts, int preci
       std::vector<long> st_(g.nseg + 1, 0);
       for (int k = 0; k < g.nseg; ++k) {
         const Dims& dm = b->host_pts[g.order[k]].ldm;
-        st_[k + 1] = st_[k] + 2L * dm.nb * dm.N;
+        st_[k + 1] = st_[k] + 2L * dm.na * dm.N;
       }
       g.total = st_[g.nseg];
       BALLOC(g.d_start, sizeof(long) * (g.nseg + 1), "ladder table");
@@ -825,7 +874,7 @@ df_status df_batch_init(df_batch** out, int npts, const df_point* pts, int preci
       for (int p : g.order) {
         const Dims& dm = b->host_pts[p].ldm;
         big = std::max(big, dm.n_w > kLuSmemOrder ? dm.n_w : 0);
-        if (g.mixed) mixed_ladders += 2L * dm.nb * dm.N;
+        if (g.mixed) mixed_ladders += 2L * dm.na * dm.N;
       }
     if (big) {
       b->ws_stride = (size_t)big * big;

@@ -379,7 +379,7 @@ class DualFermionBatch:
     one launch per stage over all points, one CUDA graph per pass."""
 
     def __init__(self, workloads, precision: int = DF_FP64, mix: float = 1.0, tol: float = 0.0,
-                 symmetry: bool = False, stream: Optional[int] = None):
+                 symmetry: int = 0, stream: Optional[int] = None):
         self.lib = load()
         self.workloads = list(workloads)
         n = len(self.workloads)
@@ -391,7 +391,7 @@ class DualFermionBatch:
             self._keep += [g, dl, gd, gm]
             arr[i] = df_point(w.dim, w.nk, w.tp, w.t, w.beta, w.mu, w.n_w, w.m_max,
                               g.ctypes.data, dl.ctypes.data, gd.ctypes.data, gm.ctypes.data,
-                              1 if symmetry else 0)
+                              int(symmetry))
         if stream is None:
             stream = current_stream_handle()
         h = C.c_void_p()

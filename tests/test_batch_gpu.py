@@ -142,3 +142,23 @@ def test_batch_point_group_reduction_equals_full(df, prec):
         red.iterate(2)
         for i in range(len(ws)):
             assert nrel(red.get_sigma(i), full.get_sigma(i)) < tol, (i, ws[i].dim, ws[i].nk, ws[i].n_w)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_batch_frequency_reflection_equals_full(df, prec):
+    # df_point.symmetry = 2: the point group and only W >= 0 solved per point
+    ws = I.uneven_batch(npts=8, seed=12, max_n_w=128, max_m=3, grids=((2, 8), (3, 4), (4, 4)))
+    p = df.DF_FP64 if prec == "fp64" else df.DF_FP32_IR
+    tol = 1e-10 if prec == "fp64" else 1e-8
+    with df.DualFermionBatch(ws, precision=p) as full, df.DualFermionBatch(ws, precision=p, symmetry=2) as red:
+        full.iterate(2)
+        red.iterate(2)
+        for i in range(len(ws)):
+            assert nrel(red.get_sigma(i), full.get_sigma(i)) < tol, (i, ws[i].dim, ws[i].nk, ws[i].n_w)
+
+
+def test_batch_refuses_inputs_without_the_reflection(df):
+    bad = I.random_nonsymmetric(8, 1, 2, 4, seed=6)
+    with pytest.raises(df.DFError) as e:
+        df.DualFermionBatch([bad], symmetry=2)
+    assert e.value.status == df.DF_ERR_ARG
