@@ -47,7 +47,7 @@ FLUSH_BYTES = 256 << 20
 NCU_TRAFFIC = {"bse_f64_kernel": None, "bse_mixed_kernel": None}
 # tensor-pipe share of the mixed ladder kernel's cycles (ncu sm__pipe_tensor_cycles_active,
 # the committed profile of the same kernel; None once the kernel changes)
-NCU_TENSOR_PIPE = {"bse_mixed_kernel": 0.082}
+NCU_TENSOR_PIPE = {"bse_mixed_kernel": None}
 
 
 def measured_alu_peaks(df):

@@ -265,7 +265,7 @@ batch_bse_mixed_kernel(const PointDev* __restrict__ pts, const int* __restrict__
   extern __shared__ __align__(1024) float2 smf[];
   __shared__ int piv_s[128];
   __shared__ unsigned long long item_s;
-  __shared__ uint64_t mbar_s;
+  __shared__ uint64_t mbar_s[2];
   __shared__ unsigned tslot_s;
   const MixedPtrs sp = mixed_ptrs(smf, NP, piv_s);
   Tc05 tc{};
@@ -275,7 +275,7 @@ batch_bse_mixed_kernel(const PointDev* __restrict__ pts, const int* __restrict__
       if (threadIdx.x == 0) atomicOr(pts[0].flags, kFlagTcLayout);
       return;
     }
-    tc05_setup(tc, &mbar_s, &tslot_s);
+    tc05_setup(tc, mbar_s, &tslot_s);
   }
   const long total = start[nseg];
   long cur = -1;                       // (point, channel, W) whose gamma digits are in shared memory
@@ -306,7 +306,7 @@ batch_bse_mixed_kernel(const PointDev* __restrict__ pts, const int* __restrict__
       cur = key;
     }
   }
-  if constexpr (use_umma_residual(NP)) tc05_teardown(tc);
+  if constexpr (use_umma_residual(NP)) tc05_teardown(tc, mixed_compute_threads(NP));
 }
 
 // mixed ladders of order 64 < n <= 128 (the shared-memory Gauss-Jordan body),

@@ -60,7 +60,7 @@ bse_mixed_kernel(Dims dm, int ch0, int nch, const double2* __restrict__ gam,
                  const unsigned char* __restrict__ gdig, int* __restrict__ flags, MixedCheck mc) {
   extern __shared__ __align__(1024) float2 smf[];
   __shared__ int piv_s[128];
-  __shared__ uint64_t mbar_s;
+  __shared__ uint64_t mbar_s[2];
   __shared__ unsigned tslot_s;
   const MixedPtrs sp = mixed_ptrs(smf, NP, piv_s);
   Tc05 tc{};
@@ -70,7 +70,7 @@ bse_mixed_kernel(Dims dm, int ch0, int nch, const double2* __restrict__ gam,
       if (threadIdx.x == 0) atomicOr(flags, kFlagTcLayout);
       return;
     }
-    tc05_setup(tc, &mbar_s, &tslot_s);
+    tc05_setup(tc, mbar_s, &tslot_s);
   }
   const int N = dm.N, nb = dm.nb, na = dm.na;
   const long systems = (long)nch * na * N;
@@ -89,7 +89,7 @@ bse_mixed_kernel(Dims dm, int ch0, int nch, const double2* __restrict__ gam,
                            gdig ? gdig + (size_t)key * gdig_bytes(NP) : nullptr, key != cur, &tc, mc);
     cur = key;
   }
-  if constexpr (use_umma_residual(NP)) tc05_teardown(tc);
+  if constexpr (use_umma_residual(NP)) tc05_teardown(tc, mixed_compute_threads(NP));
 }
 
 // Self-test of the bounded wait the tensor-core residual uses: one warp

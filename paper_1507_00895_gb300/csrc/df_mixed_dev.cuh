@@ -185,6 +185,7 @@ struct Tc05 {
   unsigned tmem;        // TMEM base address (lane 0, first allocated column)
   uint64_t* mbar;       // completion barrier of the MMA batches
   unsigned phase;       // parity of the next completion (the same in every thread)
+  uint64_t* fin;        // the tear-down's barrier: every queued MMA done before TMEM is freed
 };
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
@@ -242,7 +243,8 @@ __device__ __forceinline__ void tmem_ld16(unsigned taddr, float* v) {
 #pragma unroll
   for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
-// block-level set-up / tear-down (all threads call; warp 0 owns the TMEM allocation)
+// block-level set-up / tear-down (all threads call; warp 0 owns the TMEM allocation);
+// mbar: two barriers (the MMA batches', the tear-down's)
 __device__ __forceinline__ void tc05_setup(Tc05& tc, uint64_t* mbar, unsigned* tslot) {
   if ((threadIdx.x >> 5) == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
@@ -252,6 +254,7 @@ __device__ __forceinline__ void tc05_setup(Tc05& tc, uint64_t* mbar, unsigned* t
   }
   if (threadIdx.x == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar + 1)) : "memory");
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   tc05_fence_before();
@@ -260,8 +263,17 @@ __device__ __forceinline__ void tc05_setup(Tc05& tc, uint64_t* mbar, unsigned* t
   tc.tmem = *tslot;
   tc.mbar = mbar;
   tc.phase = 0;
+  tc.fin = mbar + 1;
 }
-__device__ __forceinline__ void tc05_teardown(const Tc05& tc) {
+// issuer: the thread that issued the block's MMAs.  Its one more commit, to
+// the tear-down's barrier, completes once every MMA it queued has (also after
+// a completion wait that gave up earlier); the wait for it is bounded.
+__device__ __forceinline__ void tc05_teardown(const Tc05& tc, int issuer) {
+  if ((int)threadIdx.x == issuer) {
+    tc05_fence_before();
+    umma_commit(tc.fin);
+    mbar_wait(tc.fin, 0u);
+  }
   tc05_fence_before();
   __syncthreads();
   tc05_fence_after();
