@@ -735,3 +735,16 @@ def test_radius_extension_changes_nothing_inside_the_radius():
     a = O.run_workload(w, n_iter=3)
     b = O.run_workload(w, n_iter=3, radius_order=2)
     assert np.array_equal(a.sigma, b.sigma)
+
+
+def test_warm_start_stated_box_lies_beyond_the_ladder_radius():
+    # the learned warm start's stated parameter box with the Hubbard-atom inputs
+    # (U in [2, 6], beta in [5, 25], mu = U/2 +- 0.5): on the first pass from
+    # Sigma~ = 0 the largest |lambda| of gamma chi~ at W = 0 exceeds 1 at every
+    # sampled point (the radius remark after Eq. lin_alg_inv), already on an 8^2
+    # grid with 16 frequencies; the GPU finds the same at the stated grid
+    for w in I.config5_points(8, nk=8, n_w=16, m_max=1):
+        st = O.run_workload(w, n_iter=1)
+        gd, gm = O.channel_vertices(w.gamma_uu, w.gamma_ud)
+        lam = max(abs(O.ladder_lambda(g, st.chi, w.m_max, q)) for g in (gd, gm) for q in range(w.N))
+        assert lam > 1.0, (w.U, w.beta, lam)
