@@ -57,7 +57,7 @@ int build_wedge(int dim, int nk, std::vector<int>& qmap, std::vector<int>& qrep)
 namespace {
 
 // chi_w[a][i][o] = chi[a][i][qrep[o]] for the planes a in [a0, a0 + na) of dm
-// (the ladder stage's planes)
+// (the ladder stage's planes; dm.N the full grid's momenta)
 __global__ void wedge_gather_kernel(Dims dm, int n_orb, const int* __restrict__ qrep, const double2* __restrict__ chi,
                                     double2* __restrict__ chi_w) {
   const long total = (long)dm.na * dm.n_w * n_orb;
@@ -138,7 +138,11 @@ int grid_for(long total) { return (int)std::min<long>(4096, (total + 255) / 256)
 
 }  // namespace
 
-cudaError_t launch_wedge_gather(df_ctx* c, const Dims& dm) {
+// the ladder stage's planes (ladder_dims.a0, .na) of the full-grid chi~ (c->dm)
+cudaError_t launch_wedge_gather(df_ctx* c, const Dims& ladder_dims) {
+  Dims dm = c->dm;
+  dm.a0 = ladder_dims.a0;
+  dm.na = ladder_dims.na;
   const long total = (long)dm.na * dm.n_w * c->n_orb;
   wedge_gather_kernel<<<grid_for(total), 256, 0, c->stream>>>(dm, c->n_orb, c->qrep, c->chi, c->chi_w);
   return cudaGetLastError();
