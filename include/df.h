@@ -140,8 +140,8 @@ typedef struct df_opts {
                        * 2: the point group and the frequency reflection -- only the planes
                        * W >= 0 are solved; those of -W are their frequency-reversed complex
                        * conjugates (bracket_{-W}(w) = bracket_W(-w)*, lambda_{-W} =
-                       * lambda_W*, a dominant pair reported by its member of larger
-                       * imaginary part on both planes).  Needs g(-w) = g(w)*, Delta(-w) = Delta(w)* and
+                       * lambda_W*; of a dominant pair of equal moduli this may be the
+                       * other member than a solve of -W reports).  Needs g(-w) = g(w)*, Delta(-w) = Delta(w)* and
                        * gamma(-W; w, w') = gamma(W; -w, -w')* (checked by df_init and
                        * df_set_inputs to 1e-12 of each array's largest entry: DF_ERR_ARG
                        * and nothing changed otherwise), Sigma~(-w) = Sigma~(w)* (kept by

@@ -94,12 +94,11 @@ __global__ void wedge_scatter_kernel(Dims dm, int n_orb, int refl, const int* __
     if (lam_w && i == 0) {
       const long lr = (long)c * dm.nb + a, ls = (long)c * dm.nb + as;
       const double2 l = lam_w[ls * n_orb + o];
-      const int f = ok_w[ls * n_orb + o];
-      // the eigenvalues of -W are the conjugates of those of W; a dominant
-      // conjugate pair (flag 2) is reported by its member of larger imaginary
-      // part on both planes
-      lam[lr * dm.N + q] = mirror ? make_double2(l.x, f == 2 ? fabs(l.y) : -l.y) : l;
-      ok[lr * dm.N + q] = f;
+      // the eigenvalues of -W are the conjugates of those of W (of a dominant pair
+      // of equal moduli, flag 2, the reflection may report the other member than
+      // the plane's own solve, whose tie-break is by imaginary part)
+      lam[lr * dm.N + q] = mirror ? make_double2(l.x, -l.y) : l;
+      ok[lr * dm.N + q] = ok_w[ls * n_orb + o];
     }
   }
 }

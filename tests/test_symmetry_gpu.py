@@ -190,10 +190,15 @@ def test_reflection_equals_full(df, name, kw, prec):
             lf, okf = full.get_lambda()
             lr, okr = red.get_lambda()
             scale = max(1.0, float(np.max(np.abs(lf))))
-            for flag, bound in ((1, 1e-5), (2, 1e-4)):
-                m = (okf == flag) & (okr == flag)
-                if np.any(m):
-                    assert np.max(np.abs(lr[m] - lf[m])) < bound * scale, flag
+            m = (okf == 1) & (okr == 1)
+            if np.any(m):
+                assert np.max(np.abs(lr[m] - lf[m])) < 1e-5 * scale
+            # a dominant pair of equal moduli (flag 2): the reflection carries the conjugate
+            # of the W plane's member, the -W plane's own solve may pick the other one
+            m = (okf == 2) & (okr == 2)
+            if np.any(m):
+                d = np.minimum(np.abs(lr[m] - lf[m]), np.abs(lr[m] - np.conj(lf[m])))
+                assert np.max(d) < 1e-4 * scale
             full.sigma()
             red.sigma()
             assert nrel(red.get_sigma(), full.get_sigma()) < tol, it
