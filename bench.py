@@ -44,10 +44,10 @@ PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FLUSH_BYTES = 256 << 20
 # DRAM bytes (read + write) per launch of the ladder kernel from one ncu capture
 # of that kernel on this workload (None once the kernel changes)
-NCU_TRAFFIC = {"bse_f64_kernel": None, "bse_mixed_kernel": None}
+NCU_TRAFFIC = {"bse_f64_kernel": None, "bse_mixed_kernel": 19867904}
 # tensor-pipe share of the mixed ladder kernel's cycles (ncu sm__pipe_tensor_cycles_active,
 # the committed profile of the same kernel; None once the kernel changes)
-NCU_TENSOR_PIPE = {"bse_mixed_kernel": None}
+NCU_TENSOR_PIPE = {"bse_mixed_kernel": 0.082}
 
 
 def measured_alu_peaks(df):
