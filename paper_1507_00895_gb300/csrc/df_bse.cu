@@ -36,7 +36,7 @@ __global__ void __launch_bounds__(kBseThreads)
 bse_f64_kernel(Dims dm, int ch0, int nch, int nc, const double2* __restrict__ gam,
                const double2* __restrict__ gg, const double2* __restrict__ chi,
                double2* __restrict__ kc, double2* __restrict__ ws, int* __restrict__ flags, int radius_K,
-               const double2* __restrict__ lam, const int* __restrict__ list) {
+               const double2* __restrict__ lam, const int* __restrict__ list, int spread) {
   extern __shared__ double2 sm[];
   __shared__ BseF64Shared sh;
   const int n = dm.n_w, N = dm.N, nb = dm.nb, na = dm.na;
@@ -44,12 +44,27 @@ bse_f64_kernel(Dims dm, int ch0, int nch, int nc, const double2* __restrict__ ga
   double2* LU = LU_SMEM ? sm + L.lu : ws + (size_t)blockIdx.x * n * n;
   // the handle's planes of channels ch0 .. ch0 + nch - 1, or with `list` the
   // list[0] systems (c N_W + a) N + q that follow it (ladders the mixed-precision
-  // kernels handed back)
-  const long systems = list ? (long)list[0] : (long)nch * na * N;
+  // kernels handed back).  A short list is spread over up to `spread` blocks:
+  // each ladder's right-hand-side chunks are split into `parts` column ranges,
+  // one block per range, each factorising the ladder itself (the FP64 pipe of
+  // one SM bounds a lone ladder's latency)
+  const int chunks = (n + nc - 1) / nc;
+  long count = list ? (long)list[0] : 0;
+  int parts = 1;
+  if (list && count > 0 && spread > count) {
+    const long p = spread / count;
+    parts = (int)(p < chunks ? p : chunks);
+  }
+  const int cpp = (chunks + parts - 1) / parts;      // chunks per part
+  const long systems = list ? count * parts : (long)nch * na * N;
   for (long s = blockIdx.x; s < systems; s += gridDim.x) {
-    int c, a, q;
+    int c, a, q, jb = 0, je = n;
     if (list) {
-      const long sys = list[1 + s];
+      const int part = (int)(s % parts);
+      jb = part * cpp * nc;
+      je = jb + cpp * nc < n ? jb + cpp * nc : n;
+      if (jb >= je) continue;                         // the same in the whole block
+      const long sys = list[1 + s / parts];
       c = (int)(sys / ((long)nb * N));
       const int rem = (int)(sys - (long)c * nb * N);
       a = rem / N;
@@ -61,7 +76,7 @@ bse_f64_kernel(Dims dm, int ch0, int nch, int nc, const double2* __restrict__ ga
       q = rem - (a - dm.a0) * N;
     }
     bse_f64_system(dm, c, a, q, nc, gam, gg, chi, kc, LU, sm + L.y, sm + L.xs, sm + L.invu, sh, flags, radius_K,
-                   lam);
+                   lam, jb, je);
   }
 }
 
@@ -1051,11 +1066,11 @@ cudaError_t launch_bse(df_ctx* c, int channel_mask) {
     const int grid = (int)(systems < c->bse_grid ? systems : c->bse_grid);
     if (bse_lu_in_smem(n)) {
       bse_f64_kernel<true><<<grid, kBseThreads, smem, c->stream>>>(dm, ch, 1, nc, c->gam, gg_ptr(c), c->chi,
-                                                                   c->kc, nullptr, flag_ptr(c), K, lam, nullptr);
+                                                                   c->kc, nullptr, flag_ptr(c), K, lam, nullptr, 0);
     } else {
       bse_f64_kernel<false><<<grid, kBseThreads, smem, c->stream>>>(dm, ch, 1, nc, c->gam, gg_ptr(c), c->chi,
                                                                     c->kc, lu_ws_ptr(c), flag_ptr(c), K, lam,
-                                                                    nullptr);
+                                                                    nullptr, 0);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -1063,23 +1078,27 @@ cudaError_t launch_bse(df_ctx* c, int channel_mask) {
 }
 
 // the FP64 LU over the ladders the mixed-precision kernels handed back: list[0]
-// (read on the device) systems (c N_W + a) N + q, on the persistent grid
+// (read on the device) systems (c N_W + a) N + q, on the persistent grid; a
+// list shorter than the SM count is spread over the SMs by right-hand-side ranges
 cudaError_t launch_bse_f64_list(df_ctx* c, const int* list) {
   const Dims& dm = c->dm;
   const int n = dm.n_w;
-  const int nc = bse_chunk(n);
+  const int nc = bse_chunk(n) < 16 ? bse_chunk(n) : 16;   // 16-column ranges to spread (fits the default layout)
   const size_t smem = bse_smem_bytes(n);
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
   cudaError_t e = cudaFuncSetAttribute(bse_lu_in_smem(n) ? (const void*)bse_f64_kernel<true>
                                                          : (const void*)bse_f64_kernel<false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (bse_lu_in_smem(n))
     bse_f64_kernel<true><<<c->bse_grid, kBseThreads, smem, c->stream>>>(dm, 0, 2, nc, c->gam, gg_ptr(c), c->chi,
-                                                                        c->kc, nullptr, flag_ptr(c), 0, nullptr, list);
+                                                                        c->kc, nullptr, flag_ptr(c), 0, nullptr, list,
+                                                                        sms);
   else
     bse_f64_kernel<false><<<c->bse_grid, kBseThreads, smem, c->stream>>>(dm, 0, 2, nc, c->gam, gg_ptr(c), c->chi,
                                                                          c->kc, lu_ws_ptr(c), flag_ptr(c), 0, nullptr,
-                                                                         list);
+                                                                         list, sms);
   return cudaGetLastError();
 }
 

@@ -140,7 +140,8 @@ __device__ __forceinline__ void bse_f64_factor(const Dims& dm, int c, int a, int
 
 // D = 1 - gamma_W diag(chi~_W(q)) factorised in LU (n x n, row-major; shared
 // or global memory), right-hand sides P gamma in chunks of nc columns in Y,
-// writes kc[c][a][:][q] = w_c (Gamma_jj - Gamma^(2)_jj / 2).  With radius_K > 0
+// writes kc[c][a][j][q] = w_c (Gamma_jj - Gamma^(2)_jj / 2) for the columns
+// j in [j_begin, j_end) (multiples of nc but the last; default all).  With radius_K > 0
 // and |lam[c][a][q]| >= 1 (outside the ladder's convergence radius) Gamma is
 // instead the low-order iterative evaluation Gamma <- gamma + gamma chi~ Gamma,
 // radius_K times from Gamma = gamma (the LU buffer holds the product).
@@ -149,7 +150,8 @@ __device__ __forceinline__ void bse_f64_system(const Dims& dm, int c, int a, int
                                                const double2* __restrict__ chi, double2* __restrict__ kc,
                                                double2* LU, double2* Y, double2* xs, double2* invu,
                                                BseF64Shared& sh, int* __restrict__ flags, int radius_K = 0,
-                                               const double2* __restrict__ lam = nullptr) {
+                                               const double2* __restrict__ lam = nullptr, int j_begin = 0,
+                                               int j_end = 1 << 30) {
   const int n = dm.n_w, N = dm.N, nb = dm.nb;
   const int tid = threadIdx.x;
   const double2* G = gam + ((size_t)c * nb + a) * n * n;
@@ -173,7 +175,8 @@ __device__ __forceinline__ void bse_f64_system(const Dims& dm, int c, int a, int
   }
 
   // ---- diag(Gamma) by chunks of nc right-hand sides ----
-  for (int j0 = 0; j0 < n; j0 += nc) {
+  const int j_stop = j_end < n ? j_end : n;
+  for (int j0 = j_begin; j0 < j_stop; j0 += nc) {
     const int w = min(nc, n - j0);
     if (series) {
       for (int idx = tid; idx < n * w; idx += blockDim.x) {
