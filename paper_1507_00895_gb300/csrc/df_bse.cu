@@ -1208,7 +1208,7 @@ cudaError_t launch_bse_both_raw(const Dims& dm, const double2* gam, const double
   const long systems = 2L * dm.nb * dm.N;
   const int grid = (int)(systems < grid_max ? systems : grid_max);
   bse_f64_kernel<true><<<grid, kBseThreads, smem, stream>>>(dm, 0, 2, nc, gam, gg, chi, kc, nullptr, flags, 0,
-                                                            nullptr, nullptr);
+                                                            nullptr, nullptr, 0);
   return cudaGetLastError();
 }
 
