@@ -240,3 +240,18 @@ def test_reflection_refuses_inputs_and_sigma_without_it(df):
         assert nrel(d.get_sigma(), st.sigmas[0]) < TOL64      # the handle's inputs are unchanged
     with pytest.raises(df.DFError):                            # needs the full bosonic range
         df.DualFermion.from_workload(w, symmetry=2, w_range=(0, 2))
+
+
+@pytest.mark.parametrize("dim,nk", [(1, 16), (2, 2), (4, 4)])
+@pytest.mark.parametrize("sym", [1, 2])
+def test_reductions_in_other_dimensions(df, dim, nk, sym):
+    # 1D (sign flip only), the 2 x 2 grid (3 orbits of 4) and the 4D hypercube
+    # (hyperoctahedral group: 15 orbits of 256), FP64, against the oracle over two passes
+    w = I.half_filled_atom("h", dim, nk, U=6.0, beta=1.5, n_w=8, m_max=2)
+    st = O.run_workload(w, n_iter=2)
+    with df.DualFermion.from_workload(w, symmetry=sym) as d:
+        for it in range(2):
+            d.bubble()
+            d.bse(3)
+            d.sigma()
+            assert nrel(d.get_sigma(), st.sigmas[it]) < TOL64, it
