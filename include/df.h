@@ -292,7 +292,8 @@ df_status df_get_sizes(const df_ctx* c, int* n_ext, int* n_bos, int* n_k_total);
  * may be NULL).  Groups: */
 enum {
   DF_T_BUBBLE = 0,   /* Eq. dual_bubble: 1 kernel per df_bubble */
-  DF_T_BSE = 1,      /* Eq. lin_alg_inv: 1 kernel per channel */
+  DF_T_BSE = 1,      /* Eq. lin_alg_inv: counted as 1 kernel per channel (both channels may
+                        * share one launch; the reductions' gather and scatter add 1 each) */
   DF_T_LAMBDA = 2,   /* leading eigenvalue: 1 kernel per channel (eig_mode != 0) */
   DF_T_SIGMA = 3,    /* Eq. sd + Eq. dyson + residual: 3 kernels per df_sigma */
   DF_T_COUNT = 4

@@ -1060,19 +1060,24 @@ cudaError_t launch_bse(df_ctx* c, int channel_mask) {
   if (c->opts.precision == DF_FP32_IR) return launch_bse_mixed(c, channel_mask, flag_ptr(c));
   const int K = c->opts.radius_order;
   const double2* lam = K > 0 ? c->lam : nullptr;
+  // both channels in one launch of the grid-stride kernel when both are asked
+  // for (one partial wave instead of two)
+  const bool both = (channel_mask & 3) == 3;
   for (int ch = 0; ch < 2; ++ch) {
     if (!(channel_mask & (1 << ch))) continue;
-    const long systems = (long)dm.na * dm.N;
+    const int nch = both ? 2 : 1;
+    const long systems = (long)nch * dm.na * dm.N;
     const int grid = (int)(systems < c->bse_grid ? systems : c->bse_grid);
     if (bse_lu_in_smem(n)) {
-      bse_f64_kernel<true><<<grid, kBseThreads, smem, c->stream>>>(dm, ch, 1, nc, c->gam, gg_ptr(c), c->chi,
+      bse_f64_kernel<true><<<grid, kBseThreads, smem, c->stream>>>(dm, ch, nch, nc, c->gam, gg_ptr(c), c->chi,
                                                                    c->kc, nullptr, flag_ptr(c), K, lam, nullptr, 0);
     } else {
-      bse_f64_kernel<false><<<grid, kBseThreads, smem, c->stream>>>(dm, ch, 1, nc, c->gam, gg_ptr(c), c->chi,
+      bse_f64_kernel<false><<<grid, kBseThreads, smem, c->stream>>>(dm, ch, nch, nc, c->gam, gg_ptr(c), c->chi,
                                                                     c->kc, lu_ws_ptr(c), flag_ptr(c), K, lam,
                                                                     nullptr, 0);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (both) break;
   }
   return cudaSuccess;
 }

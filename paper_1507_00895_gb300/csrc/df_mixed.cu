@@ -188,13 +188,20 @@ static cudaError_t launch_bse_mixed_np(df_ctx* c, int channel_mask, int* flags) 
   const size_t count = (size_t)2 * dm.nb * dm.n_w * dm.n_w;
   const float2* hi = (const float2*)c->mixed_ws;
   const MixedCheck mc = mixed_check(c);
+  // one launch per channel; both channels in one launch when a channel is only a
+  // few waves of the grid (the reduced grids), where the last partial wave of
+  // each launch would otherwise idle most blocks
+  const long per_channel = (long)dm.na * dm.N;
+  const bool both = (channel_mask & 3) == 3 && per_channel < 16L * c->mixed_grid;
   for (int ch = 0; ch < 2; ++ch) {
     if (!(channel_mask & (1 << ch))) continue;
-    const long systems = (long)dm.na * dm.N;
+    const int nch = both ? 2 : 1;
+    const long systems = nch * per_channel;
     const int grid = (int)(systems < c->mixed_grid ? systems : c->mixed_grid);
-    bse_mixed_kernel<NP><<<grid, threads, smem, c->stream>>>(dm, ch, 1, c->gam, hi, hi + count, hi + 2 * count,
+    bse_mixed_kernel<NP><<<grid, threads, smem, c->stream>>>(dm, ch, nch, c->gam, hi, hi + count, hi + 2 * count,
                                                              hi + 3 * count, c->chi, c->kc, gdig_ptr(c), flags, mc);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (both) break;
   }
   return cudaSuccess;
 }
