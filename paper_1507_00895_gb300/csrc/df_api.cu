@@ -703,7 +703,7 @@ df_status df_susceptibility(df_ctx* c, double* out, int is_device) {
   double2* chi0 = L + pw;
   double2* res = chi0 + pq;
   int* redo = (int*)(res + 2 * pq);
-  DF_CUDA(c, launch_bubble(c), "dual bubble (Eq. dual_bubble)");
+  DF_CUDA(c, launch_bubble(c, 1), "dual bubble (Eq. dual_bubble)");
   DF_CUDA(c, launch_obs_bubbles(c, planes, P, L, chi0), "susceptibility bubbles");
   DF_CUDA(c, cudaMemsetAsync(bse_flags(c), 0, sizeof(int) * 4, c->stream), "flags");
   DF_CUDA(c, launch_chi_ladder(c, L, chi0, is_device ? (double2*)out : res, redo), "susceptibility ladders");
@@ -723,6 +723,7 @@ df_status df_get_gtilde(df_ctx* c, double* out, int is_device) {
 
 df_status df_get_chi(df_ctx* c, double* out, int is_device) {
   if (!c) return DF_ERR_ARG;
+  if (c->opts.symmetry == 2) DF_CUDA(c, launch_chi_reflect(c), "chi~ of W < 0 by the frequency reflection");
   return copy_out(c, out, c->chi, sizeof(double2) * c->dm.nb * c->dm.n_w * c->dm.N, is_device, "df_get_chi");
 }
 

@@ -44,21 +44,21 @@ sigma_prod_kernel(Dims dm, const double2* __restrict__ kc, const double2* __rest
 __global__ void __launch_bounds__(kFftThreads)
 sigma_dyson_kernel(Dims dm, double mix, const double2* __restrict__ prod, const double2* __restrict__ g0,
                    double2* __restrict__ sigma, double2* __restrict__ gk, double2* __restrict__ gr,
-                   double* __restrict__ red) {
+                   double* __restrict__ red, int refl) {
   extern __shared__ double2 sm[];
   __shared__ double red_sm[32];
   sigma_dyson_plane(dm, blockIdx.x, mix, prod, g0, sigma, gk, gr, red, sm, sm + dm.nk / 2,
-                    sm + dm.nk / 2 + dm.N, red_sm);
+                    sm + dm.nk / 2 + dm.N, red_sm, refl);
 }
 
 // The Omega split: this problem's share of Eq. sd, out[i][k] = (T/2) FFT[sum over
 // its bosonic planes of prod[W][i]](k), before mixing and Dyson
 __global__ void __launch_bounds__(kFftThreads)
-sigma_partial_kernel(Dims dm, const double2* __restrict__ prod, double2* __restrict__ out) {
+sigma_partial_kernel(Dims dm, const double2* __restrict__ prod, double2* __restrict__ out, int refl) {
   extern __shared__ double2 sm[];
   const int i = blockIdx.x;
   double2* s = sm + dm.nk / 2;
-  sigma_sum_plane(dm, i, prod, sm, s);
+  sigma_sum_plane(dm, i, prod, sm, s, refl);
   const double pref = 0.5 * dm.T;
   for (int k = threadIdx.x; k < dm.N; k += blockDim.x) out[(size_t)i * dm.N + k] = cscale(s[k], pref);
 }
@@ -171,8 +171,19 @@ cudaError_t launch_dyson_ifft(df_ctx* c, int first_plane, int n_planes) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_bubble(df_ctx* c) {
-  const Dims& dm = c->dm;
+// The planes the pass needs: with the frequency reflection (df_opts.symmetry = 2)
+// only W >= 0 (the ladder stage reads those; chi~ of W < 0 is their reflection).
+static Dims pass_planes(const df_ctx* c) {
+  Dims d = c->dm;
+  if (c->opts.symmetry == 2) {
+    d.a0 = d.m_max;
+    d.na = d.m_max + 1;
+  }
+  return d;
+}
+
+cudaError_t launch_bubble(df_ctx* c, int all_planes) {
+  const Dims dm = all_planes ? c->dm : pass_planes(c);
   const size_t sm = fft_smem(dm, 1);
   cudaError_t e = set_smem((const void*)bubble_kernel, sm);
   if (e != cudaSuccess) return e;
@@ -217,13 +228,14 @@ cudaError_t launch_obs_bubbles(df_ctx* c, double2* planes, double2* P, double2* 
 // the Omega split: this problem's planes of Eq. sd into out [n_w][N] (device)
 cudaError_t launch_sigma_partial(df_ctx* c, double2* out) {
   const Dims& dm = c->dm;
+  const Dims pp = pass_planes(c);
   size_t sm = fft_smem(dm, 1);
   cudaError_t e = set_smem((const void*)sigma_prod_kernel, sm);
   if (e != cudaSuccess) return e;
-  sigma_prod_kernel<<<dm.na * dm.n_w, kFftThreads, sm, c->stream>>>(dm, c->kc, c->gr, c->prod);
+  sigma_prod_kernel<<<pp.na * pp.n_w, kFftThreads, sm, c->stream>>>(pp, c->kc, c->gr, c->prod);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if ((e = set_smem((const void*)sigma_partial_kernel, sm)) != cudaSuccess) return e;
-  sigma_partial_kernel<<<dm.n_w, kFftThreads, sm, c->stream>>>(dm, c->prod, out);
+  sigma_partial_kernel<<<dm.n_w, kFftThreads, sm, c->stream>>>(dm, c->prod, out, c->opts.symmetry == 2);
   return cudaGetLastError();
 }
 
@@ -241,15 +253,16 @@ cudaError_t launch_sigma_finish(df_ctx* c, const double2* total, double mix) {
 
 cudaError_t launch_sigma(df_ctx* c, double mix) {
   const Dims& dm = c->dm;
+  const Dims pp = pass_planes(c);
   size_t sm = fft_smem(dm, 1);
   cudaError_t e = set_smem((const void*)sigma_prod_kernel, sm);
   if (e != cudaSuccess) return e;
-  sigma_prod_kernel<<<dm.na * dm.n_w, kFftThreads, sm, c->stream>>>(dm, c->kc, c->gr, c->prod);
+  sigma_prod_kernel<<<pp.na * pp.n_w, kFftThreads, sm, c->stream>>>(pp, c->kc, c->gr, c->prod);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   sm = fft_smem(dm, 2);
   if ((e = set_smem((const void*)sigma_dyson_kernel, sm)) != cudaSuccess) return e;
   sigma_dyson_kernel<<<dm.n_w, kFftThreads, sm, c->stream>>>(dm, mix, c->prod, c->g0, c->sigma, c->gk,
-                                                             c->gr, c->red);
+                                                             c->gr, c->red, c->opts.symmetry == 2);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   residual_reduce_kernel<<<1, kFftThreads, 0, c->stream>>>(dm.n_w, c->red);
   return cudaGetLastError();

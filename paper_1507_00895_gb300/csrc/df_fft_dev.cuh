@@ -114,12 +114,23 @@ __device__ __forceinline__ double block_max(double v, double* red_sm) {
 // Eq. sd, stage 2a, box frequency i: acc(r) = sum_W prod[W][i](r) over the
 // problem's bosonic planes, s = FFT[acc] (natural order; the T/2 is applied by
 // the caller).  Loads the twiddles into tw.
+// With refl (the frequency reflection, full range) only the planes W >= 0 of
+// prod are formed: the term of -W at w is that of W at -w, conjugated and taken
+// at -r (prod_{-W,w}(r) = prod_{W,-w}(-r)*, from bracket_{-W}(w) = bracket_W(-w)*
+// and G~(-w) = G~(w)*).
 __device__ __forceinline__ void sigma_sum_plane(const Dims& dm, int i, const double2* __restrict__ prod, double2* tw,
-                                                double2* s) {
+                                                double2* s, int refl = 0) {
   load_twiddles(tw, dm.nk);
+  const int ir = dm.n_w - 1 - i;
   for (int r = threadIdx.x; r < dm.N; r += blockDim.x) {
     double2 acc = mk(0.0, 0.0);
-    for (int a = dm.a0; a < dm.a0 + dm.na; ++a) acc = acc + prod[((size_t)a * dm.n_w + i) * dm.N + r];
+    if (refl) {
+      const int rr = reflect_index(r, dm.D, dm.p);
+      for (int a = dm.m_max; a < dm.nb; ++a) acc = acc + prod[((size_t)a * dm.n_w + i) * dm.N + r];
+      for (int a = dm.m_max + 1; a < dm.nb; ++a) acc = acc + cconj(prod[((size_t)a * dm.n_w + ir) * dm.N + rr]);
+    } else {
+      for (int a = dm.a0; a < dm.a0 + dm.na; ++a) acc = acc + prod[((size_t)a * dm.n_w + i) * dm.N + r];
+    }
     s[bitrev_axes(r, dm.D, dm.p)] = acc;
   }
   __syncthreads();
@@ -167,8 +178,8 @@ __device__ __forceinline__ void sigma_dyson_plane(const Dims& dm, int i, double 
                                                   const double2* __restrict__ g0, double2* __restrict__ sigma,
                                                   double2* __restrict__ gk, double2* __restrict__ gr,
                                                   double* __restrict__ red, double2* tw, double2* s, double2* s2,
-                                                  double* red_sm) {
-  sigma_sum_plane(dm, i, prod, tw, s);
+                                                  double* red_sm, int refl = 0) {
+  sigma_sum_plane(dm, i, prod, tw, s, refl);
   sigma_finish_plane(dm, i, mix, 0.5 * dm.T, s, g0, sigma, gk, gr, red, tw, s2, red_sm);
 }
 

@@ -310,7 +310,7 @@ namespace df {
 cudaError_t launch_init_g0(df_ctx* c);
 cudaError_t launch_wait_selftest(int arrive, unsigned spins, int* flags, cudaStream_t stream);
 cudaError_t launch_dyson_ifft(df_ctx* c, int first_plane, int n_planes);
-cudaError_t launch_bubble(df_ctx* c);
+cudaError_t launch_bubble(df_ctx* c, int all_planes = 0);   // all_planes: every W even under the reflection
 cudaError_t launch_sigma(df_ctx* c, double mix);
 cudaError_t launch_sigma_partial(df_ctx* c, double2* out);
 cudaError_t launch_sigma_finish(df_ctx* c, const double2* total, double mix);
@@ -342,4 +342,5 @@ int build_wedge(int dim, int nk, std::vector<int>& qmap, std::vector<int>& qrep)
 cudaError_t launch_wedge_gather(df_ctx* c, const Dims& ladder_dims);
 cudaError_t launch_wedge_scatter(df_ctx* c, bool with_lambda);
 cudaError_t launch_sigma_invariance(df_ctx* c, unsigned long long* out);
+cudaError_t launch_chi_reflect(df_ctx* c);   // chi~ of W < 0 from W > 0 (df_opts.symmetry = 2)
 }  // namespace df

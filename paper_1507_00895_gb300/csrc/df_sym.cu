@@ -137,6 +137,19 @@ __global__ void sigma_invariance_kernel(Dims dm, int refl, const int* __restrict
   }
 }
 
+// chi~ of the planes W < 0 (a < m_max), which the pass does not form under the
+// frequency reflection: chi[a][i][q] = chi[2 m_max - a][n_w - 1 - i][q]*
+__global__ void chi_reflect_kernel(Dims dm, double2* __restrict__ chi) {
+  const long total = (long)dm.m_max * dm.n_w * dm.N;
+  for (long idx = blockIdx.x * (long)blockDim.x + threadIdx.x; idx < total; idx += (long)gridDim.x * blockDim.x) {
+    const int q = (int)(idx % dm.N);
+    const long row = idx / dm.N;
+    const int i = (int)(row % dm.n_w), a = (int)(row / dm.n_w);
+    const double2 v = chi[(((size_t)(2 * dm.m_max - a)) * dm.n_w + (dm.n_w - 1 - i)) * dm.N + q];
+    chi[idx] = make_double2(v.x, -v.y);
+  }
+}
+
 int grid_for(long total) { return (int)std::min<long>(4096, (total + 255) / 256); }
 
 }  // namespace
@@ -158,6 +171,14 @@ cudaError_t launch_wedge_scatter(df_ctx* c, bool with_lambda) {
                                                                c->kc_w, c->kc,
                                                                with_lambda ? c->lam_w : nullptr,
                                                                with_lambda ? c->lam_ok_w : nullptr, c->lam, c->lam_ok);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chi_reflect(df_ctx* c) {
+  const Dims& dm = c->dm;
+  const long total = (long)dm.m_max * dm.n_w * dm.N;
+  if (total == 0) return cudaSuccess;
+  chi_reflect_kernel<<<grid_for(total), 256, 0, c->stream>>>(dm, c->chi);
   return cudaGetLastError();
 }
 
