@@ -187,7 +187,8 @@ def test_reflection_equals_full(df, name, kw, prec):
                 d.bubble()
                 d.bse(3)
             # chi~ of W < 0 is not formed by the pass; df_get_chi fills it by the reflection
-            assert nrel(red.get_chi(), full.get_chi()) < 1e-13, it
+            # (equal to rounding on the first pass; later passes carry Sigma~'s difference)
+            assert nrel(red.get_chi(), full.get_chi()) < (1e-13 if it == 0 else tol), it
             assert nrel(red.get_kernel(), full.get_kernel()) < tol, it
             lf, okf = full.get_lambda()
             lr, okr = red.get_lambda()
