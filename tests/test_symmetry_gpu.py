@@ -1,12 +1,15 @@
-"""The point-group reduction of the ladders (df_opts.symmetry = 1) against the
-full solve and against the oracle.
+"""The reductions of the ladder stage against the full solve and against the
+oracle: the point group (df_opts.symmetry = 1) and, with it, the frequency
+reflection (df_opts.symmetry = 2).
 
-With the reduction one ladder per momentum orbit is solved and copied to
-the orbit (df_wedge).  Its results equal the full solve's wherever the
-full solve's chi~ columns agree within an orbit, i.e. up to rounding:
-FP64 within 1e-10 of the oracle (the parity bound), the mixed path within
-1e-8 of the full mixed solve (its stated bound).  The handle checks the
-invariance of a Sigma~ it is given and refuses one that breaks it.
+With the point group one ladder per momentum orbit is solved and copied to
+the orbit (df_wedge); with the reflection only the planes W >= 0 are formed
+(ladders, bubble and Eq. sd's products), those of -W entering as their
+frequency-reversed conjugates.  The results equal the full solve's up to
+rounding: FP64 within 1e-10 of the oracle (the parity bound), the mixed path
+within 1e-8 of the full mixed solve (its stated bound).  The handle checks
+its inputs and any Sigma~ it is given for the symmetries it relies on and
+refuses what breaks them.
 """
 import numpy as np
 import pytest
