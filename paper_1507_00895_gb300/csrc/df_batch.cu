@@ -78,6 +78,7 @@ batch_bubble_kernel(const PointDev* __restrict__ pts, const long* __restrict__ s
   if (!P.active) return;
   const int local = (int)(blockIdx.x - start[p]);
   const int a = local / P.dm.n_w, i = local - a * P.dm.n_w;
+  if (P.refl && a < P.dm.m_max) return;             // W < 0: not needed under the reflection
   bubble_plane(P.dm, a, i, P.gr, P.chi, sm, sm + P.dm.nk / 2);
 }
 
@@ -89,6 +90,7 @@ batch_sigma_prod_kernel(const PointDev* __restrict__ pts, const long* __restrict
   if (!P.active) return;
   const int local = (int)(blockIdx.x - start[p]);
   const int a = local / P.dm.n_w, i = local - a * P.dm.n_w;
+  if (P.refl && a < P.dm.m_max) return;             // W < 0: summed by the reflection
   sigma_prod_plane(P.dm, a, i, P.kc, P.gr, P.prod, sm, sm + P.dm.nk / 2);
 }
 
@@ -101,7 +103,7 @@ batch_sigma_dyson_kernel(const PointDev* __restrict__ pts, const long* __restric
   if (!P.active) return;
   const int i = (int)(blockIdx.x - start[p]);
   sigma_dyson_plane(P.dm, i, P.mix, P.prod, P.g0, P.sigma, P.gk, P.gr, P.red, sm, sm + P.dm.nk / 2,
-                    sm + P.dm.nk / 2 + P.dm.N, red_sm);
+                    sm + P.dm.nk / 2 + P.dm.N, red_sm, P.refl);
 }
 
 // one block per point: residual, convergence flag, result copy
