@@ -361,6 +361,56 @@ def time_to_converged(df, I, torch, max_passes=60):
     return out
 
 
+def run_ttc_3d(args, max_passes: int = 60):
+    """Time to a converged Sigma~ on the 3D critical workload (16^3, n_w = 96, N_W = 21,
+    lambda_m(Q, 0) = 0.98 on the first pass), one JSON line: Sigma~* = the FP64 loop with
+    both reductions (equal to the full FP64 loop to rounding) iterated to r <= 1e-13; each
+    path from Sigma~ = 0 until max|Sigma~ - Sigma~*| <= 1e-8 max|Sigma~*|, device time of
+    the passes (CUDA events), the distance checked between passes outside the timed region."""
+    import numpy as np
+    import torch
+    from paper_1507_00895_gb300 import build, df, inputs as I
+    build.build_lib()
+    w = I.workload("cubic16_crit")
+    stream = torch.cuda.current_stream()
+    with df.DualFermion.from_workload(w, eig_mode=0, symmetry=2, stream=stream.cuda_stream) as d:
+        it, r, _ = d.iterate(120, tol=1e-13)
+        ref = d.get_sigma()
+    out = {"probe": "time to converged Sigma~, 3D 16^3, n_w=96, N_W=21, the critical point's beta",
+           "target": "max|Sigma~ - Sigma~*| <= 1e-8 max|Sigma~*|, Sigma~* = FP64 loop (both reductions) at r <= 1e-13",
+           "reference_passes": it, "reference_residual": r}
+    if not r <= 1e-13:
+        out["error"] = "the FP64 reference did not converge"
+        print(json.dumps(out))
+        return 0
+    den = float(np.max(np.abs(ref)))
+    for name, prec, sym in (("fp64", df.DF_FP64, 0), ("fp32ir", df.DF_FP32_IR, 0),
+                            ("fp64_reduced_reflected", df.DF_FP64, 2), ("fp32ir_reduced_reflected", df.DF_FP32_IR, 2)):
+        with df.DualFermion.from_workload(w, precision=prec, eig_mode=1, symmetry=sym,
+                                          stream=stream.cuda_stream) as d:
+            d.iterate(1)
+            d.set_sigma(np.zeros((w.n_w, w.N), np.complex128))
+            total, err, passes = 0.0, None, 0
+            for passes in range(1, max_passes + 1):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                d.bubble()
+                d.bse(3)
+                d.sigma(want_residual=False)
+                e1.record(stream)
+                e1.synchronize()
+                total += e0.elapsed_time(e1)
+                err = float(np.max(np.abs(d.get_sigma() - ref)) / den)
+                if err <= 1e-8:
+                    break
+        out[name] = {"passes": passes, "ms": total, "err_vs_fp64_converged": err, "converged": err <= 1e-8}
+    out["speedup_vs_plain_fp64"] = {k: out["fp64"]["ms"] / out[k]["ms"]
+                                    for k in ("fp32ir", "fp64_reduced_reflected", "fp32ir_reduced_reflected")}
+    print(json.dumps(out))
+    return 0
+
+
 def batch_bench(df, I, torch, full: bool, passes: int = 3):
     """Throughput of the batched loop on the 64-point uneven recipe (seed 4):
     U ~ U[1,8], beta ~ U[2,20], lattices 8^2..64^2 and 8^4, n_w 16..128,
@@ -1000,6 +1050,8 @@ def main():
                     help="skip the point-group-reduced passes of the bench workload")
     ap.add_argument("--no-observables", action="store_true",
                     help="skip the lattice-observable, susceptibility and radius-extension timings")
+    ap.add_argument("--ttc-3d", action="store_true",
+                    help="only: time to a converged Sigma~ on the 3D critical workload, per path")
     ap.add_argument("--config5", action="store_true",
                     help="only: the learned warm start at its stated grid (64^2, n_w=128, N_W=31)")
     ap.add_argument("--c5-train", type=int, default=2000, help="--config5: training points")
@@ -1021,6 +1073,8 @@ def main():
         return run_omega_split(args)
     if args.config5:
         return run_config5(args)
+    if args.ttc_3d:
+        return run_ttc_3d(args)
     return run_ours(args)
 
 
