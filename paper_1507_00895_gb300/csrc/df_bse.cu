@@ -484,7 +484,7 @@ chi_ladder_ir_kernel(Dims dm, const double2* __restrict__ gam, const float2* __r
 // pairs of y = A v.
 // ---------------------------------------------------------------------------
 constexpr int kEigQ = 8;
-constexpr int kEigThreads = 256;
+constexpr int kEigThreads = 1024;   // one (row, system) pair per thread up to n_w = 128
 constexpr int kEigIter32 = 64;
 constexpr int kEigIter64 = 24;
 
