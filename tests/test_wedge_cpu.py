@@ -153,3 +153,33 @@ def test_a_vertex_without_the_reflection_breaks_it():
     assert np.max(np.abs(chi - reflect(chi, 1, 0))) < 1e-13 * np.max(np.abs(chi))
     # (relative to the typical entry: this workload has a few near-singular ladders)
     assert np.max(np.abs(kern - reflect(kern, 1, 0))) > 1e-2 * np.median(np.abs(kern))
+
+
+def test_reflection_of_the_eq_sd_products():
+    # the frequency reflection in Eq. sd's real-space products, which lets the
+    # kernels form only the planes W >= 0: with prod_{W,w}(r) = K_{W,w}(-r) G~_{w+W}(r)
+    # (K the bracket, to real space), prod_{-W,w}(r) = prod_{W,-w}(-r)*, and the sum
+    # over all W equals the sum over W >= 0 plus the conjugated, reversed W > 0 terms
+    w = I.workload("square32_tp", nk=8, n_w=8, m_max=2)
+    st = O.run_workload(w, n_iter=2)
+    eps = O.dispersion(w.dim, w.nk, w.t, w.tp)
+    gt = O.dual_g(O.bare_dual_g(w.g, w.delta, eps), st.sigma, w.n_w, w.m_max)
+    _, kern = one_pass_pieces(w, st.sigma)
+    gr = np.array([O.to_real_space(x, w.dim, w.nk) for x in gt])
+    nb, nw, m = w.n_bos, w.n_w, w.m_max
+    refl_r = lambda x: O.reflect(x, w.dim, w.nk)
+    prod = np.array([[refl_r(O.to_real_space(kern[a, i], w.dim, w.nk)) * gr[i + a] for i in range(nw)]
+                     for a in range(nb)])
+    scale = np.max(np.abs(prod))
+    for a in range(m):
+        for i in range(nw):
+            assert np.max(np.abs(prod[a, i] - np.conj(refl_r(prod[2 * m - a, nw - 1 - i])))) < 1e-13 * scale
+    total = prod.sum(axis=0)
+    folded = np.array([prod[m:, i].sum(axis=0)
+                       + sum(np.conj(refl_r(prod[a, nw - 1 - i])) for a in range(m + 1, nb))
+                       for i in range(nw)])
+    assert np.max(np.abs(folded - total)) < 1e-13 * np.max(np.abs(total))
+    # planted: pairing -W with +w (no frequency reversal) breaks it
+    wrong = np.array([prod[m:, i].sum(axis=0) + sum(np.conj(refl_r(prod[a, i])) for a in range(m + 1, nb))
+                      for i in range(nw)])
+    assert np.max(np.abs(wrong - total)) > 1e-6 * np.max(np.abs(total))
