@@ -87,3 +87,32 @@ def test_no_gpu_fails_loudly(lib):
     with pytest.raises(df.DFError) as ei:
         df.DualFermion.from_workload(w)
     assert ei.value.status == df.DF_ERR_CUDA
+
+
+def test_reduction_options_are_checked_before_any_device_call(lib):
+    from paper_1507_00895_gb300 import df, inputs
+    h = C.c_void_p()
+    opts = df.df_opts()
+    lib.df_default_opts(C.byref(opts))
+    assert opts.symmetry == 0                    # default: every ladder solved
+    opts.n_w, opts.m_max = 4, 1
+    lat = df.df_lattice(2, 4, 0.0)
+    buf = np.zeros(256, np.complex128)
+    p = buf.ctypes.data
+    opts.symmetry = 3                            # 0, 1 or 2
+    assert lib.df_init(C.byref(h), C.byref(lat), 1.0, 0.0, 1.0, p, p, p, p, C.byref(opts), None) == df.DF_ERR_ARG
+    opts.symmetry, opts.w_lo, opts.w_hi = 2, 0, 2   # the reflection needs the full bosonic range
+    assert lib.df_init(C.byref(h), C.byref(lat), 1.0, 0.0, 1.0, p, p, p, p, C.byref(opts), None) == df.DF_ERR_ARG
+    # a batch point: the symmetry field's range, and inputs without the reflection under symmetry 2
+    # (checked on the host before the batch touches the device)
+    bad = inputs.random_nonsymmetric(8, 1, 2, 4, seed=6)
+    gd, gm = df.vertex_from_spin(bad.gamma_uu, bad.gamma_ud)
+    g, dl = np.ascontiguousarray(bad.g), np.ascontiguousarray(bad.delta)
+    keep = [g, dl, gd, gm]
+    for sym in (3, 2):
+        pt = df.df_point(bad.dim, bad.nk, bad.tp, bad.t, bad.beta, bad.mu, bad.n_w, bad.m_max,
+                         g.ctypes.data, dl.ctypes.data, gd.ctypes.data, gm.ctypes.data, sym)
+        b = C.c_void_p()
+        assert lib.df_batch_init(C.byref(b), 1, C.cast(C.pointer(pt), C.c_void_p), df.DF_FP64, 1.0, 0.0,
+                                 None) == df.DF_ERR_ARG, sym
+    del keep
